@@ -1,0 +1,49 @@
+/*
+ * FP64 CPU oracle of the frequency-domain DPD downlink chain (arxiv 2205.05158).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the slow, obviously correct
+ * definition the CUDA path is checked against.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the library never
+ * does.  It shares no code, header or table with the CUDA path.
+ *
+ * Complex numbers are C99 `double complex`; all arrays are row-major.
+ *   s      [S][K][N_d]          user symbols (data bins, increasing frequency)
+ *   H      [R][N_d][K][M]       per-subcarrier channel, R = ceil(S / S_per_real)
+ *   W      [R][N_d][M][K]       unnormalised ZF precoder H^H (H H^H)^{-1}
+ *   alpha  [R][N_d]             per-subcarrier power normalisation
+ *   pa     [M][P][L+1]          memory-polynomial coefficients c^b_{p,l}
+ *   theta  flat: conv_w[N_conv][2L_U][K_C][K_C], conv_b[N_conv],
+ *                fc_w[2N_d][N_conv*Go*Go], fc_b[2N_d]   (Go = ceil(G/K_S))
+ * metrics[5] = { loss, sum|y/alpha - s|^2, sum|s|^2, guard-bin power, data-bin power }
+ */
+#ifndef FDDPD_ORACLE_H
+#define FDDPD_ORACLE_H
+#include <complex.h>
+
+typedef struct {
+    int M, K, N, N_d, first_bin;
+    int S_per_real;
+    int n_orders, orders[8], L;
+    int G, L_U, K_C, K_S, N_conv, residual;
+    double P_T;
+} orc_dims;
+
+int  orc_num_threads(void);
+void orc_dft(int N, const double complex *in, double complex *out, int inverse);
+int  orc_zf(int K, int M, const double complex *Hk, double P_T, double complex *Wk, double *alpha);
+int  orc_precode_all(const orc_dims *d, int R, const double complex *H, double complex *W, double *alpha);
+void orc_pa(int N, const double complex *x, int n_orders, const int *orders, int L,
+            const double complex *c, double complex *y);
+void orc_fdcnn(const orc_dims *d, const double complex *s_sym, const double *theta,
+               double complex *s_tilde, double *pre, double *act);
+int  orc_distort(const orc_dims *d, int S, const double complex *s, const double complex *H,
+                 const double complex *W, const double *alpha, const double complex *pa,
+                 const double *theta, double complex *y, double *metrics);
+int  orc_backward(const orc_dims *d, int S, const double complex *s, const double complex *H,
+                  const double complex *W, const double *alpha, const double complex *pa,
+                  const double *theta, double *grad, double *metrics);
+int  orc_update(const orc_dims *d, int S, const double complex *s, const double complex *H,
+                const double complex *W, const double *alpha, const double complex *pa,
+                double *theta, double lr, int iters, int adam, double *adam_m, double *adam_v,
+                int *adam_t, double *metrics);
+#endif
