@@ -1,0 +1,189 @@
+/*
+ * fddpd — frequency-domain digital predistortion for the massive MU-MIMO-OFDM
+ * downlink (arxiv 2205.05158), as a C-ABI library for one sm_103a GPU.
+ *
+ * Per OFDM symbol the library computes, on the GPU:
+ *   s_tilde = s + FD-CNN_theta(s)            (Sec. IV-A; residual form, see residual)
+ *   x_hat_k = alpha_k W_k s_tilde_k          (Eq. 1 with the ZF precoder of Eq. 6)
+ *   x_b     = IDFT_N(x_hat_{.,b})            (Eq. 2, unitary; guard bins zero)
+ *   x^PA_b  = PA_b(x_b)                      (Eq. 7 with the memory polynomial of Eq. 9)
+ *   y_k     = H_k DFT_N(x^PA)_k / alpha_k    (Eq. 4-5, noise free, then equalised)
+ *   loss    = mean |y - s|^2                 (training criterion, Sec. V-A)
+ * and its adjoint with respect to theta, and gradient-descent / Adam updates.
+ *
+ * Conventions shared by every entry point
+ *   - Complex values are interleaved (re, im) FP32 (fddpd_c32).  All arrays are
+ *     row-major, densely packed, 8-byte aligned device memory unless stated.
+ *   - Data subcarrier i (0 <= i < N_d) is FFT bin (first_bin + i) mod N; the other
+ *     N - N_d bins are guard bins (precoder zero there, Sec. II-A).
+ *   - Symbol t uses channel realisation t / S_per_real.
+ *   - theta is one flat FP32 vector:
+ *       conv_w [N_conv][2 L_U][K_C][K_C], conv_b [N_conv],
+ *       fc_w   [2 N_d][N_conv Go Go],     fc_b   [2 N_d]        (Go = ceil(G / K_S));
+ *     fc rows 0..N_d-1 give the real parts, rows N_d..2N_d-1 the imaginary parts.
+ *   - metrics (device, double[5]) receive { loss, sum |y - s|^2, sum |s|^2,
+ *     guard-bin power of DFT(x^PA), data-bin power of DFT(x^PA) } summed over the call.
+ *   - Ownership: the caller owns every data pointer; the plan owns its workspace.
+ *   - Every call is asynchronous and ordered on the plan's stream; read results
+ *     after synchronising that stream.  Calls on one plan must not overlap.
+ *   - Return value: FDDPD_OK or a negative fddpd_status; fddpd_last_error()
+ *     describes the last failure.  No call aborts or throws.
+ */
+#ifndef FDDPD_H
+#define FDDPD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } fddpd_c32;
+typedef struct fddpd_plan fddpd_plan;
+
+enum fddpd_status {
+    FDDPD_OK = 0,
+    FDDPD_ERR_ARG = -1,          /* a null pointer, a size out of range, S > max_symbols    */
+    FDDPD_ERR_LAYOUT = -2,       /* a pointer not aligned as the layout requires            */
+    FDDPD_ERR_SINGULAR = -3,     /* a Gram matrix H_k H_k^H not positive definite          */
+    FDDPD_ERR_CUDA = -4,         /* a CUDA runtime error (launch, allocation on create)     */
+    FDDPD_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up                      */
+    FDDPD_ERR_UNSUPPORTED = -6,  /* a configuration this build does not implement           */
+    FDDPD_ERR_NOMEM = -7         /* workspace allocation failed                             */
+};
+
+enum fddpd_precision {
+    FDDPD_FP32 = 0,   /* every stage in FP32 on CUDA cores                                 */
+    FDDPD_BF16 = 1,   /* FD-CNN dense layer, precoding and combining with BF16 operands,   */
+    FDDPD_FP16 = 2    /* or FP16 operands, FP32 accumulation; FFT and PA stay FP32         */
+};
+
+enum fddpd_optimizer { FDDPD_GD = 0, FDDPD_ADAM = 1 };
+
+typedef struct {
+    int M;            /* BS antennas (paper: B), 1..512                                  */
+    int K;            /* users (paper: U), 1..32, K <= M                                 */
+    int N;            /* OFDM size, a power of two in 64..4096                           */
+    int N_d;          /* data subcarriers, 1..N                                          */
+    int first_bin;    /* FFT bin of data subcarrier 0; -1 selects N - N_d/2 (DC-centred) */
+    int S_per_real;   /* OFDM symbols per channel realisation, >= 1                      */
+    int max_symbols;  /* the largest S any call on this plan passes (sizes the workspace)*/
+    int precision;    /* enum fddpd_precision                                            */
+    double P_T;       /* transmit power of the ZF normalisation, E||x_hat_k||^2 = P_T    */
+} fddpd_dims;
+
+typedef struct {
+    int n_orders;     /* 1..8                                                            */
+    int orders[8];    /* nonlinear orders p >= 1 of the basis x |x|^{p-1} (e.g. 1, 3, 5) */
+    int L;            /* memory: taps l = 0..L, 0..7                                     */
+} fddpd_pa_desc;
+
+typedef struct {
+    int G;            /* grid side, G*G >= N_d (the paper's ceil(sqrt(N_d)))             */
+    int L_U;          /* users per FD-CNN input, 1..K (users u, u+1, ... mod K)          */
+    int K_C;          /* odd kernel size                                                 */
+    int K_S;          /* stride                                                          */
+    int N_conv;       /* number of kernels                                               */
+    int residual;     /* 1: s_tilde = s + FC(.); 0: s_tilde = FC(.) as printed           */
+} fddpd_dpd_desc;
+
+/* Create a plan on `stream` (a cudaStream_t; NULL = legacy default stream).  Validates
+ * the sizes, selects the kernels and allocates the workspace for max_symbols symbols.
+ * *out receives the plan, or NULL on failure.  Errors: ARG, UNSUPPORTED, NOMEM, CUDA. */
+int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *dims, const fddpd_pa_desc *pa,
+                      const fddpd_dpd_desc *dpd, void *stream);
+
+/* Release the plan and its workspace (after its stream has finished).  NULL is a no-op. */
+int fddpd_plan_destroy(fddpd_plan *plan);
+
+/* Text of the last error on this plan (or of the last failed create when plan is NULL). */
+const char *fddpd_last_error(const fddpd_plan *plan);
+
+/* Number of FP32 entries of theta for this plan. */
+size_t fddpd_theta_len(const fddpd_plan *plan);
+
+/* Device bytes the plan holds. */
+size_t fddpd_workspace_bytes(const fddpd_plan *plan);
+
+/* Re-bind the plan to another stream. */
+int fddpd_set_stream(fddpd_plan *plan, void *stream);
+
+/* Eq. (6): zero-forcing precoder for R channel realisations (Sec. II-A).
+ *   H     [R][N_d][K][M]  in : per-subcarrier channel of the data bins
+ *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}
+ *   alpha [R][N_d]        out: sqrt(P_T / tr((H_k H_k^H)^{-1}))
+ * The Gram matrix is accumulated in FP32 and factorised (Cholesky) and inverted in
+ * FP64.  16-bit plans also cache packed 16-bit copies of alpha W and H / alpha for the
+ * next distort / backward / update calls with these same H, W and alpha pointers
+ * (calls with other pointers re-pack from the FP32 arrays).  R <= ceil(max_symbols /
+ * S_per_real).  Errors: ARG, LAYOUT, SINGULAR (reported after the kernel completes:
+ * this call synchronises the stream once to read the status word).              */
+int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha);
+
+/* Forward chain over S symbols (running mode of the FD-DPD, Sec. III-A and IV).
+ *   s       [S][K][N_d]       in : unit-power QAM symbols of the data bins
+ *   H, W, alpha               in : as produced for realisations 0..ceil(S/S_per_real)-1
+ *   pa_coef [M][n_orders][L+1] in: per-antenna PA coefficients c^b_{p,l}
+ *   theta                     in : FD-CNN parameters (layout above)
+ *   y       [S][K][N_d]       out: equalised received symbols y_k / alpha_k (may be NULL)
+ *   metrics double[5]         out: see above (may be NULL)                         */
+int fddpd_distort(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                  const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
+                  const float *theta, fddpd_c32 *y, double *metrics);
+
+/* Gradient of the loss over the S symbols with respect to theta (Sec. V-A), by the
+ * hand-written adjoint of the whole chain; the time-domain PA inputs are recomputed
+ * from x_hat, not stored.  grad [theta_len] out (overwritten).  metrics as distort. */
+int fddpd_backward(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                   const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
+                   const float *theta, float *grad, double *metrics);
+
+/* `iters` training iterations over the S symbols (Sec. V-A): each runs forward, the
+ * adjoint and one step theta -= lr * grad (FDDPD_GD), or one Adam step with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8 (FDDPD_ADAM; the moments live in the plan
+ * and persist across calls until fddpd_reset_optimizer).  theta is updated in place.
+ * metrics: those of the last iteration's forward pass (before its step).          */
+int fddpd_update(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                 const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
+                 float *theta, float lr, int iters, int optimizer, double *metrics);
+
+/* Zero the Adam moments and step counter. */
+int fddpd_reset_optimizer(fddpd_plan *plan);
+
+/* One training step from HOST memory (Sec. V-A with a new channel per mini-batch):
+ * copies s [S][K][N_d], H [R][N_d][K][M] (R = ceil(S / S_per_real)), pa_coef and theta
+ * to plan-owned device buffers (allocated on the first call), runs fddpd_precode and
+ * fddpd_update(iters), and copies theta and metrics[5] back.  Host buffers should be
+ * page-locked for full copy bandwidth.  Blocks until the step is complete.  Errors as
+ * fddpd_precode / fddpd_update, NOMEM if the staging buffers cannot be allocated.   */
+int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                      const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
+                      double *metrics);
+
+/* Stage tracing.  Stages of the chain, in execution order. */
+enum fddpd_stage {
+    FDDPD_STAGE_ZF = 0, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,
+    FDDPD_STAGE_FFTPA_FWD, FDDPD_STAGE_COMBINE, FDDPD_STAGE_ADJ_COMBINE, FDDPD_STAGE_FFTPA_ADJ,
+    FDDPD_STAGE_ADJ_PRECODE, FDDPD_STAGE_FC_BWD_W, FDDPD_STAGE_FC_BWD_B, FDDPD_STAGE_FC_BWD_D,
+    FDDPD_STAGE_CONV_BWD, FDDPD_STAGE_STEP, FDDPD_STAGE_PACK, FDDPD_N_STAGES
+};
+
+/* While enabled, every stage's kernels are bracketed by CUDA events on the plan's
+ * stream (at most 4096 brackets between reads; later ones are not timed). */
+int fddpd_profile_enable(fddpd_plan *plan, int enable);
+
+/* Synchronise the plan's stream, then write per stage the summed device time in ms
+ * (ms[FDDPD_N_STAGES]) and the number of timed brackets (count[FDDPD_N_STAGES]) since
+ * the last read, and clear them.  Either pointer may be NULL.                        */
+int fddpd_profile_read(fddpd_plan *plan, double *ms, long long *count);
+
+/* Name of a stage ("zf", "fc_fwd", ...), or NULL. */
+const char *fddpd_stage_name(int stage);
+
+/* Number of kernels this plan has launched since it was created. */
+long long fddpd_launch_count(const fddpd_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDDPD_H */

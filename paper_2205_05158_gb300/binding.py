@@ -1,0 +1,200 @@
+"""Thin ctypes binding of the fddpd C-ABI (include/fddpd.h).
+
+Argument marshalling only: every step of the chain runs in the CUDA library.
+Tensors must be contiguous CUDA tensors of the documented dtypes (complex64 for
+fddpd_c32 arrays, float32, float64 for metrics); raw integer device pointers are
+accepted too.  If the library is missing this module raises instead of falling
+back to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+
+FDDPD_OK = 0
+FDDPD_ERR_ARG, FDDPD_ERR_LAYOUT, FDDPD_ERR_SINGULAR = -1, -2, -3
+FDDPD_ERR_CUDA, FDDPD_ERR_TIMEOUT, FDDPD_ERR_UNSUPPORTED, FDDPD_ERR_NOMEM = -4, -5, -6, -7
+FDDPD_FP32, FDDPD_BF16, FDDPD_FP16 = 0, 1, 2
+FDDPD_GD, FDDPD_ADAM = 0, 1
+
+EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
+            "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
+            "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer"]
+
+
+class Dims(C.Structure):
+    _fields_ = [("M", C.c_int), ("K", C.c_int), ("N", C.c_int), ("N_d", C.c_int), ("first_bin", C.c_int),
+                ("S_per_real", C.c_int), ("max_symbols", C.c_int), ("precision", C.c_int), ("P_T", C.c_double)]
+
+
+class PaDesc(C.Structure):
+    _fields_ = [("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int)]
+
+
+class DpdDesc(C.Structure):
+    _fields_ = [("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int), ("N_conv", C.c_int),
+                ("residual", C.c_int)]
+
+
+class FddpdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fddpd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfddpd.so (building it with nvcc when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing; run paper_2205_05158_gb300.build.build()")
+        _build.build()
+    L = C.CDLL(path)
+    P, I = C.c_void_p, C.c_int
+    L.fddpd_plan_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Dims), C.POINTER(PaDesc), C.POINTER(DpdDesc), P]
+    L.fddpd_plan_destroy.argtypes = [P]
+    L.fddpd_last_error.argtypes = [P]
+    L.fddpd_last_error.restype = C.c_char_p
+    L.fddpd_theta_len.argtypes = [P]
+    L.fddpd_theta_len.restype = C.c_size_t
+    L.fddpd_workspace_bytes.argtypes = [P]
+    L.fddpd_workspace_bytes.restype = C.c_size_t
+    L.fddpd_set_stream.argtypes = [P, P]
+    L.fddpd_precode.argtypes = [P, I, P, P, P]
+    L.fddpd_distort.argtypes = [P, I, P, P, P, P, P, P, P, P]
+    L.fddpd_backward.argtypes = [P, I, P, P, P, P, P, P, P, P]
+    L.fddpd_update.argtypes = [P, I, P, P, P, P, P, P, C.c_float, I, I, P]
+    L.fddpd_reset_optimizer.argtypes = [P]
+    for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
+              "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x, dtype=None) -> Optional[int]:
+    """Device address of a contiguous CUDA tensor (or pass an int through)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    return x.data_ptr()
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Plan:
+    """Owns one fddpd_plan.  Methods mirror the C entry points one to one."""
+
+    def __init__(self, M: int, K: int, N: int, N_d: int, S_per_real: int, max_symbols: int, P_T: float,
+                 orders: Sequence[int], L: int, G: int, L_U: int = 1, K_C: int = 3, K_S: int = 1, N_conv: int = 2,
+                 residual: int = 1, precision: int = FDDPD_FP32, first_bin: int = -1, stream=None):
+        self._lib = load()
+        d = Dims(M, K, N, N_d, first_bin, S_per_real, max_symbols, precision, float(P_T))
+        pa = PaDesc()
+        pa.n_orders = len(orders)
+        for i, p in enumerate(orders):
+            pa.orders[i] = int(p)
+        pa.L = L
+        dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual)
+        h = C.c_void_p()
+        rc = self._lib.fddpd_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(dpd), _stream_ptr(stream))
+        if rc:
+            raise FddpdError(rc, self._lib.fddpd_last_error(None).decode())
+        self._h = h
+        self.M, self.K, self.N, self.N_d, self.S_per_real = M, K, N, N_d, S_per_real
+        self.precision = precision
+
+    @classmethod
+    def from_config(cls, cfg, P_T: float, max_symbols: Optional[int] = None, precision: int = FDDPD_FP32,
+                    residual: int = 1, stream=None) -> "Plan":
+        return cls(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.S_per_real, max_symbols or cfg.S, P_T, cfg.orders, cfg.L,
+                   cfg.grid, cfg.L_U, cfg.K_C, cfg.K_S, cfg.N_conv, residual, precision, cfg.first_bin, stream)
+
+    def _check(self, rc: int):
+        if rc:
+            raise FddpdError(rc, self._lib.fddpd_last_error(self._h).decode())
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    @property
+    def theta_len(self) -> int:
+        return self._lib.fddpd_theta_len(self._h)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return self._lib.fddpd_workspace_bytes(self._h)
+
+    def set_stream(self, stream):
+        self._check(self._lib.fddpd_set_stream(self._h, _stream_ptr(stream)))
+
+    def precode(self, H, W, alpha, R: Optional[int] = None):
+        import torch
+        R = H.shape[0] if R is None else R
+        self._check(self._lib.fddpd_precode(self._h, R, _ptr(H, torch.complex64), _ptr(W, torch.complex64),
+                                            _ptr(alpha, torch.float32)))
+
+    def distort(self, s, H, W, alpha, pa, theta, y=None, metrics=None, S: Optional[int] = None):
+        import torch
+        S = s.shape[0] if S is None else S
+        self._check(self._lib.fddpd_distort(self._h, S, _ptr(s, torch.complex64), _ptr(H, torch.complex64),
+                                            _ptr(W, torch.complex64), _ptr(alpha, torch.float32),
+                                            _ptr(pa, torch.complex64), _ptr(theta, torch.float32),
+                                            _ptr(y, torch.complex64), _ptr(metrics, torch.float64)))
+
+    def backward(self, s, H, W, alpha, pa, theta, grad, metrics=None, S: Optional[int] = None):
+        import torch
+        S = s.shape[0] if S is None else S
+        self._check(self._lib.fddpd_backward(self._h, S, _ptr(s, torch.complex64), _ptr(H, torch.complex64),
+                                             _ptr(W, torch.complex64), _ptr(alpha, torch.float32),
+                                             _ptr(pa, torch.complex64), _ptr(theta, torch.float32),
+                                             _ptr(grad, torch.float32), _ptr(metrics, torch.float64)))
+
+    def update(self, s, H, W, alpha, pa, theta, lr: float, iters: int = 1, optimizer: int = FDDPD_GD, metrics=None,
+               S: Optional[int] = None):
+        import torch
+        S = s.shape[0] if S is None else S
+        self._check(self._lib.fddpd_update(self._h, S, _ptr(s, torch.complex64), _ptr(H, torch.complex64),
+                                           _ptr(W, torch.complex64), _ptr(alpha, torch.float32),
+                                           _ptr(pa, torch.complex64), _ptr(theta, torch.float32), float(lr),
+                                           int(iters), int(optimizer), _ptr(metrics, torch.float64)))
+
+    def reset_optimizer(self):
+        self._check(self._lib.fddpd_reset_optimizer(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fddpd_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,415 @@
+// C-ABI of the fddpd library: plan life cycle, argument checks, workspace layout and
+// the order in which the stage kernels run on the plan's stream.
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fddpd.h"
+#include "kernels.h"
+
+using fdk::Geo;
+
+struct fddpd_plan {
+    fddpd_dims d;
+    fddpd_pa_desc pa;
+    fddpd_dpd_desc dpd;
+    Geo g;
+    cudaStream_t stream;
+    int R_max;
+    void *base;
+    size_t bytes;
+    c32 *st, *gy, *gst, *xh, *Xpa, *tw;
+    float *act, *gpre, *partials, *grad, *adam_m, *adam_v;
+    double *met;
+    int *status;
+    int *status_host;
+    long adam_t;
+    // stage tracing
+    int prof;
+    int nrec;
+    cudaEvent_t *ev;          // 2 * kMaxRec events, created on first enable
+    int rec_stage[4096];
+    long long launches;
+    // device staging of fddpd_update_host
+    void *stage_base;
+    c32 *hs, *hH, *hW, *hpa;
+    float *hal, *htheta;
+    double *hmet;
+    char err[512];
+};
+
+static constexpr int kMaxRec = 4096;
+static const char *kStageNames[FDDPD_N_STAGES] = {
+    "zf", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
+    "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"};
+
+static int stage_begin(fddpd_plan *p, int stage) {
+    if (!p->prof || p->nrec >= kMaxRec) return -1;
+    const int slot = p->nrec++;
+    p->rec_stage[slot] = stage;
+    cudaEventRecord(p->ev[2 * slot], p->stream);
+    return slot;
+}
+static void stage_end(fddpd_plan *p, int slot) {
+    if (slot >= 0) cudaEventRecord(p->ev[2 * slot + 1], p->stream);
+}
+
+static thread_local char g_create_err[512] = "";
+
+static int set_err(fddpd_plan *p, int code, const char *fmt, ...) {
+    char *dst = p ? p->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define FD_CK(p, expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return set_err(p, FDDPD_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Run one stage: `nk` kernels launched by `expr`, bracketed by events when tracing.
+#define FD_STAGE(p, stage, nk, expr)                 \
+    do {                                             \
+        const int slot_ = stage_begin(p, stage);     \
+        FD_CK(p, expr);                              \
+        stage_end(p, slot_);                         \
+        (p)->launches += (nk);                       \
+    } while (0)
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+
+static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dpd_desc *dpd) {
+    if (!d || !pa || !dpd) return set_err(nullptr, FDDPD_ERR_ARG, "null descriptor");
+    if (d->M < 1 || d->M > 512) return set_err(nullptr, FDDPD_ERR_ARG, "M=%d outside 1..512", d->M);
+    if (d->K < 1 || d->K > 32 || d->K > d->M) return set_err(nullptr, FDDPD_ERR_ARG, "K=%d outside 1..min(32,M)", d->K);
+    if (!is_pow2(d->N) || d->N < 64 || d->N > 4096) return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "N=%d is not a power of two in 64..4096", d->N);
+    if (d->N_d < 1 || d->N_d > d->N) return set_err(nullptr, FDDPD_ERR_ARG, "N_d=%d outside 1..N", d->N_d);
+    if (d->first_bin < -1 || d->first_bin >= d->N) return set_err(nullptr, FDDPD_ERR_ARG, "first_bin=%d", d->first_bin);
+    if (d->S_per_real < 1 || d->max_symbols < 1) return set_err(nullptr, FDDPD_ERR_ARG, "S_per_real / max_symbols < 1");
+    if (d->precision != FDDPD_FP32 && d->precision != FDDPD_BF16 && d->precision != FDDPD_FP16)
+        return set_err(nullptr, FDDPD_ERR_ARG, "precision=%d", d->precision);
+    if (!(d->P_T > 0)) return set_err(nullptr, FDDPD_ERR_ARG, "P_T must be positive");
+    if (pa->n_orders < 1 || pa->n_orders > 8 || pa->L < 0 || pa->L > 7) return set_err(nullptr, FDDPD_ERR_ARG, "PA orders / memory out of range");
+    for (int i = 0; i < pa->n_orders; ++i)
+        if (pa->orders[i] < 1 || pa->orders[i] > 15) return set_err(nullptr, FDDPD_ERR_ARG, "PA order %d outside 1..15", pa->orders[i]);
+    if (dpd->G < 1 || dpd->G * dpd->G < d->N_d || dpd->G > 128) return set_err(nullptr, FDDPD_ERR_ARG, "grid G=%d cannot hold N_d", dpd->G);
+    if (dpd->L_U < 1 || dpd->L_U > d->K) return set_err(nullptr, FDDPD_ERR_ARG, "L_U=%d outside 1..K", dpd->L_U);
+    if (dpd->K_C < 1 || !(dpd->K_C & 1) || dpd->K_C > 15) return set_err(nullptr, FDDPD_ERR_ARG, "K_C=%d must be odd in 1..15", dpd->K_C);
+    if (dpd->K_S < 1 || dpd->K_S > dpd->G) return set_err(nullptr, FDDPD_ERR_ARG, "K_S=%d", dpd->K_S);
+    if (dpd->N_conv < 1 || dpd->N_conv > 64) return set_err(nullptr, FDDPD_ERR_ARG, "N_conv=%d outside 1..64", dpd->N_conv);
+    if (dpd->residual != 0 && dpd->residual != 1) return set_err(nullptr, FDDPD_ERR_ARG, "residual must be 0 or 1");
+    if (d->precision != FDDPD_FP32) return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "16-bit plans are not built in this library");
+    return FDDPD_OK;
+}
+
+static Geo make_geo(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dpd_desc *dpd) {
+    Geo g;
+    memset(&g, 0, sizeof g);
+    g.M = d->M; g.K = d->K; g.N = d->N; g.N_d = d->N_d;
+    g.first_bin = d->first_bin < 0 ? d->N - d->N_d / 2 : d->first_bin;
+    g.S_per_real = d->S_per_real;
+    g.log2N = 0;
+    while ((1 << g.log2N) < d->N) ++g.log2N;
+    g.n_orders = pa->n_orders;
+    for (int i = 0; i < 8; ++i) g.orders[i] = i < pa->n_orders ? pa->orders[i] : 0;
+    g.L = pa->L;
+    g.G = dpd->G; g.K_S = dpd->K_S; g.Go = (dpd->G + dpd->K_S - 1) / dpd->K_S;
+    g.L_U = dpd->L_U; g.Cin = 2 * dpd->L_U; g.K_C = dpd->K_C; g.pad = dpd->K_C / 2;
+    g.N_conv = dpd->N_conv; g.F = dpd->N_conv * g.Go * g.Go; g.residual = dpd->residual;
+    g.n_convw = g.N_conv * g.Cin * g.K_C * g.K_C;
+    g.off_cb = g.n_convw;
+    g.off_fw = g.off_cb + g.N_conv;
+    g.off_fb = g.off_fw + 2L * g.N_d * g.F;
+    g.theta_len = g.off_fb + 2L * g.N_d;
+    g.P_T = d->P_T;
+    return g;
+}
+
+extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fddpd_pa_desc *pa,
+                                 const fddpd_dpd_desc *dpd, void *stream) {
+    if (!out) return set_err(nullptr, FDDPD_ERR_ARG, "out is null");
+    *out = nullptr;
+    int rc = validate(d, pa, dpd);
+    if (rc) return rc;
+    fddpd_plan *p = new (std::nothrow) fddpd_plan;
+    if (!p) return set_err(nullptr, FDDPD_ERR_NOMEM, "host allocation failed");
+    memset(p, 0, sizeof *p);
+    p->d = *d; p->pa = *pa; p->dpd = *dpd;
+    p->g = make_geo(d, pa, dpd);
+    p->stream = static_cast<cudaStream_t>(stream);
+    const Geo &g = p->g;
+    const long S = d->max_symbols, cols = S * g.K;
+    p->R_max = (int)((S + g.S_per_real - 1) / g.S_per_real);
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_st = take(sizeof(c32) * cols * g.N_d), o_gy = take(sizeof(c32) * cols * g.N_d),
+                 o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(sizeof(c32) * S * g.M * g.N_d),
+                 o_X = take(sizeof(c32) * S * g.M * g.N_d), o_tw = take(sizeof(c32) * g.N),
+                 o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * g.F),
+                 o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
+                 o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
+                 o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(sizeof(int));
+    p->bytes = off;
+    cudaError_t e = cudaMalloc(&p->base, off);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return set_err(nullptr, FDDPD_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
+    }
+    char *b = static_cast<char *>(p->base);
+    p->st = (c32 *)(b + o_st); p->gy = (c32 *)(b + o_gy); p->gst = (c32 *)(b + o_gst);
+    p->xh = (c32 *)(b + o_xh); p->Xpa = (c32 *)(b + o_X); p->tw = (c32 *)(b + o_tw);
+    p->act = (float *)(b + o_act); p->gpre = (float *)(b + o_gpre); p->partials = (float *)(b + o_part);
+    p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
+    p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
+    e = cudaMallocHost(&p->status_host, sizeof(int));
+    if (e == cudaSuccess) e = fdk::twiddles(g.N, p->tw, p->stream);
+    p->launches = 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_m, 0, sizeof(float) * g.theta_len, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_v, 0, sizeof(float) * g.theta_len, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        set_err(nullptr, FDDPD_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e));
+        fddpd_plan_destroy(p);
+        return FDDPD_ERR_CUDA;
+    }
+    *out = p;
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_plan_destroy(fddpd_plan *p) {
+    if (!p) return FDDPD_OK;
+    if (p->base) cudaFree(p->base);
+    if (p->stage_base) cudaFree(p->stage_base);
+    if (p->status_host) cudaFreeHost(p->status_host);
+    if (p->ev) {
+        for (int i = 0; i < 2 * kMaxRec; ++i) cudaEventDestroy(p->ev[i]);
+        delete[] p->ev;
+    }
+    delete p;
+    return FDDPD_OK;
+}
+
+extern "C" const char *fddpd_last_error(const fddpd_plan *p) { return p ? p->err : g_create_err; }
+extern "C" size_t fddpd_theta_len(const fddpd_plan *p) { return p ? (size_t)p->g.theta_len : 0; }
+extern "C" size_t fddpd_workspace_bytes(const fddpd_plan *p) { return p ? p->bytes : 0; }
+
+extern "C" int fddpd_set_stream(fddpd_plan *p, void *stream) {
+    if (!p) return FDDPD_ERR_ARG;
+    p->stream = static_cast<cudaStream_t>(stream);
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {
+    if (!p) return FDDPD_ERR_ARG;
+    p->adam_t = 0;
+    FD_CK(p, cudaMemsetAsync(p->adam_m, 0, sizeof(float) * p->g.theta_len, p->stream));
+    FD_CK(p, cudaMemsetAsync(p->adam_v, 0, sizeof(float) * p->g.theta_len, p->stream));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (R < 0 || R > p->R_max) return set_err(p, FDDPD_ERR_ARG, "R=%d outside 0..%d", R, p->R_max);
+    if (R == 0) return FDDPD_OK;
+    if (!H || !W || !alpha) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    cudaStream_t st = p->stream;
+    FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    FD_STAGE(p, FDDPD_STAGE_ZF, 1, fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status, st));
+    FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FD_CK(p, cudaStreamSynchronize(st));
+    if (*p->status_host) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
+    return FDDPD_OK;
+}
+
+static int check_chain(fddpd_plan *p, int S, const void *s, const void *H, const void *W, const void *alpha,
+                       const void *pa, const void *theta) {
+    if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
+    if (!s || !H || !W || !alpha || !pa || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (!aligned(s, 8) || !aligned(H, 8) || !aligned(W, 8) || !aligned(pa, 8) || !aligned(alpha, 4) || !aligned(theta, 4))
+        return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    return FDDPD_OK;
+}
+
+// Forward chain; gy (loss gradient at y) is written when non-null.
+static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
+                       const c32 *pa, const float *theta, c32 *y, c32 *gy) {
+    const Geo &g = p->g;
+    cudaStream_t st = p->stream;
+    const long cols = (long)S * g.K;
+    const double inv_count = 1.0 / ((double)cols * g.N_d);
+    FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
+    FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
+    FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
+    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, fdk::bin_expand(g, fdk::PRECODE, S, W, alpha, p->st, p->xh, st));
+    FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1, fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, st));
+    FD_STAGE(p, FDDPD_STAGE_COMBINE, 1, fdk::bin_reduce(g, fdk::COMBINE, S, H, alpha, p->Xpa, y, s, gy, p->met, inv_count, st));
+    FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
+    p->launches += 1;
+    return FDDPD_OK;
+}
+
+static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
+                        const c32 *pa, const float *theta, float *grad) {
+    const Geo &g = p->g;
+    cudaStream_t st = p->stream;
+    const int cols = S * g.K;
+    int rc = run_forward(p, S, s, H, W, alpha, pa, theta, nullptr, p->gy);
+    if (rc) return rc;
+    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, fdk::bin_expand(g, fdk::ADJ_COMBINE, S, H, alpha, p->gy, p->Xpa, st));
+    FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1, fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, st));
+    FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1, fdk::bin_reduce(g, fdk::ADJ_PRECODE, S, W, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, st));
+    const float *gd = reinterpret_cast<const float *>(p->gst);
+    FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
+    FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, st));
+    FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
+    FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, cols, gd, theta, p->act, p->gpre, st));
+    FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, p->gpre, p->act, p->partials, st));
+    FD_CK(p, fdk::conv_reduce(g, cols, p->partials, grad, st));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_distort(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
+                             const float *alpha, const fddpd_c32 *pa_coef, const float *theta, fddpd_c32 *y,
+                             double *metrics) {
+    if (!p) return FDDPD_ERR_ARG;
+    int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
+    if (rc) return rc;
+    if ((y && !aligned(y, 8)) || (metrics && !aligned(metrics, 8))) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned output");
+    rc = run_forward(p, S, (const c32 *)s, (const c32 *)H, (const c32 *)W, alpha, (const c32 *)pa_coef, theta,
+                     (c32 *)y, nullptr);
+    if (rc) return rc;
+    if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->met, sizeof(double) * 5, cudaMemcpyDeviceToDevice, p->stream));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_backward(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
+                              const float *alpha, const fddpd_c32 *pa_coef, const float *theta, float *grad,
+                              double *metrics) {
+    if (!p) return FDDPD_ERR_ARG;
+    int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
+    if (rc) return rc;
+    if (!grad) return set_err(p, FDDPD_ERR_ARG, "grad is null");
+    if (!aligned(grad, 4) || (metrics && !aligned(metrics, 8))) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned output");
+    rc = run_backward(p, S, (const c32 *)s, (const c32 *)H, (const c32 *)W, alpha, (const c32 *)pa_coef, theta, grad);
+    if (rc) return rc;
+    if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->met, sizeof(double) * 5, cudaMemcpyDeviceToDevice, p->stream));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_update(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
+                            const float *alpha, const fddpd_c32 *pa_coef, float *theta, float lr, int iters,
+                            int optimizer, double *metrics) {
+    if (!p) return FDDPD_ERR_ARG;
+    int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
+    if (rc) return rc;
+    if (iters < 0) return set_err(p, FDDPD_ERR_ARG, "iters < 0");
+    if (optimizer != FDDPD_GD && optimizer != FDDPD_ADAM) return set_err(p, FDDPD_ERR_ARG, "optimizer=%d", optimizer);
+    if (metrics && !aligned(metrics, 8)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned metrics");
+    for (int it = 0; it < iters; ++it) {
+        rc = run_backward(p, S, (const c32 *)s, (const c32 *)H, (const c32 *)W, alpha, (const c32 *)pa_coef, theta,
+                          p->grad);
+        if (rc) return rc;
+        if (optimizer == FDDPD_GD) {
+            FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, p->grad, lr, p->stream));
+        } else {
+            const long t = ++p->adam_t;
+            const float c1 = (float)(1.0 - pow(0.9, (double)t)), c2 = (float)(1.0 - pow(0.999, (double)t));
+            FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::adam_step(p->g.theta_len, theta, p->grad, p->adam_m, p->adam_v, lr, c1, c2, p->stream));
+        }
+    }
+    if (metrics && iters > 0)
+        FD_CK(p, cudaMemcpyAsync(metrics, p->met, sizeof(double) * 5, cudaMemcpyDeviceToDevice, p->stream));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_profile_enable(fddpd_plan *p, int enable) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (enable && !p->ev) {
+        p->ev = new (std::nothrow) cudaEvent_t[2 * kMaxRec];
+        if (!p->ev) return set_err(p, FDDPD_ERR_NOMEM, "event pool");
+        for (int i = 0; i < 2 * kMaxRec; ++i) FD_CK(p, cudaEventCreate(&p->ev[i]));
+    }
+    p->prof = enable ? 1 : 0;
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_profile_read(fddpd_plan *p, double *ms, long long *count) {
+    if (!p) return FDDPD_ERR_ARG;
+    FD_CK(p, cudaStreamSynchronize(p->stream));
+    double acc[FDDPD_N_STAGES] = {0};
+    long long cnt[FDDPD_N_STAGES] = {0};
+    for (int i = 0; i < p->nrec; ++i) {
+        float t = 0.f;
+        FD_CK(p, cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]));
+        acc[p->rec_stage[i]] += t;
+        cnt[p->rec_stage[i]] += 1;
+    }
+    p->nrec = 0;
+    for (int k = 0; k < FDDPD_N_STAGES; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (count) count[k] = cnt[k];
+    }
+    return FDDPD_OK;
+}
+
+extern "C" const char *fddpd_stage_name(int stage) {
+    return (stage >= 0 && stage < FDDPD_N_STAGES) ? kStageNames[stage] : nullptr;
+}
+
+extern "C" long long fddpd_launch_count(const fddpd_plan *p) { return p ? p->launches : 0; }
+
+extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                                 const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
+                                 double *metrics) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
+    if (!s || !H || !pa_coef || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    const Geo &g = p->g;
+    const long R = (S + g.S_per_real - 1) / g.S_per_real;
+    const size_t n_s = sizeof(c32) * (size_t)p->d.max_symbols * g.K * g.N_d,
+                 n_H = sizeof(c32) * (size_t)p->R_max * g.N_d * g.K * g.M,
+                 n_al = sizeof(float) * (size_t)p->R_max * g.N_d,
+                 n_pa = sizeof(c32) * (size_t)g.M * g.n_orders * (g.L + 1),
+                 n_th = sizeof(float) * (size_t)g.theta_len;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    if (!p->stage_base) {
+        const size_t tot = up(n_s) + 2 * up(n_H) + up(n_al) + up(n_pa) + up(n_th) + up(8 * sizeof(double));
+        if (cudaMalloc(&p->stage_base, tot) != cudaSuccess) {
+            cudaGetLastError();
+            p->stage_base = nullptr;
+            return set_err(p, FDDPD_ERR_NOMEM, "staging buffers (%zu bytes)", tot);
+        }
+        char *b = static_cast<char *>(p->stage_base);
+        p->hs = (c32 *)b; b += up(n_s);
+        p->hH = (c32 *)b; b += up(n_H);
+        p->hW = (c32 *)b; b += up(n_H);
+        p->hal = (float *)b; b += up(n_al);
+        p->hpa = (c32 *)b; b += up(n_pa);
+        p->htheta = (float *)b; b += up(n_th);
+        p->hmet = (double *)b;
+    }
+    cudaStream_t st = p->stream;
+    FD_CK(p, cudaMemcpyAsync(p->hs, s, sizeof(c32) * (size_t)S * g.K * g.N_d, cudaMemcpyHostToDevice, st));
+    FD_CK(p, cudaMemcpyAsync(p->hH, H, sizeof(c32) * (size_t)R * g.N_d * g.K * g.M, cudaMemcpyHostToDevice, st));
+    FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, st));
+    FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, st));
+    int rc = fddpd_precode(p, (int)R, (const fddpd_c32 *)p->hH, (fddpd_c32 *)p->hW, p->hal);
+    if (rc) return rc;
+    rc = fddpd_update(p, S, (const fddpd_c32 *)p->hs, (const fddpd_c32 *)p->hH, (const fddpd_c32 *)p->hW, p->hal,
+                      (const fddpd_c32 *)p->hpa, p->htheta, lr, iters, optimizer, p->hmet);
+    if (rc) return rc;
+    FD_CK(p, cudaMemcpyAsync(theta, p->htheta, n_th, cudaMemcpyDeviceToHost, st));
+    if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FD_CK(p, cudaStreamSynchronize(st));
+    return FDDPD_OK;
+}

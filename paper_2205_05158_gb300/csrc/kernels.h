@@ -1,0 +1,62 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace fdk {
+
+enum OutKind { OUT_F32 = 0, OUT_BF16 = 1, OUT_F16 = 2 };
+
+// Every size a kernel needs, derived once at plan creation.
+struct Geo {
+    int M, K, N, N_d, first_bin, S_per_real, log2N;
+    int n_orders, orders[8], L;
+    int G, Go, L_U, Cin, K_C, K_S, pad, N_conv, F, residual;
+    int n_convw;             // N_conv * Cin * K_C * K_C
+    long off_cb, off_fw, off_fb, theta_len;
+    double P_T;
+};
+
+// zero-forcing precoder (Eq. 6): FP32 Gram, FP64 Cholesky + triangular inverse
+cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, cudaStream_t st);
+
+// FD-CNN
+cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
+cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gact, const float *act, float *partials,
+                          cudaStream_t st);
+cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, cudaStream_t st);
+cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st);
+
+// FP32 GEMM with the FD-CNN dense-layer layouts (rows of fc_w interleaved Re/Im)
+cudaError_t fc_forward_f32(const Geo &g, int cols, const float *act, const float *theta, const c32 *s, c32 *st,
+                           cudaStream_t stm);
+cudaError_t fc_backward_data_f32(const Geo &g, int cols, const float *gd, const float *theta, const float *act,
+                                 float *gpre, cudaStream_t stm);
+cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, const float *act, float *grad,
+                                   cudaStream_t stm);
+
+// per-subcarrier complex contractions (FP32 operands)
+enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3 };
+cudaError_t bin_expand(const Geo &g, int mode, int S, const c32 *A, const float *alpha, const c32 *B, c32 *out,
+                       cudaStream_t st);
+cudaError_t bin_reduce(const Geo &g, int mode, int S, const c32 *A, const float *alpha, const c32 *B, c32 *out,
+                       const c32 *s_ref, c32 *gy, double *metrics, double inv_count, cudaStream_t st);
+
+// OFDM + PA rows
+size_t fftpa_smem_bytes(const Geo &g, bool adjoint);
+cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, void *X, int out_kind,
+                          double *metrics, cudaStream_t st);
+cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const c32 *gX, c32 *gxh,
+                          cudaStream_t st);
+
+// parameter updates and bookkeeping
+cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);
+cudaError_t adam_step(long n, float *theta, const float *grad, float *m, float *v, float lr, float c1, float c2,
+                      cudaStream_t st);
+cudaError_t finalize_metrics(double *metrics, double inv_count, cudaStream_t st);
+cudaError_t twiddles(int N, c32 *tw, cudaStream_t st);
+
+}  // namespace fdk

@@ -1,0 +1,84 @@
+"""C-ABI library: it loads, exports every declared entry point, and rejects bad
+arguments on the host before any device work (no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2205_05158_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(fddpd_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    decl = declared_symbols()
+    assert decl, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fddpd_[a-z_0-9]+)", out))
+    assert decl <= exported, decl - exported
+    assert set(binding.EXPORTED) == decl
+    for name in decl:
+        assert getattr(lib, name) is not None
+
+
+def _create(lib, **over):
+    d = dict(M=16, K=2, N=64, N_d=48, first_bin=-1, S_per_real=10, max_symbols=10, precision=0, P_T=10.0)
+    pa = dict(orders=[1, 3], L=0)
+    dpd = dict(G=7, L_U=1, K_C=3, K_S=1, N_conv=2, residual=1)
+    for k, v in over.items():
+        (d if k in d else pa if k in pa else dpd)[k] = v
+    dims = binding.Dims(d["M"], d["K"], d["N"], d["N_d"], d["first_bin"], d["S_per_real"], d["max_symbols"],
+                        d["precision"], d["P_T"])
+    pad = binding.PaDesc()
+    pad.n_orders = len(pa["orders"])
+    for i, p in enumerate(pa["orders"]):
+        pad.orders[i] = p
+    pad.L = pa["L"]
+    dd = binding.DpdDesc(dpd["G"], dpd["L_U"], dpd["K_C"], dpd["K_S"], dpd["N_conv"], dpd["residual"])
+    h = C.c_void_p()
+    rc = lib.fddpd_plan_create(C.byref(h), C.byref(dims), C.byref(pad), C.byref(dd), None)
+    return rc, h
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(M=0), binding.FDDPD_ERR_ARG), (dict(K=40), binding.FDDPD_ERR_ARG), (dict(K=20, M=16), binding.FDDPD_ERR_ARG),
+    (dict(N=100), binding.FDDPD_ERR_UNSUPPORTED), (dict(N=8192), binding.FDDPD_ERR_UNSUPPORTED),
+    (dict(N_d=65), binding.FDDPD_ERR_ARG), (dict(N_d=0), binding.FDDPD_ERR_ARG),
+    (dict(first_bin=64), binding.FDDPD_ERR_ARG), (dict(S_per_real=0), binding.FDDPD_ERR_ARG),
+    (dict(max_symbols=0), binding.FDDPD_ERR_ARG), (dict(P_T=0.0), binding.FDDPD_ERR_ARG),
+    (dict(precision=7), binding.FDDPD_ERR_ARG), (dict(G=6), binding.FDDPD_ERR_ARG),
+    (dict(L_U=3), binding.FDDPD_ERR_ARG), (dict(K_C=2), binding.FDDPD_ERR_ARG),
+    (dict(N_conv=0), binding.FDDPD_ERR_ARG), (dict(residual=2), binding.FDDPD_ERR_ARG),
+    (dict(orders=[0]), binding.FDDPD_ERR_ARG), (dict(L=9), binding.FDDPD_ERR_ARG),
+])
+def test_plan_rejects_bad_descriptors(lib, over, code):
+    rc, h = _create(lib, **over)
+    assert rc == code
+    assert not h.value
+    assert lib.fddpd_last_error(None)
+
+
+def test_null_plan_calls(lib):
+    assert lib.fddpd_plan_destroy(None) == 0
+    assert lib.fddpd_precode(None, 1, None, None, None) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_distort(None, 1, *([None] * 8)) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_theta_len(None) == 0
