@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Throughput of the FD-DPD downlink chain on one GB300: DPD'd OFDM symbols/s.
+
+Workload: M=128 antennas, K=16 users, N=2048 with N_d=1200 data subcarriers,
+256-QAM, exponentially correlated (rho=0.5) Rayleigh channel with a new
+realisation every 14 symbols, memory-polynomial PAs (orders 1,3,5, taps 0..3),
+FD-CNN G=35, N_conv=2, K_C=3; 2000 symbols per step (143 realisations).
+
+One step = the whole hot path once over the 2000 symbols: zero-forcing build for
+every realisation, FD-CNN, precoding, IFFT, PA, FFT, combining, loss, the adjoint
+of all of it, and one gradient-descent update of theta.  Inputs are resident in
+HBM and larger than L2 (H alone is 2.8 GB).  `value` is device-timed with CUDA
+events; `e2e` runs the same step through fddpd_update_host from pinned host memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|bf16|fp16]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DPD'd OFDM symbols/s at M=128,K=16,N=2048; % roofline; EVM vs FP64 oracle"
+UNIT = "symbols/s"
+LR = 1e-4
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--symbols", type=int, default=2000)
+    ap.add_argument("--cpu-sample", type=int, default=6, help="symbols in the oracle's cpu_baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=2, help="symbols per step of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return mp, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of each stage (bytes or flops)
+# ---------------------------------------------------------------------------
+def stage_work(cfg, S: int, prec: str):
+    M, K, Nd, F, L_U = cfg.M, cfg.K, cfg.N_d, cfg.N_conv * (-(-cfg.grid // cfg.K_S)) ** 2, cfg.L_U
+    R = -(-S // cfg.S_per_real)
+    cols = S * K
+    c8 = 8
+    opb = 8 if prec == "fp32" else 4          # bytes of one complex H / W operand
+    fc_bound = "alu" if prec == "fp32" else "tensor"
+    theta_len = cfg.N_conv * 2 * L_U * cfg.K_C ** 2 + cfg.N_conv + 2 * Nd * F + 2 * Nd
+    return {
+        "zf": ("hbm", R * Nd * K * M * c8 * 2 + R * Nd * 4),
+        "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
+        "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
+        "precode": ("hbm", R * Nd * M * K * opb + S * K * Nd * c8 + S * M * Nd * c8),
+        "fftpa_fwd": ("hbm", 2 * S * M * Nd * c8),
+        "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * c8 + 2 * S * K * Nd * c8),
+        "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * c8),
+        "fftpa_adj": ("hbm", 3 * S * M * Nd * c8),
+        "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * c8 + S * K * Nd * c8),
+        "fc_bwd_w": (fc_bound, 2.0 * 2 * Nd * F * cols),
+        "fc_bwd_b": ("hbm", cols * 2 * Nd * 4),
+        "fc_bwd_d": (fc_bound, 2.0 * cols * F * 2 * Nd),
+        "conv_bwd": ("hbm", cols * (Nd * c8 * L_U + F * 4)),
+        "step": ("hbm", 3 * theta_len * 4),
+    }
+
+
+def source_hash(stage: str) -> str:
+    files = {"zf": "zf.cu", "fftpa_fwd": "fftpa.cu", "fftpa_adj": "fftpa.cu", "precode": "bingemm.cu",
+             "combine": "bingemm.cu", "adj_combine": "bingemm.cu", "adj_precode": "bingemm.cu",
+             "fc_fwd": "fdcnn.cu", "fc_bwd_w": "fdcnn.cu", "fc_bwd_d": "fdcnn.cu", "fc_bwd_b": "fdcnn.cu",
+             "conv_fwd": "fdcnn.cu", "conv_bwd": "fdcnn.cu", "step": "update.cu"}
+    path = os.path.join(ROOT, "paper_2205_05158_gb300", "csrc", files.get(stage, "api.cu"))
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def measured_traffic(stage: str, prec: str):
+    """DRAM bytes per launch of `stage` from a committed ncu summary, if it was taken
+    on the current source of that kernel (profiles/traffic.txt: stage precision
+    source-hash bytes-per-launch)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = source_hash(stage)
+    for line in open(path):
+        t = line.split()
+        if len(t) >= 4 and not line.startswith("#") and t[0] == stage and t[1] == prec and t[2] == h:
+            return float(t[3])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                sm.append(float(t[1]))
+                mx = max(mx, float(t[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_step(cfg, w, n_sym: int):
+    """ZF of the first realisation + one update iteration over n_sym symbols."""
+    import oracle
+    d = oracle.dims_from_config(cfg, w.P_T)
+    W, al = oracle.precode(d, w.H[:1])
+    th, met = oracle.update(d, w.s[:n_sym], w.H[:1], W, al, w.pa, w.theta, LR, 1)
+    return met
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    cfg = synth.CONFIGS["cfg3"]
+    n = max(1, args.ref_sample)
+    w = synth.make_workload(cfg, S=cfg.S_per_real, fc_scale=0.05)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_step(cfg, w, n)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(cfg, w, n)
+        t.append(time.perf_counter() - t0)
+    sec = sum(t) / len(t)
+    value = n / sec
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation",
+                      "sample": f"{n} symbols per step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"ZF of one 1200-subcarrier realisation + forward, adjoint and GD step "
+                                      f"over {n} symbols"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2205_05158_gb300 as fd
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prec_name = args.precision or "fp32"
+    prec = {"fp32": fd.FDDPD_FP32, "bf16": fd.FDDPD_BF16, "fp16": fd.FDDPD_FP16}[prec_name]
+    cfg = synth.CONFIGS["cfg3"].with_(seed=rank, S=args.symbols)
+    S = cfg.S
+    w = synth.make_workload(cfg, fc_scale=0.05)
+    R = w.H.shape[0]
+    stream = torch.cuda.current_stream()
+    plan = fd.Plan.from_config(cfg, w.P_T, max_symbols=S, precision=prec, stream=stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s, H, pa, theta0 = dev(w.s), dev(w.H), dev(w.pa), dev(w.theta)
+    theta = theta0.clone()
+    W = torch.empty((R, cfg.N_d, cfg.M, cfg.K), dtype=torch.complex64, device="cuda")
+    al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
+    met = torch.zeros(5, dtype=torch.float64, device="cuda")
+
+    def step():
+        plan.precode(H, W, al)
+        plan.update(s, H, W, al, pa, theta, LR, 1, fd.FDDPD_GD, met)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile(True)
+    plan.profile_read()
+    launches0 = plan.launch_count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = plan.profile_read()
+    plan.profile(False)
+    launches = plan.launch_count - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * S / (ms / 1e3)
+
+    # forward-only (running mode) throughput on the same inputs, informational
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        plan.distort(s, H, W, al, pa, theta, None, met)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / args.steps
+    m = met.cpu().numpy()
+    evm_db = 10 * math.log10(m[1] / m[2])
+    acpr_db = 10 * math.log10(m[3] / m[4])
+
+    # roofline of the dominant stage
+    mp, src = peaks()
+    work = stage_work(cfg, S, prec_name)
+    stage, (tot_ms, cnt) = max(((k, v) for k, v in prof.items() if k in work and v[1] > 0), key=lambda kv: kv[1][0])
+    bound, amount = work[stage]
+    per_launch_ms = tot_ms / cnt
+    if bound == "hbm":
+        achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e9, mp["hbm_gbs"], "GB/s"
+        peak_src = f"{src} hbm_gbs (copy)"
+    elif bound == "tensor":
+        achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e12, mp["bf16_tflops_sustained"], "TFLOP/s"
+        peak_src = f"{src} bf16_tflops_sustained"
+    else:
+        clk_mhz = mp.get("sm_max_mhz", 2070.0)
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+        achieved, unit = amount / (per_launch_ms / 1e3) / 1e12, "TFLOP/s"
+        peak_src = f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz"
+    traffic = measured_traffic(stage, prec_name)
+    stages_out = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                  for k, v in prof.items() if v[1] > 0}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if prec_name == "fp32" else f"{prec_name}+f32",
+           "data": "synthetic",
+           "config": {"workload": "cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, "
+                                  "orders 1,3,5 taps 0..3, FD-CNN G=35 N_conv=2 K_C=3",
+                      "symbols_per_step": S, "realisations_per_step": R, "precision": prec_name,
+                      "step": "ZF + FD-CNN + precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
+                      "l2": "inputs larger than L2 (H 2.8 GB), no flush",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "roofline": {"kernel": stage, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                        "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                        "work_per_launch": amount},
+           "stages": stages_out,
+           "forward_only": {"value": world * S / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
+           "quality": {"evm_db": evm_db, "acpr_db": acpr_db},
+           "gpu_launches": launches,
+           "clocks": clk}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    if not args.no_e2e:
+        hs = torch.from_numpy(w.s).pin_memory().numpy()
+        hH = torch.from_numpy(w.H).pin_memory().numpy()
+        hpa = torch.from_numpy(w.pa).pin_memory().numpy()
+        hth = torch.from_numpy(w.theta.copy()).pin_memory().numpy()
+        hmet = torch.zeros(5, dtype=torch.float64).pin_memory().numpy()
+        plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
+        sec = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([sec], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        out["e2e"] = {"value": world * S / sec, "unit": UNIT,
+                      "h2d_bytes_per_step": int(hs.nbytes + hH.nbytes + hpa.nbytes + hth.nbytes),
+                      "d2h_bytes_per_step": int(hth.nbytes + 5 * 8)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, w, args.cpu_sample, plan, s, H, W, al, pa, theta0)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, w, n_sym, plan, s, H, W, al, pa, theta0):
+    """Oracle (as it stands) on a bounded sample; also the EVM delta of the GPU on it."""
+    import numpy as np
+    import torch
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    met_o = oracle_step(cfg, w, n_sym)
+    sec = time.perf_counter() - t0
+    d = oracle.dims_from_config(cfg, w.P_T)
+    Wo, alo = oracle.precode(d, w.H[:1])
+    _, meto = oracle.distort(d, w.s[:n_sym], w.H[:1], Wo, alo, w.pa, w.theta)
+    met = torch.zeros(5, dtype=torch.float64, device="cuda")
+    plan.distort(s[:n_sym], H, W, al, pa, theta0, None, met, S=n_sym)
+    m = met.cpu().numpy()
+    return {"value": n_sym / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"ZF of one 1200-subcarrier realisation + forward, adjoint and GD step over {n_sym} symbols",
+            "seconds": sec,
+            "evm_db_oracle": 10 * math.log10(meto[1] / meto[2]),
+            "evm_db_gpu": 10 * math.log10(m[1] / m[2]),
+            "acpr_db_oracle": 10 * math.log10(meto[3] / meto[4]),
+            "acpr_db_gpu": 10 * math.log10(m[3] / m[4])}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

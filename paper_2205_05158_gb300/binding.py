@@ -22,7 +22,11 @@ FDDPD_GD, FDDPD_ADAM = 0, 1
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
-            "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer"]
+            "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
+            "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count"]
+
+STAGES = ["zf", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
+          "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
 
 
 class Dims(C.Structure):
@@ -78,8 +82,16 @@ def load(build_if_missing: bool = True):
     L.fddpd_backward.argtypes = [P, I, P, P, P, P, P, P, P, P]
     L.fddpd_update.argtypes = [P, I, P, P, P, P, P, P, C.c_float, I, I, P]
     L.fddpd_reset_optimizer.argtypes = [P]
+    L.fddpd_update_host.argtypes = [P, I, P, P, P, P, C.c_float, I, I, P]
+    L.fddpd_profile_enable.argtypes = [P, I]
+    L.fddpd_profile_read.argtypes = [P, P, P]
+    L.fddpd_stage_name.argtypes = [I]
+    L.fddpd_stage_name.restype = C.c_char_p
+    L.fddpd_launch_count.argtypes = [P]
+    L.fddpd_launch_count.restype = C.c_longlong
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
-              "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer"):
+              "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
+              "fddpd_profile_enable", "fddpd_profile_read"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -187,6 +199,38 @@ class Plan:
 
     def reset_optimizer(self):
         self._check(self._lib.fddpd_reset_optimizer(self._h))
+
+    def update_host(self, s, H, pa, theta, lr: float, iters: int = 1, optimizer: int = FDDPD_GD, metrics=None,
+                    S: Optional[int] = None):
+        """Training step from host numpy arrays (complex64 / float32, C-contiguous);
+        theta (and metrics, float64[5]) are updated in place."""
+        import numpy as np
+
+        def hp(a, dt):
+            if a is None:
+                return None
+            if not (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous):
+                raise TypeError(f"expected a C-contiguous {dt} numpy array")
+            return a.ctypes.data
+
+        S = s.shape[0] if S is None else S
+        self._check(self._lib.fddpd_update_host(self._h, S, hp(s, np.complex64), hp(H, np.complex64),
+                                                hp(pa, np.complex64), hp(theta, np.float32), float(lr), int(iters),
+                                                int(optimizer), hp(metrics, np.float64)))
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.fddpd_profile_enable(self._h, int(enable)))
+
+    def profile_read(self):
+        """{stage: (milliseconds, brackets)} since the last read (synchronises the stream)."""
+        ms = (C.c_double * len(STAGES))()
+        cnt = (C.c_longlong * len(STAGES))()
+        self._check(self._lib.fddpd_profile_read(self._h, ms, cnt))
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(len(STAGES))}
+
+    @property
+    def launch_count(self) -> int:
+        return self._lib.fddpd_launch_count(self._h)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

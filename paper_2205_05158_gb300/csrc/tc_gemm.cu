@@ -1,0 +1,340 @@
+// 5th-generation tensor-core GEMM for sm_103a: C[m][n] = sum_k A[m][k] B[n][k]
+// with 16-bit A, B (both K-major, row-major in global memory) and FP32 accumulation
+// in tensor memory.  Used for the FD-CNN dense layer (forward, data gradient and
+// weight gradient) in 16-bit plans.
+//
+// One CTA computes one 128 x BN output tile (optionally a K slice of it, split-K):
+//   warp 0 lane 0 : TMA producer, 128-byte-swizzled 128 x 64 / BN x 64 tiles into a
+//                   STAGES-deep shared-memory ring (mbarrier full / empty pairs);
+//   warp 1 lane 0 : issues tcgen05.mma (M = 128, N = BN, K = 16) into a TMEM
+//                   accumulator of BN columns, commits each stage back to its
+//                   producer barrier and the last one to `done`;
+//   warps 2..5    : epilogue, tcgen05.ld of the accumulator lanes of their quarter,
+//                   then a caller-supplied per-element functor.
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); a timeout sets the
+// error word, the waiting role stops, the MMA warp still drains its commits, and
+// TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+namespace fdk {
+namespace tc {
+
+constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+FD_D uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+FD_D unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+FD_D void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+FD_D void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+FD_D bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false (and *err set) on timeout.
+FD_D bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) {
+            atomicOr(err, 2);
+            return false;
+        }
+    }
+}
+
+FD_D void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+FD_D uint64_t smem_desc(const void *p) {
+    const uint64_t a = smem_u32(p);
+    uint64_t d = (a >> 4) & 0x3FFFull;
+    d |= 1ull << 16;                  // leading byte offset (unused with 128-byte swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32; // stride byte offset
+    d |= 1ull << 46;                  // version
+    d |= 2ull << 61;                  // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A/B type (0 = F16, 1 = BF16),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int ab_type, int M, int N) {
+    return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+FD_D void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+FD_D void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+FD_D void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+FD_D void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+FD_D void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct Smem {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = STAGES * STAGE + 1024;   // + alignment slack
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int BN, class Epi>
+__global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                          const __grid_constant__ CUtensorMap tb, int Mdim, int Ndim,
+                                                          int Kdim, int k_per_split, int ab_type, Epi epi, int *err) {
+    using L = Smem<BN>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * k_per_split;
+    const int kend = min(Kdim, kbeg + k_per_split);
+    const int nkb = (kend - kbeg + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(L::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t use = kb / STAGES;
+                if (kb >= STAGES && !mbar_wait(&empty[s], (use & 1) ^ 1, err)) break;
+                uint8_t *sa = base + s * L::STAGE;
+                uint8_t *sb = sa + L::A_BYTES;
+                mbar_expect_tx(&full[s], L::STAGE);
+                const int kx = kbeg + kb * BK;
+                tma_load_2d(sa, &ta, &full[s], kx, m0);
+                tma_load_2d(sb, &tb, &full[s], kx, n0);
+                ++issued;
+            }
+            // no copy may still be landing in shared memory when the CTA exits
+            for (int s = 0; s < STAGES && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
+                mbar_wait(&full[s], (uint32_t)(last / STAGES) & 1, err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(ab_type, BM, BN);
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t use = kb / STAGES;
+                if (!mbar_wait(&full[s], use & 1, err)) break;
+                fence_after();
+                const uint64_t ad = smem_desc(base + s * L::STAGE);
+                const uint64_t bd = smem_desc(base + s * L::STAGE + L::A_BYTES);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
+                mma_commit(&empty[s]);
+                ++issued;
+            }
+            mma_commit(&done);   // arrives once every MMA issued above has completed
+            (void)issued;
+        }
+    } else {
+        const bool ok = mbar_wait(&done, 0, err) && nkb > 0;
+        fence_after();
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+            if (ok && row < Mdim) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + c0 + j < Ndim) epi(row, n0 + c0 + j, v[j]);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map over a [rows][ld] 16-bit array whose first `cols` entries of each row are valid;
+// box = 64 x box_rows with 128-byte swizzle; out-of-range reads return zero.
+static cudaError_t make_map(CUtensorMap *map, const void *ptr, long rows, long cols, long ld, int box_rows, int ab_type) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * 2) & 15)) return cudaErrorMisalignedAddress;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, ab_type ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, class Epi>
+static cudaError_t launch(const GemmArgs &g, const Epi &epi, int *err, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+    CUtensorMap ta, tb;
+    cudaError_t e = make_map(&ta, g.A, g.M, g.K, g.lda, BM, g.ab_type);
+    if (e != cudaSuccess) return e;
+    e = make_map(&tb, g.B, g.N, g.K, g.ldb, BN, g.ab_type);
+    if (e != cudaSuccess) return e;
+    int splits = g.splits < 1 ? 1 : g.splits;
+    int kps = (g.K + splits - 1) / splits;
+    kps = (kps + BK - 1) / BK * BK;
+    splits = (g.K + kps - 1) / kps;          // every split gets at least one k-block
+    const int smem = Smem<BN>::BYTES;
+    e = cudaFuncSetAttribute(gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
+    gemm_kernel<BN, Epi><<<grid, THREADS, smem, st>>>(ta, tb, g.M, g.N, g.K, kps, g.ab_type, epi, err);
+    return cudaGetLastError();
+}
+
+// --- epilogues --------------------------------------------------------------
+struct EpiStore {          // C[m][n] = acc (plain GEMM, ldc)
+    float *C;
+    long ldc;
+    FD_D void operator()(int m, int n, float v) const { C[(long)m * ldc + n] = v; }
+};
+struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] + residual * s
+    float *st;
+    const float *s, *fb;
+    int Nd, residual;
+    FD_D void operator()(int m, int n, float v) const {
+        const long idx = (long)m * 2 * Nd + n;
+        st[idx] = v + fb[(n & 1) * Nd + (n >> 1)] + (residual ? s[idx] : 0.f);
+    }
+};
+struct EpiFcBwdData {      // gpre[m][f] = acc where act > 0
+    float *gpre;
+    const __nv_bfloat16 *act;
+    long ld_act;
+    int F;
+    FD_D void operator()(int m, int n, float v) const {
+        gpre[(long)m * F + n] = __bfloat162float(act[(long)m * ld_act + n]) > 0.f ? v : 0.f;
+    }
+};
+struct EpiFcBwdWeight {    // grad fc_w[pi(n')][f] += acc (split-K partial sums)
+    float *gfw;
+    int Nd, F;
+    FD_D void operator()(int m, int n, float v) const {
+        atomicAdd(gfw + (long)((m & 1) * Nd + (m >> 1)) * F + n, v);
+    }
+};
+
+}  // namespace tc
+
+cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st) {
+    return tc::launch<256>(g, tc::EpiStore{C, ldc}, err, st);
+}
+
+cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
+                          int *err, cudaStream_t st) {
+    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fb, Nd, residual}, err, st);
+}
+
+cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, const __nv_bfloat16 *act, long ld_act, int F, int *err,
+                                cudaStream_t st) {
+    return tc::launch<256>(g, tc::EpiFcBwdData{gpre, act, ld_act, F}, err, st);
+}
+
+cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, int *err, cudaStream_t st) {
+    return tc::launch<256>(g, tc::EpiFcBwdWeight{gfw, Nd, F}, err, st);
+}
+
+}  // namespace fdk

@@ -1,0 +1,42 @@
+// Tensor-core (tcgen05) GEMM launchers: C[m][n] = sum_k A[m][k] B[n][k], 16-bit operands,
+// both row-major with k contiguous (leading dimensions in elements, multiples of 8).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace fdk {
+
+struct GemmArgs {
+    const void *A;   // [M][lda]
+    const void *B;   // [N][ldb]
+    int M, N, K;
+    long lda, ldb;
+    int ab_type;     // 1 = BF16, 0 = FP16
+    int splits;      // K slices (partial sums are added by the epilogue)
+};
+
+cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st);
+cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
+                          int *err, cudaStream_t st);
+cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, const __nv_bfloat16 *act, long ld_act, int F, int *err,
+                                cudaStream_t st);
+cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, int *err, cudaStream_t st);
+
+// 16-bit operand preparation (pack16.cu)
+cudaError_t conv_forward_bf16(const struct Geo &g, int S, const float2 *s, const float *theta, __nv_bfloat16 *act,
+                              long ld, cudaStream_t st);
+// fc_w rows in interleaved order: out[n'][f] = bf16(fc_w[pi(n')][f]), ld_out
+cudaError_t pack_fcw(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st);
+// transposed: out[f][n'] = bf16(fc_w[pi(n')][f]), ld_out
+cudaError_t pack_fcw_t(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st);
+// out[r][c] = bf16(in[r][c]) for a float matrix
+cudaError_t to_bf16(const float *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
+                    cudaStream_t st);
+// out[c][r] = in[r][c] (float or bf16 input)
+cudaError_t transpose_bf16(const float *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
+                           cudaStream_t st);
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
+                           cudaStream_t st);
+
+}  // namespace fdk
