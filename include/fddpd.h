@@ -183,6 +183,20 @@ const char *fddpd_stage_name(int stage);
 /* Number of kernels this plan has launched since it was created. */
 long long fddpd_launch_count(const fddpd_plan *plan);
 
+/* Synchronise the plan's stream and report device-side failures recorded since the
+ * last report: FDDPD_ERR_TIMEOUT when a bounded wait inside a tensor-core kernel gave
+ * up (its results are then invalid).  Clears the record.                           */
+int fddpd_sync(fddpd_plan *plan);
+
+/* The library's tensor-core GEMM on its own (used to validate it):
+ *   C[m][n] (+)= sum_k A[m][k] B[n][k],  A [M][lda], B [N][ldb] 16-bit (ab_type 1 = BF16,
+ *   0 = FP16), K-major, lda / ldb multiples of 8, 16-byte aligned; C [M][ldc] FP32.
+ * splits > 1 slices K and adds the partial sums into C (which the caller zeroes).
+ * Runs on `stream` and synchronises it.  Errors: ARG, LAYOUT, CUDA, TIMEOUT.  No
+ * counterpart in the paper: a building block of the dense layer of Sec. IV-A.      */
+int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                  int ab_type, int splits, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

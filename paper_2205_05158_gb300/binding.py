@@ -23,7 +23,8 @@ FDDPD_GD, FDDPD_ADAM = 0, 1
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
-            "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count"]
+            "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
+            "fddpd_sync", "fddpd_tc_gemm"]
 
 STAGES = ["zf", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -89,9 +90,11 @@ def load(build_if_missing: bool = True):
     L.fddpd_stage_name.restype = C.c_char_p
     L.fddpd_launch_count.argtypes = [P]
     L.fddpd_launch_count.restype = C.c_longlong
+    L.fddpd_sync.argtypes = [P]
+    L.fddpd_tc_gemm.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
-              "fddpd_profile_enable", "fddpd_profile_read"):
+              "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -231,6 +234,27 @@ class Plan:
     @property
     def launch_count(self) -> int:
         return self._lib.fddpd_launch_count(self._h)
+
+    def sync(self):
+        """Synchronise the plan's stream; raises on a recorded device-side timeout."""
+        self._check(self._lib.fddpd_sync(self._h))
+
+
+def tc_gemm(A, B, C, splits: int = 1, stream=None):
+    """C (+)= A @ B.T on the tensor cores; A [M][lda], B [N][ldb] bf16/fp16 CUDA tensors
+    (row strides multiples of 8), C [M][ldc] float32."""
+    import torch
+    L = load()
+    if A.dtype != B.dtype or A.dtype not in (torch.bfloat16, torch.float16):
+        raise TypeError("A and B must both be bfloat16 or both float16")
+    if C.dtype != torch.float32:
+        raise TypeError("C must be float32")
+    M, K = A.shape
+    N = B.shape[0]
+    rc = L.fddpd_tc_gemm(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), C.data_ptr(), C.stride(0),
+                         1 if A.dtype == torch.bfloat16 else 0, splits, _stream_ptr(stream))
+    if rc:
+        raise FddpdError(rc, L.fddpd_last_error(None).decode())
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfddpd.so")
-SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "fftpa.cu", "update.cu"]
+SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "fftpa.cu", "update.cu", "tc_gemm.cu", "pack16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -52,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp], capture_output=True, text=True)
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp], capture_output=True,
+                       text=True)
     if r.returncode:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

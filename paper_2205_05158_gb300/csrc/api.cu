@@ -8,6 +8,7 @@
 
 #include "fddpd.h"
 #include "kernels.h"
+#include "tc_gemm.h"
 
 using fdk::Geo;
 
@@ -23,8 +24,12 @@ struct fddpd_plan {
     c32 *st, *gy, *gst, *xh, *Xpa, *tw;
     float *act, *gpre, *partials, *grad, *adam_m, *adam_v;
     double *met;
-    int *status;
+    int *status;        // [0] singular subcarriers of the last precode, [1] sticky device timeouts
     int *status_host;
+    // 16-bit plans: dense-layer operands (leading dimensions in elements)
+    bool p16;
+    long ldF, ld2N, ldC;
+    __nv_bfloat16 *act16, *actT16, *gd16, *gdT16, *fcw16, *fcwT16;
     long adam_t;
     // stage tracing
     int prof;
@@ -105,7 +110,6 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (dpd->K_S < 1 || dpd->K_S > dpd->G) return set_err(nullptr, FDDPD_ERR_ARG, "K_S=%d", dpd->K_S);
     if (dpd->N_conv < 1 || dpd->N_conv > 64) return set_err(nullptr, FDDPD_ERR_ARG, "N_conv=%d outside 1..64", dpd->N_conv);
     if (dpd->residual != 0 && dpd->residual != 1) return set_err(nullptr, FDDPD_ERR_ARG, "residual must be 0 or 1");
-    if (d->precision != FDDPD_FP32) return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "16-bit plans are not built in this library");
     return FDDPD_OK;
 }
 
@@ -156,7 +160,21 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
                  o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * g.F),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
-                 o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(sizeof(int));
+                 o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int));
+    p->p16 = d->precision != FDDPD_FP32;
+    auto r8 = [](long v) { return (v + 7) / 8 * 8; };
+    p->ldF = r8(g.F);
+    p->ld2N = r8(2L * g.N_d);
+    p->ldC = r8(cols);
+    size_t o_a16 = 0, o_aT = 0, o_g16 = 0, o_gT = 0, o_w16 = 0, o_wT = 0;
+    if (p->p16) {
+        o_a16 = take(2 * (size_t)cols * p->ldF);
+        o_aT = take(2 * (size_t)g.F * p->ldC);
+        o_g16 = take(2 * (size_t)cols * p->ld2N);
+        o_gT = take(2 * (size_t)2 * g.N_d * p->ldC);
+        o_w16 = take(2 * (size_t)2 * g.N_d * p->ldF);
+        o_wT = take(2 * (size_t)g.F * p->ld2N);
+    }
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
     if (e != cudaSuccess) {
@@ -170,9 +188,15 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->act = (float *)(b + o_act); p->gpre = (float *)(b + o_gpre); p->partials = (float *)(b + o_part);
     p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
     p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
-    e = cudaMallocHost(&p->status_host, sizeof(int));
+    if (p->p16) {
+        p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
+        p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
+        p->fcw16 = (__nv_bfloat16 *)(b + o_w16); p->fcwT16 = (__nv_bfloat16 *)(b + o_wT);
+    }
+    e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
     if (e == cudaSuccess) e = fdk::twiddles(g.N, p->tw, p->stream);
     p->launches = 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 2 * sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_m, 0, sizeof(float) * g.theta_len, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_v, 0, sizeof(float) * g.theta_len, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -227,7 +251,7 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
     FD_STAGE(p, FDDPD_STAGE_ZF, 1, fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status, st));
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FD_CK(p, cudaStreamSynchronize(st));
-    if (*p->status_host) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
+    if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
     return FDDPD_OK;
 }
 
@@ -248,8 +272,17 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
     const long cols = (long)S * g.K;
     const double inv_count = 1.0 / ((double)cols * g.N_d);
     FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
-    FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
-    FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
+    if (p->p16) {
+        FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, theta, p->act16, p->ldF, st));
+        FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, st));
+        const fdk::GemmArgs ga{p->act16, p->fcw16, (int)cols, 2 * g.N_d, g.F, p->ldF, p->ldF, 1, 1};
+        FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
+                 fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
+                                    theta + g.off_fb, g.N_d, g.residual, p->status + 1, st));
+    } else {
+        FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
+    }
     FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, fdk::bin_expand(g, fdk::PRECODE, S, W, alpha, p->st, p->xh, st));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1, fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1, fdk::bin_reduce(g, fdk::COMBINE, S, H, alpha, p->Xpa, y, s, gy, p->met, inv_count, st));
@@ -270,9 +303,25 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1, fdk::bin_reduce(g, fdk::ADJ_PRECODE, S, W, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, st));
     const float *gd = reinterpret_cast<const float *>(p->gst);
     FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
-    FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, st));
-    FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
-    FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, cols, gd, theta, p->act, p->gpre, st));
+    if (p->p16) {
+        const long W2 = 2L * g.N_d;
+        FD_STAGE(p, FDDPD_STAGE_PACK, 4,
+                 (fdk::to_bf16(gd, cols, W2, W2, p->gd16, p->ld2N, st) == cudaSuccess &&
+                  fdk::transpose_bf16(gd, cols, W2, W2, p->gdT16, p->ldC, st) == cudaSuccess &&
+                  fdk::transpose_bf16(p->act16, cols, g.F, p->ldF, p->actT16, p->ldC, st) == cudaSuccess)
+                     ? fdk::pack_fcw_t(g, theta, p->fcwT16, p->ld2N, st)
+                     : cudaGetLastError());
+        FD_CK(p, cudaMemsetAsync(grad + g.off_fw, 0, sizeof(float) * W2 * g.F, st));
+        const fdk::GemmArgs gw{p->gdT16, p->actT16, (int)W2, g.F, cols, p->ldC, p->ldC, 1, 4};
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::tc_fc_backward_weight(gw, grad + g.off_fw, g.N_d, g.F, p->status + 1, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
+        const fdk::GemmArgs gdx{p->gd16, p->fcwT16, cols, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->act16, p->ldF, g.F, p->status + 1, st));
+    } else {
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, cols, gd, theta, p->act, p->gpre, st));
+    }
     FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, p->gpre, p->act, p->partials, st));
     FD_CK(p, fdk::conv_reduce(g, cols, p->partials, grad, st));
     return FDDPD_OK;
@@ -410,6 +459,38 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     if (rc) return rc;
     FD_CK(p, cudaMemcpyAsync(theta, p->htheta, n_th, cudaMemcpyDeviceToHost, st));
     if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    FD_CK(p, cudaStreamSynchronize(st));
+    return fddpd_sync(p);
+}
+
+extern "C" int fddpd_sync(fddpd_plan *p) {
+    if (!p) return FDDPD_ERR_ARG;
+    FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    FD_CK(p, cudaStreamSynchronize(p->stream));
+    if (p->status_host[1]) {
+        FD_CK(p, cudaMemsetAsync(p->status + 1, 0, sizeof(int), p->stream));
+        return set_err(p, FDDPD_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel timed out");
+    }
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                             int ab_type, int splits, void *stream) {
+    if (M < 0 || N < 0 || K < 0 || !A || !B || !C || lda < K || ldb < K || ldc < N || splits < 1 ||
+        (ab_type != 0 && ab_type != 1))
+        return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_tc_gemm: bad argument");
+    if ((lda % 8) || (ldb % 8) || !aligned(A, 16) || !aligned(B, 16) || !aligned(C, 4))
+        return set_err(nullptr, FDDPD_ERR_LAYOUT, "fddpd_tc_gemm: A/B need 16-byte rows and alignment");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    int herr = 0;
+    cudaError_t e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    const fdk::GemmArgs g{A, B, M, N, K, lda, ldb, ab_type, splits};
+    if (e == cudaSuccess) e = fdk::tc_gemm_store(g, C, ldc, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (err) cudaFree(err);
+    if (e != cudaSuccess) return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_tc_gemm: %s", cudaGetErrorString(e));
+    if (herr) return set_err(nullptr, FDDPD_ERR_TIMEOUT, "fddpd_tc_gemm: bounded wait timed out");
     return FDDPD_OK;
 }

@@ -291,6 +291,11 @@ struct EpiStore {          // C[m][n] = acc (plain GEMM, ldc)
     long ldc;
     FD_D void operator()(int m, int n, float v) const { C[(long)m * ldc + n] = v; }
 };
+struct EpiAdd {            // C[m][n] += acc (split-K partial sums)
+    float *C;
+    long ldc;
+    FD_D void operator()(int m, int n, float v) const { atomicAdd(C + (long)m * ldc + n, v); }
+};
 struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] + residual * s
     float *st;
     const float *s, *fb;
@@ -320,6 +325,7 @@ struct EpiFcBwdWeight {    // grad fc_w[pi(n')][f] += acc (split-K partial sums)
 }  // namespace tc
 
 cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st) {
+    if (g.splits > 1) return tc::launch<256>(g, tc::EpiAdd{C, ldc}, err, st);
     return tc::launch<256>(g, tc::EpiStore{C, ldc}, err, st);
 }
 

@@ -1,0 +1,40 @@
+"""16-bit plans (BF16 / FP16 operands on the tensor cores, FP32 accumulation, FFT and
+PA in FP32) against the FP64 oracle: EVM within 0.1 dB and ACPR within 0.2 dB;
+gradients within 2e-2 relative L2 (BF16 keeps 8 significant bits)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import Case, nmse, rel_l2, small_cfg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,mk", [
+    ("ragged", lambda p: Case(small_cfg(), fc_scale=0.3, precision=p)),
+    ("cfg2_28", lambda p: Case(synth.CONFIGS["cfg2"], S=28, fc_scale=0.2, precision=p)),
+    ("cfg3_28", lambda p: Case(synth.CONFIGS["cfg3"].with_(S=28), fc_scale=0.05, precision=p)),
+])
+def test_mixed_forward_quality(name, mk, prec):
+    c = mk(prec)
+    c.gpu_zf()
+    y, met = c.gpu_distort()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert abs(oracle.evm_db(met) - oracle.evm_db(meto)) <= 0.1
+    assert abs(oracle.acpr_db(met) - oracle.acpr_db(meto)) <= 0.2
+    assert nmse(y, yo) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+def test_mixed_backward(prec):
+    c = Case(small_cfg(), fc_scale=0.3, precision=prec)
+    c.use_oracle_zf_on_gpu()
+    g, met = c.gpu_backward()
+    c.plan.sync()
+    Wo, alo = c.oracle_zf()
+    go, meto = oracle.backward(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert rel_l2(g, go) <= 2e-2, rel_l2(g, go)
+    assert abs(met[0] - meto[0]) <= 1e-2 * meto[0]
