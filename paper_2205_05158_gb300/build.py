@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfddpd.so")
-SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "fftpa.cu", "update.cu", "tc_gemm.cu", "pack16.cu"]
+SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "fftpa.cu", "fftpa_small.cu", "fftpa_n10.cu",
+           "fftpa_n11.cu", "fftpa_n12.cu", "update.cu", "tc_gemm.cu", "pack16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -22,6 +22,7 @@ struct fddpd_plan {
     void *base;
     size_t bytes;
     c32 *st, *gy, *gst, *xh, *Xpa, *tw;
+    void *zf_scratch;
     float *act, *gpre, *partials, *grad, *adam_m, *adam_v;
     double *met;
     int *status;        // [0] singular subcarriers of the last precode, [1] sticky device timeouts
@@ -161,6 +162,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
                  o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int));
+    const size_t o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N_d));
     p->p16 = d->precision != FDDPD_FP32;
     auto r8 = [](long v) { return (v + 7) / 8 * 8; };
     p->ldF = r8(g.F);
@@ -188,13 +190,14 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->act = (float *)(b + o_act); p->gpre = (float *)(b + o_gpre); p->partials = (float *)(b + o_part);
     p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
     p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
+    p->zf_scratch = b + o_zf;
     if (p->p16) {
         p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
         p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
         p->fcw16 = (__nv_bfloat16 *)(b + o_w16); p->fcwT16 = (__nv_bfloat16 *)(b + o_wT);
     }
     e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
-    if (e == cudaSuccess) e = fdk::twiddles(g.N, p->tw, p->stream);
+    if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
     p->launches = 1;
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 2 * sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_m, 0, sizeof(float) * g.theta_len, p->stream);
@@ -248,7 +251,7 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
     if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     cudaStream_t st = p->stream;
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
-    FD_STAGE(p, FDDPD_STAGE_ZF, 1, fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status, st));
+    FD_STAGE(p, FDDPD_STAGE_ZF, 1, fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status, p->zf_scratch, st));
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FD_CK(p, cudaStreamSynchronize(st));
     if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");

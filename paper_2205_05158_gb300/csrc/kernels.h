@@ -21,7 +21,9 @@ struct Geo {
 };
 
 // zero-forcing precoder (Eq. 6): FP32 Gram, FP64 Cholesky + triangular inverse
-cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, cudaStream_t st);
+size_t zf_scratch_bytes(const Geo &g, long nbins);
+cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                     cudaStream_t st);
 
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
@@ -58,5 +60,6 @@ cudaError_t adam_step(long n, float *theta, const float *grad, float *m, float *
                       cudaStream_t st);
 cudaError_t finalize_metrics(double *metrics, double inv_count, cudaStream_t st);
 cudaError_t twiddles(int N, c32 *tw, cudaStream_t st);
+cudaError_t pass_twiddles(int log2N, c32 *tw, cudaStream_t st);
 
 }  // namespace fdk

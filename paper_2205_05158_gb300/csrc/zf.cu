@@ -2,155 +2,298 @@
 // normalisation alpha_k = sqrt(P_T / tr((H_k H_k^H)^{-1})), so that the precoded
 // vector alpha_k W_k s has E||.||^2 = P_T for unit-power symbols.
 //
-// One CTA per (realisation, data subcarrier):
-//   1. G = H H^H (lower triangle) from FP32 products and FP32 accumulation;
-//   2. Cholesky G = L L^H and the triangular inverse Y = L^{-1} in FP64 by one warp
-//      (lane i owns row i of L, then column i of Y); tr(G^{-1}) = ||Y||_F^2 in FP64;
-//   3. W^H = Y^H (Y H): Q = Y H and W[m][u] = sum_{i>=u} Y[i][u] conj(Q[i][m]) in FP32,
-//      one thread per antenna.
-// A non-positive pivot (relative to its diagonal) flags the subcarrier as singular:
-// its W and alpha are written as zero and the status word is set.
+// Three kernels over all (realisation, data subcarrier) pairs ("bins"):
+//   gram   : one warp per bin, G = H H^H from FP32 products and FP32 sums; each lane a
+//            4 x 2 block of G (6 shared loads per 8 complex multiply-adds).  The lower
+//            triangle goes to a scratch array laid out [bin / 32][entry][bin % 32].
+//   factor : one bin per LANE, so every FP64 instruction is a full-warp instruction:
+//            Cholesky G = L L^H (left-looking) and the in-place triangular inverse
+//            Y = L^{-1} in FP64; tr(G^{-1}) = ||Y||_F^2 in FP64.  1/sqrt(d) starts from
+//            the FP32 rsqrtf and takes two Newton-Raphson steps y <- y (3 - d y^2) / 2
+//            in FP64.  Y (FP32) and alpha go out; a pivot <= 1e-9 of its Gram diagonal
+//            marks the bin singular (alpha = 0, W = 0, status bit 0).
+//   apply  : one warp per bin, W^H = Y^H (Y H) in FP32 (one antenna per lane), staged
+//            through shared memory for coalesced stores.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace fdk {
 
-static constexpr int ZF_THREADS = 128;
+static constexpr int ZF_WARPS = 8;
 
-__host__ __device__ static inline size_t zf_align(size_t b) { return (b + 15) & ~size_t(15); }
+__host__ __device__ static inline size_t al16(size_t b) { return (b + 15) & ~size_t(15); }
+__host__ __device__ static inline int tri(int K) { return K * (K + 1) / 2; }
+FD_HD long soa(long b, int e, int T) { return (b >> 5) * (long)T * 32 + (long)e * 32 + (b & 31); }
 
-template <int KM>
-__global__ void __launch_bounds__(ZF_THREADS) zf_kernel(Geo g, const c32 *__restrict__ H, c32 *__restrict__ W,
-                                                        float *__restrict__ alpha, int *status) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int K = g.K, M = g.M, ld = M + 1;
-    const long b = blockIdx.x;
-    c32 *sH = reinterpret_cast<c32 *>(sm);
-    double2 *sG = reinterpret_cast<double2 *>(sm + zf_align(sizeof(c32) * K * ld));   // G, then Y = L^{-1}
-    double2 *sL = sG + K * K;
-    c32 *sY = reinterpret_cast<c32 *>(sL + K * K);
-    __shared__ int bad;
-    __shared__ double trace;
+size_t zf_scratch_bytes(const Geo &g, long nbins) {
+    const long nb32 = (nbins + 31) / 32 * 32;
+    return 2 * al16(sizeof(c32) * (size_t)nb32 * tri(g.K)) + 256;
+}
 
-    const c32 *Hb = H + b * K * M;
-    for (int idx = threadIdx.x; idx < K * M; idx += blockDim.x) sH[(idx / M) * ld + idx % M] = Hb[idx];
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-
-    for (int p = threadIdx.x; p < K * K; p += blockDim.x) {
-        const int i = p / K, j = p % K;
-        if (j > i) continue;
-        c32 acc = make_float2(0.f, 0.f);
-        const c32 *hi = sH + i * ld, *hj = sH + j * ld;
-        for (int m = 0; m < M; ++m) acc = cfma(hi[m], cconj(hj[m]), acc);
-        sG[i * K + j] = make_double2(acc.x, acc.y);
-    }
-    __syncthreads();
-
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int j = 0; j < K; ++j) {
-            if (lane == j) {
-                const double g0 = sG[j * K + j].x;
-                double d = g0;
-                for (int k = 0; k < j; ++k) {
-                    const double2 l = sL[j * K + k];
-                    d -= l.x * l.x + l.y * l.y;
-                }
-                if (!(d > 1e-9 * g0)) {
-                    bad = 1;
-                    d = 1.0;
-                }
-                sL[j * K + j] = make_double2(sqrt(d), 0.0);
-            }
-            __syncwarp();
-            if (lane > j && lane < K) {
-                double2 s = sG[lane * K + j];
-                for (int k = 0; k < j; ++k) {
-                    const double2 a = sL[lane * K + k], c = sL[j * K + k];   // s -= a conj(c)
-                    s.x -= a.x * c.x + a.y * c.y;
-                    s.y -= a.y * c.x - a.x * c.y;
-                }
-                const double inv = 1.0 / sL[j * K + j].x;
-                sL[lane * K + j] = make_double2(s.x * inv, s.y * inv);
-            }
-            __syncwarp();
+FD_D void load_h(const c32 *__restrict__ Hb, c32 *sH, int K, int M, int ld, bool vec4, int lane) {
+    if (vec4) {
+        const float4 *Hb4 = reinterpret_cast<const float4 *>(Hb);
+        for (int e = lane; e < K * M / 2; e += 32) {
+            const float4 v = Hb4[e];
+            const int idx = 2 * e, u = idx / M, m = idx % M;
+            sH[u * ld + m] = make_float2(v.x, v.y);
+            sH[u * ld + m + 1] = make_float2(v.z, v.w);
         }
-        // Y = L^{-1}: lane c solves L y = e_c; Y kept in sG (no longer needed)
-        double tr = 0.0;
-        if (lane < K) {
-            const int c = lane;
-            for (int i = 0; i < c; ++i) sG[i * K + c] = make_double2(0.0, 0.0);
-            const double y0 = 1.0 / sL[c * K + c].x;
-            sG[c * K + c] = make_double2(y0, 0.0);
-            tr = y0 * y0;
-            for (int i = c + 1; i < K; ++i) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int k = c; k < i; ++k) {
-                    const double2 a = sL[i * K + k], y = sG[k * K + c];
-                    s.x += a.x * y.x - a.y * y.y;
-                    s.y += a.x * y.y + a.y * y.x;
-                }
-                const double inv = -1.0 / sL[i * K + i].x;
-                const double2 yi = make_double2(s.x * inv, s.y * inv);
-                sG[i * K + c] = yi;
-                tr += yi.x * yi.x + yi.y * yi.y;
+    } else {
+        for (int e = lane; e < K * M; e += 32) sH[(e / M) * ld + e % M] = Hb[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * ZF_WARPS) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
+                                                                c32 *__restrict__ Gs) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int K = g.K, M = g.M, ld = M + 1, T = tri(K);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    c32 *sH = reinterpret_cast<c32 *>(sm) + (size_t)warp * K * ld;
+    const bool vec4 = !(M & 1) && !(reinterpret_cast<uintptr_t>(H) & 15);
+    const int nib = (K + 3) / 4, njb = (K + 1) / 2;
+    for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
+        load_h(H + b * K * M, sH, K, M, ld, vec4, lane);
+        __syncwarp();
+        for (int blk = lane; blk < nib * njb; blk += 32) {
+            const int i0 = (blk / njb) * 4, j0 = (blk % njb) * 2;
+            if (j0 > i0 + 3) continue;   // block entirely above the diagonal
+            const int ni = min(4, K - i0), nj = min(2, K - j0);
+            c32 acc[4][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
+            for (int m = 0; m < M; ++m) {
+                c32 hi[4], hj[2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) hi[a] = a < ni ? sH[(i0 + a) * ld + m] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) hj[c] = c < nj ? cconj(sH[(j0 + c) * ld + m]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) acc[a][c] = cfma(hi[a], hj[c], acc[a][c]);
             }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = i0 + a, j = j0 + c;
+                    if (a < ni && c < nj && j <= i) Gs[soa(b, tri(i) + j, T)] = acc[a][c];
+                }
         }
         __syncwarp();
-        tr = warp_sum(tr);
-        if (lane == 0) trace = tr;
-        for (int p = lane; p < K * K; p += 32) sY[p] = make_float2((float)sG[p].x, (float)sG[p].y);
     }
-    __syncthreads();
+}
 
-    const bool singular = bad != 0;
-    if (threadIdx.x == 0) {
-        alpha[b] = singular ? 0.0f : (float)sqrt(g.P_T / trace);
-        if (singular) atomicOr(status, 1);
+// ---------------------------------------------------------------------------
+FD_D double rsqrt_f64(double d) {
+    double y = (double)rsqrtf((float)d);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
+__global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const c32 *__restrict__ Gs,
+                                                       c32 *__restrict__ Ys, float *__restrict__ alpha, int *status) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int K = g.K, T = tri(K);
+    const int lane = threadIdx.x, NB = blockDim.x;          // NB bins per CTA, one per thread
+    double2 *A = reinterpret_cast<double2 *>(sm);          // [T][NB]: lower triangle, becomes L, then Y
+    double *inv = reinterpret_cast<double *>(A + (size_t)T * NB);   // [K][NB]
+    const long b = (long)blockIdx.x * NB + lane;
+    const bool live = b < nbins;
+    const long bb = live ? b : 0;
+    for (int e = 0; e < T; ++e) {
+        const c32 v = Gs[soa(bb, e, T)];
+        A[e * NB + lane] = make_double2(v.x, v.y);
     }
-    c32 *Wb = W + b * M * K;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        c32 q[KM];
-#pragma unroll
-        for (int i = 0; i < KM; ++i) {
-            c32 acc = make_float2(0.f, 0.f);
-            if (i < K) {
-#pragma unroll
-                for (int k = 0; k <= i; ++k) acc = cfma(sY[i * K + k], sH[k * ld + m], acc);
-            }
-            q[i] = acc;
+    bool bad = false;
+    // Cholesky, left-looking: column j from the columns left of it
+    for (int j = 0; j < K; ++j) {
+        const int dj = tri(j) + j;
+        double d = A[dj * NB + lane].x;
+        const double g0 = d;
+        for (int k = 0; k < j; ++k) {
+            const double2 l = A[(tri(j) + k) * NB + lane];
+            d -= l.x * l.x + l.y * l.y;
         }
-#pragma unroll
-        for (int u = 0; u < KM; ++u) {
-            if (u < K) {
-                c32 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = u; i < KM; ++i)
-                    if (i < K) acc = cfma(sY[i * K + u], cconj(q[i]), acc);
-                Wb[m * K + u] = singular ? make_float2(0.f, 0.f) : acc;
+        const bool ok = d > 1e-9 * g0;
+        bad |= !ok;
+        const double r = ok ? rsqrt_f64(d) : 1.0;
+        A[dj * NB + lane] = make_double2(ok ? d * r : 1.0, 0.0);
+        inv[j * NB + lane] = r;
+        for (int i = j + 1; i < K; ++i) {
+            double2 s = A[(tri(i) + j) * NB + lane];
+            for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
+                const double2 a = A[(tri(i) + k) * NB + lane], c = A[(tri(j) + k) * NB + lane];
+                s.x -= a.x * c.x + a.y * c.y;
+                s.y -= a.y * c.x - a.x * c.y;
             }
+            A[(tri(i) + j) * NB + lane] = make_double2(s.x * r, s.y * r);
+        }
+    }
+    // in-place inverse: for j = K-1..0, Y[j][j] = 1/L[j][j], and for i = K-1..j+1
+    // Y[i][j] = -(1/L[j][j]) sum_{k=j+1}^{i} Y[i][k] L[k][j]  (L[k][j], k <= i, not yet overwritten)
+    double tr = 0.0;
+    for (int j = K - 1; j >= 0; --j) {
+        const double r = inv[j * NB + lane];
+        for (int i = K - 1; i > j; --i) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int k = j + 1; k <= i; ++k) {
+                const double2 y = A[(tri(i) + k) * NB + lane], l = A[(tri(k) + j) * NB + lane];
+                s.x += y.x * l.x - y.y * l.y;
+                s.y += y.x * l.y + y.y * l.x;
+            }
+            const double2 v = make_double2(-s.x * r, -s.y * r);
+            A[(tri(i) + j) * NB + lane] = v;
+            tr += v.x * v.x + v.y * v.y;
+        }
+        A[(tri(j) + j) * NB + lane] = make_double2(r, 0.0);
+        tr += r * r;
+    }
+    if (live) {
+        for (int e = 0; e < T; ++e) {
+            const double2 v = A[e * NB + lane];
+            Ys[soa(b, e, T)] = make_float2((float)v.x, (float)v.y);
+        }
+        alpha[b] = bad ? 0.0f : (float)sqrt(g.P_T / tr);
+    }
+    if (live && bad) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+template <int KM>
+__global__ void __launch_bounds__(32 * ZF_WARPS) zf_apply_kernel(Geo g, long nbins, const c32 *__restrict__ H,
+                                                                 const c32 *__restrict__ Ys,
+                                                                 const float *__restrict__ alpha,
+                                                                 c32 *__restrict__ W) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int K = g.K, M = g.M, ld = M + 1, T = tri(K);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const size_t per_warp = al16(sizeof(c32) * K * ld) + al16(sizeof(c32) * K * K) + al16(sizeof(c32) * 32 * (K + 1));
+    unsigned char *base = sm + warp * per_warp;
+    c32 *sH = reinterpret_cast<c32 *>(base);
+    c32 *sY = reinterpret_cast<c32 *>(base + al16(sizeof(c32) * K * ld));
+    c32 *sW = reinterpret_cast<c32 *>(base + al16(sizeof(c32) * K * ld) + al16(sizeof(c32) * K * K));
+    const bool vec4 = !(M & 1) && !(reinterpret_cast<uintptr_t>(H) & 15);
+    for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
+        load_h(H + b * K * M, sH, K, M, ld, vec4, lane);
+        for (int p = lane; p < K * K; p += 32) {
+            const int i = p / K, k = p % K;
+            sY[p] = k <= i ? Ys[soa(b, tri(i) + k, T)] : make_float2(0.f, 0.f);
+        }
+        const bool bad = alpha[b] == 0.0f;
+        __syncwarp();
+        c32 *Wb = W + b * M * K;
+        for (int m0 = 0; m0 < M; m0 += 32) {
+            const int m = m0 + lane;
+            if (m < M) {
+                c32 q[KM];
+#pragma unroll
+                for (int i = 0; i < KM; ++i) {
+                    c32 acc = make_float2(0.f, 0.f);
+                    if (i < K) {
+#pragma unroll
+                        for (int k = 0; k <= i; ++k) acc = cfma(sY[i * K + k], sH[k * ld + m], acc);
+                    }
+                    q[i] = acc;
+                }
+#pragma unroll
+                for (int u = 0; u < KM; ++u) {
+                    if (u < K) {
+                        c32 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int i = u; i < KM; ++i)
+                            if (i < K) acc = cfma(sY[i * K + u], cconj(q[i]), acc);
+                        sW[lane * (K + 1) + u] = bad ? make_float2(0.f, 0.f) : acc;
+                    }
+                }
+            }
+            __syncwarp();
+            const int nm = min(32, M - m0);
+            for (int e = lane; e < nm * K; e += 32) Wb[(long)m0 * K + e] = sW[(e / K) * (K + 1) + e % K];
+            __syncwarp();
         }
     }
 }
 
-template <int KM>
-static cudaError_t launch_zf(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, cudaStream_t st) {
-    const size_t smem = zf_align(sizeof(c32) * g.K * (g.M + 1)) + 2 * sizeof(double2) * g.K * g.K +
-                        sizeof(c32) * g.K * g.K;
-    cudaError_t e = cudaFuncSetAttribute(zf_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <class Kern>
+static cudaError_t persistent_launch_dims(Kern k, int threads, size_t smem, long work_items, int items_per_cta,
+                                          long &blocks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long blocks = (long)R * g.N_d;
-    if (blocks == 0) return cudaSuccess;
-    zf_kernel<KM><<<(unsigned)blocks, ZF_THREADS, smem, st>>>(g, H, W, alpha, status);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return e;
+    blocks = (long)(per_sm > 0 ? per_sm : 1) * sm_count();
+    const long need = (work_items + items_per_cta - 1) / items_per_cta;
+    if (blocks > need) blocks = need;
+    return cudaSuccess;
+}
+
+template <int KM>
+static cudaError_t launch_apply(const Geo &g, long nbins, const c32 *H, const c32 *Ys, const float *alpha, c32 *W,
+                                cudaStream_t st) {
+    const size_t per_warp = al16(sizeof(c32) * g.K * (g.M + 1)) + al16(sizeof(c32) * g.K * g.K) +
+                            al16(sizeof(c32) * 32 * (g.K + 1));
+    int nw = (int)((200 * 1024) / per_warp);
+    nw = nw > ZF_WARPS ? ZF_WARPS : nw;
+    if (nw < 1) return cudaErrorInvalidConfiguration;
+    long blocks = 0;
+    cudaError_t e = persistent_launch_dims(zf_apply_kernel<KM>, 32 * nw, nw * per_warp, nbins, nw, blocks);
+    if (e != cudaSuccess) return e;
+    zf_apply_kernel<KM><<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Ys, alpha, W);
     return cudaGetLastError();
 }
 
-cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, cudaStream_t st) {
-    if (g.K <= 4) return launch_zf<4>(g, R, H, W, alpha, status, st);
-    if (g.K <= 8) return launch_zf<8>(g, R, H, W, alpha, status, st);
-    if (g.K <= 16) return launch_zf<16>(g, R, H, W, alpha, status, st);
-    return launch_zf<32>(g, R, H, W, alpha, status, st);
+cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                     cudaStream_t st) {
+    const long nbins = (long)R * g.N_d;
+    if (nbins == 0) return cudaSuccess;
+    const int T = tri(g.K);
+    const long nb32 = (nbins + 31) / 32 * 32;
+    c32 *Gs = reinterpret_cast<c32 *>(scratch);
+    c32 *Ys = reinterpret_cast<c32 *>(reinterpret_cast<char *>(scratch) + al16(sizeof(c32) * (size_t)nb32 * T));
+    // gram
+    {
+        const size_t per_warp = sizeof(c32) * g.K * (g.M + 1);
+        int nw = (int)((200 * 1024) / per_warp);
+        nw = nw > ZF_WARPS ? ZF_WARPS : nw;
+        if (nw < 1) return cudaErrorInvalidConfiguration;
+        long blocks = 0;
+        cudaError_t e = persistent_launch_dims(zf_gram_kernel, 32 * nw, nw * per_warp, nbins, nw, blocks);
+        if (e != cudaSuccess) return e;
+        zf_gram_kernel<<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Gs);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // factor
+    {
+        int NB = 32;
+        size_t smem = (sizeof(double2) * T + sizeof(double) * g.K) * NB;
+        if (smem > 200 * 1024) {
+            NB = 16;
+            smem = (sizeof(double2) * T + sizeof(double) * g.K) * NB;
+        }
+        cudaError_t e = cudaFuncSetAttribute(zf_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        zf_factor_kernel<<<(unsigned)((nbins + NB - 1) / NB), NB, smem, st>>>(g, nbins, Gs, Ys, alpha, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // apply
+    if (g.K <= 4) return launch_apply<4>(g, nbins, H, Ys, alpha, W, st);
+    if (g.K <= 8) return launch_apply<8>(g, nbins, H, Ys, alpha, W, st);
+    if (g.K <= 16) return launch_apply<16>(g, nbins, H, Ys, alpha, W, st);
+    return launch_apply<32>(g, nbins, H, Ys, alpha, W, st);
 }
 
 }  // namespace fdk

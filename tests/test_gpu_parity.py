@@ -14,6 +14,10 @@ from gpu_common import Case, dev, nmse, rel_l2, small_cfg, torch
 pytestmark = pytest.mark.gpu
 
 NMSE_FP32 = 1e-9
+# PA shapes beyond the compiled fast paths: odd orders with memory, even orders, order 7
+PA_13_MEM = {1: [1.0, 0.05 - 0.02j, 0.01, -0.004], 3: [-0.08 + 0.02j, 0.01j, -0.003, 0.001]}
+PA_EVEN = {1: [1.0, 0.03j], 2: [0.02 - 0.01j, 0.004], 3: [-0.06 + 0.02j, -0.002]}
+PA_1357 = {1: [1.0], 3: [-0.08 + 0.02j], 5: [-0.002 + 0.0005j], 7: [1e-4 - 2e-5j]}
 
 
 def _blocks(d, g):
@@ -59,6 +63,9 @@ FWD_CASES = [
     ("n4096_nd_full", lambda: Case(small_cfg(M=8, K=2, N=4096, N_d=4096, S=3, S_per_real=2, G=64, L_U=1, K_S=1),
                                    fc_scale=0.05)),
     ("n64_siso", lambda: Case(small_cfg(M=1, K=1, N=64, N_d=40, S=5, S_per_real=5, G=7, L_U=1, K_S=1), fc_scale=0.3)),
+    ("pa13_mem3", lambda: Case(small_cfg(N=512, pa_nominal=PA_13_MEM), fc_scale=0.3)),
+    ("pa_general_even", lambda: Case(small_cfg(N=128, N_d=100, G=10, pa_nominal=PA_EVEN), fc_scale=0.3)),
+    ("pa_general_1357", lambda: Case(small_cfg(N=2048, N_d=1200, M=12, G=35, pa_nominal=PA_1357), fc_scale=0.1)),
 ]
 
 
@@ -102,6 +109,10 @@ def test_linear_pa_is_identity():
 # --- adjoint -----------------------------------------------------------------------
 BWD_CASES = [
     ("cfg1", lambda: Case(synth.CONFIGS["cfg1"], fc_scale=0.3)),
+    ("pa13_mem3", lambda: Case(small_cfg(N=512, pa_nominal=PA_13_MEM), fc_scale=0.3)),
+    ("pa_general_even", lambda: Case(small_cfg(N=128, N_d=100, G=10, pa_nominal=PA_EVEN), fc_scale=0.3)),
+    ("n4096", lambda: Case(small_cfg(M=8, K=2, N=4096, N_d=2400, S=3, S_per_real=2, G=49, L_U=1, K_S=1),
+                           fc_scale=0.05)),
     ("ragged", lambda: Case(small_cfg(), fc_scale=0.3)),
     ("ragged_literal", lambda: Case(small_cfg(L_U=1, K_S=1), fc_scale=0.5, residual=0)),
     ("cfg2_14", lambda: Case(synth.CONFIGS["cfg2"], S=14, fc_scale=0.2)),
