@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfddpd.so")
-SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "fftpa.cu", "fftpa_small.cu", "fftpa_n10.cu",
-           "fftpa_n11.cu", "fftpa_n12.cu", "update.cu", "tc_gemm.cu", "pack16.cu"]
+SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "bingemm_f32.cu", "bingemm_bf16.cu", "bingemm_f16.cu",
+           "fftpa.cu", "fftpa_small.cu", "fftpa_n10.cu", "fftpa_n11.cu", "fftpa_n12.cu", "update.cu", "tc_gemm.cu",
+           "pack16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -50,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(SOURCES))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp], capture_output=True,

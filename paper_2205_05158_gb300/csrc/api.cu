@@ -31,6 +31,10 @@ struct fddpd_plan {
     bool p16;
     long ldF, ld2N, ldC;
     __nv_bfloat16 *act16, *actT16, *gd16, *gdT16, *fcw16, *fcwT16;
+    int kind16;                    // OUT_BF16 or OUT_F16: storage of the H / W copies
+    void *H16, *W16;               // [R_max][N_d][K][M] and [R_max][N_d][M][K]
+    const void *pk_H, *pk_W;       // the FP32 arrays the copies were made from
+    int pk_R;
     long adam_t;
     // stage tracing
     int prof;
@@ -177,6 +181,11 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_w16 = take(2 * (size_t)2 * g.N_d * p->ldF);
         o_wT = take(2 * (size_t)g.F * p->ld2N);
     }
+    size_t o_h16 = 0, o_wq16 = 0;
+    if (p->p16) {
+        o_h16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
+        o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
+    }
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
     if (e != cudaSuccess) {
@@ -195,6 +204,9 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
         p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
         p->fcw16 = (__nv_bfloat16 *)(b + o_w16); p->fcwT16 = (__nv_bfloat16 *)(b + o_wT);
+        p->H16 = b + o_h16;
+        p->W16 = b + o_wq16;
+        p->kind16 = d->precision == FDDPD_FP16 ? fdk::OUT_F16 : fdk::OUT_BF16;
     }
     e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
     if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
@@ -251,7 +263,14 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
     if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     cudaStream_t st = p->stream;
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
-    FD_STAGE(p, FDDPD_STAGE_ZF, 1, fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status, p->zf_scratch, st));
+    FD_STAGE(p, FDDPD_STAGE_ZF, 3,
+             fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status,
+                           p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr, p->kind16, st));
+    if (p->p16) {
+        p->pk_H = H;
+        p->pk_W = W;
+        p->pk_R = R;
+    }
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FD_CK(p, cudaStreamSynchronize(st));
     if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
@@ -267,6 +286,33 @@ static int check_chain(fddpd_plan *p, int S, const void *s, const void *H, const
     return FDDPD_OK;
 }
 
+// Precode / combine operands: FP32 H and W, or the plan's 16-bit copies (made by
+// fddpd_precode, or here when the caller passes arrays they were not made from).
+struct BinOps {
+    const void *H, *W;
+    int kind;
+};
+static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps &o) {
+    if (!p->p16) {
+        o = BinOps{H, W, fdk::OUT_F32};
+        return FDDPD_OK;
+    }
+    const Geo &g = p->g;
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    if (p->pk_H != H || p->pk_W != W || p->pk_R < R) {
+        const long n = (long)R * g.N_d * g.K * g.M;
+        FD_STAGE(p, FDDPD_STAGE_PACK, 2,
+                 fdk::to_16bit(n, H, p->H16, p->kind16, p->stream) == cudaSuccess
+                     ? fdk::to_16bit(n, W, p->W16, p->kind16, p->stream)
+                     : cudaGetLastError());
+        p->pk_H = H;
+        p->pk_W = W;
+        p->pk_R = R;
+    }
+    o = BinOps{p->H16, p->W16, p->kind16};
+    return FDDPD_OK;
+}
+
 // Forward chain; gy (loss gradient at y) is written when non-null.
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
                        const c32 *pa, const float *theta, c32 *y, c32 *gy) {
@@ -274,6 +320,9 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
     cudaStream_t st = p->stream;
     const long cols = (long)S * g.K;
     const double inv_count = 1.0 / ((double)cols * g.N_d);
+    BinOps ops;
+    int rc0 = bin_operands(p, S, H, W, ops);
+    if (rc0) return rc0;
     FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
     if (p->p16) {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, theta, p->act16, p->ldF, st));
@@ -286,9 +335,10 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
     }
-    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, fdk::bin_expand(g, fdk::PRECODE, S, W, alpha, p->st, p->xh, st));
+    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, fdk::bin_expand(g, fdk::PRECODE, S, ops.W, ops.kind, alpha, p->st, p->xh, st));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1, fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, st));
-    FD_STAGE(p, FDDPD_STAGE_COMBINE, 1, fdk::bin_reduce(g, fdk::COMBINE, S, H, alpha, p->Xpa, y, s, gy, p->met, inv_count, st));
+    FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
+             fdk::bin_reduce(g, fdk::COMBINE, S, ops.H, ops.kind, alpha, p->Xpa, y, s, gy, p->met, inv_count, st));
     FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
     p->launches += 1;
     return FDDPD_OK;
@@ -301,9 +351,15 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     const int cols = S * g.K;
     int rc = run_forward(p, S, s, H, W, alpha, pa, theta, nullptr, p->gy);
     if (rc) return rc;
-    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, fdk::bin_expand(g, fdk::ADJ_COMBINE, S, H, alpha, p->gy, p->Xpa, st));
+    BinOps ops;
+    rc = bin_operands(p, S, H, W, ops);
+    if (rc) return rc;
+    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1,
+             fdk::bin_expand(g, fdk::ADJ_COMBINE, S, ops.H, ops.kind, alpha, p->gy, p->Xpa, st));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1, fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, st));
-    FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1, fdk::bin_reduce(g, fdk::ADJ_PRECODE, S, W, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, st));
+    FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
+             fdk::bin_reduce(g, fdk::ADJ_PRECODE, S, ops.W, ops.kind, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr,
+                             0.0, st));
     const float *gd = reinterpret_cast<const float *>(p->gst);
     FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {

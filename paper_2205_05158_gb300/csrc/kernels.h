@@ -22,8 +22,9 @@ struct Geo {
 
 // zero-forcing precoder (Eq. 6): FP32 Gram, FP64 Cholesky + triangular inverse
 size_t zf_scratch_bytes(const Geo &g, long nbins);
+// H16 / W16 (optional, kind OUT_BF16 / OUT_F16): 16-bit copies of H and W written on the way
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     cudaStream_t st);
+                     void *H16, void *W16, int kind, cudaStream_t st);
 
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
@@ -42,10 +43,12 @@ cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, cons
 
 // per-subcarrier complex contractions (FP32 operands)
 enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3 };
-cudaError_t bin_expand(const Geo &g, int mode, int S, const c32 *A, const float *alpha, const c32 *B, c32 *out,
-                       cudaStream_t st);
-cudaError_t bin_reduce(const Geo &g, int mode, int S, const c32 *A, const float *alpha, const c32 *B, c32 *out,
-                       const c32 *s_ref, c32 *gy, double *metrics, double inv_count, cudaStream_t st);
+// A is FP32 (a_kind OUT_F32) or the 16-bit copy (OUT_BF16 / OUT_F16) of W or H
+cudaError_t bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                       c32 *out, cudaStream_t st);
+cudaError_t bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                       c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, cudaStream_t st);
+cudaError_t to_16bit(long n, const c32 *in, void *out, int kind, cudaStream_t st);
 
 // OFDM + PA rows
 size_t fftpa_smem_bytes(const Geo &g, bool adjoint);

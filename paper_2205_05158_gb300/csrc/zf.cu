@@ -45,8 +45,9 @@ FD_D void load_h(const c32 *__restrict__ Hb, c32 *sH, int K, int M, int ld, bool
 }
 
 // ---------------------------------------------------------------------------
+template <typename T16>
 __global__ void __launch_bounds__(32 * ZF_WARPS) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
-                                                                c32 *__restrict__ Gs) {
+                                                                c32 *__restrict__ Gs, T16 *__restrict__ H16) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int K = g.K, M = g.M, ld = M + 1, T = tri(K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -56,6 +57,8 @@ __global__ void __launch_bounds__(32 * ZF_WARPS) zf_gram_kernel(Geo g, long nbin
     for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
         load_h(H + b * K * M, sH, K, M, ld, vec4, lane);
         __syncwarp();
+        if (H16)
+            for (int e = lane; e < K * M; e += 32) H16[b * K * M + e] = Operand<T16>::from(sH[(e / M) * ld + e % M]);
         for (int blk = lane; blk < nib * njb; blk += 32) {
             const int i0 = (blk / njb) * 4, j0 = (blk % njb) * 2;
             if (j0 > i0 + 3) continue;   // block entirely above the diagonal
@@ -116,7 +119,8 @@ __global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const 
         const double g0 = d;
         for (int k = 0; k < j; ++k) {
             const double2 l = A[(tri(j) + k) * NB + lane];
-            d -= l.x * l.x + l.y * l.y;
+            d = fma(-l.x, l.x, d);
+            d = fma(-l.y, l.y, d);
         }
         const bool ok = d > 1e-9 * g0;
         bad |= !ok;
@@ -127,8 +131,10 @@ __global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const 
             double2 s = A[(tri(i) + j) * NB + lane];
             for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
                 const double2 a = A[(tri(i) + k) * NB + lane], c = A[(tri(j) + k) * NB + lane];
-                s.x -= a.x * c.x + a.y * c.y;
-                s.y -= a.y * c.x - a.x * c.y;
+                s.x = fma(-a.x, c.x, s.x);
+                s.x = fma(-a.y, c.y, s.x);
+                s.y = fma(-a.y, c.x, s.y);
+                s.y = fma(a.x, c.y, s.y);
             }
             A[(tri(i) + j) * NB + lane] = make_double2(s.x * r, s.y * r);
         }
@@ -142,15 +148,18 @@ __global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const 
             double2 s = make_double2(0.0, 0.0);
             for (int k = j + 1; k <= i; ++k) {
                 const double2 y = A[(tri(i) + k) * NB + lane], l = A[(tri(k) + j) * NB + lane];
-                s.x += y.x * l.x - y.y * l.y;
-                s.y += y.x * l.y + y.y * l.x;
+                s.x = fma(y.x, l.x, s.x);
+                s.x = fma(-y.y, l.y, s.x);
+                s.y = fma(y.x, l.y, s.y);
+                s.y = fma(y.y, l.x, s.y);
             }
             const double2 v = make_double2(-s.x * r, -s.y * r);
             A[(tri(i) + j) * NB + lane] = v;
-            tr += v.x * v.x + v.y * v.y;
+            tr = fma(v.x, v.x, tr);
+            tr = fma(v.y, v.y, tr);
         }
         A[(tri(j) + j) * NB + lane] = make_double2(r, 0.0);
-        tr += r * r;
+        tr = fma(r, r, tr);
     }
     if (live) {
         for (int e = 0; e < T; ++e) {
@@ -163,41 +172,42 @@ __global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const 
 }
 
 // ---------------------------------------------------------------------------
-template <int KM>
-__global__ void __launch_bounds__(32 * ZF_WARPS) zf_apply_kernel(Geo g, long nbins, const c32 *__restrict__ H,
+template <int KM, typename T16>
+__global__ void __launch_bounds__(32 * ZF_WARPS, 2) zf_apply_kernel(Geo g, long nbins, const c32 *__restrict__ H,
                                                                  const c32 *__restrict__ Ys,
                                                                  const float *__restrict__ alpha,
-                                                                 c32 *__restrict__ W) {
+                                                                 c32 *__restrict__ W, T16 *__restrict__ W16) {
     extern __shared__ __align__(16) unsigned char sm[];
-    const int K = g.K, M = g.M, ld = M + 1, T = tri(K);
+    const int K = g.K, M = g.M, T = tri(K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const size_t per_warp = al16(sizeof(c32) * K * ld) + al16(sizeof(c32) * K * K) + al16(sizeof(c32) * 32 * (K + 1));
+    const size_t per_warp = al16(sizeof(c32) * K * K) + al16(sizeof(c32) * 32 * (K + 1));
     unsigned char *base = sm + warp * per_warp;
-    c32 *sH = reinterpret_cast<c32 *>(base);
-    c32 *sY = reinterpret_cast<c32 *>(base + al16(sizeof(c32) * K * ld));
-    c32 *sW = reinterpret_cast<c32 *>(base + al16(sizeof(c32) * K * ld) + al16(sizeof(c32) * K * K));
-    const bool vec4 = !(M & 1) && !(reinterpret_cast<uintptr_t>(H) & 15);
+    c32 *sY = reinterpret_cast<c32 *>(base);
+    c32 *sW = reinterpret_cast<c32 *>(base + al16(sizeof(c32) * K * K));
     for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
-        load_h(H + b * K * M, sH, K, M, ld, vec4, lane);
         for (int p = lane; p < K * K; p += 32) {
             const int i = p / K, k = p % K;
             sY[p] = k <= i ? Ys[soa(b, tri(i) + k, T)] : make_float2(0.f, 0.f);
         }
         const bool bad = alpha[b] == 0.0f;
         __syncwarp();
+        const c32 *Hb = H + b * K * M;
         c32 *Wb = W + b * M * K;
         for (int m0 = 0; m0 < M; m0 += 32) {
             const int m = m0 + lane;
             if (m < M) {
+                // h = H[:, m], then in place q = Y h (descending, q[i] needs h[k <= i])
                 c32 q[KM];
 #pragma unroll
-                for (int i = 0; i < KM; ++i) {
-                    c32 acc = make_float2(0.f, 0.f);
-                    if (i < K) {
+                for (int k = 0; k < KM; ++k) q[k] = k < K ? Hb[(long)k * M + m] : make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int k = 0; k <= i; ++k) acc = cfma(sY[i * K + k], sH[k * ld + m], acc);
+                for (int i = KM - 1; i >= 0; --i) {
+                    if (i < K) {
+                        c32 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k <= i; ++k) acc = cfma(sY[i * K + k], q[k], acc);
+                        q[i] = acc;
                     }
-                    q[i] = acc;
                 }
 #pragma unroll
                 for (int u = 0; u < KM; ++u) {
@@ -212,7 +222,11 @@ __global__ void __launch_bounds__(32 * ZF_WARPS) zf_apply_kernel(Geo g, long nbi
             }
             __syncwarp();
             const int nm = min(32, M - m0);
-            for (int e = lane; e < nm * K; e += 32) Wb[(long)m0 * K + e] = sW[(e / K) * (K + 1) + e % K];
+            for (int e = lane; e < nm * K; e += 32) {
+                const c32 w = sW[(e / K) * (K + 1) + e % K];
+                Wb[(long)m0 * K + e] = w;
+                if (W16) W16[b * M * K + (long)m0 * K + e] = Operand<T16>::from(w);
+            }
             __syncwarp();
         }
     }
@@ -239,23 +253,23 @@ static cudaError_t persistent_launch_dims(Kern k, int threads, size_t smem, long
     return cudaSuccess;
 }
 
-template <int KM>
+template <int KM, typename T16>
 static cudaError_t launch_apply(const Geo &g, long nbins, const c32 *H, const c32 *Ys, const float *alpha, c32 *W,
-                                cudaStream_t st) {
-    const size_t per_warp = al16(sizeof(c32) * g.K * (g.M + 1)) + al16(sizeof(c32) * g.K * g.K) +
-                            al16(sizeof(c32) * 32 * (g.K + 1));
+                                T16 *W16, cudaStream_t st) {
+    const size_t per_warp = al16(sizeof(c32) * g.K * g.K) + al16(sizeof(c32) * 32 * (g.K + 1));
     int nw = (int)((200 * 1024) / per_warp);
     nw = nw > ZF_WARPS ? ZF_WARPS : nw;
     if (nw < 1) return cudaErrorInvalidConfiguration;
     long blocks = 0;
-    cudaError_t e = persistent_launch_dims(zf_apply_kernel<KM>, 32 * nw, nw * per_warp, nbins, nw, blocks);
+    cudaError_t e = persistent_launch_dims(zf_apply_kernel<KM, T16>, 32 * nw, nw * per_warp, nbins, nw, blocks);
     if (e != cudaSuccess) return e;
-    zf_apply_kernel<KM><<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Ys, alpha, W);
+    zf_apply_kernel<KM, T16><<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Ys, alpha, W, W16);
     return cudaGetLastError();
 }
 
-cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     cudaStream_t st) {
+template <typename T16>
+static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                              T16 *H16, T16 *W16, cudaStream_t st) {
     const long nbins = (long)R * g.N_d;
     if (nbins == 0) return cudaSuccess;
     const int T = tri(g.K);
@@ -269,9 +283,9 @@ cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, in
         nw = nw > ZF_WARPS ? ZF_WARPS : nw;
         if (nw < 1) return cudaErrorInvalidConfiguration;
         long blocks = 0;
-        cudaError_t e = persistent_launch_dims(zf_gram_kernel, 32 * nw, nw * per_warp, nbins, nw, blocks);
+        cudaError_t e = persistent_launch_dims(zf_gram_kernel<T16>, 32 * nw, nw * per_warp, nbins, nw, blocks);
         if (e != cudaSuccess) return e;
-        zf_gram_kernel<<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Gs);
+        zf_gram_kernel<T16><<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Gs, H16);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -290,10 +304,16 @@ cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, in
         if (e != cudaSuccess) return e;
     }
     // apply
-    if (g.K <= 4) return launch_apply<4>(g, nbins, H, Ys, alpha, W, st);
-    if (g.K <= 8) return launch_apply<8>(g, nbins, H, Ys, alpha, W, st);
-    if (g.K <= 16) return launch_apply<16>(g, nbins, H, Ys, alpha, W, st);
-    return launch_apply<32>(g, nbins, H, Ys, alpha, W, st);
+    if (g.K <= 4) return launch_apply<4>(g, nbins, H, Ys, alpha, W, W16, st);
+    if (g.K <= 8) return launch_apply<8>(g, nbins, H, Ys, alpha, W, W16, st);
+    if (g.K <= 16) return launch_apply<16>(g, nbins, H, Ys, alpha, W, W16, st);
+    return launch_apply<32>(g, nbins, H, Ys, alpha, W, W16, st);
+}
+
+cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                     void *H16, void *W16, int kind, cudaStream_t st) {
+    if (kind == OUT_F16) return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, st);
+    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, st);
 }
 
 }  // namespace fdk
