@@ -17,122 +17,215 @@
 namespace fdk {
 
 // ---------------------------------------------------------------------------
-// conv + ReLU forward: one CTA per (symbol, user) column
+// conv + ReLU forward and the conv parameter gradient.  The input grids sit in
+// shared memory zero padded to Gp = (Go - 1) K_S + K_C per side (data at offset pad),
+// so no tap needs a bounds test; KC > 0 fixes the kernel size at compile time.
 // ---------------------------------------------------------------------------
-FD_D void load_grid(const Geo &g, const c32 *s, long t, int u, float *X) {
-    const int GG = g.G * g.G;
+FD_HD int padded_side(const Geo &g) { return (g.Go - 1) * g.K_S + g.K_C; }
+
+FD_D void load_padded(const Geo &g, const c32 *s, long t, int u, float *Xp) {
+    const int Gp = padded_side(g), GpGp = Gp * Gp;
+    for (int idx = threadIdx.x; idx < g.Cin * GpGp; idx += blockDim.x) Xp[idx] = 0.f;
+    __syncthreads();
     for (int l = 0; l < g.L_U; ++l) {
         const int v = (u + l) % g.K;
         const c32 *sv = s + (t * g.K + v) * g.N_d;
-        for (int idx = threadIdx.x; idx < GG; idx += blockDim.x) {
-            const c32 val = idx < g.N_d ? sv[idx] : make_float2(0.f, 0.f);
-            X[(2 * l) * GG + idx] = val.x;
-            X[(2 * l + 1) * GG + idx] = val.y;
+        for (int idx = threadIdx.x; idx < g.N_d; idx += blockDim.x) {
+            const c32 val = sv[idx];
+            const int r = idx / g.G + g.pad, q = idx % g.G + g.pad;
+            Xp[(2 * l) * GpGp + r * Gp + q] = val.x;
+            Xp[(2 * l + 1) * GpGp + r * Gp + q] = val.y;
         }
     }
 }
 
-__global__ void conv_fwd_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ theta,
-                                float *__restrict__ act) {
-    extern __shared__ float smf[];
-    float *X = smf;                                  // Cin * G * G
-    float *w = X + g.Cin * g.G * g.G;                // n_convw + N_conv
-    const long col = blockIdx.x;
-    const long t = col / g.K;
-    const int u = (int)(col % g.K);
-    for (int i = threadIdx.x; i < g.n_convw + g.N_conv; i += blockDim.x) w[i] = theta[i];
-    load_grid(g, s, t, u, X);
-    __syncthreads();
-    const int GoGo = g.Go * g.Go, KC = g.K_C;
-    const float *bias = w + g.n_convw;
-    for (int f = threadIdx.x; f < g.F; f += blockDim.x) {
-        const int o = f / GoGo, rem = f % GoGo, i = rem / g.Go, j = rem % g.Go;
-        float acc = bias[o];
-        for (int c = 0; c < g.Cin; ++c) {
-            const float *Xc = X + c * g.G * g.G;
-            const float *wc = w + (o * g.Cin + c) * KC * KC;
-            for (int a = 0; a < KC; ++a) {
-                const int r = i * g.K_S + a - g.pad;
-                if (r < 0 || r >= g.G) continue;
-                for (int b = 0; b < KC; ++b) {
-                    const int q = j * g.K_S + b - g.pad;
-                    if (q < 0 || q >= g.G) continue;
-                    acc = fmaf(wc[a * KC + b], Xc[r * g.G + q], acc);
-                }
+template <int KC, typename TOut>
+__global__ void __launch_bounds__(256) conv_fwd_kernel(Geo g, int cols_per_cta, long cols,
+                                                       const c32 *__restrict__ s, const float *__restrict__ theta,
+                                                       TOut *__restrict__ act, long ld) {
+    extern __shared__ float Xp[];
+    const int kc = KC > 0 ? KC : g.K_C;
+    const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go;
+    const long c0 = (long)blockIdx.x * cols_per_cta;
+    for (long col = c0; col < min(cols, c0 + cols_per_cta); ++col) {
+        __syncthreads();
+        load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
+        __syncthreads();
+        for (int f = threadIdx.x; f < g.F; f += blockDim.x) {
+            const int o = f / GoGo, rem = f % GoGo, i = rem / g.Go, j = rem % g.Go;
+            float acc = theta[g.off_cb + o];
+            const float *x0 = Xp + (i * g.K_S) * Gp + j * g.K_S;
+            for (int c = 0; c < g.Cin; ++c) {
+                const float *w = theta + ((o * g.Cin + c) * kc) * kc;
+                const float *x = x0 + c * GpGp;
+#pragma unroll
+                for (int a = 0; a < (KC > 0 ? KC : 1); ++a)
+#pragma unroll
+                    for (int b = 0; b < (KC > 0 ? KC : 1); ++b) acc = fmaf(__ldg(w + a * kc + b), x[a * Gp + b], acc);
+                if (KC == 0)
+                    for (int a = 0; a < kc; ++a)
+                        for (int b = 0; b < kc; ++b)
+                            if (a | b) acc = fmaf(__ldg(w + a * kc + b), x[a * Gp + b], acc);
             }
+            acc = fmaxf(acc, 0.0f);
+            if constexpr (sizeof(TOut) == 4) act[col * ld + f] = acc;
+            else act[col * ld + f] = __float2bfloat16_rn(acc);
         }
-        act[col * g.F + f] = fmaxf(acc, 0.0f);
     }
 }
 
-cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st) {
+static int conv_cols_per_cta(long cols) { return cols >= 152 * 64 ? 8 : 1; }
+
+template <typename TOut>
+static cudaError_t conv_fwd_launch(const Geo &g, int S, const c32 *s, const float *theta, TOut *act, long ld,
+                                   cudaStream_t st) {
     const long cols = (long)S * g.K;
     if (!cols) return cudaSuccess;
-    const size_t sm = sizeof(float) * ((size_t)g.Cin * g.G * g.G + g.n_convw + g.N_conv);
-    conv_fwd_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, theta, act);
+    const int Gp = padded_side(g);
+    const size_t sm = sizeof(float) * (size_t)g.Cin * Gp * Gp;
+    const int cpc = conv_cols_per_cta(cols);
+    const unsigned blocks = (unsigned)((cols + cpc - 1) / cpc);
+    if (g.K_C == 3) conv_fwd_kernel<3, TOut><<<blocks, 256, sm, st>>>(g, cpc, cols, s, theta, act, ld);
+    else conv_fwd_kernel<0, TOut><<<blocks, 256, sm, st>>>(g, cpc, cols, s, theta, act, ld);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// conv backward: per-column partial gradients of conv_w and conv_b from the
-// masked activation gradient gpre, then a column reduction.
-// ---------------------------------------------------------------------------
-__global__ void conv_bwd_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ gpre,
-                                float *__restrict__ partials) {
+cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st) {
+    return conv_fwd_launch(g, S, s, theta, act, g.F, st);
+}
+
+cudaError_t conv_forward_bf16(const Geo &g, int S, const c32 *s, const float *theta, __nv_bfloat16 *act, long ld,
+                              cudaStream_t st) {
+    return conv_fwd_launch(g, S, s, theta, act, ld, st);
+}
+
+// Parameter gradient: thread owns output positions (o-independent) and, for a batch of
+// columns, accumulates every (o, c, a, b) product and the bias sums in registers; one
+// block reduction per CTA writes the CTA's partial sums.
+template <int KC, int NCONV, int CIN>
+__global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, long cols,
+                                                       const c32 *__restrict__ s, const float *__restrict__ gpre,
+                                                       float *__restrict__ partials) {
     extern __shared__ float smf[];
-    float *X = smf;
-    float *gp = X + g.Cin * g.G * g.G;
+    constexpr int NW = NCONV * CIN * KC * KC + NCONV;
+    const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go;
+    float *Xp = smf;
+    float *gp = Xp + CIN * GpGp;
+    float acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0.f;
+    const long c0 = (long)blockIdx.x * cols_per_cta;
+    for (long col = c0; col < min(cols, c0 + cols_per_cta); ++col) {
+        __syncthreads();
+        load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
+        for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * g.F + f];
+        __syncthreads();
+        for (int p = threadIdx.x; p < GoGo; p += blockDim.x) {
+            const int i = p / g.Go, j = p % g.Go;
+            const float *x0 = Xp + (i * g.K_S) * Gp + j * g.K_S;
+            float gv[NCONV];
+#pragma unroll
+            for (int o = 0; o < NCONV; ++o) {
+                gv[o] = gp[o * GoGo + p];
+                acc[NCONV * CIN * KC * KC + o] += gv[o];
+            }
+#pragma unroll
+            for (int c = 0; c < CIN; ++c)
+#pragma unroll
+                for (int a = 0; a < KC; ++a)
+#pragma unroll
+                    for (int b = 0; b < KC; ++b) {
+                        const float x = x0[c * GpGp + a * Gp + b];
+#pragma unroll
+                        for (int o = 0; o < NCONV; ++o) acc[((o * CIN + c) * KC + a) * KC + b] = fmaf(gv[o], x, acc[((o * CIN + c) * KC + a) * KC + b]);
+                    }
+        }
+    }
+    __shared__ float red[8][NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float v = warp_sum(acc[w]);
+        if (lane == 0) red[warp][w] = v;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < NW; w += blockDim.x) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][w];
+        partials[(long)blockIdx.x * NW + w] = t;
+    }
+}
+
+// generic fallback (any kernel size / channel count): one warp per parameter, lanes
+// over positions, one column per CTA
+__global__ void conv_bwd_generic_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ gpre,
+                                        float *__restrict__ partials) {
+    extern __shared__ float smf[];
+    const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go, KC = g.K_C;
+    float *Xp = smf;
+    float *gp = Xp + g.Cin * GpGp;
     const long col = blockIdx.x;
-    const long t = col / g.K;
-    const int u = (int)(col % g.K);
-    load_grid(g, s, t, u, X);
+    load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
     for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * g.F + f];
     __syncthreads();
-    const int GoGo = g.Go * g.Go, KC = g.K_C, nw = g.n_convw + g.N_conv;
+    const int nw = g.n_convw + g.N_conv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int widx = warp; widx < nw; widx += nwarps) {
         float acc = 0.f;
         if (widx < g.n_convw) {
             const int b = widx % KC, a = (widx / KC) % KC, c = (widx / (KC * KC)) % g.Cin, o = widx / (KC * KC * g.Cin);
-            const float *Xc = X + c * g.G * g.G;
-            const float *go = gp + o * GoGo;
             for (int p = lane; p < GoGo; p += 32) {
                 const int i = p / g.Go, j = p % g.Go;
-                const int r = i * g.K_S + a - g.pad, q = j * g.K_S + b - g.pad;
-                if (r >= 0 && r < g.G && q >= 0 && q < g.G) acc = fmaf(go[p], Xc[r * g.G + q], acc);
+                acc = fmaf(gp[o * GoGo + p], Xp[c * GpGp + (i * g.K_S + a) * Gp + j * g.K_S + b], acc);
             }
         } else {
-            const float *go = gp + (widx - g.n_convw) * GoGo;
-            for (int p = lane; p < GoGo; p += 32) acc += go[p];
+            for (int p = lane; p < GoGo; p += 32) acc += gp[(widx - g.n_convw) * GoGo + p];
         }
         acc = warp_sum(acc);
         if (lane == 0) partials[col * nw + widx] = acc;
     }
 }
 
+static bool conv_bwd_fast(const Geo &g) { return g.K_C == 3 && g.N_conv == 2 && g.Cin == 2; }
+static const int kConvColsPerCta = 16;
+// rows of `partials` written by conv_backward for `cols` columns
+static long conv_partial_rows(const Geo &g, long cols) {
+    return conv_bwd_fast(g) ? (cols + kConvColsPerCta - 1) / kConvColsPerCta : cols;
+}
+
 cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, const float * /*act*/,
                           float *partials, cudaStream_t st) {
     const long cols = (long)S * g.K;
     if (!cols) return cudaSuccess;
-    const size_t sm = sizeof(float) * ((size_t)g.Cin * g.G * g.G + g.F);
-    cudaError_t e = cudaFuncSetAttribute(conv_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    conv_bwd_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, gpre, partials);
+    const int Gp = padded_side(g);
+    const size_t sm = sizeof(float) * ((size_t)g.Cin * Gp * Gp + g.F);
+    cudaError_t e;
+    if (conv_bwd_fast(g)) {
+        const int cpc = kConvColsPerCta;
+        const unsigned blocks = (unsigned)conv_partial_rows(g, cols);
+        e = cudaFuncSetAttribute(conv_bwd_kernel<3, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        conv_bwd_kernel<3, 2, 2><<<blocks, 256, sm, st>>>(g, cpc, cols, s, gpre, partials);
+    } else {
+        e = cudaFuncSetAttribute(conv_bwd_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        conv_bwd_generic_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, gpre, partials);
+    }
     return cudaGetLastError();
 }
 
-__global__ void conv_reduce_kernel(int cols, int nw, const float *__restrict__ partials, float *__restrict__ out) {
+__global__ void conv_reduce_kernel(int rows, int nw, const float *__restrict__ partials, float *__restrict__ out) {
     __shared__ double red[32];
     const int w = blockIdx.x;
     double acc = 0;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) acc += partials[(long)c * nw + w];
+    for (int c = threadIdx.x; c < rows; c += blockDim.x) acc += partials[(long)c * nw + w];
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) out[w] = (float)acc;
 }
 
 cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, cudaStream_t st) {
     const int nw = g.n_convw + g.N_conv;
-    conv_reduce_kernel<<<nw, 256, 0, st>>>(cols, nw, partials, grad);   // conv_w then conv_b: contiguous in theta
+    conv_reduce_kernel<<<nw, 256, 0, st>>>((int)conv_partial_rows(g, cols), nw, partials, grad);   // conv_w, conv_b
     return cudaGetLastError();
 }
 

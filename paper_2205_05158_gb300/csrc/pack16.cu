@@ -7,57 +7,6 @@
 
 namespace fdk {
 
-__global__ void conv_fwd_bf16_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ theta,
-                                     __nv_bfloat16 *__restrict__ act, long ld) {
-    extern __shared__ float smf[];
-    float *X = smf;
-    float *w = X + g.Cin * g.G * g.G;
-    const long col = blockIdx.x;
-    const long t = col / g.K;
-    const int u = (int)(col % g.K);
-    for (int i = threadIdx.x; i < g.n_convw + g.N_conv; i += blockDim.x) w[i] = theta[i];
-    const int GG = g.G * g.G;
-    for (int l = 0; l < g.L_U; ++l) {
-        const int v = (u + l) % g.K;
-        const c32 *sv = s + (t * g.K + v) * g.N_d;
-        for (int idx = threadIdx.x; idx < GG; idx += blockDim.x) {
-            const c32 val = idx < g.N_d ? sv[idx] : make_float2(0.f, 0.f);
-            X[(2 * l) * GG + idx] = val.x;
-            X[(2 * l + 1) * GG + idx] = val.y;
-        }
-    }
-    __syncthreads();
-    const int GoGo = g.Go * g.Go, KC = g.K_C;
-    const float *bias = w + g.n_convw;
-    for (int f = threadIdx.x; f < g.F; f += blockDim.x) {
-        const int o = f / GoGo, rem = f % GoGo, i = rem / g.Go, j = rem % g.Go;
-        float acc = bias[o];
-        for (int c = 0; c < g.Cin; ++c) {
-            const float *Xc = X + c * GG;
-            const float *wc = w + (o * g.Cin + c) * KC * KC;
-            for (int a = 0; a < KC; ++a) {
-                const int r = i * g.K_S + a - g.pad;
-                if (r < 0 || r >= g.G) continue;
-                for (int b = 0; b < KC; ++b) {
-                    const int q = j * g.K_S + b - g.pad;
-                    if (q < 0 || q >= g.G) continue;
-                    acc = fmaf(wc[a * KC + b], Xc[r * g.G + q], acc);
-                }
-            }
-        }
-        act[col * ld + f] = __float2bfloat16_rn(fmaxf(acc, 0.0f));
-    }
-}
-
-cudaError_t conv_forward_bf16(const Geo &g, int S, const c32 *s, const float *theta, __nv_bfloat16 *act, long ld,
-                              cudaStream_t st) {
-    const long cols = (long)S * g.K;
-    if (!cols) return cudaSuccess;
-    const size_t sm = sizeof(float) * ((size_t)g.Cin * g.G * g.G + g.n_convw + g.N_conv);
-    conv_fwd_bf16_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, theta, act, ld);
-    return cudaGetLastError();
-}
-
 // out[n'][f] = bf16(fc_w[pi(n')][f])
 __global__ void pack_fcw_kernel(Geo g, const float *__restrict__ fw, __nv_bfloat16 *__restrict__ out, long ld) {
     const long n = blockIdx.y;
