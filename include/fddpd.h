@@ -197,6 +197,25 @@ int fddpd_sync(fddpd_plan *plan);
 int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
                   int ab_type, int splits, void *stream);
 
+/* Zero-forcing precoder (same result as fddpd_precode) for callers that cannot allocate
+ * device memory, e.g. a real-time baseband pipeline that reserves all device memory up
+ * front and forbids cudaMalloc on its processing path.  The paper has no counterpart;
+ * this is a deployment variant of Eq. (6).
+ *   H [R][N_d][K][M] in, W [R][N_d][M][K] out, alpha [R][N_d] out: device memory owned by
+ *   the caller, as for fddpd_precode (data subcarriers only; no plan is needed).
+ * No device memory is allocated: the scratch of the ZF kernels is one static device
+ * array of FDDPD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit.  It fits R * N_d * K * (K + 1) * 8 + 512 bytes or less (about 15,400 subcarriers
+ * at K = 16); larger requests return FDDPD_ERR_UNSUPPORTED before any work.  The first
+ * call on each device looks up the array's device address (with that device current),
+ * so that call should come before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race.  Runs on `stream` and synchronises it to
+ * read the singular-matrix flag.  Errors: ARG, LAYOUT, UNSUPPORTED, SINGULAR, CUDA
+ * (text via fddpd_last_error(NULL)).                                                  */
+#define FDDPD_NOALLOC_SCRATCH_BYTES (32u << 20)
+int fddpd_precode_noalloc(int M, int K, int N_d, int R, double P_T, const fddpd_c32 *H, fddpd_c32 *W,
+                          float *alpha, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
-            "fddpd_sync", "fddpd_tc_gemm"]
+            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc"]
 
 STAGES = ["zf", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -92,9 +92,11 @@ def load(build_if_missing: bool = True):
     L.fddpd_launch_count.restype = C.c_longlong
     L.fddpd_sync.argtypes = [P]
     L.fddpd_tc_gemm.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P]
+    L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
-              "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm"):
+              "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
+              "fddpd_precode_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -266,3 +268,16 @@ def tc_gemm(A, B, C, splits: int = 1, stream=None):
             self.close()
         except Exception:
             pass
+
+
+def precode_noalloc(H, W, alpha, P_T: float, stream=None):
+    """Zero-forcing precoder without a plan and without any device allocation (for
+    callers that may not allocate device memory); H [R][N_d][K][M] complex64 CUDA
+    tensor in, W [R][N_d][M][K] complex64 and alpha [R][N_d] float32 out."""
+    import torch
+    L = load()
+    R, N_d, K, M = H.shape
+    rc = L.fddpd_precode_noalloc(M, K, N_d, R, float(P_T), _ptr(H, torch.complex64), _ptr(W, torch.complex64),
+                                 _ptr(alpha, torch.float32), _stream_ptr(stream))
+    if rc:
+        raise FddpdError(rc, L.fddpd_last_error(None).decode())

@@ -553,3 +553,6 @@ extern "C" int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const 
     if (herr) return set_err(nullptr, FDDPD_ERR_TIMEOUT, "fddpd_tc_gemm: bounded wait timed out");
     return FDDPD_OK;
 }
+
+// Error text for entry points that have no plan (see fddpd_last_error(NULL)).
+void fddpd_internal_set_error(const char *msg) { set_err(nullptr, FDDPD_ERR_ARG, "%s", msg); }
