@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=2, help="symbols per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -232,7 +233,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    prec_name = args.precision or "fp32"
+    prec_name = args.precision or "bf16"
     prec = {"fp32": fd.FDDPD_FP32, "bf16": fd.FDDPD_BF16, "fp16": fd.FDDPD_FP16}[prec_name]
     cfg = synth.CONFIGS["cfg3"].with_(seed=rank, S=args.symbols)
     S = cfg.S
@@ -334,6 +335,36 @@ def run_ours(args):
            "quality": {"evm_db": evm_db, "acpr_db": acpr_db},
            "gpu_launches": launches,
            "clocks": clk}
+
+    # the plain FP32 plan on the same inputs and the same step (the mixed-precision plan's
+    # comparison point), timed the same way
+    if prec_name != "fp32" and not args.no_fp32_compare:
+        plan32 = fd.Plan.from_config(cfg, w.P_T, max_symbols=S, precision=fd.FDDPD_FP32, stream=stream)
+        th32 = theta0.clone()
+        met32 = torch.zeros(5, dtype=torch.float64, device="cuda")
+        W32 = torch.empty_like(W)
+        al32 = torch.empty_like(al)
+
+        def step32():
+            plan32.precode(H, W32, al32)
+            plan32.update(s, H, W32, al32, pa, th32, LR, 1, fd.FDDPD_GD, met32)
+
+        for _ in range(2):
+            step32()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n32 = max(2, args.steps // 2)
+        g0.record(stream)
+        for _ in range(n32):
+            step32()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = g0.elapsed_time(g1) / n32
+        plan32.distort(s, H, W32, al32, pa, theta, None, met32)
+        m32 = met32.cpu().numpy()
+        out["fp32_plan"] = {"value": world * S / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+                            "evm_db": 10 * math.log10(m32[1] / m32[2]), "acpr_db": 10 * math.log10(m32[3] / m32[4])}
+        del plan32
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     if not args.no_e2e:

@@ -4,22 +4,22 @@
 
 namespace fdk {
 
-// Twiddle tables of all radix-8 passes: entry [tw_off(i) + (r - 1) Ns + k] = exp(-j 2 pi r k / (8 Ns)).
+// Twiddle tables of the radix-16 passes: entry [tw_off(i) + (r - 1) Ns + k] =
+// exp(-j 2 pi r k / (16 Ns)) for the pass of span Ns (Ns = R0, 16 R0, ... < N).
 __global__ void pass_twiddle_kernel(int log2N, c32 *out) {
     const int N = 1 << log2N;
-    const int R0 = log2N % 3 == 0 ? 8 : (log2N % 3 == 1 ? 2 : 4);
+    const int R0 = 1 << (log2N % 4 == 0 ? 4 : log2N % 4);
     int off = 0;
-    for (int Ns = R0; Ns < N; Ns *= 8) {
-        for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < 7 * Ns; e += blockDim.x * gridDim.x) {
+    for (int Ns = R0; Ns < N; Ns *= 16) {
+        for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < 15 * Ns; e += blockDim.x * gridDim.x) {
             const int r = e / Ns + 1, k = e % Ns;
             double s, c;
-            sincospi(-2.0 * (double)(r * k) / (double)(8 * Ns), &s, &c);
+            sincospi(-2.0 * (double)(r * k) / (double)(16 * Ns), &s, &c);
             out[off + e] = make_float2((float)c, (float)s);
         }
-        off += 7 * Ns;
+        off += 15 * Ns;
     }
 }
-
 
 size_t fftpa_smem_bytes(const Geo &g, bool /*adjoint*/) { return fftpa_smem_bytes_(g); }
 

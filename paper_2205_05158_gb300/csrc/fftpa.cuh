@@ -12,18 +12,17 @@
 //                    a_p = (p+1)/2 |x|^{p-1}, b_p = (p-1)/2 x^2 |x|^{p-3}  (Wirtinger)
 //             g_xhat = DFT_N(gx) on the data bins (adjoint of the unitary IDFT).
 //
-// A row is transformed by T = N/8 threads holding 8 points each: one radix-2/4 pass
-// (when log2 N is not a multiple of 3) and radix-8 Stockham passes, ping-ponging
-// between two padded shared buffers (one barrier per pass).  The pass structure is a
-// template parameter, so every index is a compile-time expression, and each radix-8
-// pass with span Ns reads its twiddles from its own table laid out [r][k] (k = the
-// thread's position in the span), which consecutive threads read without bank
-// conflicts.  The last pass of an inverse transform leaves thread t with samples
-// t + q T (q = 0..7) -- the inputs of its first-pass butterflies of the next forward
-// transform -- so the time-domain row stays in registers: the PA (or its adjoint) is
-// applied there, its memory taps (samples n - l, or n + l for the adjoint) come from
-// neighbouring lanes by warp shuffles and, across warp boundaries, from a small
-// shared array.  CTAs are persistent.  All arithmetic is FP32.
+// A row is transformed by T = N/16 threads holding 16 points each: one radix-2/4/8/16
+// pass (absorbing log2 N mod 4) and radix-16 Stockham passes (a 16-point DFT is two
+// radix-4 layers in registers), ping-ponging between two shared buffers indexed
+// i + i/16, which keeps every store pattern of N = 256..4096 free of bank conflicts.
+// The pass structure is a template parameter; each radix-16 pass with span Ns reads its
+// twiddles from its own table laid out [r][k].  The last pass of an inverse transform
+// leaves thread t with samples t + q T (q = 0..15) -- exactly the inputs of its first-pass
+// butterflies of the next forward transform -- so the row is transformed back in
+// registers after the PA.  The PA (or its adjoint) reads the memory taps (samples n - l,
+// or n + l) from a natural-order copy of the row in shared memory.  CTAs are persistent.
+// All arithmetic is FP32.
 #pragma once
 #include "common.cuh"
 #include "kernels.h"
@@ -31,167 +30,143 @@
 namespace fdk {
 
 static constexpr float kSqrtHalf = 0.70710678118654752f;
+static constexpr float kCos8 = 0.92387953251128676f;   // cos(pi/8)
+static constexpr float kSin8 = 0.38268343236508977f;   // sin(pi/8)
 
-FD_HD int pidx(int i) { return i + (i >> 3); }   // one pad word per 8 entries
+FD_HD int pidx(int i) { return i + (i >> 4); }   // one pad word per 16 entries
 
 template <bool INV> FD_D c32 mul_mi(c32 a) {      // a * (-i) forward, a * (+i) inverse
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 template <bool INV> FD_D c32 twmul(c32 v, c32 w) { return INV ? cmulc(v, w) : cmul(v, w); }
 
+// a * W16^m, W16 = exp(-/+ j 2 pi / 16), for the constant m used inside dft16
+template <bool INV, int MM> FD_D c32 w16(c32 a) {
+    constexpr int m = MM & 15;
+    if (m == 0) return a;
+    if (m == 4) return mul_mi<INV>(a);
+    if (m == 8) return make_float2(-a.x, -a.y);
+    const float sg = INV ? 1.f : -1.f;   // exp(sg j pi m / 8)
+    float c, s;
+    switch (m) {
+        case 1: c = kCos8; s = kSin8; break;
+        case 2: c = kSqrtHalf; s = kSqrtHalf; break;
+        case 3: c = kSin8; s = kCos8; break;
+        case 6: c = -kSqrtHalf; s = kSqrtHalf; break;
+        case 9: c = -kCos8; s = -kSin8; break;
+        default: c = 1.f; s = 0.f; break;
+    }
+    s *= sg;
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
 template <bool INV> FD_D void dft2(c32 *v) {
     c32 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
-template <bool INV> FD_D void dft4(c32 *v) {
-    c32 a0 = cadd(v[0], v[2]), a2 = csub(v[0], v[2]);
-    c32 a1 = cadd(v[1], v[3]), a3 = mul_mi<INV>(csub(v[1], v[3]));
-    v[0] = cadd(a0, a1);
-    v[2] = csub(a0, a1);
-    v[1] = cadd(a2, a3);
-    v[3] = csub(a2, a3);
+template <bool INV> FD_D void dft4s(c32 &x0, c32 &x1, c32 &x2, c32 &x3) {
+    c32 a0 = cadd(x0, x2), a2 = csub(x0, x2);
+    c32 a1 = cadd(x1, x3), a3 = mul_mi<INV>(csub(x1, x3));
+    x0 = cadd(a0, a1);
+    x2 = csub(a0, a1);
+    x1 = cadd(a2, a3);
+    x3 = csub(a2, a3);
 }
+template <bool INV> FD_D void dft4(c32 *v) { dft4s<INV>(v[0], v[1], v[2], v[3]); }
 template <bool INV> FD_D void dft8(c32 *v) {
     c32 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
     dft4<INV>(e);
     dft4<INV>(o);
-    // W8^1 = (1 -/+ i)/sqrt2, W8^2 = -/+ i, W8^3 = (-1 -/+ i)/sqrt2
-    c32 o1 = INV ? make_float2((o[1].x - o[1].y) * kSqrtHalf, (o[1].x + o[1].y) * kSqrtHalf)
-                 : make_float2((o[1].x + o[1].y) * kSqrtHalf, (o[1].y - o[1].x) * kSqrtHalf);
-    c32 o2 = mul_mi<INV>(o[2]);
-    c32 o3 = INV ? make_float2(-(o[3].x + o[3].y) * kSqrtHalf, (o[3].x - o[3].y) * kSqrtHalf)
-                 : make_float2((o[3].y - o[3].x) * kSqrtHalf, -(o[3].x + o[3].y) * kSqrtHalf);
+    c32 o1 = w16<INV, 2>(o[1]), o2 = w16<INV, 4>(o[2]), o3 = w16<INV, 6>(o[3]);
     v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
     v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
     v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
 }
+// 16-point DFT, natural order in and out: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV> FD_D void dft16(c32 *v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4s<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);   // over n1 -> k1
+    // v[4 k1 + n2] now holds A[n2][k1]; twiddle W16^(n2 k1)
+    v[5] = w16<INV, 1>(v[5]);   v[6] = w16<INV, 2>(v[6]);   v[7] = w16<INV, 3>(v[7]);
+    v[9] = w16<INV, 2>(v[9]);   v[10] = w16<INV, 4>(v[10]); v[11] = w16<INV, 6>(v[11]);
+    v[13] = w16<INV, 3>(v[13]); v[14] = w16<INV, 6>(v[14]); v[15] = w16<INV, 9>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4s<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);   // over n2 -> k2
+    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 block into natural order
+    c32 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int R, bool INV> FD_D void dftR(c32 *v) {
+    if (R == 2) dft2<INV>(v);
+    else if (R == 4) dft4<INV>(v);
+    else if (R == 8) dft8<INV>(v);
+    else dft16<INV>(v);
+}
 
 // Compile-time pass structure of an N = 2^LOG2N transform.
 template <int LOG2N>
 struct Fft {
-    static constexpr int N = 1 << LOG2N, T = N / 8, PADN = N + N / 8;
-    static constexpr int R0 = LOG2N % 3 == 0 ? 8 : (LOG2N % 3 == 1 ? 2 : 4);   // first pass radix
-    static constexpr int LOGR0 = R0 == 8 ? 3 : (R0 == 2 ? 1 : 2);
-    static constexpr int NP8 = (LOG2N - LOGR0) / 3;                           // radix-8 passes after it
-    static constexpr int ns(int i) { return i == 0 ? 1 : R0 << (3 * (i - 1)); }   // span of pass i (1..NP8)
-    static constexpr int tw_off(int i) {                                          // table offset of pass i >= 1
+    static constexpr int N = 1 << LOG2N, T = N / 16, PADN = N + N / 16;
+    static constexpr int LOGR0 = LOG2N % 4 == 0 ? 4 : LOG2N % 4;
+    static constexpr int R0 = 1 << LOGR0;                      // first pass radix
+    static constexpr int NP = (LOG2N - LOGR0) / 4;             // radix-16 passes after it
+    static constexpr int ns(int i) { return R0 << (4 * (i - 1)); }   // span of pass i (1..NP)
+    static constexpr int tw_off(int i) {
         int o = 0;
-        for (int j = 1; j < i; ++j) o += 7 * ns(j);
+        for (int j = 1; j < i; ++j) o += 15 * ns(j);
         return o;
     }
-    static constexpr int TW = tw_off(NP8 + 1);                                   // table entries
-    static constexpr int pos(int b, int r) { return R0 == 8 ? r : (R0 == 4 ? b + 2 * r : b + 4 * r); }
+    static constexpr int TW = tw_off(NP + 1);
+    // first pass: butterfly b (0..16/R0-1) input r holds sample t + pos(b, r) T
+    static constexpr int pos(int b, int r) { return b + r * (16 / R0); }
 };
 
-// One transform.  in[q] holds input sample t + q T; on return out[q] holds output
-// t + q T scaled by `scale`.  Uses bufA, bufB; returns after a barrier that lets the
-// caller reuse both buffers only after its own next barrier (the last pass reads
-// bufX without a trailing barrier).
+// One transform in place: x[q] is input sample t + q T; on return output t + q T,
+// scaled.  The last pass reads a buffer with no barrier after it: the caller must
+// barrier before either buffer is written again.
 template <int LOG2N, bool INV>
-FD_D void transform(const c32 (&in)[8], c32 (&out)[8], c32 *bufA, c32 *bufB, const c32 *twp, int t, float scale) {
+FD_D void transform(c32 (&x)[16], c32 *bufA, c32 *bufB, const c32 *twp, int t, float scale) {
     using F = Fft<LOG2N>;
-    c32 v[8];
-    // ---- first pass, radix R0, span 1 (no twiddles) ----
-    constexpr int B0 = 8 / F::R0;
+    constexpr int B0 = 16 / F::R0;
+    c32 v[16];
 #pragma unroll
     for (int b = 0; b < B0; ++b) {
 #pragma unroll
-        for (int r = 0; r < F::R0; ++r) v[b * F::R0 + r] = in[F::pos(b, r)];
-        if (F::R0 == 2) dft2<INV>(v + 2 * b);
-        else if (F::R0 == 4) dft4<INV>(v + 4 * b);
-        else dft8<INV>(v);
-        const int j = t + b * F::T;   // span 1: k = 0, base = j R0
+        for (int r = 0; r < F::R0; ++r) v[b * F::R0 + r] = x[F::pos(b, r)];
+        dftR<F::R0, INV>(v + b * F::R0);
+        const int j = t + b * F::T;   // span 1: outputs j R0 + q
 #pragma unroll
         for (int q = 0; q < F::R0; ++q) bufA[pidx(j * F::R0 + q)] = v[b * F::R0 + q];
     }
     __syncthreads();
     c32 *src = bufA, *dst = bufB;
-    // ---- radix-8 passes; the last one stays in registers ----
 #pragma unroll
-    for (int i = 1; i <= F::NP8; ++i) {
+    for (int i = 1; i <= F::NP; ++i) {
         const int Ns = F::ns(i);
         const int k = t & (Ns - 1);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = src[pidx(t + r * F::T)];
+        for (int r = 0; r < 16; ++r) v[r] = src[pidx(t + r * F::T)];
         const c32 *tw = twp + F::tw_off(i);
 #pragma unroll
-        for (int r = 1; r < 8; ++r) v[r] = twmul<INV>(v[r], tw[(r - 1) * Ns + k]);
-        dft8<INV>(v);
-        if (i == F::NP8) {   // Ns = N/8, k = t: outputs t + q T
+        for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], tw[(r - 1) * Ns + k]);
+        dft16<INV>(v);
+        if (i == F::NP) {   // Ns = N/16, k = t: outputs t + q T
 #pragma unroll
-            for (int q = 0; q < 8; ++q) out[q] = cscale(v[q], scale);
+            for (int q = 0; q < 16; ++q) x[q] = cscale(v[q], scale);
         } else {
-            const int base = (t - k) * 8 + k;
+            const int base = (t - k) * 16 + k;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) dst[pidx(base + q * Ns)] = v[q];
+            for (int q = 0; q < 16; ++q) dst[pidx(base + q * Ns)] = v[q];
             __syncthreads();
             c32 *tmp = src; src = dst; dst = tmp;
-        }
-    }
-}
-
-struct TapCtx {      // where the neighbours of thread t (row-local index) live
-    int T, lane, t, wrow, nwarps_row, wbase;   // wbase: CTA warp index of the row's first warp
-};
-
-FD_D TapCtx tap_ctx(int T, int t, int grp) {
-    TapCtx c;
-    c.T = T;
-    c.t = t;
-    c.lane = threadIdx.x & 31;
-    c.nwarps_row = T >= 32 ? T / 32 : 1;
-    c.wrow = T >= 32 ? t / 32 : 0;
-    c.wbase = T >= 32 ? grp * c.nwarps_row : 0;
-    return c;
-}
-
-// Publish what other warps of the row need: for d < 0 the last D lanes of each warp,
-// for d > 0 the first D lanes.  pub: [CTA warp][D][8] complex.
-template <bool NEXT>
-FD_D void publish(const TapCtx &c, const c32 (&v)[8], int D, c32 *pub) {
-    if (c.T < 32 || D == 0) return;
-    const int slot = NEXT ? c.lane : c.lane - (32 - D);
-    if (slot >= 0 && slot < D) {
-        const int w = c.wbase + c.wrow;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) pub[(w * D + slot) * 8 + q] = v[q];
-    }
-}
-
-// out[q] = v at sample (t + q T) + d of the same row (circular), |d| <= D.
-// Every lane of the warp must call this with the same d.
-FD_D void neighbour(const TapCtx &c, const c32 (&v)[8], int d, int D, const c32 *pub, c32 (&out)[8]) {
-    int st = c.t + d, dq = 0;
-    if (st < 0) { st += c.T; dq = -1; }
-    else if (st >= c.T) { st -= c.T; dq = 1; }
-    int src_lane;
-    bool in_warp;
-    if (c.T < 32) {
-        src_lane = (c.lane - c.t) + st;
-        in_warp = true;
-    } else {
-        src_lane = c.lane + d;
-        in_warp = src_lane >= 0 && src_lane < 32;
-    }
-    const int sl = src_lane & 31;
-    c32 tmp[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        tmp[q].x = __shfl_sync(0xffffffffu, v[q].x, sl);
-        tmp[q].y = __shfl_sync(0xffffffffu, v[q].y, sl);
-    }
-    if (in_warp) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) out[q] = dq == 0 ? tmp[q] : (dq < 0 ? tmp[(q + 7) & 7] : tmp[(q + 1) & 7]);
-    } else {
-        const int wsrc = c.wbase + (d < 0 ? (c.wrow + c.nwarps_row - 1) % c.nwarps_row : (c.wrow + 1) % c.nwarps_row);
-        const int slot = d < 0 ? (src_lane + 32) - (32 - D) : src_lane - 32;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int qs = dq == 0 ? q : (dq < 0 ? ((q + 7) & 7) : ((q + 1) & 7));
-            out[q] = pub[(wsrc * D + slot) * 8 + qs];
         }
     }
 }
@@ -207,76 +182,57 @@ FD_D float powabs(float r2, float mag, int e) {
 // PA shape: P_ > 0 means orders 1, 3, ..., 2 P_ - 1 and memory L_ (compile time);
 // P_ == 0 is the general case (orders and memory from Geo at run time).
 template <int P_, int L_>
-struct PaShape {
-    static constexpr bool fixed = P_ > 0;
-};
-
-template <int LOG2N, int P_, int L_>
-struct FwdRow {
-    // y_n = sum_l sum_p c_{p,l} x_{n-l} |x_{n-l}|^{p-1}
-    static FD_D void pa(const Geo &g, const TapCtx &tc, const c32 (&x)[8], const c32 *cp, const c32 *pub, int D,
-                        bool any_even, c32 (&y)[8]) {
+struct RowPa {
+    // y_n = sum_l sum_p c_{p,l} x_{n-l} |x_{n-l}|^{p-1}; xs holds the row in natural order
+    static FD_D void forward(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *xs, const c32 *cp,
+                             bool any_even, c32 (&y)[16]) {
         const int P = P_ > 0 ? P_ : g.n_orders;
         const int L = P_ > 0 ? L_ : g.L;
         const int L1 = L + 1;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) y[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < 16; ++q) y[q] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int l = 0; l <= (P_ > 0 ? L_ : 7); ++l) {
             if (l > L) break;
-            c32 xl[8];
-            if (l == 0) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) xl[q] = x[q];
-            } else {
-                neighbour(tc, x, -l, D, pub, xl);
-            }
+            c32 c[P_ > 0 ? P_ : 1];
             if (P_ > 0) {
-                c32 c[P_ > 0 ? P_ : 1];
 #pragma unroll
-                for (int p = 0; p < P_; ++p) c[p] = cp[p * L1 + l];
+                for (int p = 0; p < (P_ > 0 ? P_ : 1); ++p) c[p] = cp[p * L1 + l];
+            }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float r2 = cabs2(xl[q]);
-                    c32 phi = xl[q];
+            for (int q = 0; q < 16; ++q) {
+                const c32 xl = l == 0 ? x[q] : xs[pidx((t + q * T - l) & (N - 1))];
+                const float r2 = cabs2(xl);
+                if (P_ > 0) {
+                    c32 phi = xl;
                     y[q] = cfma(c[0], phi, y[q]);
 #pragma unroll
-                    for (int p = 1; p < P_; ++p) {
+                    for (int p = 1; p < (P_ > 0 ? P_ : 1); ++p) {
                         phi = cscale(phi, r2);
                         y[q] = cfma(c[p], phi, y[q]);
                     }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float r2 = cabs2(xl[q]);
+                } else {
                     const float mg = any_even ? sqrtf(r2) : 0.f;
                     for (int p = 0; p < P; ++p)
-                        y[q] = cfma(cp[p * L1 + l], cscale(xl[q], powabs(r2, mg, g.orders[p] - 1)), y[q]);
+                        y[q] = cfma(cp[p * L1 + l], cscale(xl, powabs(r2, mg, g.orders[p] - 1)), y[q]);
                 }
             }
         }
     }
-    // gx_n = sum_l A_l g_{n+l} + B_l conj(g_{n+l})
-    static FD_D void pa_adjoint(const Geo &g, const TapCtx &tc, const c32 (&x)[8], const c32 (&gv)[8],
-                                const c32 *cp, const c32 *pub, int D, c32 (&gx)[8]) {
+    // gx_n = sum_l A_l(x_n) g_{n+l} + B_l(x_n) conj(g_{n+l}); gs holds g in natural order
+    static FD_D void adjoint(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *gs, const c32 *cp,
+                             c32 (&gx)[16]) {
         const int P = P_ > 0 ? P_ : g.n_orders;
         const int L = P_ > 0 ? L_ : g.L;
         const int L1 = L + 1;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) gx[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < 16; ++q) gx[q] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int l = 0; l <= (P_ > 0 ? L_ : 7); ++l) {
             if (l > L) break;
-            c32 gl[8];
-            if (l == 0) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) gl[q] = gv[q];
-            } else {
-                neighbour(tc, gv, l, D, pub, gl);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 16; ++q) {
+                const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
                 const float r2 = cabs2(x[q]);
                 const c32 xx = cmul(x[q], x[q]);
                 c32 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
@@ -284,7 +240,7 @@ struct FwdRow {
                     // order 2k+1: a = (k+1) r2^k, b = k x^2 r2^(k-1)
                     float rk = 1.0f, rk1 = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < P_; ++k) {
+                    for (int k = 0; k < (P_ > 0 ? P_ : 1); ++k) {
                         const c32 c = cp[k * L1 + l];
                         A = cadd(A, cscale(cconj(c), (float)(k + 1) * rk));
                         if (k >= 1) B = cfma(cscale(xx, (float)k * rk1), c, B);
@@ -301,46 +257,44 @@ struct FwdRow {
                         if (e >= 1 && mag > 0.0f) B = cfma(cscale(xx, 0.5f * (float)e * w / r2), c, B);
                     }
                 }
-                gx[q] = cfma(A, gl[q], gx[q]);
-                gx[q] = cfma(B, cconj(gl[q]), gx[q]);
+                gx[q] = cfma(A, gl, gx[q]);
+                gx[q] = cfma(B, cconj(gl), gx[q]);
             }
         }
     }
 };
 
 template <int LOG2N>
-FD_HD constexpr int rows_per_cta_t() { return LOG2N >= 11 ? 1 : (1 << (11 - LOG2N)); }
+FD_HD constexpr int rows_per_cta_t() { return LOG2N >= 12 ? 1 : (1 << (12 - LOG2N)); }
 
-inline int rows_per_cta(int N) { return N >= 2048 ? 1 : 2048 / N; }
+inline int rows_per_cta(int N) { return N >= 4096 ? 1 : 4096 / N; }
 
-// smem: per-pass twiddles, 2 buffers per row, coefficients per row, boundary array
+// smem: per-pass twiddles, 2 buffers per row, coefficients per row
 inline size_t fftpa_smem_bytes_(const Geo &g) {
-    const int N = g.N, padN = N + (N >> 3), r = rows_per_cta(N);
-    const int T = N >> 3, nw = (r * T + 31) / 32, D = g.L > 0 ? g.L : 1;
-    return sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * g.n_orders * (g.L + 1) + (size_t)nw * D * 8);
+    const int N = g.N, padN = N + (N >> 4), r = rows_per_cta(N);
+    return sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * g.n_orders * (g.L + 1));
 }
 
 template <int LOG2N, int P_, int L_, typename TOut>
-__global__ void __launch_bounds__(LOG2N == 12 ? 512 : 256, LOG2N == 12 ? 1 : 2) fftpa_forward_kernel(
-    Geo g, long rows, const c32 *__restrict__ xh, const c32 *__restrict__ pa, const c32 *__restrict__ twp_g,
-    TOut *__restrict__ Xout, double *__restrict__ metrics) {
+__global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows, const c32 *__restrict__ xh,
+                                                               const c32 *__restrict__ pa,
+                                                               const c32 *__restrict__ twp_g, TOut *__restrict__ Xout,
+                                                               double *__restrict__ metrics) {
     using F = Fft<LOG2N>;
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1), D = L > 0 ? L : 1;
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
-    c32 *pub = coef + RPC * PL;
     __shared__ double red[32];
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
-    const TapCtx tc = tap_ctx(F::T, t, grp);
     bool any_even = false;
     for (int p = 0; p < P; ++p) any_even |= !(g.orders[p] & 1);
     const float rs = rsqrtf((float)F::N);
-    double gpow = 0, dpow = 0;
+    float gpow = 0.f, dpow = 0.f;
     const long ngroups = (rows + RPC - 1) / RPC;
 
     for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
@@ -348,44 +302,41 @@ __global__ void __launch_bounds__(LOG2N == 12 ? 512 : 256, LOG2N == 12 ? 1 : 2) 
         const bool active = row < rows;
         const long rowc = active ? row : 0;
         const int m = (int)(rowc % g.M);
-        __syncthreads();   // the previous row is done with coef, pub and both buffers
+        __syncthreads();   // the previous row is done with coef and both buffers
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
         const c32 *xrow = xh + rowc * g.N_d;
-        c32 in[8], x[8];
+        c32 x[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 16; ++q) {
             const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            in[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+            x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
         }
-        transform<LOG2N, true>(in, x, bufA, bufB, twp, t, rs);
-        publish<false>(tc, x, D, pub);
+        transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
+        __syncthreads();   // the last pass has read its buffer
+#pragma unroll
+        for (int q = 0; q < 16; ++q) bufB[pidx(t + q * F::T)] = x[q];
         __syncthreads();
-        c32 y[8];
-        FwdRow<LOG2N, P_, L_>::pa(g, tc, x, cp, pub, D, any_even, y);
-        c32 v[8];
-        transform<LOG2N, false>(y, v, bufA, bufB, twp, t, rs);
+        c32 y[16];
+        RowPa<P_, L_>::forward(g, F::N, F::T, t, x, bufB, cp, any_even, y);
+        __syncthreads();   // taps read; bufA / bufB are free
+        transform<LOG2N, false>(y, bufA, bufB, twp, t, rs);
         TOut *orow = Xout + rowc * g.N_d;
-        float gp = 0.f, dp = 0.f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 16; ++q) {
             const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            const float p2 = cabs2(v[q]);
+            const float p2 = active ? cabs2(y[q]) : 0.f;
             if (i >= 0) {
-                dp += p2;
-                if (active) orow[i] = Operand<TOut>::from(v[q]);
+                dpow += p2;
+                if (active) orow[i] = Operand<TOut>::from(y[q]);
             } else {
-                gp += p2;
+                gpow += p2;
             }
-        }
-        if (active) {
-            gpow += gp;
-            dpow += dp;
         }
     }
     if (metrics) {
-        const double gs = block_sum(gpow, red);
-        const double ds = block_sum(dpow, red);
+        const double gs = block_sum((double)gpow, red);
+        const double ds = block_sum((double)dpow, red);
         if (threadIdx.x == 0) {
             atomicAdd(metrics + 3, gs);
             atomicAdd(metrics + 4, ds);
@@ -394,21 +345,19 @@ __global__ void __launch_bounds__(LOG2N == 12 ? 512 : 256, LOG2N == 12 ? 1 : 2) 
 }
 
 template <int LOG2N, int P_, int L_, typename TIn>
-__global__ void __launch_bounds__(LOG2N == 12 ? 512 : 256, LOG2N == 12 ? 1 : 2) fftpa_adjoint_kernel(
-    Geo g, long rows, const c32 *__restrict__ xh, const c32 *__restrict__ pa, const c32 *__restrict__ twp_g,
-    const TIn *gX, c32 *gxh) {
+__global__ void __launch_bounds__(256, 1) fftpa_adjoint_kernel(Geo g, long rows, const c32 *__restrict__ xh,
+                                                               const c32 *__restrict__ pa,
+                                                               const c32 *__restrict__ twp_g, const TIn *gX, c32 *gxh) {
     using F = Fft<LOG2N>;
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1), D = L > 0 ? L : 1;
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
-    c32 *pub = coef + RPC * PL;
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
-    const TapCtx tc = tap_ctx(F::T, t, grp);
     const float rs = rsqrtf((float)F::N);
     const long ngroups = (rows + RPC - 1) / RPC;
 
@@ -422,32 +371,29 @@ __global__ void __launch_bounds__(LOG2N == 12 ? 512 : 256, LOG2N == 12 ? 1 : 2) 
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
         const c32 *xrow = xh + rowc * g.N_d;
         const TIn *grow = gX + rowc * g.N_d;
-        c32 in[8], x[8], gv[8];
+        c32 x[16], gv[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 16; ++q) {
             const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            in[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+            x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+            gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
         }
-        transform<LOG2N, true>(in, x, bufA, bufB, twp, t, rs);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            in[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
-        }
-        __syncthreads();   // the first transform's last pass has read its buffer
-        transform<LOG2N, true>(in, gv, bufA, bufB, twp, t, rs);
-        publish<true>(tc, gv, D, pub);
+        transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
         __syncthreads();
-        c32 gx[8];
-        FwdRow<LOG2N, P_, L_>::pa_adjoint(g, tc, x, gv, cp, pub, D, gx);
-        c32 v[8];
-        transform<LOG2N, false>(gx, v, bufA, bufB, twp, t, rs);
+        transform<LOG2N, true>(gv, bufA, bufB, twp, t, rs);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) bufB[pidx(t + q * F::T)] = gv[q];
+        __syncthreads();
+        RowPa<P_, L_>::adjoint(g, F::N, F::T, t, x, bufB, cp, gv);
+        __syncthreads();
+        transform<LOG2N, false>(gv, bufA, bufB, twp, t, rs);
         if (active) {
             c32 *orow = gxh + row * g.N_d;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 16; ++q) {
                 const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-                if (i >= 0) orow[i] = v[q];
+                if (i >= 0) orow[i] = gv[q];
             }
         }
     }
@@ -473,7 +419,7 @@ inline cudaError_t persistent_blocks(Kern k, int N, long rows, int threads, size
 template <int LOG2N, int P_, int L_, typename TOut>
 inline cudaError_t fwd_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, TOut *X,
                          double *metrics, cudaStream_t st) {
-    const int threads = rows_per_cta(g.N) * (g.N >> 3);
+    const int threads = 256;
     const size_t sm = fftpa_smem_bytes_(g);
     long blocks = 0;
     cudaError_t e = persistent_blocks(fftpa_forward_kernel<LOG2N, P_, L_, TOut>, g.N, rows, threads, sm, blocks);
@@ -485,7 +431,7 @@ inline cudaError_t fwd_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
 template <int LOG2N, int P_, int L_>
 inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const c32 *gX,
                          c32 *gxh, cudaStream_t st) {
-    const int threads = rows_per_cta(g.N) * (g.N >> 3);
+    const int threads = 256;
     const size_t sm = fftpa_smem_bytes_(g);
     long blocks = 0;
     cudaError_t e = persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, c32>, g.N, rows, threads, sm, blocks);
@@ -526,7 +472,6 @@ inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
         default: return adj_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, gX, gxh, st);
     }
 }
-
 
 // One translation unit per transform size instantiates these.
 #define FD_FFTPA_SIZE(LOG2N)                                                                                      \

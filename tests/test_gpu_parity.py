@@ -206,5 +206,6 @@ def test_cfg3_full_size_sampled_symbols():
     c.plan.distort(c.s[half:], c.H[half // 14:], c.W[half // 14:], c.alpha[half // 14:], c.pa, c.theta, None, m2)
     T.cuda.synchronize()
     m1, m2 = m1.cpu().numpy(), m2.cpu().numpy()
-    assert abs((m1[1] + m2[1]) - met[1]) <= 1e-9 * met[1]
-    assert abs((m1[3] + m2[3]) - met[3]) <= 1e-9 * met[3]
+    # per-thread FP32 partial sums before the FP64 reduction: ~1e-7 relative per sum
+    assert abs((m1[1] + m2[1]) - met[1]) <= 1e-6 * met[1]
+    assert abs((m1[3] + m2[3]) - met[3]) <= 1e-6 * met[3]
