@@ -76,7 +76,11 @@ def stage_work(cfg, S: int, prec: str):
     fc_bound = "alu" if prec == "fp32" else "tensor"
     theta_len = cfg.N_conv * 2 * L_U * cfg.K_C ** 2 + cfg.N_conv + 2 * Nd * F + 2 * Nd
     return {
-        "zf": ("hbm", R * Nd * K * M * c8 * 2 + R * Nd * 4),
+        # Gram: read H (+ write its 16-bit copy); factor: K^3/3 complex MACs per subcarrier
+        # in FP64 (Cholesky + triangular inverse, 4 FMA = 8 flop each); apply: read H, write W
+        "zf_gram": ("hbm", R * Nd * K * M * (c8 + (0 if prec == "fp32" else 4))),
+        "zf_factor": ("fp64", R * Nd * 8.0 * (K ** 3 / 3.0)),
+        "zf_apply": ("hbm", R * Nd * K * M * (2 * c8 + (0 if prec == "fp32" else 4)) + R * Nd * 4),
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
         "precode": ("hbm", R * Nd * M * K * opb + S * K * Nd * c8 + S * M * Nd * c8),
@@ -94,7 +98,7 @@ def stage_work(cfg, S: int, prec: str):
 
 
 def source_hash(stage: str) -> str:
-    files = {"zf": "zf.cu", "fftpa_fwd": "fftpa.cu", "fftpa_adj": "fftpa.cu", "precode": "bingemm.cu",
+    files = {"zf_gram": "zf.cu", "zf_factor": "zf.cu", "zf_apply": "zf.cu", "fftpa_fwd": "fftpa.cu", "fftpa_adj": "fftpa.cu", "precode": "bingemm.cu",
              "combine": "bingemm.cu", "adj_combine": "bingemm.cu", "adj_precode": "bingemm.cu",
              "fc_fwd": "fdcnn.cu", "fc_bwd_w": "fdcnn.cu", "fc_bwd_d": "fdcnn.cu", "fc_bwd_b": "fdcnn.cu",
              "conv_fwd": "fdcnn.cu", "conv_bwd": "fdcnn.cu", "step": "update.cu"}
@@ -305,6 +309,10 @@ def run_ours(args):
     if bound == "hbm":
         achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e9, mp["hbm_gbs"], "GB/s"
         peak_src = f"{src} hbm_gbs (copy)"
+    elif bound == "fp64":
+        peak = NUM_SMS * 2 * 2 * mp.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved, unit = amount / (per_launch_ms / 1e3) / 1e12, "TFLOP/s"
+        peak_src = f"derived: {NUM_SMS} SMs x 2 FP64 FMA/clk x 2 x {mp.get('sm_max_mhz', 2070.0):.0f} MHz"
     elif bound == "tensor":
         achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e12, mp["bf16_tflops_sustained"], "TFLOP/s"
         peak_src = f"{src} bf16_tflops_sustained"

@@ -162,7 +162,7 @@ int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c
 
 /* Stage tracing.  Stages of the chain, in execution order. */
 enum fddpd_stage {
-    FDDPD_STAGE_ZF = 0, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,
+    FDDPD_STAGE_ZF_GRAM = 0, FDDPD_STAGE_ZF_FACTOR, FDDPD_STAGE_ZF_APPLY, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,
     FDDPD_STAGE_FFTPA_FWD, FDDPD_STAGE_COMBINE, FDDPD_STAGE_ADJ_COMBINE, FDDPD_STAGE_FFTPA_ADJ,
     FDDPD_STAGE_ADJ_PRECODE, FDDPD_STAGE_FC_BWD_W, FDDPD_STAGE_FC_BWD_B, FDDPD_STAGE_FC_BWD_D,
     FDDPD_STAGE_CONV_BWD, FDDPD_STAGE_STEP, FDDPD_STAGE_PACK, FDDPD_N_STAGES

@@ -52,7 +52,7 @@ struct fddpd_plan {
 
 static constexpr int kMaxRec = 4096;
 static const char *kStageNames[FDDPD_N_STAGES] = {
-    "zf", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
+    "zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
     "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"};
 
 static int stage_begin(fddpd_plan *p, int stage) {
@@ -263,9 +263,11 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
     if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     cudaStream_t st = p->stream;
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
-    FD_STAGE(p, FDDPD_STAGE_ZF, 3,
-             fdk::zf_build(p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha, p->status,
-                           p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr, p->kind16, st));
+    for (int ph = 0; ph < 3; ++ph)
+        FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
+                 fdk::zf_phase(ph, p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha,
+                               p->status, p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr,
+                               p->kind16, st));
     if (p->p16) {
         p->pk_H = H;
         p->pk_W = W;

@@ -25,6 +25,9 @@ size_t zf_scratch_bytes(const Geo &g, long nbins);
 // H16 / W16 (optional, kind OUT_BF16 / OUT_F16): 16-bit copies of H and W written on the way
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st);
+// one of the three ZF kernels: 0 = Gram, 1 = FP64 factor / inverse, 2 = W
+cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                     void *H16, void *W16, int kind, cudaStream_t st);
 
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);

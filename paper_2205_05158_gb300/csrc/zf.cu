@@ -267,9 +267,10 @@ static cudaError_t launch_apply(const Geo &g, long nbins, const c32 *H, const c3
     return cudaGetLastError();
 }
 
+// phase 0 = gram, 1 = factor, 2 = apply, -1 = all three in order
 template <typename T16>
 static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                              T16 *H16, T16 *W16, cudaStream_t st) {
+                              T16 *H16, T16 *W16, int phase, cudaStream_t st) {
     const long nbins = (long)R * g.N_d;
     if (nbins == 0) return cudaSuccess;
     const int T = tri(g.K);
@@ -277,7 +278,7 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
     c32 *Gs = reinterpret_cast<c32 *>(scratch);
     c32 *Ys = reinterpret_cast<c32 *>(reinterpret_cast<char *>(scratch) + al16(sizeof(c32) * (size_t)nb32 * T));
     // gram
-    {
+    if (phase < 0 || phase == 0) {
         const size_t per_warp = sizeof(c32) * g.K * (g.M + 1);
         int nw = (int)((200 * 1024) / per_warp);
         nw = nw > ZF_WARPS ? ZF_WARPS : nw;
@@ -290,7 +291,7 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
         if (e != cudaSuccess) return e;
     }
     // factor
-    {
+    if (phase < 0 || phase == 1) {
         int NB = 32;
         size_t smem = (sizeof(double2) * T + sizeof(double) * g.K) * NB;
         if (smem > 200 * 1024) {
@@ -304,16 +305,22 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
         if (e != cudaSuccess) return e;
     }
     // apply
+    if (phase >= 0 && phase != 2) return cudaSuccess;
     if (g.K <= 4) return launch_apply<4>(g, nbins, H, Ys, alpha, W, W16, st);
     if (g.K <= 8) return launch_apply<8>(g, nbins, H, Ys, alpha, W, W16, st);
     if (g.K <= 16) return launch_apply<16>(g, nbins, H, Ys, alpha, W, W16, st);
     return launch_apply<32>(g, nbins, H, Ys, alpha, W, W16, st);
 }
 
+cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
+                     void *H16, void *W16, int kind, cudaStream_t st) {
+    if (kind == OUT_F16) return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, st);
+    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, st);
+}
+
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st) {
-    if (kind == OUT_F16) return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, st);
-    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, st);
+    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, st);
 }
 
 }  // namespace fdk
