@@ -77,9 +77,10 @@ def stage_work(cfg, S: int, prec: str):
     theta_len = cfg.N_conv * 2 * L_U * cfg.K_C ** 2 + cfg.N_conv + 2 * Nd * F + 2 * Nd
     return {
         # Gram: read H (+ write its 16-bit copy); factor: K^3/3 complex MACs per subcarrier
-        # in FP64 (Cholesky + triangular inverse, 4 FMA = 8 flop each); apply: read H, write W
+        # (Cholesky + triangular inverse, 4 FMA = 8 flop each), FP64 in FP32 plans and FP32
+        # in 16-bit plans; apply: read H, write W
         "zf_gram": ("hbm", R * Nd * K * M * (c8 + (0 if prec == "fp32" else 4))),
-        "zf_factor": ("fp64", R * Nd * 8.0 * (K ** 3 / 3.0)),
+        "zf_factor": ("fp64" if prec == "fp32" else "alu", R * Nd * 8.0 * (K ** 3 / 3.0)),
         "zf_apply": ("hbm", R * Nd * K * M * (2 * c8 + (0 if prec == "fp32" else 4)) + R * Nd * 4),
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
@@ -97,14 +98,26 @@ def stage_work(cfg, S: int, prec: str):
     }
 
 
-def source_hash(stage: str) -> str:
-    files = {"zf_gram": "zf.cu", "zf_factor": "zf.cu", "zf_apply": "zf.cu", "fftpa_fwd": "fftpa.cu", "fftpa_adj": "fftpa.cu", "precode": "bingemm.cu",
-             "combine": "bingemm.cu", "adj_combine": "bingemm.cu", "adj_precode": "bingemm.cu",
-             "fc_fwd": "fdcnn.cu", "fc_bwd_w": "fdcnn.cu", "fc_bwd_d": "fdcnn.cu", "fc_bwd_b": "fdcnn.cu",
-             "conv_fwd": "fdcnn.cu", "conv_bwd": "fdcnn.cu", "step": "update.cu"}
-    path = os.path.join(ROOT, "paper_2205_05158_gb300", "csrc", files.get(stage, "api.cu"))
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+def source_files(stage: str, prec: str):
+    """Sources of the kernel(s) a stage launches in a plan of precision `prec`."""
+    p16 = prec != "fp32"
+    bins = ("tcbin.cu", "tc_ptx.cuh") if p16 else ("bingemm.cu", "bingemm.cuh", "bingemm_f32.cu")
+    fc = ("tc_gemm.cu", "tc_ptx.cuh", "pack16.cu") if p16 else ("fdcnn.cu",)
+    files = {"zf_gram": ("zf.cu",), "zf_factor": ("zf.cu",), "zf_apply": ("zf.cu",),
+             "fftpa_fwd": ("fftpa.cu", "fftpa.cuh", "fftpa_n11.cu"),
+             "fftpa_adj": ("fftpa.cu", "fftpa.cuh", "fftpa_n11.cu"),
+             "precode": bins, "combine": bins, "adj_combine": bins, "adj_precode": bins,
+             "fc_fwd": fc, "fc_bwd_w": fc, "fc_bwd_d": fc, "fc_bwd_b": ("fdcnn.cu",),
+             "conv_fwd": ("fdcnn.cu",), "conv_bwd": ("fdcnn.cu",), "step": ("update.cu",)}
+    return files.get(stage, ("api.cu",))
+
+
+def source_hash(stage: str, prec: str) -> str:
+    h = hashlib.sha256()
+    for f in source_files(stage, prec):
+        with open(os.path.join(ROOT, "paper_2205_05158_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def measured_traffic(stage: str, prec: str):
@@ -114,7 +127,7 @@ def measured_traffic(stage: str, prec: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    h = source_hash(stage)
+    h = source_hash(stage, prec)
     for line in open(path):
         t = line.split()
         if len(t) >= 4 and not line.startswith("#") and t[0] == stage and t[1] == prec and t[2] == h:

@@ -108,6 +108,19 @@ size_t fddpd_workspace_bytes(const fddpd_plan *plan);
 /* Re-bind the plan to another stream. */
 int fddpd_set_stream(fddpd_plan *plan, void *stream);
 
+/* Plan options (no counterpart in the paper; they select among implementations of the
+ * same arithmetic).
+ *   FDDPD_OPT_TENSOR_CONTRACTIONS  1 (default): in 16-bit plans with M <= 128 and
+ *       K <= 16, the four per-subcarrier contractions (precode, combine and their
+ *       adjoints) run as tcgen05 MMAs with 16-bit B operands (the activations rounded
+ *       to the plan's 16-bit type), and the ZF matrix W = H^H (H H^H)^{-1} as tcgen05
+ *       MMAs on BF16 high / low splits of H and (H H^H)^{-1} (relative error near
+ *       2^-16); 0: CUDA-core kernels with FP32 activations and an FP32 W.
+ *       Ignored by FP32 plans.
+ * Returns FDDPD_ERR_ARG for an unknown option or value. */
+enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1 };
+int fddpd_set_option(fddpd_plan *plan, int option, int value);
+
 /* Eq. (6): zero-forcing precoder for R channel realisations (Sec. II-A).
  *   H     [R][N_d][K][M]  in : per-subcarrier channel of the data bins
  *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}

@@ -19,12 +19,13 @@ FDDPD_ERR_ARG, FDDPD_ERR_LAYOUT, FDDPD_ERR_SINGULAR = -1, -2, -3
 FDDPD_ERR_CUDA, FDDPD_ERR_TIMEOUT, FDDPD_ERR_UNSUPPORTED, FDDPD_ERR_NOMEM = -4, -5, -6, -7
 FDDPD_FP32, FDDPD_BF16, FDDPD_FP16 = 0, 1, 2
 FDDPD_GD, FDDPD_ADAM = 0, 1
+FDDPD_OPT_TENSOR_CONTRACTIONS = 1
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
-            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc"]
+            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -93,10 +94,11 @@ def load(build_if_missing: bool = True):
     L.fddpd_sync.argtypes = [P]
     L.fddpd_tc_gemm.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P]
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
+    L.fddpd_set_option.argtypes = [P, I, I]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
-              "fddpd_precode_noalloc"):
+              "fddpd_precode_noalloc", "fddpd_set_option"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -204,6 +206,11 @@ class Plan:
 
     def reset_optimizer(self):
         self._check(self._lib.fddpd_reset_optimizer(self._h))
+
+    def set_option(self, option: int, value: int):
+        """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
+        contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
+        self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
 
     def update_host(self, s, H, pa, theta, lr: float, iters: int = 1, optimizer: int = FDDPD_GD, metrics=None,
                     S: Optional[int] = None):

@@ -32,6 +32,7 @@ struct fddpd_plan {
     long ldF, ld2N, ldC;
     __nv_bfloat16 *act16, *actT16, *gd16, *gdT16, *fcw16, *fcwT16;
     int kind16;                    // OUT_BF16 or OUT_F16: storage of the H / W copies
+    bool tc_bin;                   // per-subcarrier contractions on the tensor cores
     void *H16, *W16;               // [R_max][N_d][K][M] and [R_max][N_d][M][K]
     const void *pk_H, *pk_W;       // the FP32 arrays the copies were made from
     int pk_R;
@@ -168,6 +169,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
                  o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int));
     const size_t o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N_d));
     p->p16 = d->precision != FDDPD_FP32;
+    p->tc_bin = true;
     auto r8 = [](long v) { return (v + 7) / 8 * 8; };
     p->ldF = r8(g.F);
     p->ld2N = r8(2L * g.N_d);
@@ -247,6 +249,15 @@ extern "C" int fddpd_set_stream(fddpd_plan *p, void *stream) {
     return FDDPD_OK;
 }
 
+extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (option == FDDPD_OPT_TENSOR_CONTRACTIONS && (value == 0 || value == 1)) {
+        p->tc_bin = value != 0;
+        return FDDPD_OK;
+    }
+    return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
+}
+
 extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {
     if (!p) return FDDPD_ERR_ARG;
     p->adam_t = 0;
@@ -267,7 +278,7 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
         FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
                  fdk::zf_phase(ph, p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha,
                                p->status, p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr,
-                               p->kind16, st));
+                               p->kind16, p->tc_bin, p->status + 1, st));
     if (p->p16) {
         p->pk_H = H;
         p->pk_W = W;
@@ -293,6 +304,7 @@ static int check_chain(fddpd_plan *p, int S, const void *s, const void *H, const
 struct BinOps {
     const void *H, *W;
     int kind;
+    const void *W_or_H(int mode) const { return (mode == fdk::PRECODE || mode == fdk::ADJ_PRECODE) ? W : H; }
 };
 static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps &o) {
     if (!p->p16) {
@@ -314,6 +326,27 @@ static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps
     o = BinOps{p->H16, p->W16, p->kind16};
     return FDDPD_OK;
 }
+
+// Per-subcarrier contractions: tensor cores in 16-bit plans where supported, else CUDA
+// cores.  b_scale multiplies the activations before their 16-bit rounding (and divides
+// the results): a power of two that lifts the loss gradients, O(1 / count), out of the
+// FP16 subnormal range.
+static bool use_tc_bin(const fddpd_plan *p) { return p->p16 && p->tc_bin && fdk::tc_bin_supported(p->g); }
+static cudaError_t expand_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const c32 *B,
+                             c32 *out, float b_scale) {
+    if (use_tc_bin(p)) return fdk::tc_bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, b_scale,
+                                                 p->status + 1, p->stream);
+    return fdk::bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, p->stream);
+}
+static cudaError_t reduce_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const c32 *B,
+                             c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale) {
+    if (use_tc_bin(p))
+        return fdk::tc_bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, s_ref, gy, metrics, inv_count,
+                                  b_scale, p->status + 1, p->stream);
+    return fdk::bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, s_ref, gy, metrics, inv_count,
+                           p->stream);
+}
+static float grad_scale(double inv_count) { return exp2f(rintf(log2f((float)(0.5 / inv_count)))); }
 
 // Forward chain; gy (loss gradient at y) is written when non-null.
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
@@ -337,10 +370,10 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
     }
-    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, fdk::bin_expand(g, fdk::PRECODE, S, ops.W, ops.kind, alpha, p->st, p->xh, st));
+    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1, fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
-             fdk::bin_reduce(g, fdk::COMBINE, S, ops.H, ops.kind, alpha, p->Xpa, y, s, gy, p->met, inv_count, st));
+             reduce_op(p, fdk::COMBINE, S, ops, alpha, p->Xpa, y, s, gy, p->met, inv_count, 1.0f));
     FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
     p->launches += 1;
     return FDDPD_OK;
@@ -356,12 +389,11 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     BinOps ops;
     rc = bin_operands(p, S, H, W, ops);
     if (rc) return rc;
-    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1,
-             fdk::bin_expand(g, fdk::ADJ_COMBINE, S, ops.H, ops.kind, alpha, p->gy, p->Xpa, st));
+    const float gsc = grad_scale(1.0 / ((double)cols * g.N_d));
+    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1, fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, st));
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
-             fdk::bin_reduce(g, fdk::ADJ_PRECODE, S, ops.W, ops.kind, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr,
-                             0.0, st));
+             reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);
     FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {

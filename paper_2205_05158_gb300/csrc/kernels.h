@@ -20,14 +20,21 @@ struct Geo {
     double P_T;
 };
 
-// zero-forcing precoder (Eq. 6): FP32 Gram, FP64 Cholesky + triangular inverse
+// zero-forcing precoder (Eq. 6): FP32 Gram, Cholesky + triangular inverse (FP64, or FP32
+// when kind is 16-bit), W = H^H G^{-1}
 size_t zf_scratch_bytes(const Geo &g, long nbins);
 // H16 / W16 (optional, kind OUT_BF16 / OUT_F16): 16-bit copies of H and W written on the way
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st);
-// one of the three ZF kernels: 0 = Gram, 1 = FP64 factor / inverse, 2 = W
+// one of the three ZF kernels: 0 = Gram, 1 = factor / inverse, 2 = W (-1: all three).
+// tc: W on the tensor cores when kind is 16-bit and M <= 128, K <= 16 (err: timeout word)
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, cudaStream_t st);
+                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st);
+// W = H^H Z (Z = G^{-1}, lower triangle in the factor's scratch layout) with BF16 hi / lo
+// operand splits on the tensor cores; W16 of the given 16-bit kind beside it
+cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,
+                        int kind, int *err, cudaStream_t st);
+bool tc_bin_supported(const Geo &g);
 
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
@@ -51,6 +58,12 @@ cudaError_t bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind,
                        c32 *out, cudaStream_t st);
 cudaError_t bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                        c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, cudaStream_t st);
+// tcgen05 versions for 16-bit H / W copies (M <= 128, K <= 16); err: sticky timeout word
+cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                          c32 *out, float b_scale, int *err, cudaStream_t st);
+cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                          c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale,
+                          int *err, cudaStream_t st);
 cudaError_t to_16bit(long n, const c32 *in, void *out, int kind, cudaStream_t st);
 
 // OFDM + PA rows

@@ -1,0 +1,545 @@
+// Per-subcarrier contractions of the downlink on the 5th-generation tensor cores, for
+// plans that keep H and W as 16-bit copies (BF16 or FP16 operands, FP32 accumulation in
+// tensor memory).  Same operations as the CUDA-core kernels of bingemm.cuh:
+//   expand (users -> antennas)   PRECODE      x = alpha_i W_i s~           (Eq. 1)
+//                                ADJ_COMBINE  g_x = H_i^H g_y / alpha_i
+//   reduce (antennas -> users)   COMBINE      y = H_i x / alpha_i and the loss terms (Eq. 5)
+//                                ADJ_PRECODE  g_s = alpha_i W_i^H g_x
+// i runs over data subcarriers; every realisation's symbols share its H_i and W_i.
+//
+// Complex products as real MMAs.  An A row holds complex entries a_j as interleaved
+// (re, im) pairs along k = 2j + c, which is how the 16-bit copies store them, so A needs
+// no arithmetic.  The B operand gets two real rows per symbol t, built from the FP32
+// activations b_j(t):
+//   plain      sum_j a_j b_j        row 2t = (br, -bi), row 2t+1 = (bi,  br)
+//   conjugate  sum_j conj(a_j) b_j  row 2t = (br,  bi), row 2t+1 = (bi, -br)
+// so that D[row][2t] and D[row][2t+1] are the real and imaginary parts of the result (in
+// the reduce, where the activations are the A operand, D[2t][row] and D[2t+1][row]).
+// Symbols go 16 at a time: N = 32 real columns per MMA.
+//
+// expand: an item is 8 consecutive subcarriers of one realisation.  A_i = [m][(u, c)]
+//   (antenna rows, 16 user slots = 32 k), two subcarriers side by side in each 128-byte
+//   row of a swizzled tile; MMA i (M = 128, N = 32, K = 2 x 16) accumulates into TMEM
+//   columns 32 i .. 32 i + 31, and the epilogue reads antenna m from lane m.
+// reduce: an item is 4 subcarriers, computed transposed (y^T = x^T H^T): A holds the real
+//   form of all 4 subcarriers' activations (rows (b, t, c'), 128), B their 4 x 16 user
+//   rows of H (or W^H), so one MMA (M = 128, N = 64) per K step covers the item and the
+//   diagonal blocks b = b' of its result are kept.  The discarded blocks cost tensor-core
+//   time, which this HBM-bound contraction has to spare.
+//
+// The threads write every operand tile (the 16-bit conversion and the real-form signs
+// are needed anyway) in the K-major, 128-byte-swizzled layout, make the writes visible
+// to the tensor core with fence.proxy.async, and one thread issues tcgen05.mma and
+// tcgen05.commit onto an mbarrier; every wait on it is bounded (about 2 s), after which
+// the error word is set, the CTA stops, and its tensor memory is freed.  Two CTAs share
+// an SM, so one builds operands while the other's MMAs and epilogue run.
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace fdk {
+namespace tcb {
+using namespace tc;
+
+constexpr int THREADS = 256;
+constexpr int TS = 16;            // symbols per MMA
+constexpr int EXB = 8, RDB = 4;   // subcarriers per item: expand, reduce
+
+// expand: A [4 pair tiles][128 rows][128 B], B [4 pair tiles][32 rows][128 B]
+constexpr int EX_A = 4 * 128 * 128, EX_B = 4 * 32 * 128;
+constexpr int EX_SMEM = EX_A + EX_B + 1024;
+// reduce: A (activations) [4 k-blocks][128 rows][128 B], B (H or W^H) [4 k-blocks][64
+// rows][128 B], then the staging of the results [16 t][16 u][4 subcarriers]
+constexpr int RD_A = 4 * 128 * 128, RD_B = 4 * 64 * 128, RD_Y = TS * 16 * RDB * 8;
+constexpr int RD_SMEM = RD_A + RD_B + RD_Y + 1024;
+
+template <typename T16> struct Pk;
+template <> struct Pk<cbf16> {
+    static constexpr int type = 1;
+    FD_D static uint32_t two(float lo, float hi) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+};
+template <> struct Pk<cf16> {
+    static constexpr int type = 0;
+    FD_D static uint32_t two(float lo, float hi) {
+        __half2 v = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+};
+
+template <typename T16, bool CONJ> FD_D void real_rows(float br, float bi, uint32_t &w0, uint32_t &w1) {
+    if (CONJ) {
+        w0 = Pk<T16>::two(br, bi);
+        w1 = Pk<T16>::two(bi, -br);
+    } else {
+        w0 = Pk<T16>::two(br, -bi);
+        w1 = Pk<T16>::two(bi, br);
+    }
+}
+
+FD_D void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+FD_D void st128(uint8_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+FD_D uint8_t *align1024(uint8_t *p) {
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// Setup shared by both kernels: the mbarrier and `cols` columns of tensor memory.
+FD_D uint32_t setup(uint64_t *bar, uint32_t *slot, uint32_t cols) {
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, cols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    return *slot;
+}
+
+// Waits for the MMAs of this round; false in every thread of the CTA if any timed out.
+FD_D bool wait_mma(uint64_t *bar, uint32_t &phase, int *err) {
+    const bool ok = mbar_wait(bar, phase, err);
+    phase ^= 1u;
+    const bool all = __syncthreads_and(ok) != 0;
+    fence_after();
+    return all;
+}
+
+FD_D void teardown(uint64_t *bar, uint32_t phase, bool alive, uint32_t tmem, uint32_t cols, int *err) {
+    // after a timeout, give the outstanding commit one more bounded wait before the
+    // tensor memory it targets is released
+    if (!alive && threadIdx.x == 0) mbar_wait(bar, phase ^ 1u, err);
+    fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        fence_after();
+        tmem_dealloc(tmem, cols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// expand.  AT = false: A = W16 [bin][m][u] (rows m, PRECODE); AT = true: A = H16
+// [bin][u][m] read transposed (ADJ_COMBINE).  out[t][m][i] = scale_i D / b_scale.
+template <typename T16, bool CONJ, bool AT>
+__global__ void __launch_bounds__(THREADS, 2)
+    expand_kernel(Geo g, int S, const uint32_t *__restrict__ A, const float *__restrict__ alpha,
+                  const c32 *__restrict__ B, c32 *__restrict__ out, int inv_alpha, float b_scale, int vec_ok,
+                  int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sA = align1024(smem_raw);
+    uint8_t *sB = sA + EX_A;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int M = g.M, K = g.K, Nd = g.N_d;
+    const int ngroups = (Nd + EXB - 1) / EXB;
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long nitems = (long)R * ngroups;
+    const uint32_t tmem = setup(&bar, &tmem_slot, 256);
+    const uint32_t idesc = instr_desc(Pk<T16>::type, 128, 32);
+    const int nks = K > 8 ? 2 : 1;
+    uint32_t phase = 0;
+    bool alive = true;
+
+    for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
+        const int r = (int)(item / ngroups), i0 = (int)(item % ngroups) * EXB;
+        const long t0 = (long)r * g.S_per_real;
+        const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
+        const long bin0 = (long)r * Nd + i0;
+        const int nb = min(EXB, Nd - i0);
+
+        // A: chunk (tile p, row m, 16-byte chunk ch) = users 4 (ch & 3) .. + 3 of
+        // subcarrier 2p + (ch >> 2) at antenna m, copied with cp.async (zero outside)
+        if (!AT) {
+            if (K == 16) {
+                for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
+                    const int ch = c & 7, m = (c >> 3) & 127, b = 2 * (c >> 10) + (ch >> 2);
+                    const bool ok = b < nb && m < M;
+                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m) * 16 + 4 * (ch & 3) : A;
+                    cp_async16(sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8), src, ok);
+                }
+            } else {
+                for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
+                    const int ch = c & 7, m = (c >> 3) & 127, b = 2 * (c >> 10) + (ch >> 2);
+                    const int u0 = 4 * (ch & 3);
+                    uint8_t *dst = sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8);
+                    const bool ok = b < nb && m < M;
+                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m) * K : A;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cp_async4(dst + 4 * j, ok && u0 + j < K ? src + u0 + j : A, ok && u0 + j < K);
+                }
+            }
+        } else {
+            // transposed: the four users of a chunk are M entries apart; lanes run along m
+            for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
+                const int m = c & 127, ch = (c >> 7) & 7, b = 2 * (c >> 10) + (ch >> 2);
+                const int u0 = 4 * (ch & 3);
+                uint8_t *dst = sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8);
+                const bool ok = b < nb && m < M;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool okj = ok && u0 + j < K;
+                    cp_async4(dst + 4 * j, okj ? A + ((bin0 + b) * K + u0 + j) * M + m : A, okj);
+                }
+            }
+        }
+
+        for (int s0 = 0; s0 < nsym && alive; s0 += TS) {
+            const int ns = min(TS, nsym - s0);
+            // B: element (t, u, subcarrier b), b fastest; rows 2t and 2t + 1 of pair tile
+            // b >> 1, k = 32 (b & 1) + 2u
+            for (int e0 = tid; e0 < TS * 16 * EXB; e0 += 8 * THREADS) {
+                c32 v[8];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const int e = e0 + h * THREADS, b = e & 7, u = (e >> 3) & 15, t = e >> 7;
+                    v[h] = (t < ns && u < K && b < nb) ? B[((t0 + s0 + t) * K + u) * Nd + i0 + b]
+                                                       : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const int e = e0 + h * THREADS, b = e & 7, u = (e >> 3) & 15, t = e >> 7;
+                    uint32_t w0, w1;
+                    real_rows<T16, CONJ>(v[h].x * b_scale, v[h].y * b_scale, w0, w1);
+                    uint8_t *tile = sB + (b >> 1) * 4096;
+                    const int k = 32 * (b & 1) + 2 * u;
+                    st32(tile + sw128_offset(2 * t, k), w0);
+                    st32(tile + sw128_offset(2 * t + 1, k), w1);
+                }
+            }
+            cp_async_wait_all();
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                for (int b = 0; b < nb; ++b)
+                    for (int ks = 0; ks < nks; ++ks) {
+                        const uint32_t off = (b & 1) * 64 + ks * 32;
+                        mma_f16(tmem + 32 * b, smem_desc(sA + (b >> 1) * 16384 + off),
+                                smem_desc(sB + (b >> 1) * 4096 + off), idesc, ks ? 1u : 0u);
+                    }
+                mma_commit(&bar);
+            }
+            alive = wait_mma(&bar, phase, err);
+            if (alive) {
+                // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3
+                const int q = warp & 3, hb = 4 * (warp >> 2);
+                const int m = 32 * q + lane;
+                const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+                float sc[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int b = hb + j;
+                    const float al = b < nb ? alpha[bin0 + b] : 0.f;
+                    sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
+                }
+                const bool vec = vec_ok && hb + 4 <= nb;
+                for (int tb = 0; 4 * tb < ns; ++tb) {
+                    float v[4][8];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) tmem_ld8(trow + 32 * (hb + j) + 8 * tb, v[j]);
+                    if (m < M) {
+#pragma unroll
+                        for (int tt = 0; tt < 4; ++tt) {
+                            const int t = 4 * tb + tt;
+                            if (t >= ns) break;
+                            c32 *dst = out + ((t0 + s0 + t) * M + m) * Nd + i0 + hb;
+                            if (vec) {
+                                reinterpret_cast<float4 *>(dst)[0] =
+                                    make_float4(v[0][2 * tt] * sc[0], v[0][2 * tt + 1] * sc[0], v[1][2 * tt] * sc[1],
+                                                v[1][2 * tt + 1] * sc[1]);
+                                reinterpret_cast<float4 *>(dst)[1] =
+                                    make_float4(v[2][2 * tt] * sc[2], v[2][2 * tt + 1] * sc[2], v[3][2 * tt] * sc[3],
+                                                v[3][2 * tt + 1] * sc[3]);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 4; ++j)
+                                    if (hb + j < nb) dst[j] = make_float2(v[j][2 * tt] * sc[j], v[j][2 * tt + 1] * sc[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            fence_before();
+            __syncthreads();
+        }
+    }
+    teardown(&bar, phase, alive, tmem, 256, err);
+}
+
+// ---------------------------------------------------------------------------
+// reduce, transposed: y_i^T[t][u] = sum_m x_i^T[t][m] H_i^T[m][u].  A = the real form of
+// the activations of 4 subcarriers, rows (b, t, c') = 32 b + 2 t + c' over k = (m, c);
+// B = the 16 user rows of all 4 subcarriers, (b', u) = 16 b' + u over k = (m, c), as the
+// 16-bit copies store them (AT = false: H16 [bin][u][m], COMBINE) or read transposed
+// (AT = true: W16 [bin][m][u], ADJ_PRECODE).  One MMA per K step (M = 128, N = 64) gives
+// every cross product of the 4 subcarriers; the diagonal blocks b = b' are kept: warp b
+// reads TMEM lanes 32 b .. (its subcarrier's symbols) at columns 16 b .. 16 b + 15.
+template <typename T16, bool CONJ, bool AT, bool COMB>
+__global__ void __launch_bounds__(THREADS, 2)
+    reduce_kernel(Geo g, int S, const uint32_t *__restrict__ Wt, const float *__restrict__ alpha,
+                  const c32 *__restrict__ X, c32 *__restrict__ out, const c32 *__restrict__ s_ref,
+                  c32 *__restrict__ gy, double *metrics, double inv_count, int inv_alpha, float b_scale, int vec_ok,
+                  int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sA = align1024(smem_raw);          // activations [4 k-blocks][128 rows][128 B]
+    uint8_t *sB = sA + RD_A;                    // H / W^H     [4 k-blocks][64 rows][128 B]
+    float *sY = reinterpret_cast<float *>(sB + RD_B);   // [t][u][b][re, im]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double red[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int M = g.M, K = g.K, Nd = g.N_d;
+    const int MP = (M + 7) & ~7;          // antennas padded to one K step (8 complex)
+    const int MC = MP / 4, nks = MP / 8;
+    const int ngroups = (Nd + RDB - 1) / RDB;
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long nitems = (long)R * ngroups;
+    const uint32_t tmem = setup(&bar, &tmem_slot, 64);
+    const uint32_t idesc = instr_desc(Pk<T16>::type, 128, 64);
+    const float gscale = (float)(2.0 * inv_count);
+    uint32_t phase = 0;
+    bool alive = true;
+    float err_acc = 0.f, sig_acc = 0.f;
+
+    for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
+        const int r = (int)(item / ngroups), i0 = (int)(item % ngroups) * RDB;
+        const long t0 = (long)r * g.S_per_real;
+        const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
+        const long bin0 = (long)r * Nd + i0;
+        const int nb = min(RDB, Nd - i0);
+
+        // B rows 16 b + u (u < K), k-block m / 32, copied with cp.async; antennas
+        // M .. MP - 1 are zero
+        if (!AT) {
+            const int n = RDB * K * MC;
+            for (int c = tid; c < n; c += THREADS) {
+                const int mc = c % MC, bu = c / MC, u = bu % K, b = bu / K;
+                uint8_t *dst = sB + (mc >> 3) * 8192 + sw128_offset(16 * b + u, (mc & 7) * 8);
+                const uint32_t *src = Wt + ((bin0 + (b < nb ? b : 0)) * K + u) * M + 4 * mc;
+                if (!(M & 3)) {
+                    const bool ok = b < nb && 4 * mc < M;
+                    cp_async16(dst, ok ? src : Wt, ok);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool ok = b < nb && 4 * mc + j < M;
+                        cp_async4(dst + 4 * j, ok ? src + j : Wt, ok);
+                    }
+                }
+            }
+        } else {
+            // transposed: a 16-byte run of W16 (4 users at antenna m) feeds 4 rows
+            const int UQ = (K + 3) / 4, n = RDB * MP * UQ;
+            for (int c = tid; c < n; c += THREADS) {
+                const int uq = c % UQ, bm = c / UQ, m = bm % MP, b = bm / MP;
+                const bool ok = b < nb && m < M;
+                const uint32_t *src = ok ? Wt + ((bin0 + b) * M + m) * K + 4 * uq : Wt;
+                uint8_t *dst = sB + (m >> 5) * 8192;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int u = 4 * uq + j;
+                    if (u < K) cp_async4(dst + sw128_offset(16 * b + u, 2 * (m & 31)), ok ? src + j : Wt, ok);
+                }
+            }
+        }
+
+        for (int s0 = 0; s0 < nsym && alive; s0 += TS) {
+            const int ns = min(TS, nsym - s0);
+            const bool vec = vec_ok && nb == RDB;
+            // A: (t, m) pairs, m fastest, all 4 subcarriers (32 contiguous bytes) each;
+            // rows 32 b + 2t and 32 b + 2t + 1 of k-block m / 32
+            for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
+                c32 v[4][RDB];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                    const bool ok = e < TS * MP && t < ns && m < M;
+                    const c32 *src = X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0;
+                    if (ok && vec) {
+                        const float4 lo = reinterpret_cast<const float4 *>(src)[0];
+                        const float4 hi = reinterpret_cast<const float4 *>(src)[1];
+                        v[h][0] = make_float2(lo.x, lo.y);
+                        v[h][1] = make_float2(lo.z, lo.w);
+                        v[h][2] = make_float2(hi.x, hi.y);
+                        v[h][3] = make_float2(hi.z, hi.w);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < RDB; ++b) v[h][b] = (ok && b < nb) ? src[b] : make_float2(0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                    if (e >= TS * MP) break;
+                    uint8_t *tile = sA + (m >> 5) * 16384;
+                    const int k = 2 * (m & 31);
+#pragma unroll
+                    for (int b = 0; b < RDB; ++b) {
+                        uint32_t w0, w1;
+                        real_rows<T16, CONJ>(v[h][b].x * b_scale, v[h][b].y * b_scale, w0, w1);
+                        st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
+                        st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
+                    }
+                }
+            }
+            cp_async_wait_all();
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                fence_after();
+                for (int ks = 0; ks < nks; ++ks)
+                    mma_f16(tmem, smem_desc(sA + (ks >> 2) * 16384 + (ks & 3) * 32),
+                            smem_desc(sB + (ks >> 2) * 8192 + (ks & 3) * 32), idesc, ks ? 1u : 0u);
+                mma_commit(&bar);
+            }
+            alive = wait_mma(&bar, phase, err);
+            if (alive) {
+                if (warp < RDB) {
+                    // lane = (t, c') of subcarrier b = warp; columns 16 b + u
+                    const int b = warp, t = lane >> 1, c = lane & 1;
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
+                    if (b < nb && t < ns) {
+                        const float al = alpha[bin0 + b];
+                        const float sc = (inv_alpha ? 1.0f / al : al) / b_scale;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (u < K) sY[((t * 16 + u) * RDB + b) * 2 + c] = v[u] * sc;
+                    }
+                }
+                __syncthreads();
+                // (t, u, b), b fastest: 4 subcarriers = 32 contiguous bytes
+                const c32 *sYc = reinterpret_cast<const c32 *>(sY);
+                const int n = ns * K * RDB;
+                for (int e = tid; e < n; e += THREADS) {
+                    const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
+                    if (b >= nb) continue;
+                    const c32 v = sYc[(t * 16 + u) * RDB + b];
+                    const long idx = ((t0 + s0 + t) * K + u) * Nd + i0 + b;
+                    if (COMB) {
+                        const c32 sr = s_ref[idx];
+                        const c32 d = csub(v, sr);
+                        err_acc += cabs2(d);
+                        sig_acc += cabs2(sr);
+                        if (out) out[idx] = v;
+                        if (gy) gy[idx] = cscale(d, gscale);
+                    } else {
+                        out[idx] = v;
+                    }
+                }
+            }
+            fence_before();
+            __syncthreads();
+        }
+    }
+    teardown(&bar, phase, alive, tmem, 64, err);
+    if (COMB && metrics) {
+        const double es = block_sum((double)err_acc, red);
+        const double ss = block_sum((double)sig_acc, red);
+        if (tid == 0) {
+            atomicAdd(metrics + 1, es);
+            atomicAdd(metrics + 2, ss);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Two CTAs per SM only fit with the largest shared-memory carveout; the occupancy query
+// assumes the function's preferred carveout, so it is set first.
+template <class Kern> static cudaError_t grid_for(Kern k, int smem, long items, unsigned &blocks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
+    if (e != cudaSuccess) return e;
+    long b = (long)(per_sm > 0 ? per_sm : 1) * sm_count();
+    if (b > items) b = items;
+    blocks = (unsigned)(b > 0 ? b : 1);
+    return cudaSuccess;
+}
+
+static bool aligned16(const void *p) { return !(reinterpret_cast<uintptr_t>(p) & 15); }
+
+template <typename T16>
+static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, c32 *out,
+                            float b_scale, int *err, cudaStream_t st) {
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long items = (long)R * ((g.N_d + EXB - 1) / EXB);
+    if (items == 0) return cudaSuccess;
+    const int vec_ok = !(g.N_d & 1) && aligned16(out);
+    const uint32_t *a = static_cast<const uint32_t *>(A);
+    unsigned blocks = 0;
+    cudaError_t e;
+    if (mode == PRECODE) {
+        auto k = expand_kernel<T16, false, false>;
+        if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+        k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 0, b_scale, vec_ok, err);
+    } else {
+        auto k = expand_kernel<T16, true, true>;
+        if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+        k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 1, b_scale, vec_ok, err);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T16>
+static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, c32 *out,
+                            const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale, int *err,
+                            cudaStream_t st) {
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long items = (long)R * ((g.N_d + RDB - 1) / RDB);
+    if (items == 0) return cudaSuccess;
+    const int vec_ok = !(g.N_d & 1) && aligned16(B);
+    const uint32_t *a = static_cast<const uint32_t *>(A);
+    unsigned blocks = 0;
+    cudaError_t e;
+    if (mode == COMBINE) {
+        auto k = reduce_kernel<T16, false, false, true>;
+        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, b_scale, vec_ok,
+                                            err);
+    } else {
+        auto k = reduce_kernel<T16, true, true, false>;
+        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, b_scale,
+                                            vec_ok, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tcb
+
+bool tc_bin_supported(const Geo &g) { return g.M >= 1 && g.M <= 128 && g.K >= 1 && g.K <= 16; }
+
+cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                          c32 *out, float b_scale, int *err, cudaStream_t st) {
+    if (!tc_bin_supported(g) || (mode != PRECODE && mode != ADJ_COMBINE)) return cudaErrorInvalidValue;
+    if (a_kind == OUT_BF16) return tcb::expand_t<cbf16>(g, mode, S, A, alpha, B, out, b_scale, err, st);
+    if (a_kind == OUT_F16) return tcb::expand_t<cf16>(g, mode, S, A, alpha, B, out, b_scale, err, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
+                          c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale,
+                          int *err, cudaStream_t st) {
+    if (!tc_bin_supported(g) || (mode != COMBINE && mode != ADJ_PRECODE)) return cudaErrorInvalidValue;
+    if (a_kind == OUT_BF16)
+        return tcb::reduce_t<cbf16>(g, mode, S, A, alpha, B, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
+    if (a_kind == OUT_F16)
+        return tcb::reduce_t<cf16>(g, mode, S, A, alpha, B, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fdk

@@ -4,16 +4,20 @@
 //
 // Three kernels over all (realisation, data subcarrier) pairs ("bins"):
 //   gram   : one warp per bin, G = H H^H from FP32 products and FP32 sums; each lane a
-//            4 x 2 block of G (6 shared loads per 8 complex multiply-adds).  The lower
-//            triangle goes to a scratch array laid out [bin / 32][entry][bin % 32].
-//   factor : one bin per LANE, so every FP64 instruction is a full-warp instruction:
+//            4 x 4 block of the lower triangle over one group of antennas (8 shared
+//            loads per 16 complex multiply-adds).  The lower triangle goes to a scratch
+//            array laid out [bin / 32][entry][bin % 32].
+//   factor : one bin per LANE, so every instruction is a full-warp instruction:
 //            Cholesky G = L L^H (left-looking) and the in-place triangular inverse
-//            Y = L^{-1} in FP64; tr(G^{-1}) = ||Y||_F^2 in FP64.  1/sqrt(d) starts from
-//            the FP32 rsqrtf and takes two Newton-Raphson steps y <- y (3 - d y^2) / 2
-//            in FP64.  Y (FP32) and alpha go out; a pivot <= 1e-9 of its Gram diagonal
-//            marks the bin singular (alpha = 0, W = 0, status bit 0).
+//            Y = L^{-1}; tr(G^{-1}) = ||Y||_F^2.  FP64 for FP32 plans (1/sqrt(d) from
+//            the FP32 rsqrtf and two Newton-Raphson steps y <- y (3 - d y^2) / 2 in
+//            FP64), FP32 for 16-bit plans (one Newton step).  Y (FP32) and alpha go out;
+//            a pivot <= 1e-9 (FP64) or 1e-5 (FP32) of its Gram diagonal marks the bin
+//            singular (alpha = 0, W = 0, status bit 0).
 //   apply  : one warp per bin, W^H = Y^H (Y H) in FP32 (one antenna per lane), staged
 //            through shared memory for coalesced stores.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -30,145 +34,260 @@ size_t zf_scratch_bytes(const Geo &g, long nbins) {
     return 2 * al16(sizeof(c32) * (size_t)nb32 * tri(g.K)) + 256;
 }
 
-FD_D void load_h(const c32 *__restrict__ Hb, c32 *sH, int K, int M, int ld, bool vec4, int lane) {
-    if (vec4) {
-        const float4 *Hb4 = reinterpret_cast<const float4 *>(Hb);
-        for (int e = lane; e < K * M / 2; e += 32) {
-            const float4 v = Hb4[e];
-            const int idx = 2 * e, u = idx / M, m = idx % M;
-            sH[u * ld + m] = make_float2(v.x, v.y);
-            sH[u * ld + m + 1] = make_float2(v.z, v.w);
-        }
-    } else {
-        for (int e = lane; e < K * M; e += 32) sH[(e / M) * ld + e % M] = Hb[e];
-    }
+// ---------------------------------------------------------------------------
+// Gram G = H H^H, one warp per subcarrier.  The lower triangle is tiled into 4 x 4 blocks
+// (10 for K = 16) and the antennas of each 32-antenna chunk into ng groups, one (block,
+// group) task per lane (30 of 32 lanes for K = 16): per antenna a lane loads 4 + 4
+// entries for 16 complex multiply-adds.  Partial sums of the groups meet in shared memory
+// at the end.  A warp holds one chunk ([K][33] complex, 4.2 KB for K = 16), so many warps
+// fit on an SM and hide each other's loads.
+constexpr int GR_CHUNK = 32, GR_LD = GR_CHUNK + 1;
+
+FD_HD int gram_tasks(int K, int &nbt, int &ng) {
+    const int nblk = (K + 3) / 4;
+    nbt = nblk * (nblk + 1) / 2;
+    ng = 32 / nbt;
+    if (ng < 1) ng = 1;
+    if (ng > GR_CHUNK) ng = GR_CHUNK;
+    return nbt * ng;
+}
+size_t gram_warp_bytes(int K) {
+    int nbt, ng;
+    const int tasks = gram_tasks(K, nbt, ng);
+    const size_t chunk = sizeof(c32) * K * GR_LD, red = sizeof(c32) * 16 * tasks;
+    return al16(chunk > red ? chunk : red);
 }
 
-// ---------------------------------------------------------------------------
-template <typename T16>
-__global__ void __launch_bounds__(32 * ZF_WARPS) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
-                                                                c32 *__restrict__ Gs, T16 *__restrict__ H16) {
+template <typename T16, int NT>   // NT: tasks per lane (2 when K > 28)
+__global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
+                                                                c32 *__restrict__ Gs, T16 *__restrict__ H16,
+                                                                int warp_bytes) {
     extern __shared__ __align__(16) unsigned char sm[];
-    const int K = g.K, M = g.M, ld = M + 1, T = tri(K);
+    const int K = g.K, M = g.M, T = tri(K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    c32 *sH = reinterpret_cast<c32 *>(sm) + (size_t)warp * K * ld;
-    const bool vec4 = !(M & 1) && !(reinterpret_cast<uintptr_t>(H) & 15);
-    const int nib = (K + 3) / 4, njb = (K + 1) / 2;
+    c32 *sH = reinterpret_cast<c32 *>(sm + (size_t)warp * warp_bytes);
+    int nbt, ng;
+    const int tasks = gram_tasks(K, nbt, ng);
+    // this lane's tasks: task = group * nbt + block
+    int bi[NT], bj[NT], glo[NT], ghi[NT], ntask = 0;
+    for (int t = lane; t < tasks && ntask < NT; t += 32, ++ntask) {
+        int blk = t % nbt, r = 0;
+        while (blk > r) { blk -= r + 1; ++r; }
+        bi[ntask] = r;
+        bj[ntask] = blk;
+        const int grp = t / nbt;
+        glo[ntask] = grp * GR_CHUNK / ng;
+        ghi[ntask] = (grp + 1) * GR_CHUNK / ng;
+    }
     for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
-        load_h(H + b * K * M, sH, K, M, ld, vec4, lane);
-        __syncwarp();
-        if (H16)
-            for (int e = lane; e < K * M; e += 32) H16[b * K * M + e] = Operand<T16>::from(sH[(e / M) * ld + e % M]);
-        for (int blk = lane; blk < nib * njb; blk += 32) {
-            const int i0 = (blk / njb) * 4, j0 = (blk % njb) * 2;
-            if (j0 > i0 + 3) continue;   // block entirely above the diagonal
-            const int ni = min(4, K - i0), nj = min(2, K - j0);
-            c32 acc[4][2];
+        const c32 *Hb = H + b * K * M;
+        c32 acc[NT][4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
-            for (int m = 0; m < M; ++m) {
-                c32 hi[4], hj[2];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) hi[a] = a < ni ? sH[(i0 + a) * ld + m] : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int c = 0; c < 2; ++c) hj[c] = c < nj ? cconj(sH[(j0 + c) * ld + m]) : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) acc[a][c] = cfma(hi[a], hj[c], acc[a][c]);
-            }
+        for (int q = 0; q < NT; ++q)
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int i = i0 + a, j = j0 + c;
-                    if (a < ni && c < nj && j <= i) Gs[soa(b, tri(i) + j, T)] = acc[a][c];
+                for (int c = 0; c < 4; ++c) acc[q][a][c] = make_float2(0.f, 0.f);
+        for (int m0 = 0; m0 < M; m0 += GR_CHUNK) {
+            const int m = m0 + lane;
+            // chunk of 32 antennas, 8 rows of loads in flight
+            for (int u0 = 0; u0 < K; u0 += 8) {
+                c32 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = (u0 + j < K && m < M) ? Hb[(long)(u0 + j) * M + m] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (u0 + j < K) {
+                        sH[(u0 + j) * GR_LD + lane] = v[j];
+                        if (H16 && m < M) H16[(b * K + u0 + j) * M + m] = Operand<T16>::from(v[j]);
+                    }
                 }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                if (q >= ntask) break;
+                const int ri = 4 * bi[q], rj = 4 * bj[q];
+                for (int mm = glo[q]; mm < ghi[q]; ++mm) {
+                    c32 hi[4], hj[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        hi[a] = ri + a < K ? sH[(ri + a) * GR_LD + mm] : make_float2(0.f, 0.f);
+                        hj[a] = rj + a < K ? cconj(sH[(rj + a) * GR_LD + mm]) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[q][a][c] = cfma(hi[a], hj[c], acc[q][a][c]);
+                }
+            }
+            __syncwarp();
+        }
+        // sum the antenna groups of each block: partials [task][16]
+        c32 *red = sH;
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            if (q >= ntask) break;
+            const int t = lane + 32 * q;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) red[t * 16 + a * 4 + c] = acc[q][a][c];
+        }
+        __syncwarp();
+        for (int idx = lane; idx < nbt * 16; idx += 32) {
+            int blk = idx >> 4, r = 0;
+            while (blk > r) { blk -= r + 1; ++r; }
+            const int i = 4 * r + ((idx >> 2) & 3), j = 4 * blk + (idx & 3);
+            if (i < K && j <= i) {
+                c32 sum = make_float2(0.f, 0.f);
+                for (int grp = 0; grp < ng; ++grp) {
+                    const c32 v = red[(grp * nbt + (idx >> 4)) * 16 + (idx & 15)];
+                    sum.x += v.x;
+                    sum.y += v.y;
+                }
+                Gs[soa(b, tri(i) + j, T)] = sum;
+            }
         }
         __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------------------
-FD_D double rsqrt_f64(double d) {
-    double y = (double)rsqrtf((float)d);
+// Scalar type of the factor: FP64 for FP32 plans; FP32 for 16-bit plans, whose W is
+// rounded to 16 bits afterwards (the FP32 factor's relative error, about the Gram
+// condition number times 2^-24, stays far below that rounding).
+template <typename Real> struct Fac;
+template <> struct Fac<double> {
+    using C = double2;
+    static constexpr double kPivot = 1e-9;   // singular below this fraction of the Gram diagonal
+    FD_D static double rsqrt(double d) {     // FP32 estimate, two Newton-Raphson steps in FP64
+        double y = (double)rsqrtf((float)d);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) y = y * (1.5 - 0.5 * d * y * y);
-    return y;
-}
+        for (int it = 0; it < 2; ++it) y = y * (1.5 - 0.5 * d * y * y);
+        return y;
+    }
+};
+template <> struct Fac<float> {
+    using C = float2;
+    static constexpr float kPivot = 1e-5f;   // a pivot this small is lost in FP32 rounding
+    FD_D static float rsqrt(float d) {
+        const float y = rsqrtf(d);
+        return y * (1.5f - 0.5f * d * y * y);
+    }
+};
 
+template <typename Real>
 __global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const c32 *__restrict__ Gs,
-                                                       c32 *__restrict__ Ys, float *__restrict__ alpha, int *status) {
+                                                       c32 *__restrict__ Ys, float *__restrict__ alpha, int *status,
+                                                       int emit_z) {
+    using F = Fac<Real>;
+    using C = typename F::C;
     extern __shared__ __align__(16) unsigned char sm[];
     const int K = g.K, T = tri(K);
     const int lane = threadIdx.x, NB = blockDim.x;          // NB bins per CTA, one per thread
-    double2 *A = reinterpret_cast<double2 *>(sm);          // [T][NB]: lower triangle, becomes L, then Y
-    double *inv = reinterpret_cast<double *>(A + (size_t)T * NB);   // [K][NB]
+    C *A = reinterpret_cast<C *>(sm);                       // [T][NB]: lower triangle, becomes L, then Y
+    Real *inv = reinterpret_cast<Real *>(A + (size_t)T * NB);   // [K][NB]
     const long b = (long)blockIdx.x * NB + lane;
     const bool live = b < nbins;
     const long bb = live ? b : 0;
     for (int e = 0; e < T; ++e) {
         const c32 v = Gs[soa(bb, e, T)];
-        A[e * NB + lane] = make_double2(v.x, v.y);
+        A[e * NB + lane] = C{(Real)v.x, (Real)v.y};
     }
     bool bad = false;
     // Cholesky, left-looking: column j from the columns left of it
     for (int j = 0; j < K; ++j) {
         const int dj = tri(j) + j;
-        double d = A[dj * NB + lane].x;
-        const double g0 = d;
+        Real d = A[dj * NB + lane].x;
+        const Real g0 = d;
         for (int k = 0; k < j; ++k) {
-            const double2 l = A[(tri(j) + k) * NB + lane];
+            const C l = A[(tri(j) + k) * NB + lane];
             d = fma(-l.x, l.x, d);
             d = fma(-l.y, l.y, d);
         }
-        const bool ok = d > 1e-9 * g0;
+        const bool ok = d > F::kPivot * g0;
         bad |= !ok;
-        const double r = ok ? rsqrt_f64(d) : 1.0;
-        A[dj * NB + lane] = make_double2(ok ? d * r : 1.0, 0.0);
+        const Real r = ok ? F::rsqrt(d) : Real(1);
+        A[dj * NB + lane] = C{ok ? d * r : Real(1), Real(0)};
         inv[j * NB + lane] = r;
         for (int i = j + 1; i < K; ++i) {
-            double2 s = A[(tri(i) + j) * NB + lane];
+            C s = A[(tri(i) + j) * NB + lane];
             for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
-                const double2 a = A[(tri(i) + k) * NB + lane], c = A[(tri(j) + k) * NB + lane];
+                const C a = A[(tri(i) + k) * NB + lane], c = A[(tri(j) + k) * NB + lane];
                 s.x = fma(-a.x, c.x, s.x);
                 s.x = fma(-a.y, c.y, s.x);
                 s.y = fma(-a.y, c.x, s.y);
                 s.y = fma(a.x, c.y, s.y);
             }
-            A[(tri(i) + j) * NB + lane] = make_double2(s.x * r, s.y * r);
+            A[(tri(i) + j) * NB + lane] = C{s.x * r, s.y * r};
         }
     }
     // in-place inverse: for j = K-1..0, Y[j][j] = 1/L[j][j], and for i = K-1..j+1
     // Y[i][j] = -(1/L[j][j]) sum_{k=j+1}^{i} Y[i][k] L[k][j]  (L[k][j], k <= i, not yet overwritten)
-    double tr = 0.0;
+    Real tr = 0;
     for (int j = K - 1; j >= 0; --j) {
-        const double r = inv[j * NB + lane];
+        const Real r = inv[j * NB + lane];
         for (int i = K - 1; i > j; --i) {
-            double2 s = make_double2(0.0, 0.0);
+            C s = C{Real(0), Real(0)};
             for (int k = j + 1; k <= i; ++k) {
-                const double2 y = A[(tri(i) + k) * NB + lane], l = A[(tri(k) + j) * NB + lane];
+                const C y = A[(tri(i) + k) * NB + lane], l = A[(tri(k) + j) * NB + lane];
                 s.x = fma(y.x, l.x, s.x);
                 s.x = fma(-y.y, l.y, s.x);
                 s.y = fma(y.x, l.y, s.y);
                 s.y = fma(y.y, l.x, s.y);
             }
-            const double2 v = make_double2(-s.x * r, -s.y * r);
+            const C v = C{-s.x * r, -s.y * r};
             A[(tri(i) + j) * NB + lane] = v;
             tr = fma(v.x, v.x, tr);
             tr = fma(v.y, v.y, tr);
         }
-        A[(tri(j) + j) * NB + lane] = make_double2(r, 0.0);
+        A[(tri(j) + j) * NB + lane] = C{r, Real(0)};
         tr = fma(r, r, tr);
     }
     if (live) {
-        for (int e = 0; e < T; ++e) {
-            const double2 v = A[e * NB + lane];
-            Ys[soa(b, e, T)] = make_float2((float)v.x, (float)v.y);
+        if (emit_z) {
+            // Z = Y^H Y = G^{-1}, lower triangle: Z[i][u] = sum_{k >= i} conj(Y[k][i]) Y[k][u]
+            for (int i = 0; i < K; ++i)
+                for (int u = 0; u <= i; ++u) {
+                    C z = C{Real(0), Real(0)};
+                    for (int k = i; k < K; ++k) {
+                        const C yi = A[(tri(k) + i) * NB + lane], yu = A[(tri(k) + u) * NB + lane];
+                        z.x = fma(yi.x, yu.x, z.x);
+                        z.x = fma(yi.y, yu.y, z.x);
+                        z.y = fma(yi.x, yu.y, z.y);
+                        z.y = fma(-yi.y, yu.x, z.y);
+                    }
+                    Ys[soa(b, tri(i) + u, T)] = make_float2((float)z.x, (float)z.y);
+                }
+        } else {
+            for (int e = 0; e < T; ++e) {
+                const C v = A[e * NB + lane];
+                Ys[soa(b, e, T)] = make_float2((float)v.x, (float)v.y);
+            }
         }
-        alpha[b] = bad ? 0.0f : (float)sqrt(g.P_T / tr);
+        alpha[b] = bad ? 0.0f : (float)sqrt(g.P_T / (double)tr);
     }
     if (live && bad) atomicOr(status, 1);
+}
+
+template <typename Real>
+static cudaError_t launch_factor(const Geo &g, long nbins, const c32 *Gs, c32 *Ys, float *alpha, int *status,
+                                 int emit_z, cudaStream_t st) {
+    using C = typename Fac<Real>::C;
+    const int T = tri(g.K);
+    int NB = 32;
+    size_t smem = (sizeof(C) * T + sizeof(Real) * g.K) * NB;
+    if (smem > 200 * 1024) {
+        NB = 16;
+        smem = (sizeof(C) * T + sizeof(Real) * g.K) * NB;
+    }
+    cudaError_t e = cudaFuncSetAttribute(zf_factor_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    zf_factor_kernel<Real><<<(unsigned)((nbins + NB - 1) / NB), NB, smem, st>>>(g, nbins, Gs, Ys, alpha, status,
+                                                                                emit_z);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -270,7 +389,8 @@ static cudaError_t launch_apply(const Geo &g, long nbins, const c32 *H, const c3
 // phase 0 = gram, 1 = factor, 2 = apply, -1 = all three in order
 template <typename T16>
 static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                              T16 *H16, T16 *W16, int phase, cudaStream_t st) {
+                              T16 *H16, T16 *W16, int phase, bool fp64_factor, bool tc_apply, int *err,
+                              cudaStream_t st) {
     const long nbins = (long)R * g.N_d;
     if (nbins == 0) return cudaSuccess;
     const int T = tri(g.K);
@@ -279,33 +399,33 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
     c32 *Ys = reinterpret_cast<c32 *>(reinterpret_cast<char *>(scratch) + al16(sizeof(c32) * (size_t)nb32 * T));
     // gram
     if (phase < 0 || phase == 0) {
-        const size_t per_warp = sizeof(c32) * g.K * (g.M + 1);
-        int nw = (int)((200 * 1024) / per_warp);
-        nw = nw > ZF_WARPS ? ZF_WARPS : nw;
-        if (nw < 1) return cudaErrorInvalidConfiguration;
+        const int per_warp = (int)gram_warp_bytes(g.K);
+        const size_t smem = (size_t)ZF_WARPS * per_warp;
         long blocks = 0;
-        cudaError_t e = persistent_launch_dims(zf_gram_kernel<T16>, 32 * nw, nw * per_warp, nbins, nw, blocks);
-        if (e != cudaSuccess) return e;
-        zf_gram_kernel<T16><<<(unsigned)blocks, 32 * nw, nw * per_warp, st>>>(g, nbins, H, Gs, H16);
+        cudaError_t e;
+        if (g.K <= 28) {
+            e = persistent_launch_dims(zf_gram_kernel<T16, 1>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
+            if (e != cudaSuccess) return e;
+            zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_warp);
+        } else {
+            e = persistent_launch_dims(zf_gram_kernel<T16, 2>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
+            if (e != cudaSuccess) return e;
+            zf_gram_kernel<T16, 2><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_warp);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     // factor
     if (phase < 0 || phase == 1) {
-        int NB = 32;
-        size_t smem = (sizeof(double2) * T + sizeof(double) * g.K) * NB;
-        if (smem > 200 * 1024) {
-            NB = 16;
-            smem = (sizeof(double2) * T + sizeof(double) * g.K) * NB;
-        }
-        cudaError_t e = cudaFuncSetAttribute(zf_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        zf_factor_kernel<<<(unsigned)((nbins + NB - 1) / NB), NB, smem, st>>>(g, nbins, Gs, Ys, alpha, status);
-        e = cudaGetLastError();
+        cudaError_t e = fp64_factor ? launch_factor<double>(g, nbins, Gs, Ys, alpha, status, tc_apply, st)
+                                    : launch_factor<float>(g, nbins, Gs, Ys, alpha, status, tc_apply, st);
         if (e != cudaSuccess) return e;
     }
     // apply
     if (phase >= 0 && phase != 2) return cudaSuccess;
+    if (tc_apply)
+        return zf_apply_tc(g, nbins, H, Ys, alpha, W, W16, std::is_same<T16, cbf16>::value ? OUT_BF16 : OUT_F16, err,
+                           st);
     if (g.K <= 4) return launch_apply<4>(g, nbins, H, Ys, alpha, W, W16, st);
     if (g.K <= 8) return launch_apply<8>(g, nbins, H, Ys, alpha, W, W16, st);
     if (g.K <= 16) return launch_apply<16>(g, nbins, H, Ys, alpha, W, W16, st);
@@ -313,14 +433,19 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
 }
 
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, cudaStream_t st) {
-    if (kind == OUT_F16) return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, st);
-    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, st);
+                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st) {
+    // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128
+    const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_bin_supported(g);
+    if (kind == OUT_F16)
+        return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, false, tc_apply, err,
+                          st);
+    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, kind == OUT_F32,
+                      tc_apply, err, st);
 }
 
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st) {
-    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, st);
+    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, false, nullptr, st);
 }
 
 }  // namespace fdk

@@ -38,3 +38,28 @@ def test_mixed_backward(prec):
     go, meto = oracle.backward(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
     assert rel_l2(g, go) <= 2e-2, rel_l2(g, go)
     assert abs(met[0] - meto[0]) <= 1e-2 * meto[0]
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("cfg", [small_cfg(), synth.CONFIGS["cfg3"].with_(S=28)], ids=["ragged", "cfg3_28"])
+def test_mixed_zf_fp32_factor(cfg, prec):
+    """16-bit plans factor the Gram matrix in FP32: W and alpha (Eq. 6) still agree with
+    the FP64 oracle far inside the 16-bit rounding that W undergoes afterwards."""
+    c = Case(cfg, S=cfg.S, precision=prec)
+    W, al = c.gpu_zf()
+    Wo, alo = c.oracle_zf()
+    Wg, alg = W.cpu().numpy().astype(np.complex128), al.cpu().numpy().astype(np.float64)
+    assert np.abs(Wg - Wo).max() <= 1e-4 * np.abs(Wo).max()
+    assert np.abs(alg - alo).max() <= 1e-4 * alo.max()
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+def test_mixed_zf_singular_flagged(prec):
+    import paper_2205_05158_gb300 as fd
+    from gpu_common import dev
+    c = Case(synth.CONFIGS["cfg1"], precision=prec)
+    H = c.w.H.copy()
+    H[0, 5, 1] = H[0, 5, 0]          # two identical users on one subcarrier
+    with pytest.raises(fd.FddpdError) as e:
+        c.plan.precode(dev(H), c.W, c.alpha)
+    assert e.value.code == fd.FDDPD_ERR_SINGULAR

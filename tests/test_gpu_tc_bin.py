@@ -1,0 +1,102 @@
+"""tcgen05 per-subcarrier contractions (precode, combine and their adjoints) of 16-bit
+plans against the FP64 oracle and against the CUDA-core kernels with FP32 activations.
+
+The tensor-core path also rounds the activations (s~, x, g_y, g_x) to the plan's 16-bit
+type, which adds about 2^-9 relative error per BF16 operand: NMSE of y within 1e-4 of
+the oracle, EVM within 0.1 dB, gradients within 2e-2 relative L2, as for the other
+16-bit results.  ZF comes from the oracle so that only the contractions differ.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import Case, nmse, rel_l2, small_cfg
+
+pytestmark = pytest.mark.gpu
+
+CFGS = [
+    ("ragged", small_cfg()),                                           # M 40, K 3, realisations of 3
+    ("pad", small_cfg(M=100, K=13, S=45, S_per_real=20)),               # M % 8 = 4, K % 4 = 1, 2 symbol chunks
+    ("full", small_cfg(M=128, K=16, S=33, S_per_real=14)),             # full tiles, ragged subcarrier groups
+    ("cfg3_140", synth.CONFIGS["cfg3"].with_(S=140)),                   # several items per CTA
+]
+
+
+def _opt(c, on):
+    import paper_2205_05158_gb300 as fd
+    c.plan.set_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS, 1 if on else 0)
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg", CFGS, ids=[n for n, _ in CFGS])
+def test_tc_forward(name, cfg, prec):
+    c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=prec)
+    c.use_oracle_zf_on_gpu()
+    _opt(c, True)
+    y_tc, met_tc = c.gpu_distort()
+    _opt(c, False)
+    y_cc, met_cc = c.gpu_distort()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert np.isfinite(y_tc).all()
+    assert nmse(y_tc, yo) <= 1e-4, nmse(y_tc, yo)
+    assert nmse(y_tc, y_cc) <= 1e-4, nmse(y_tc, y_cc)
+    assert abs(oracle.evm_db(met_tc) - oracle.evm_db(meto)) <= 0.1
+    assert abs(met_tc[0] - meto[0]) <= 1e-2 * meto[0]
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg", CFGS[:3], ids=[n for n, _ in CFGS[:3]])
+def test_tc_backward(name, cfg, prec):
+    c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=prec)
+    c.use_oracle_zf_on_gpu()
+    _opt(c, True)
+    g_tc, _ = c.gpu_backward()
+    _opt(c, False)
+    g_cc, _ = c.gpu_backward()
+    Wo, alo = c.oracle_zf()
+    go, _ = oracle.backward(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert np.isfinite(g_tc).all()
+    assert rel_l2(g_tc, go) <= 2e-2, rel_l2(g_tc, go)
+    assert rel_l2(g_tc, g_cc) <= 2e-2, rel_l2(g_tc, g_cc)
+
+
+def test_option_ignored_by_fp32_plans():
+    c = Case(small_cfg(), fc_scale=0.3, precision=0)
+    c.use_oracle_zf_on_gpu()
+    _opt(c, True)
+    y1, _ = c.gpu_distort()
+    _opt(c, False)
+    y0, _ = c.gpu_distort()
+    assert np.array_equal(y1, y0)
+
+
+def test_option_rejects_unknown():
+    import paper_2205_05158_gb300 as fd
+    c = Case(synth.CONFIGS["cfg1"], precision=1)
+    with pytest.raises(fd.FddpdError) as e:
+        c.plan.set_option(99, 1)
+    assert e.value.code == fd.FDDPD_ERR_ARG
+    with pytest.raises(fd.FddpdError):
+        c.plan.set_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS, 2)
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg", [CFGS[0], CFGS[1], ("cfg3_28", synth.CONFIGS["cfg3"].with_(S=28))],
+                         ids=["ragged", "pad", "cfg3_28"])
+def test_tc_zf_apply(name, cfg, prec):
+    """W = H^H (H H^H)^{-1} (Eq. 6) from the tensor-core apply (BF16 hi / lo splits)
+    against the oracle and against the CUDA-core apply; alpha comes from the same factor."""
+    c = Case(cfg, S=cfg.S, precision=prec)
+    _opt(c, True)
+    W1, a1 = (x.clone() for x in c.gpu_zf())
+    _opt(c, False)
+    W0, a0 = (x.clone() for x in c.gpu_zf())
+    Wo, alo = c.oracle_zf()
+    W1n, W0n = W1.cpu().numpy().astype(np.complex128), W0.cpu().numpy().astype(np.complex128)
+    assert np.array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    assert np.abs(W1n - Wo).max() <= 1e-4 * np.abs(Wo).max()
+    assert np.abs(W1n - W0n).max() <= 1e-4 * np.abs(Wo).max()
+    HW = np.einsum("rbkm,rbmu->rbku", c.w.H.astype(np.complex128), W1n)
+    assert np.abs(HW - np.eye(cfg.K)).max() <= 1e-3
