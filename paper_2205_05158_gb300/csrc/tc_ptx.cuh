@@ -137,6 +137,18 @@ FD_D void cp_async4(void *dst, const void *src, bool valid) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
                  : "memory");
 }
+// one full 32-byte sector per thread (256-bit store; the address must be 32-byte aligned)
+FD_D void st_global_v8(void *p, float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2), "f"(a3),
+                 "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+                 : "memory");
+}
+FD_D void st_global_v8(void *p, const uint32_t (&w)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                 "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 FD_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // generic-proxy shared-memory writes become visible to the tensor core (async proxy)

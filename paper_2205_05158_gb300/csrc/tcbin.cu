@@ -149,6 +149,16 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
         const long bin0 = (long)r * Nd + i0;
         const int nb = min(EXB, Nd - i0);
+        // this warp's 4 subcarrier scales, loaded before they are needed
+        float sc[4];
+        {
+            const int hb = 4 * (warp >> 2);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float al = hb + j < nb ? alpha[bin0 + hb + j] : 0.f;
+                sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
+            }
+        }
 
         // A: chunk (tile p, row m, 16-byte chunk ch) = users 4 (ch & 3) .. + 3 of
         // subcarrier 2p + (ch >> 2) at antenna m, copied with cp.async (zero outside)
@@ -224,17 +234,11 @@ __global__ void __launch_bounds__(THREADS, 2)
             }
             alive = wait_mma(&bar, phase, err);
             if (alive) {
-                // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3
+                // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3: one
+                // 32-byte sector of out[t][m][i0 + 4 (w >> 2) ..] per symbol
                 const int q = warp & 3, hb = 4 * (warp >> 2);
                 const int m = 32 * q + lane;
                 const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-                float sc[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int b = hb + j;
-                    const float al = b < nb ? alpha[bin0 + b] : 0.f;
-                    sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
-                }
                 const bool vec = vec_ok && hb + 4 <= nb;
                 for (int tb = 0; 4 * tb < ns; ++tb) {
                     float v[4][8];
@@ -247,12 +251,9 @@ __global__ void __launch_bounds__(THREADS, 2)
                             if (t >= ns) break;
                             c32 *dst = out + ((t0 + s0 + t) * M + m) * Nd + i0 + hb;
                             if (vec) {
-                                reinterpret_cast<float4 *>(dst)[0] =
-                                    make_float4(v[0][2 * tt] * sc[0], v[0][2 * tt + 1] * sc[0], v[1][2 * tt] * sc[1],
-                                                v[1][2 * tt + 1] * sc[1]);
-                                reinterpret_cast<float4 *>(dst)[1] =
-                                    make_float4(v[2][2 * tt] * sc[2], v[2][2 * tt + 1] * sc[2], v[3][2 * tt] * sc[3],
-                                                v[3][2 * tt + 1] * sc[3]);
+                                st_global_v8(dst, v[0][2 * tt] * sc[0], v[0][2 * tt + 1] * sc[0], v[1][2 * tt] * sc[1],
+                                             v[1][2 * tt + 1] * sc[1], v[2][2 * tt] * sc[2], v[2][2 * tt + 1] * sc[2],
+                                             v[3][2 * tt] * sc[3], v[3][2 * tt + 1] * sc[3]);
                             } else {
 #pragma unroll
                                 for (int j = 0; j < 4; ++j)
@@ -310,6 +311,12 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
         const long bin0 = (long)r * Nd + i0;
         const int nb = min(RDB, Nd - i0);
+        // scale of the subcarrier whose TMEM lanes this warp reads, loaded early
+        float sc = 0.f;
+        if (warp < nb) {
+            const float al = alpha[bin0 + warp];
+            sc = (inv_alpha ? 1.0f / al : al) / b_scale;
+        }
 
         // B rows 16 b + u (u < K), k-block m / 32, copied with cp.async; antennas
         // M .. MP - 1 are zero
@@ -349,6 +356,17 @@ __global__ void __launch_bounds__(THREADS, 2)
         for (int s0 = 0; s0 < nsym && alive; s0 += TS) {
             const int ns = min(TS, nsym - s0);
             const bool vec = vec_ok && nb == RDB;
+            // outputs (t, u, b), b fastest (4 subcarriers = 32 contiguous bytes): at most
+            // 16 x 16 x 4 = 4 per thread; the reference symbols are loaded ahead
+            const int nout = ns * K * RDB;
+            c32 sref[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = tid + k * THREADS;
+                const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
+                sref[k] = (COMB && e < nout && b < nb) ? s_ref[((t0 + s0 + t) * K + u) * Nd + i0 + b]
+                                                       : make_float2(0.f, 0.f);
+            }
             // A: (t, m) pairs, m fastest, all 4 subcarriers (32 contiguous bytes) each;
             // rows 32 b + 2t and 32 b + 2t + 1 of k-block m / 32
             for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
@@ -403,24 +421,22 @@ __global__ void __launch_bounds__(THREADS, 2)
                     float v[16];
                     tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
                     if (b < nb && t < ns) {
-                        const float al = alpha[bin0 + b];
-                        const float sc = (inv_alpha ? 1.0f / al : al) / b_scale;
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
                             if (u < K) sY[((t * 16 + u) * RDB + b) * 2 + c] = v[u] * sc;
                     }
                 }
                 __syncthreads();
-                // (t, u, b), b fastest: 4 subcarriers = 32 contiguous bytes
                 const c32 *sYc = reinterpret_cast<const c32 *>(sY);
-                const int n = ns * K * RDB;
-                for (int e = tid; e < n; e += THREADS) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * THREADS;
                     const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
-                    if (b >= nb) continue;
+                    if (e >= nout || b >= nb) continue;
                     const c32 v = sYc[(t * 16 + u) * RDB + b];
                     const long idx = ((t0 + s0 + t) * K + u) * Nd + i0 + b;
                     if (COMB) {
-                        const c32 sr = s_ref[idx];
+                        const c32 sr = sref[k];
                         const c32 d = csub(v, sr);
                         err_acc += cabs2(d);
                         sig_acc += cabs2(sr);
@@ -456,20 +472,20 @@ static int sm_count() {
 
 // Two CTAs per SM only fit with the largest shared-memory carveout; the occupancy query
 // assumes the function's preferred carveout, so it is set first.
+// Two CTAs per SM (both kernels are sized for it: shared memory below half the SM's, at
+// most 128 registers a thread, at most 256 TMEM columns each) with the largest carveout.
 template <class Kern> static cudaError_t grid_for(Kern k, int smem, long items, unsigned &blocks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
-    if (e != cudaSuccess) return e;
-    long b = (long)(per_sm > 0 ? per_sm : 1) * sm_count();
+    long b = 2L * sm_count();
     if (b > items) b = items;
     blocks = (unsigned)(b > 0 ? b : 1);
     return cudaSuccess;
 }
 
+static bool aligned32(const void *p) { return !(reinterpret_cast<uintptr_t>(p) & 31); }
 static bool aligned16(const void *p) { return !(reinterpret_cast<uintptr_t>(p) & 15); }
 
 template <typename T16>
@@ -478,7 +494,7 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long items = (long)R * ((g.N_d + EXB - 1) / EXB);
     if (items == 0) return cudaSuccess;
-    const int vec_ok = !(g.N_d & 1) && aligned16(out);
+    const int vec_ok = !(g.N_d & 3) && aligned32(out);   // 4 subcarriers = one 32-byte sector
     const uint32_t *a = static_cast<const uint32_t *>(A);
     unsigned blocks = 0;
     cudaError_t e;

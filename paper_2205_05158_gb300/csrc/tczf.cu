@@ -45,7 +45,7 @@ FD_D void split(c32 v, uint32_t &hi, uint32_t &lo) {
 template <typename T16>
 __global__ void __launch_bounds__(THREADS, 2)
     apply_kernel(Geo g, long nbins, const c32 *__restrict__ H, const c32 *__restrict__ Zs,
-                 const float *__restrict__ alpha, c32 *__restrict__ W, T16 *__restrict__ W16, int *err) {
+                 const float *__restrict__ alpha, c32 *__restrict__ W, T16 *__restrict__ W16, int vec, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *aHi = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *aLo = aHi + A_BYTES;
@@ -73,6 +73,13 @@ __global__ void __launch_bounds__(THREADS, 2)
     for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
         const long bin0 = item * NBI;
         const int nb = (int)min((long)NBI, nbins - bin0);
+        // singular flags of this warp's two subcarriers, loaded early
+        bool zero_b[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int b = 2 * (warp >> 2) + j;
+            zero_b[j] = b < nb ? alpha[bin0 + b] == 0.0f : true;
+        }
         // A: chunk (pair tile p, antenna m, 16-byte chunk ch) = users 4 (ch & 3) .. + 3 of
         // subcarrier 2p + (ch >> 2); lanes run along m, so every load is coalesced
         for (int c0 = tid; c0 < 2 * 128 * 8; c0 += 2 * THREADS) {
@@ -153,10 +160,10 @@ __global__ void __launch_bounds__(THREADS, 2)
                 }
                 if (b < nb && m < M) {
                     const long bin = bin0 + b;
-                    const bool zero = alpha[bin] == 0.0f;
+                    const bool zero = zero_b[j];
                     c32 *Wr = W + (bin * M + m) * K;
                     T16 *W16r = W16 + (bin * M + m) * K;
-                    if (K == 16) {
+                    if (vec) {
                         uint32_t w16[16];
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
@@ -165,13 +172,18 @@ __global__ void __launch_bounds__(THREADS, 2)
                             w16[u] = *reinterpret_cast<const uint32_t *>(&q16);
                             if (zero) v[2 * u] = v[2 * u + 1] = 0.f;
                         }
-                        float4 *W4 = reinterpret_cast<float4 *>(Wr);
+                        // whole 32-byte sectors: 4 of FP32 W, 2 of the 16-bit copy
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            W4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-                        uint4 *Q4 = reinterpret_cast<uint4 *>(W16r);
+                        for (int u = 0; u < 4; ++u)
+                            st_global_v8(Wr + 4 * u, v[8 * u], v[8 * u + 1], v[8 * u + 2], v[8 * u + 3], v[8 * u + 4],
+                                         v[8 * u + 5], v[8 * u + 6], v[8 * u + 7]);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) Q4[u] = make_uint4(w16[4 * u], w16[4 * u + 1], w16[4 * u + 2], w16[4 * u + 3]);
+                        for (int u = 0; u < 2; ++u) {
+                            uint32_t w8[8];
+#pragma unroll
+                            for (int x = 0; x < 8; ++x) w8[x] = w16[8 * u + x];
+                            st_global_v8(W16r + 8 * u, w8);
+                        }
                     } else {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
@@ -208,19 +220,16 @@ static cudaError_t launch(const Geo &g, long nbins, const c32 *H, const c32 *Zs,
                           int *err, cudaStream_t st) {
     const long items = (nbins + NBI - 1) / NBI;
     if (items == 0) return cudaSuccess;
-    if (g.K == 16 && ((reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(W16)) & 15))
-        return cudaErrorMisalignedAddress;
+    // whole-sector stores need K = 16 and 32-byte aligned rows; W is the caller's array
+    const int vec = g.K == 16 && !((reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(W16)) & 31);
     cudaError_t e = cudaFuncSetAttribute(apply_kernel<T16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e == cudaSuccess)   // two CTAs per SM need the largest shared-memory carveout
         e = cudaFuncSetAttribute(apply_kernel<T16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<T16>, THREADS, SMEM);
-    if (e != cudaSuccess) return e;
-    long blocks = (long)(per_sm > 0 ? per_sm : 1) * sm_count();
+    long blocks = 2L * sm_count();   // two CTAs per SM: 82 KB of shared memory, 128 TMEM columns each
     if (blocks > items) blocks = items;
-    apply_kernel<T16><<<(unsigned)blocks, THREADS, SMEM, st>>>(g, nbins, H, Zs, alpha, W, W16, err);
+    apply_kernel<T16><<<(unsigned)blocks, THREADS, SMEM, st>>>(g, nbins, H, Zs, alpha, W, W16, vec, err);
     return cudaGetLastError();
 }
 
