@@ -73,6 +73,7 @@ def stage_work(cfg, S: int, prec: str):
     cols = S * K
     c8 = 8
     opb = 8 if prec == "fp32" else 4          # bytes of one complex H / W operand
+    ab = 4 if prec == "bf16" else 8           # bytes of one complex X^PA, gX, g_xhat entry
     fc_bound = "alu" if prec == "fp32" else "tensor"
     theta_len = cfg.N_conv * 2 * L_U * cfg.K_C ** 2 + cfg.N_conv + 2 * Nd * F + 2 * Nd
     return {
@@ -85,11 +86,11 @@ def stage_work(cfg, S: int, prec: str):
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
         "precode": ("hbm", R * Nd * M * K * opb + S * K * Nd * c8 + S * M * Nd * c8),
-        "fftpa_fwd": ("hbm", 2 * S * M * Nd * c8),
-        "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * c8 + 2 * S * K * Nd * c8),
-        "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * c8),
-        "fftpa_adj": ("hbm", 3 * S * M * Nd * c8),
-        "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * c8 + S * K * Nd * c8),
+        "fftpa_fwd": ("hbm", S * M * Nd * (c8 + ab)),
+        "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * ab + 2 * S * K * Nd * c8),
+        "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * ab),
+        "fftpa_adj": ("hbm", S * M * Nd * (c8 + 2 * ab)),
+        "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * ab + S * K * Nd * c8),
         "fc_bwd_w": (fc_bound, 2.0 * 2 * Nd * F * cols),
         "fc_bwd_b": ("hbm", cols * 2 * Nd * 4),
         "fc_bwd_d": (fc_bound, 2.0 * cols * F * 2 * Nd),
@@ -103,7 +104,8 @@ def source_files(stage: str, prec: str):
     p16 = prec != "fp32"
     bins = ("tcbin.cu", "tc_ptx.cuh") if p16 else ("bingemm.cu", "bingemm.cuh", "bingemm_f32.cu")
     fc = ("tc_gemm.cu", "tc_ptx.cuh", "pack16.cu") if p16 else ("fdcnn.cu",)
-    files = {"zf_gram": ("zf.cu",), "zf_factor": ("zf.cu",), "zf_apply": ("zf.cu",),
+    files = {"zf_gram": ("zf.cu",), "zf_factor": ("zf.cu",),
+             "zf_apply": ("tczf.cu", "tc_ptx.cuh") if p16 else ("zf.cu",),
              "fftpa_fwd": ("fftpa.cu", "fftpa.cuh", "fftpa_n11.cu"),
              "fftpa_adj": ("fftpa.cu", "fftpa.cuh", "fftpa_n11.cu"),
              "precode": bins, "combine": bins, "adj_combine": bins, "adj_precode": bins,

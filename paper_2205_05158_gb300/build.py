@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfddpd.so")
 SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "bingemm_f32.cu", "bingemm_bf16.cu", "bingemm_f16.cu",
-           "fftpa.cu", "fftpa_small.cu", "fftpa_n10.cu", "fftpa_n11.cu", "fftpa_n12.cu", "update.cu", "tc_gemm.cu",
+           "fftpa.cu", *[f"fftpa_n{n}.cu" for n in range(6, 13)],
+           *[f"fftpa16_n{n}.cu" for n in range(6, 13)], "update.cu", "tc_gemm.cu",
            "pack16.cu", "noalloc.cu", "tcbin.cu", "tczf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

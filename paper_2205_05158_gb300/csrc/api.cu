@@ -330,23 +330,31 @@ static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps
 // Per-subcarrier contractions: tensor cores in 16-bit plans where supported, else CUDA
 // cores.  b_scale multiplies the activations before their 16-bit rounding (and divides
 // the results): a power of two that lifts the loss gradients, O(1 / count), out of the
-// FP16 subnormal range.
+// FP16 subnormal range (BF16 has the FP32 range and needs none).
 static bool use_tc_bin(const fddpd_plan *p) { return p->p16 && p->tc_bin && fdk::tc_bin_supported(p->g); }
-static cudaError_t expand_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const c32 *B,
-                             c32 *out, float b_scale) {
-    if (use_tc_bin(p)) return fdk::tc_bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, b_scale,
-                                                 p->status + 1, p->stream);
-    return fdk::bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, p->stream);
+// BF16 plans on the tensor-core path keep the antenna-side frequency-domain planes (X^PA,
+// its gradient and the gradient of x_hat) in BF16: the MMAs round them to BF16 anyway.
+static int act_kind(const fddpd_plan *p) {
+    return use_tc_bin(p) && p->kind16 == fdk::OUT_BF16 ? fdk::OUT_BF16 : fdk::OUT_F32;
 }
-static cudaError_t reduce_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const c32 *B,
+static cudaError_t expand_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const c32 *B,
+                             void *out, float b_scale) {
+    if (use_tc_bin(p))
+        return fdk::tc_bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out,
+                                  mode == fdk::PRECODE ? fdk::OUT_F32 : act_kind(p), b_scale, p->status + 1, p->stream);
+    return fdk::bin_expand(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, static_cast<c32 *>(out), p->stream);
+}
+static cudaError_t reduce_op(fddpd_plan *p, int mode, int S, const BinOps &o, const float *alpha, const void *B,
                              c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale) {
     if (use_tc_bin(p))
-        return fdk::tc_bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, s_ref, gy, metrics, inv_count,
-                                  b_scale, p->status + 1, p->stream);
-    return fdk::bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, out, s_ref, gy, metrics, inv_count,
-                           p->stream);
+        return fdk::tc_bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, B, act_kind(p), out, s_ref, gy, metrics,
+                                  inv_count, b_scale, p->status + 1, p->stream);
+    return fdk::bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, static_cast<const c32 *>(B), out, s_ref, gy,
+                           metrics, inv_count, p->stream);
 }
-static float grad_scale(double inv_count) { return exp2f(rintf(log2f((float)(0.5 / inv_count)))); }
+static float grad_scale(const fddpd_plan *p, double inv_count) {
+    return p->kind16 == fdk::OUT_F16 ? exp2f(rintf(log2f((float)(0.5 / inv_count)))) : 1.0f;
+}
 
 // Forward chain; gy (loss gradient at y) is written when non-null.
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
@@ -371,7 +379,8 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
     }
     FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
-    FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1, fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, st));
+    FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1,
+             fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, act_kind(p), p->met, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
              reduce_op(p, fdk::COMBINE, S, ops, alpha, p->Xpa, y, s, gy, p->met, inv_count, 1.0f));
     FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
@@ -389,9 +398,10 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     BinOps ops;
     rc = bin_operands(p, S, H, W, ops);
     if (rc) return rc;
-    const float gsc = grad_scale(1.0 / ((double)cols * g.N_d));
+    const float gsc = grad_scale(p, 1.0 / ((double)cols * g.N_d));
     FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
-    FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1, fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, st));
+    FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
+             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, act_kind(p), st));
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
              reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);

@@ -80,6 +80,25 @@ FD_D T block_sum(T v, T *scratch /* >= 32 entries */) {
 }
 
 // Index of data subcarrier for FFT bin k, or -1 for a guard bin.
+// CTAs of kernel k that fit on one SM at once: the register / thread limit from the
+// occupancy query (asked without dynamic shared memory, which it counts against a smaller
+// carveout than the one launches get), and the shared memory against the SM's capacity at
+// the largest carveout, which is requested here.
+template <class Kern> inline int resident_ctas(Kern k, int threads, size_t dyn_smem) {
+    int dev = 0, cap = 0, resv = 0, by_regs = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&by_regs, k, threads, 0) != cudaSuccess || by_regs < 1) by_regs = 1;
+    const size_t per = dyn_smem + fa.sharedSizeBytes + (size_t)resv;
+    const int by_smem = cap > 0 ? (int)((size_t)cap / per) : 1;
+    const int n = by_regs < by_smem ? by_regs : by_smem;
+    return n > 0 ? n : 1;
+}
+
 FD_HD int data_index(int k, int first_bin, int N, int N_d) {
     int i = (k - first_bin) & (N - 1);  // N is a power of two
     return i < N_d ? i : -1;

@@ -222,32 +222,56 @@ struct RowPa {
     // gx_n = sum_l A_l(x_n) g_{n+l} + B_l(x_n) conj(g_{n+l}); gs holds g in natural order
     static FD_D void adjoint(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *gs, const c32 *cp,
                              c32 (&gx)[16]) {
-        const int P = P_ > 0 ? P_ : g.n_orders;
-        const int L = P_ > 0 ? L_ : g.L;
-        const int L1 = L + 1;
+        if constexpr (P_ > 0) {
+            // odd orders 2k+1, k < P_: a_k = (k+1) |x|^(2k), b_k = k x^2 |x|^(2k-2); both depend
+            // on x_n only, so they are formed once per sample and the taps run inside
+            constexpr int L1 = L_ + 1;
+            c32 c[P_][L1];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) gx[q] = make_float2(0.f, 0.f);
+            for (int k = 0; k < P_; ++k)
 #pragma unroll
-        for (int l = 0; l <= (P_ > 0 ? L_ : 7); ++l) {
-            if (l > L) break;
+                for (int l = 0; l < L1; ++l) c[k][l] = cp[k * L1 + l];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
                 const float r2 = cabs2(x[q]);
                 const c32 xx = cmul(x[q], x[q]);
-                c32 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-                if (P_ > 0) {
-                    // order 2k+1: a = (k+1) r2^k, b = k x^2 r2^(k-1)
-                    float rk = 1.0f, rk1 = 0.0f;
+                float a[P_];    // (k+1) r2^k
+                c32 bt[P_];     // k x^2 r2^(k-1), k >= 1
+                float rk = 1.0f, rkm1 = 0.0f;   // r2^k, r2^(k-1)
 #pragma unroll
-                    for (int k = 0; k < (P_ > 0 ? P_ : 1); ++k) {
-                        const c32 c = cp[k * L1 + l];
-                        A = cadd(A, cscale(cconj(c), (float)(k + 1) * rk));
-                        if (k >= 1) B = cfma(cscale(xx, (float)k * rk1), c, B);
-                        rk1 = rk;
-                        rk *= r2;
+                for (int k = 0; k < P_; ++k) {
+                    a[k] = (float)(k + 1) * rk;
+                    bt[k] = cscale(xx, (float)k * rkm1);
+                    rkm1 = rk;
+                    rk *= r2;
+                }
+                c32 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int l = 0; l < L1; ++l) {
+                    const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
+                    c32 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < P_; ++k) {
+                        A.x = fmaf(a[k], c[k][l].x, A.x);      // a_k conj(c_{k,l})
+                        A.y = fmaf(-a[k], c[k][l].y, A.y);
+                        if (k >= 1) B = cfma(bt[k], c[k][l], B);
                     }
-                } else {
+                    acc = cfma(A, gl, acc);
+                    acc = cfma(B, cconj(gl), acc);
+                }
+                gx[q] = acc;
+            }
+        } else {
+            const int P = g.n_orders, L = g.L, L1 = L + 1;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) gx[q] = make_float2(0.f, 0.f);
+            for (int l = 0; l <= L; ++l) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
+                    const float r2 = cabs2(x[q]);
+                    const c32 xx = cmul(x[q], x[q]);
+                    c32 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
                     const float mag = sqrtf(r2);
                     for (int p = 0; p < P; ++p) {
                         const int e = g.orders[p] - 1;
@@ -256,9 +280,9 @@ struct RowPa {
                         A = cadd(A, cscale(cconj(c), 0.5f * (float)(e + 2) * w));
                         if (e >= 1 && mag > 0.0f) B = cfma(cscale(xx, 0.5f * (float)e * w / r2), c, B);
                     }
+                    gx[q] = cfma(A, gl, gx[q]);
+                    gx[q] = cfma(B, cconj(gl), gx[q]);
                 }
-                gx[q] = cfma(A, gl, gx[q]);
-                gx[q] = cfma(B, cconj(gl), gx[q]);
             }
         }
     }
@@ -344,10 +368,10 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     }
 }
 
-template <int LOG2N, int P_, int L_, typename TIn>
-__global__ void __launch_bounds__(256, 1) fftpa_adjoint_kernel(Geo g, long rows, const c32 *__restrict__ xh,
+template <int LOG2N, int P_, int L_, typename TIn, typename TOut>
+__global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows, const c32 *__restrict__ xh,
                                                                const c32 *__restrict__ pa,
-                                                               const c32 *__restrict__ twp_g, const TIn *gX, c32 *gxh) {
+                                                               const c32 *__restrict__ twp_g, const TIn *gX, TOut *gxh) {
     using F = Fft<LOG2N>;
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -389,11 +413,11 @@ __global__ void __launch_bounds__(256, 1) fftpa_adjoint_kernel(Geo g, long rows,
         __syncthreads();
         transform<LOG2N, false>(gv, bufA, bufB, twp, t, rs);
         if (active) {
-            c32 *orow = gxh + row * g.N_d;
+            TOut *orow = gxh + row * g.N_d;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-                if (i >= 0) orow[i] = gv[q];
+                if (i >= 0) orow[i] = Operand<TOut>::from(gv[q]);
             }
         }
     }
@@ -403,9 +427,7 @@ template <class Kern>
 inline cudaError_t persistent_blocks(Kern k, int N, long rows, int threads, size_t sm, long &blocks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm);
-    if (e != cudaSuccess) return e;
+    const int per_sm = resident_ctas(k, threads, sm);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -428,15 +450,15 @@ inline cudaError_t fwd_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     return cudaGetLastError();
 }
 
-template <int LOG2N, int P_, int L_>
-inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const c32 *gX,
-                         c32 *gxh, cudaStream_t st) {
+template <int LOG2N, int P_, int L_, typename TA>
+inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const TA *gX,
+                         TA *gxh, cudaStream_t st) {
     const int threads = 256;
     const size_t sm = fftpa_smem_bytes_(g);
     long blocks = 0;
-    cudaError_t e = persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, c32>, g.N, rows, threads, sm, blocks);
+    cudaError_t e = persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA>, g.N, rows, threads, sm, blocks);
     if (e != cudaSuccess) return e;
-    fftpa_adjoint_kernel<LOG2N, P_, L_, c32><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, gX, gxh);
+    fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, gX, gxh);
     return cudaGetLastError();
 }
 
@@ -462,9 +484,9 @@ inline cudaError_t fwd_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     }
 }
 
-template <int LOG2N>
-inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const c32 *gX,
-                         c32 *gxh, cudaStream_t st) {
+template <int LOG2N, typename TA>
+inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const TA *gX, TA *gxh,
+                         cudaStream_t st) {
     switch (pa_shape(g)) {
         case 1: return adj_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, gX, gxh, st);
         case 2: return adj_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, gX, gxh, st);
@@ -473,9 +495,11 @@ inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     }
 }
 
-// One translation unit per transform size instantiates these.
+// Translation units per transform size instantiate these, the FP32-plane variants
+// (FD_FFTPA_SIZE) and the BF16-plane ones (FD_FFTPA_SIZE16: X out of the forward, gX in
+// and g_xhat out of the adjoint in BF16) separately, so they compile in parallel.
 #define FD_FFTPA_SIZE(LOG2N)                                                                                      \
-    cudaError_t fftpa_fwd_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, c32 *X, \
+    cudaError_t fftpa_fwd_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, c32 *X,  \
                                   double *metrics, cudaStream_t st) {                                            \
         return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, st);                                               \
     }                                                                                                            \
@@ -483,12 +507,25 @@ inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
                                   const c32 *gX, c32 *gxh, cudaStream_t st) {                                    \
         return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, st);                                                  \
     }
+#define FD_FFTPA_SIZE16(LOG2N)                                                                                    \
+    cudaError_t fftpa_fwd16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
+                                    cbf16 *X, double *metrics, cudaStream_t st) {                                \
+        return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, st);                                               \
+    }                                                                                                            \
+    cudaError_t fftpa_adj16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
+                                    const cbf16 *gX, cbf16 *gxh, cudaStream_t st) {                              \
+        return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, st);                                                  \
+    }
 
 #define FD_FFTPA_DECL(LOG2N)                                                                                      \
-    cudaError_t fftpa_fwd_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, c32 *X, \
+    cudaError_t fftpa_fwd_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, c32 *X,  \
                                   double *metrics, cudaStream_t st);                                             \
     cudaError_t fftpa_adj_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,         \
-                                  const c32 *gX, c32 *gxh, cudaStream_t st);
+                                  const c32 *gX, c32 *gxh, cudaStream_t st);                                     \
+    cudaError_t fftpa_fwd16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
+                                    cbf16 *X, double *metrics, cudaStream_t st);                                 \
+    cudaError_t fftpa_adj16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
+                                    const cbf16 *gX, cbf16 *gxh, cudaStream_t st);
 FD_FFTPA_DECL(6) FD_FFTPA_DECL(7) FD_FFTPA_DECL(8) FD_FFTPA_DECL(9) FD_FFTPA_DECL(10) FD_FFTPA_DECL(11) FD_FFTPA_DECL(12)
 
 }  // namespace fdk

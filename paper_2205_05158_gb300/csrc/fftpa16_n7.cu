@@ -1,0 +1,6 @@
+// Instantiations of the OFDM + PA row kernels with BF16 frequency-domain planes for N = 128.
+#include "fftpa.cuh"
+
+namespace fdk {
+FD_FFTPA_SIZE16(7)
+}  // namespace fdk

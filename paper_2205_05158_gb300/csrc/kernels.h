@@ -59,19 +59,21 @@ cudaError_t bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind,
 cudaError_t bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                        c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, cudaStream_t st);
 // tcgen05 versions for 16-bit H / W copies (M <= 128, K <= 16); err: sticky timeout word
+// act_kind: storage of the antenna-side activations (the expand's output, the reduce's
+// input): OUT_F32, or OUT_BF16 in BF16 plans (then b_scale must be 1)
 cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
-                          c32 *out, float b_scale, int *err, cudaStream_t st);
-cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
-                          c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale,
-                          int *err, cudaStream_t st);
+                          void *out, int act_kind, float b_scale, int *err, cudaStream_t st);
+cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const void *B,
+                          int act_kind, c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count,
+                          float b_scale, int *err, cudaStream_t st);
 cudaError_t to_16bit(long n, const c32 *in, void *out, int kind, cudaStream_t st);
 
 // OFDM + PA rows
 size_t fftpa_smem_bytes(const Geo &g, bool adjoint);
 cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, void *X, int out_kind,
                           double *metrics, cudaStream_t st);
-cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const c32 *gX, c32 *gxh,
-                          cudaStream_t st);
+cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const void *gX, void *gxh,
+                          int act_kind, cudaStream_t st);
 
 // parameter updates and bookkeeping
 cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);

@@ -33,6 +33,8 @@
 // tcgen05.commit onto an mbarrier; every wait on it is bounded (about 2 s), after which
 // the error word is set, the CTA stops, and its tensor memory is freed.  Two CTAs share
 // an SM, so one builds operands while the other's MMAs and epilogue run.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
@@ -79,6 +81,23 @@ template <typename T16, bool CONJ> FD_D void real_rows(float br, float bi, uint3
     }
 }
 
+// the same rows from a BF16 (re, im) pair already packed as stored (low half = re): the
+// sign flips and the swap are bit operations
+template <bool CONJ> FD_D void real_rows_packed(uint32_t w, uint32_t &w0, uint32_t &w1) {
+    const uint32_t sw = __byte_perm(w, 0u, 0x1032u);   // (im, re)
+    if (CONJ) {
+        w0 = w;
+        w1 = sw ^ 0x80000000u;
+    } else {
+        w0 = w ^ 0x80000000u;
+        w1 = sw;
+    }
+}
+FD_D uint32_t pack_bf16(float re, float im) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(re, im);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
 FD_D void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 FD_D void st128(uint8_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 FD_D uint8_t *align1024(uint8_t *p) {
@@ -121,11 +140,12 @@ FD_D void teardown(uint64_t *bar, uint32_t phase, bool alive, uint32_t tmem, uin
 
 // ---------------------------------------------------------------------------
 // expand.  AT = false: A = W16 [bin][m][u] (rows m, PRECODE); AT = true: A = H16
-// [bin][u][m] read transposed (ADJ_COMBINE).  out[t][m][i] = scale_i D / b_scale.
-template <typename T16, bool CONJ, bool AT>
+// [bin][u][m] read transposed (ADJ_COMBINE).  out[t][m][i] = scale_i D / b_scale, stored
+// as TO (c32, or cbf16 for the BF16 activation planes).
+template <typename T16, bool CONJ, bool AT, typename TO>
 __global__ void __launch_bounds__(THREADS, 2)
     expand_kernel(Geo g, int S, const uint32_t *__restrict__ A, const float *__restrict__ alpha,
-                  const c32 *__restrict__ B, c32 *__restrict__ out, int inv_alpha, float b_scale, int vec_ok,
+                  const c32 *__restrict__ B, TO *__restrict__ out, int inv_alpha, float b_scale, int vec_ok,
                   int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sA = align1024(smem_raw);
@@ -149,15 +169,12 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
         const long bin0 = (long)r * Nd + i0;
         const int nb = min(EXB, Nd - i0);
-        // this warp's 4 subcarrier scales, loaded before they are needed
-        float sc[4];
-        {
-            const int hb = 4 * (warp >> 2);
+        // the subcarrier scales, loaded before they are needed
+        float sc[EXB];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float al = hb + j < nb ? alpha[bin0 + hb + j] : 0.f;
-                sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
-            }
+        for (int j = 0; j < EXB; ++j) {
+            const float al = j < nb ? alpha[bin0 + j] : 0.f;
+            sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
         }
 
         // A: chunk (tile p, row m, 16-byte chunk ch) = users 4 (ch & 3) .. + 3 of
@@ -234,30 +251,66 @@ __global__ void __launch_bounds__(THREADS, 2)
             }
             alive = wait_mma(&bar, phase, err);
             if (alive) {
-                // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3: one
-                // 32-byte sector of out[t][m][i0 + 4 (w >> 2) ..] per symbol
-                const int q = warp & 3, hb = 4 * (warp >> 2);
-                const int m = 32 * q + lane;
+                const int q = warp & 3, m = 32 * q + lane;
                 const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-                const bool vec = vec_ok && hb + 4 <= nb;
-                for (int tb = 0; 4 * tb < ns; ++tb) {
-                    float v[4][8];
+                if constexpr (std::is_same<TO, c32>::value) {
+                    // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3: one
+                    // 32-byte sector of out[t][m][i0 + 4 (w >> 2) ..] per symbol
+                    const int hb = 4 * (warp >> 2);
+                    const bool vec = vec_ok && hb + 4 <= nb;
+                    float sch[4];   // this warp's 4 scales, without indexing sc at run time
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) tmem_ld8(trow + 32 * (hb + j) + 8 * tb, v[j]);
-                    if (m < M) {
+                    for (int j = 0; j < 4; ++j) sch[j] = hb ? sc[4 + j] : sc[j];
+                    for (int tb = 0; 4 * tb < ns; ++tb) {
+                        float v[4][8];
 #pragma unroll
-                        for (int tt = 0; tt < 4; ++tt) {
-                            const int t = 4 * tb + tt;
-                            if (t >= ns) break;
-                            c32 *dst = out + ((t0 + s0 + t) * M + m) * Nd + i0 + hb;
-                            if (vec) {
-                                st_global_v8(dst, v[0][2 * tt] * sc[0], v[0][2 * tt + 1] * sc[0], v[1][2 * tt] * sc[1],
-                                             v[1][2 * tt + 1] * sc[1], v[2][2 * tt] * sc[2], v[2][2 * tt + 1] * sc[2],
-                                             v[3][2 * tt] * sc[3], v[3][2 * tt + 1] * sc[3]);
-                            } else {
+                        for (int j = 0; j < 4; ++j) tmem_ld8(trow + 32 * (hb + j) + 8 * tb, v[j]);
+                        if (m < M) {
 #pragma unroll
-                                for (int j = 0; j < 4; ++j)
-                                    if (hb + j < nb) dst[j] = make_float2(v[j][2 * tt] * sc[j], v[j][2 * tt + 1] * sc[j]);
+                            for (int tt = 0; tt < 4; ++tt) {
+                                const int t = 4 * tb + tt;
+                                if (t >= ns) break;
+                                c32 *dst = out + ((t0 + s0 + t) * M + m) * Nd + i0 + hb;
+                                if (vec) {
+                                    st_global_v8(dst, v[0][2 * tt] * sch[0], v[0][2 * tt + 1] * sch[0],
+                                                 v[1][2 * tt] * sch[1], v[1][2 * tt + 1] * sch[1], v[2][2 * tt] * sch[2],
+                                                 v[2][2 * tt + 1] * sch[2], v[3][2 * tt] * sch[3],
+                                                 v[3][2 * tt + 1] * sch[3]);
+                                } else {
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j)
+                                        if (hb + j < nb)
+                                            dst[j] = make_float2(v[j][2 * tt] * sch[j], v[j][2 * tt + 1] * sch[j]);
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    // BF16 planes: warp w: antennas 32 (w & 3) .., symbol blocks tb with
+                    // tb % 2 = w >> 2, all 8 subcarriers = one 32-byte sector per symbol
+                    const bool vec = vec_ok && nb == EXB;
+                    for (int tb = warp >> 2; 4 * tb < ns; tb += 2) {
+                        uint32_t w[4][EXB];
+#pragma unroll
+                        for (int b = 0; b < EXB; ++b) {
+                            float v[8];
+                            tmem_ld8(trow + 32 * b + 8 * tb, v);
+#pragma unroll
+                            for (int tt = 0; tt < 4; ++tt) w[tt][b] = pack_bf16(v[2 * tt] * sc[b], v[2 * tt + 1] * sc[b]);
+                        }
+                        if (m < M) {
+#pragma unroll
+                            for (int tt = 0; tt < 4; ++tt) {
+                                const int t = 4 * tb + tt;
+                                if (t >= ns) break;
+                                uint32_t *dst = reinterpret_cast<uint32_t *>(out + ((t0 + s0 + t) * M + m) * Nd + i0);
+                                if (vec) {
+                                    st_global_v8(dst, w[tt]);
+                                } else {
+#pragma unroll
+                                    for (int b = 0; b < EXB; ++b)
+                                        if (b < nb) dst[b] = w[tt][b];
+                                }
                             }
                         }
                     }
@@ -278,10 +331,12 @@ __global__ void __launch_bounds__(THREADS, 2)
 // (AT = true: W16 [bin][m][u], ADJ_PRECODE).  One MMA per K step (M = 128, N = 64) gives
 // every cross product of the 4 subcarriers; the diagonal blocks b = b' are kept: warp b
 // reads TMEM lanes 32 b .. (its subcarrier's symbols) at columns 16 b .. 16 b + 15.
-template <typename T16, bool CONJ, bool AT, bool COMB>
+// FULL: M = 128 antennas and K = 16 users as compile-time constants, so the index
+// arithmetic of the tile builds and the epilogue is shifts and masks.
+template <typename T16, bool CONJ, bool AT, bool COMB, typename TX, bool FULL>
 __global__ void __launch_bounds__(THREADS, 2)
     reduce_kernel(Geo g, int S, const uint32_t *__restrict__ Wt, const float *__restrict__ alpha,
-                  const c32 *__restrict__ X, c32 *__restrict__ out, const c32 *__restrict__ s_ref,
+                  const TX *__restrict__ X, c32 *__restrict__ out, const c32 *__restrict__ s_ref,
                   c32 *__restrict__ gy, double *metrics, double inv_count, int inv_alpha, float b_scale, int vec_ok,
                   int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -292,8 +347,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     __shared__ uint32_t tmem_slot;
     __shared__ double red[32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int M = g.M, K = g.K, Nd = g.N_d;
-    const int MP = (M + 7) & ~7;          // antennas padded to one K step (8 complex)
+    const int M = FULL ? 128 : g.M, K = FULL ? 16 : g.K, Nd = g.N_d;
+    const int MP = FULL ? 128 : (M + 7) & ~7;   // antennas padded to one K step (8 complex)
     const int MC = MP / 4, nks = MP / 8;
     const int ngroups = (Nd + RDB - 1) / RDB;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
@@ -367,37 +422,74 @@ __global__ void __launch_bounds__(THREADS, 2)
                 sref[k] = (COMB && e < nout && b < nb) ? s_ref[((t0 + s0 + t) * K + u) * Nd + i0 + b]
                                                        : make_float2(0.f, 0.f);
             }
-            // A: (t, m) pairs, m fastest, all 4 subcarriers (32 contiguous bytes) each;
-            // rows 32 b + 2t and 32 b + 2t + 1 of k-block m / 32
-            for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
-                c32 v[4][RDB];
+            // A: (t, m) pairs, m fastest, all 4 subcarriers (32 contiguous bytes of FP32,
+            // 16 of BF16) each; rows 32 b + 2t and 32 b + 2t + 1 of k-block m / 32
+            if constexpr (std::is_same<TX, c32>::value) {
+                for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
+                    c32 v[4][RDB];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                    for (int h = 0; h < 4; ++h) {
+                        const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                        const bool ok = e < TS * MP && t < ns && m < M;
+                        const c32 *src = X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0;
+                        if (ok && vec) {
+                            const float4 lo = reinterpret_cast<const float4 *>(src)[0];
+                            const float4 hi = reinterpret_cast<const float4 *>(src)[1];
+                            v[h][0] = make_float2(lo.x, lo.y);
+                            v[h][1] = make_float2(lo.z, lo.w);
+                            v[h][2] = make_float2(hi.x, hi.y);
+                            v[h][3] = make_float2(hi.z, hi.w);
+                        } else {
+#pragma unroll
+                            for (int b = 0; b < RDB; ++b) v[h][b] = (ok && b < nb) ? src[b] : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                        if (e >= TS * MP) break;
+                        uint8_t *tile = sA + (m >> 5) * 16384;
+                        const int k = 2 * (m & 31);
+#pragma unroll
+                        for (int b = 0; b < RDB; ++b) {
+                            uint32_t w0, w1;
+                            real_rows<T16, CONJ>(v[h][b].x * b_scale, v[h][b].y * b_scale, w0, w1);
+                            st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
+                            st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
+                        }
+                    }
+                }
+            } else {
+                // BF16 planes (BF16 plans, b_scale 1): every load of the unit in flight at once
+                constexpr int PER = TS * 128 / THREADS;
+                uint32_t w[PER][RDB];
+#pragma unroll
+                for (int h = 0; h < PER; ++h) {
+                    const int e = tid + h * THREADS, m = e % MP, t = e / MP;
                     const bool ok = e < TS * MP && t < ns && m < M;
-                    const c32 *src = X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0;
+                    const uint32_t *src =
+                        reinterpret_cast<const uint32_t *>(X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0);
                     if (ok && vec) {
-                        const float4 lo = reinterpret_cast<const float4 *>(src)[0];
-                        const float4 hi = reinterpret_cast<const float4 *>(src)[1];
-                        v[h][0] = make_float2(lo.x, lo.y);
-                        v[h][1] = make_float2(lo.z, lo.w);
-                        v[h][2] = make_float2(hi.x, hi.y);
-                        v[h][3] = make_float2(hi.z, hi.w);
+                        const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
+                        w[h][0] = q4.x;
+                        w[h][1] = q4.y;
+                        w[h][2] = q4.z;
+                        w[h][3] = q4.w;
                     } else {
 #pragma unroll
-                        for (int b = 0; b < RDB; ++b) v[h][b] = (ok && b < nb) ? src[b] : make_float2(0.f, 0.f);
+                        for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < nb) ? src[b] : 0u;
                     }
                 }
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                for (int h = 0; h < PER; ++h) {
+                    const int e = tid + h * THREADS, m = e % MP, t = e / MP;
                     if (e >= TS * MP) break;
                     uint8_t *tile = sA + (m >> 5) * 16384;
                     const int k = 2 * (m & 31);
 #pragma unroll
                     for (int b = 0; b < RDB; ++b) {
                         uint32_t w0, w1;
-                        real_rows<T16, CONJ>(v[h][b].x * b_scale, v[h][b].y * b_scale, w0, w1);
+                        real_rows_packed<CONJ>(w[h][b], w0, w1);
                         st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
                         st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
                     }
@@ -488,46 +580,49 @@ template <class Kern> static cudaError_t grid_for(Kern k, int smem, long items, 
 static bool aligned32(const void *p) { return !(reinterpret_cast<uintptr_t>(p) & 31); }
 static bool aligned16(const void *p) { return !(reinterpret_cast<uintptr_t>(p) & 15); }
 
-template <typename T16>
-static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, c32 *out,
+template <typename T16, typename TO>
+static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, TO *out,
                             float b_scale, int *err, cudaStream_t st) {
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long items = (long)R * ((g.N_d + EXB - 1) / EXB);
     if (items == 0) return cudaSuccess;
-    const int vec_ok = !(g.N_d & 3) && aligned32(out);   // 4 subcarriers = one 32-byte sector
+    // one 32-byte sector = 4 FP32 or 8 BF16 subcarriers
+    const int vec_ok = !(g.N_d & (std::is_same<TO, c32>::value ? 3 : 7)) && aligned32(out);
     const uint32_t *a = static_cast<const uint32_t *>(A);
     unsigned blocks = 0;
     cudaError_t e;
     if (mode == PRECODE) {
-        auto k = expand_kernel<T16, false, false>;
+        auto k = expand_kernel<T16, false, false, TO>;
         if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 0, b_scale, vec_ok, err);
     } else {
-        auto k = expand_kernel<T16, true, true>;
+        auto k = expand_kernel<T16, true, true, TO>;
         if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 1, b_scale, vec_ok, err);
     }
     return cudaGetLastError();
 }
 
-template <typename T16>
-static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, c32 *out,
+template <typename T16, typename TX>
+static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const TX *B, c32 *out,
                             const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale, int *err,
                             cudaStream_t st) {
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long items = (long)R * ((g.N_d + RDB - 1) / RDB);
     if (items == 0) return cudaSuccess;
-    const int vec_ok = !(g.N_d & 1) && aligned16(B);
+    // 4 subcarriers: two 16-byte FP32 loads, or one of BF16
+    const int vec_ok = !(g.N_d & (std::is_same<TX, c32>::value ? 1 : 3)) && aligned16(B);
     const uint32_t *a = static_cast<const uint32_t *>(A);
     unsigned blocks = 0;
     cudaError_t e;
+    const bool full = g.M == 128 && g.K == 16;
     if (mode == COMBINE) {
-        auto k = reduce_kernel<T16, false, false, true>;
+        auto k = full ? reduce_kernel<T16, false, false, true, TX, true> : reduce_kernel<T16, false, false, true, TX, false>;
         if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, b_scale, vec_ok,
                                             err);
     } else {
-        auto k = reduce_kernel<T16, true, true, false>;
+        auto k = full ? reduce_kernel<T16, true, true, false, TX, true> : reduce_kernel<T16, true, true, false, TX, false>;
         if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, b_scale,
                                             vec_ok, err);
@@ -540,21 +635,34 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
 bool tc_bin_supported(const Geo &g) { return g.M >= 1 && g.M <= 128 && g.K >= 1 && g.K <= 16; }
 
 cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
-                          c32 *out, float b_scale, int *err, cudaStream_t st) {
+                          void *out, int act_kind, float b_scale, int *err, cudaStream_t st) {
     if (!tc_bin_supported(g) || (mode != PRECODE && mode != ADJ_COMBINE)) return cudaErrorInvalidValue;
-    if (a_kind == OUT_BF16) return tcb::expand_t<cbf16>(g, mode, S, A, alpha, B, out, b_scale, err, st);
-    if (a_kind == OUT_F16) return tcb::expand_t<cf16>(g, mode, S, A, alpha, B, out, b_scale, err, st);
+    if (act_kind == OUT_BF16) {
+        if (a_kind != OUT_BF16 || b_scale != 1.0f) return cudaErrorInvalidValue;
+        return tcb::expand_t<cbf16>(g, mode, S, A, alpha, B, static_cast<cbf16 *>(out), b_scale, err, st);
+    }
+    if (act_kind != OUT_F32) return cudaErrorInvalidValue;
+    c32 *o = static_cast<c32 *>(out);
+    if (a_kind == OUT_BF16) return tcb::expand_t<cbf16>(g, mode, S, A, alpha, B, o, b_scale, err, st);
+    if (a_kind == OUT_F16) return tcb::expand_t<cf16>(g, mode, S, A, alpha, B, o, b_scale, err, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
-                          c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale,
-                          int *err, cudaStream_t st) {
+cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const void *B,
+                          int act_kind, c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count,
+                          float b_scale, int *err, cudaStream_t st) {
     if (!tc_bin_supported(g) || (mode != COMBINE && mode != ADJ_PRECODE)) return cudaErrorInvalidValue;
+    if (act_kind == OUT_BF16) {
+        if (a_kind != OUT_BF16 || b_scale != 1.0f) return cudaErrorInvalidValue;
+        return tcb::reduce_t<cbf16>(g, mode, S, A, alpha, static_cast<const cbf16 *>(B), out, s_ref, gy, metrics,
+                                    inv_count, b_scale, err, st);
+    }
+    if (act_kind != OUT_F32) return cudaErrorInvalidValue;
+    const c32 *x = static_cast<const c32 *>(B);
     if (a_kind == OUT_BF16)
-        return tcb::reduce_t<cbf16>(g, mode, S, A, alpha, B, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
+        return tcb::reduce_t<cbf16>(g, mode, S, A, alpha, x, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
     if (a_kind == OUT_F16)
-        return tcb::reduce_t<cf16>(g, mode, S, A, alpha, B, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
+        return tcb::reduce_t<cf16>(g, mode, S, A, alpha, x, out, s_ref, gy, metrics, inv_count, b_scale, err, st);
     return cudaErrorInvalidValue;
 }
 

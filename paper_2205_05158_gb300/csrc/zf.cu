@@ -39,8 +39,9 @@ size_t zf_scratch_bytes(const Geo &g, long nbins) {
 // (10 for K = 16) and the antennas of each 32-antenna chunk into ng groups, one (block,
 // group) task per lane (30 of 32 lanes for K = 16): per antenna a lane loads 4 + 4
 // entries for 16 complex multiply-adds.  Partial sums of the groups meet in shared memory
-// at the end.  A warp holds one chunk ([K][33] complex, 4.2 KB for K = 16), so many warps
-// fit on an SM and hide each other's loads.
+// at the end.  A warp streams its (subcarrier, chunk) sequence through two chunk buffers
+// ([K][33] complex, 4.2 KB for K = 16) with cp.async, so the next chunk -- also the next
+// subcarrier's first -- is in flight while the current one is multiplied.
 constexpr int GR_CHUNK = 32, GR_LD = GR_CHUNK + 1;
 
 FD_HD int gram_tasks(int K, int &nbt, int &ng) {
@@ -51,21 +52,29 @@ FD_HD int gram_tasks(int K, int &nbt, int &ng) {
     if (ng > GR_CHUNK) ng = GR_CHUNK;
     return nbt * ng;
 }
-size_t gram_warp_bytes(int K) {
+// one of the two per-warp buffers: a chunk, or the partial sums of the tasks
+size_t gram_buf_bytes(int K) {
     int nbt, ng;
     const int tasks = gram_tasks(K, nbt, ng);
     const size_t chunk = sizeof(c32) * K * GR_LD, red = sizeof(c32) * 16 * tasks;
     return al16(chunk > red ? chunk : red);
 }
 
+FD_D void cp_async8z(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
 template <typename T16, int NT>   // NT: tasks per lane (2 when K > 28)
 __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
                                                                 c32 *__restrict__ Gs, T16 *__restrict__ H16,
-                                                                int warp_bytes) {
+                                                                int buf_bytes) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int K = g.K, M = g.M, T = tri(K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    c32 *sH = reinterpret_cast<c32 *>(sm + (size_t)warp * warp_bytes);
+    unsigned char *wbuf = sm + (size_t)(2 * warp) * buf_bytes;   // this warp's two buffers
+    auto buf = [&](long it) { return reinterpret_cast<c32 *>(wbuf + (it & 1) * (size_t)buf_bytes); };
     int nbt, ng;
     const int tasks = gram_tasks(K, nbt, ng);
     // this lane's tasks: task = group * nbt + block
@@ -79,78 +88,89 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel
         glo[ntask] = grp * GR_CHUNK / ng;
         ghi[ntask] = (grp + 1) * GR_CHUNK / ng;
     }
-    for (long b = (long)blockIdx.x * nwarps + warp; b < nbins; b += (long)gridDim.x * nwarps) {
-        const c32 *Hb = H + b * K * M;
-        c32 acc[NT][4][4];
-#pragma unroll
-        for (int q = 0; q < NT; ++q)
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[q][a][c] = make_float2(0.f, 0.f);
-        for (int m0 = 0; m0 < M; m0 += GR_CHUNK) {
-            const int m = m0 + lane;
-            // chunk of 32 antennas, 8 rows of loads in flight
-            for (int u0 = 0; u0 < K; u0 += 8) {
-                c32 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = (u0 + j < K && m < M) ? Hb[(long)(u0 + j) * M + m] : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (u0 + j < K) {
-                        sH[(u0 + j) * GR_LD + lane] = v[j];
-                        if (H16 && m < M) H16[(b * K + u0 + j) * M + m] = Operand<T16>::from(v[j]);
-                    }
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < NT; ++q) {
-                if (q >= ntask) break;
-                const int ri = 4 * bi[q], rj = 4 * bj[q];
-                for (int mm = glo[q]; mm < ghi[q]; ++mm) {
-                    c32 hi[4], hj[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        hi[a] = ri + a < K ? sH[(ri + a) * GR_LD + mm] : make_float2(0.f, 0.f);
-                        hj[a] = rj + a < K ? cconj(sH[(rj + a) * GR_LD + mm]) : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[q][a][c] = cfma(hi[a], hj[c], acc[q][a][c]);
-                }
-            }
-            __syncwarp();
+    const int nch = (M + GR_CHUNK - 1) / GR_CHUNK;
+    const long b0 = (long)blockIdx.x * nwarps + warp, bstep = (long)gridDim.x * nwarps;
+    const long nmine = b0 < nbins ? (nbins - 1 - b0) / bstep + 1 : 0;
+    const long nitems = nmine * nch;   // (subcarrier, chunk) pairs of this warp, in order
+    auto issue = [&](long it) {
+        const long b = b0 + (it / nch) * bstep;
+        const int m = (int)(it % nch) * GR_CHUNK + lane;
+        c32 *dst = buf(it);
+        for (int u = 0; u < K; ++u)
+            cp_async8z(dst + u * GR_LD + lane, m < M ? H + (b * K + u) * M + m : H, m < M);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    c32 acc[NT][4][4];
+    if (nitems > 0) issue(0);
+    for (long it = 0; it < nitems; ++it) {
+        const long b = b0 + (it / nch) * bstep;
+        const int ch = (int)(it % nch), m0 = ch * GR_CHUNK;
+        c32 *sH = buf(it);
+        if (it + 1 < nitems) {
+            issue(it + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        // sum the antenna groups of each block: partials [task][16]
-        c32 *red = sH;
+        __syncwarp();
+        if (ch == 0) {
+#pragma unroll
+            for (int q = 0; q < NT; ++q)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][a][c] = make_float2(0.f, 0.f);
+        }
+        if (H16 && m0 + lane < M)
+            for (int u = 0; u < K; ++u) H16[(b * K + u) * M + m0 + lane] = Operand<T16>::from(sH[u * GR_LD + lane]);
 #pragma unroll
         for (int q = 0; q < NT; ++q) {
             if (q >= ntask) break;
-            const int t = lane + 32 * q;
+            const int ri = 4 * bi[q], rj = 4 * bj[q];
+            for (int mm = glo[q]; mm < ghi[q]; ++mm) {
+                c32 hi[4], hj[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) red[t * 16 + a * 4 + c] = acc[q][a][c];
-        }
-        __syncwarp();
-        for (int idx = lane; idx < nbt * 16; idx += 32) {
-            int blk = idx >> 4, r = 0;
-            while (blk > r) { blk -= r + 1; ++r; }
-            const int i = 4 * r + ((idx >> 2) & 3), j = 4 * blk + (idx & 3);
-            if (i < K && j <= i) {
-                c32 sum = make_float2(0.f, 0.f);
-                for (int grp = 0; grp < ng; ++grp) {
-                    const c32 v = red[(grp * nbt + (idx >> 4)) * 16 + (idx & 15)];
-                    sum.x += v.x;
-                    sum.y += v.y;
+                for (int a = 0; a < 4; ++a) {
+                    hi[a] = ri + a < K ? sH[(ri + a) * GR_LD + mm] : make_float2(0.f, 0.f);
+                    hj[a] = rj + a < K ? cconj(sH[(rj + a) * GR_LD + mm]) : make_float2(0.f, 0.f);
                 }
-                Gs[soa(b, tri(i) + j, T)] = sum;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][a][c] = cfma(hi[a], hj[c], acc[q][a][c]);
             }
         }
         __syncwarp();
+        if (ch == nch - 1) {
+            // sum the antenna groups of each block in this (now free) buffer: partials
+            // [task][16]; the other buffer may already hold the next subcarrier's chunk
+            c32 *red = sH;
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                if (q >= ntask) break;
+                const int t = lane + 32 * q;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) red[t * 16 + a * 4 + c] = acc[q][a][c];
+            }
+            __syncwarp();
+            for (int idx = lane; idx < nbt * 16; idx += 32) {
+                int blk = idx >> 4, r = 0;
+                while (blk > r) { blk -= r + 1; ++r; }
+                const int i = 4 * r + ((idx >> 2) & 3), j = 4 * blk + (idx & 3);
+                if (i < K && j <= i) {
+                    c32 sum = make_float2(0.f, 0.f);
+                    for (int grp = 0; grp < ng; ++grp) {
+                        const c32 v = red[(grp * nbt + (idx >> 4)) * 16 + (idx & 15)];
+                        sum.x += v.x;
+                        sum.y += v.y;
+                    }
+                    Gs[soa(b, tri(i) + j, T)] = sum;
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -363,10 +383,7 @@ static cudaError_t persistent_launch_dims(Kern k, int threads, size_t smem, long
                                           long &blocks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
-    if (e != cudaSuccess) return e;
-    blocks = (long)(per_sm > 0 ? per_sm : 1) * sm_count();
+    blocks = (long)resident_ctas(k, threads, smem) * sm_count();
     const long need = (work_items + items_per_cta - 1) / items_per_cta;
     if (blocks > need) blocks = need;
     return cudaSuccess;
@@ -399,18 +416,18 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
     c32 *Ys = reinterpret_cast<c32 *>(reinterpret_cast<char *>(scratch) + al16(sizeof(c32) * (size_t)nb32 * T));
     // gram
     if (phase < 0 || phase == 0) {
-        const int per_warp = (int)gram_warp_bytes(g.K);
-        const size_t smem = (size_t)ZF_WARPS * per_warp;
+        const int per_buf = (int)gram_buf_bytes(g.K);
+        const size_t smem = (size_t)ZF_WARPS * 2 * per_buf;
         long blocks = 0;
         cudaError_t e;
         if (g.K <= 28) {
             e = persistent_launch_dims(zf_gram_kernel<T16, 1>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
-            zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_warp);
+            zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_buf);
         } else {
             e = persistent_launch_dims(zf_gram_kernel<T16, 2>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
-            zf_gram_kernel<T16, 2><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_warp);
+            zf_gram_kernel<T16, 2><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_buf);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
