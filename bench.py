@@ -86,10 +86,12 @@ def stage_work(cfg, S: int, prec: str):
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
         "precode": ("hbm", R * Nd * M * K * opb + S * K * Nd * c8 + S * M * Nd * c8),
-        "fftpa_fwd": ("hbm", S * M * Nd * (c8 + ab)),
+        # BF16 plans: the forward also keeps the time-domain PA input (4 bytes per sample)
+        # that the adjoint reads instead of transforming x_hat again
+        "fftpa_fwd": ("hbm", S * M * Nd * (c8 + ab) + (S * M * cfg.N * 4 if prec == "bf16" else 0)),
         "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * ab + 2 * S * K * Nd * c8),
         "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * ab),
-        "fftpa_adj": ("hbm", S * M * Nd * (c8 + 2 * ab)),
+        "fftpa_adj": ("hbm", S * M * (cfg.N * 4 + 2 * Nd * ab) if prec == "bf16" else S * M * Nd * (c8 + 2 * ab)),
         "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * ab + S * K * Nd * c8),
         "fc_bwd_w": (fc_bound, 2.0 * 2 * Nd * F * cols),
         "fc_bwd_b": ("hbm", cols * 2 * Nd * 4),

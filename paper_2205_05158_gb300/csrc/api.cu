@@ -34,6 +34,7 @@ struct fddpd_plan {
     int kind16;                    // OUT_BF16 or OUT_F16: storage of the H / W copies
     bool tc_bin;                   // per-subcarrier contractions on the tensor cores
     void *H16, *W16;               // [R_max][N_d][K][M] and [R_max][N_d][M][K]
+    void *xt16;                    // BF16 plans: time-domain PA input [S][M][N], forward -> adjoint
     const void *pk_H, *pk_W;       // the FP32 arrays the copies were made from
     int pk_R;
     long adam_t;
@@ -183,11 +184,12 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_w16 = take(2 * (size_t)2 * g.N_d * p->ldF);
         o_wT = take(2 * (size_t)g.F * p->ld2N);
     }
-    size_t o_h16 = 0, o_wq16 = 0;
+    size_t o_h16 = 0, o_wq16 = 0, o_xt = 0;
     if (p->p16) {
         o_h16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
         o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
     }
+    if (d->precision == FDDPD_BF16) o_xt = take(4 * (size_t)S * g.M * g.N);
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
     if (e != cudaSuccess) {
@@ -210,6 +212,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         p->W16 = b + o_wq16;
         p->kind16 = d->precision == FDDPD_FP16 ? fdk::OUT_F16 : fdk::OUT_BF16;
     }
+    if (d->precision == FDDPD_BF16) p->xt16 = b + o_xt;
     e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
     if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
     p->launches = 1;
@@ -379,8 +382,10 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
     }
     FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
+    // a backward follows when gy is wanted: keep the time-domain PA input for its adjoint
+    void *xt = (gy && act_kind(p) == fdk::OUT_BF16) ? p->xt16 : nullptr;
     FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1,
-             fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, act_kind(p), p->met, st));
+             fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, act_kind(p), p->met, xt, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
              reduce_op(p, fdk::COMBINE, S, ops, alpha, p->Xpa, y, s, gy, p->met, inv_count, 1.0f));
     FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
@@ -401,7 +406,8 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     const float gsc = grad_scale(p, 1.0 / ((double)cols * g.N_d));
     FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
-             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, act_kind(p), st));
+             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, act_kind(p),
+                                act_kind(p) == fdk::OUT_BF16 ? p->xt16 : nullptr, st));
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
              reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);

@@ -24,55 +24,59 @@ __global__ void pass_twiddle_kernel(int log2N, c32 *out) {
 size_t fftpa_smem_bytes(const Geo &g, bool /*adjoint*/) { return fftpa_smem_bytes_(g); }
 
 cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *twp, void *X, int out_kind,
-                          double *metrics, cudaStream_t st) {
+                          double *metrics, void *xt_out, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     if (out_kind != OUT_F32 && out_kind != OUT_BF16) return cudaErrorInvalidValue;
+    if (xt_out && out_kind != OUT_BF16) return cudaErrorInvalidValue;
+    cbf16 *xt = static_cast<cbf16 *>(xt_out);
     const bool a16 = out_kind == OUT_BF16;
     switch (g.log2N) {
-        case 6: return a16 ? fftpa_fwd16_6(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 6: return a16 ? fftpa_fwd16_6(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_6(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 7: return a16 ? fftpa_fwd16_7(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 7: return a16 ? fftpa_fwd16_7(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_7(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 8: return a16 ? fftpa_fwd16_8(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 8: return a16 ? fftpa_fwd16_8(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_8(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 9: return a16 ? fftpa_fwd16_9(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 9: return a16 ? fftpa_fwd16_9(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_9(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 10: return a16 ? fftpa_fwd16_10(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 10: return a16 ? fftpa_fwd16_10(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_10(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 11: return a16 ? fftpa_fwd16_11(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 11: return a16 ? fftpa_fwd16_11(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_11(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
-        case 12: return a16 ? fftpa_fwd16_12(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, st)
+        case 12: return a16 ? fftpa_fwd16_12(g, rows, xh, pa, twp, static_cast<cbf16 *>(X), metrics, xt, st)
                      : fftpa_fwd_12(g, rows, xh, pa, twp, static_cast<c32 *>(X), metrics, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *twp, const void *gX,
-                          void *gxh, int act_kind, cudaStream_t st) {
+                          void *gxh, int act_kind, const void *xt_in, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     if (act_kind != OUT_F32 && act_kind != OUT_BF16) return cudaErrorInvalidValue;
+    if (xt_in && act_kind != OUT_BF16) return cudaErrorInvalidValue;
+    const cbf16 *xt = static_cast<const cbf16 *>(xt_in);
     const bool a16 = act_kind == OUT_BF16;
     switch (g.log2N) {
         case 6:
-            return a16 ? fftpa_adj16_6(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_6(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_6(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 7:
-            return a16 ? fftpa_adj16_7(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_7(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_7(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 8:
-            return a16 ? fftpa_adj16_8(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_8(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_8(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 9:
-            return a16 ? fftpa_adj16_9(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_9(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_9(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 10:
-            return a16 ? fftpa_adj16_10(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_10(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_10(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 11:
-            return a16 ? fftpa_adj16_11(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_11(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_11(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         case 12:
-            return a16 ? fftpa_adj16_12(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), st)
+            return a16 ? fftpa_adj16_12(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)
                        : fftpa_adj_12(g, rows, xh, pa, twp, static_cast<const c32 *>(gX), static_cast<c32 *>(gxh), st);
         default: return cudaErrorInvalidValue;
     }

@@ -24,6 +24,8 @@
 // or n + l) from a natural-order copy of the row in shared memory.  CTAs are persistent.
 // All arithmetic is FP32.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -34,6 +36,15 @@ static constexpr float kCos8 = 0.92387953251128676f;   // cos(pi/8)
 static constexpr float kSin8 = 0.38268343236508977f;   // sin(pi/8)
 
 FD_HD int pidx(int i) { return i + (i >> 4); }   // one pad word per 16 entries
+
+// cp.async of 4, 8 or 16 bytes (the row inputs of the next row group, staged in shared memory)
+template <int BYTES> FD_D void cp_async_n(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+FD_D void cp_async_commit_all() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+FD_D void cp_async_wait_none() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <bool INV> FD_D c32 mul_mi(c32 a) {      // a * (-i) forward, a * (+i) inverse
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
@@ -183,7 +194,9 @@ FD_D float powabs(float r2, float mag, int e) {
 // P_ == 0 is the general case (orders and memory from Geo at run time).
 template <int P_, int L_>
 struct RowPa {
-    // y_n = sum_l sum_p c_{p,l} x_{n-l} |x_{n-l}|^{p-1}; xs holds the row in natural order
+    // y_n = sum_l sum_p c_{p,l} x_{n-l} |x_{n-l}|^{p-1}; xs holds the row in natural order.
+    // With odd orders 2k+1 each tap is x * poly_l(|x|^2), poly_l(r) = sum_k c_{k,l} r^k,
+    // evaluated by Horner's rule in the real variable r.
     static FD_D void forward(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *xs, const c32 *cp,
                              bool any_even, c32 (&y)[16]) {
         const int P = P_ > 0 ? P_ : g.n_orders;
@@ -204,13 +217,11 @@ struct RowPa {
                 const c32 xl = l == 0 ? x[q] : xs[pidx((t + q * T - l) & (N - 1))];
                 const float r2 = cabs2(xl);
                 if (P_ > 0) {
-                    c32 phi = xl;
-                    y[q] = cfma(c[0], phi, y[q]);
+                    c32 poly = c[(P_ > 0 ? P_ : 1) - 1];
 #pragma unroll
-                    for (int p = 1; p < (P_ > 0 ? P_ : 1); ++p) {
-                        phi = cscale(phi, r2);
-                        y[q] = cfma(c[p], phi, y[q]);
-                    }
+                    for (int p = (P_ > 0 ? P_ : 1) - 2; p >= 0; --p)
+                        poly = make_float2(fmaf(poly.x, r2, c[p].x), fmaf(poly.y, r2, c[p].y));
+                    y[q] = cfma(xl, poly, y[q]);
                 } else {
                     const float mg = any_even ? sqrtf(r2) : 0.f;
                     for (int p = 0; p < P; ++p)
@@ -223,43 +234,41 @@ struct RowPa {
     static FD_D void adjoint(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *gs, const c32 *cp,
                              c32 (&gx)[16]) {
         if constexpr (P_ > 0) {
-            // odd orders 2k+1, k < P_: a_k = (k+1) |x|^(2k), b_k = k x^2 |x|^(2k-2); both depend
-            // on x_n only, so they are formed once per sample and the taps run inside
+            // odd orders 2k+1, k < P_, r = |x_n|^2:
+            //   sum_l A_l g_{n+l} = sum_k (k+1) r^k G_k(n),  G_k(n) = sum_l conj(c_{k,l}) g_{n+l}
+            //   sum_l B_l conj(g_{n+l}) = x_n^2 sum_{k>=1} k r^(k-1) conj(G_k(n))
+            // (the B sums are the conjugates of the same tap sums), so each sample takes
+            // P_ four-tap filters of g and two Horner evaluations in r
             constexpr int L1 = L_ + 1;
-            c32 c[P_][L1];
+            c32 cc[P_][L1];   // conj(c_{k,l})
 #pragma unroll
             for (int k = 0; k < P_; ++k)
 #pragma unroll
-                for (int l = 0; l < L1; ++l) c[k][l] = cp[k * L1 + l];
+                for (int l = 0; l < L1; ++l) cc[k][l] = cconj(cp[k * L1 + l]);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float r2 = cabs2(x[q]);
-                const c32 xx = cmul(x[q], x[q]);
-                float a[P_];    // (k+1) r2^k
-                c32 bt[P_];     // k x^2 r2^(k-1), k >= 1
-                float rk = 1.0f, rkm1 = 0.0f;   // r2^k, r2^(k-1)
+                c32 G[P_];
 #pragma unroll
-                for (int k = 0; k < P_; ++k) {
-                    a[k] = (float)(k + 1) * rk;
-                    bt[k] = cscale(xx, (float)k * rkm1);
-                    rkm1 = rk;
-                    rk *= r2;
-                }
-                c32 acc = make_float2(0.f, 0.f);
+                for (int k = 0; k < P_; ++k) G[k] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int l = 0; l < L1; ++l) {
                     const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
-                    c32 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < P_; ++k) {
-                        A.x = fmaf(a[k], c[k][l].x, A.x);      // a_k conj(c_{k,l})
-                        A.y = fmaf(-a[k], c[k][l].y, A.y);
-                        if (k >= 1) B = cfma(bt[k], c[k][l], B);
-                    }
-                    acc = cfma(A, gl, acc);
-                    acc = cfma(B, cconj(gl), acc);
+                    for (int k = 0; k < P_; ++k) G[k] = cfma(cc[k][l], gl, G[k]);
                 }
-                gx[q] = acc;
+                const float r2 = cabs2(x[q]);
+                c32 A = cscale(G[P_ - 1], (float)P_);
+#pragma unroll
+                for (int k = P_ - 2; k >= 0; --k)
+                    A = make_float2(fmaf(A.x, r2, (float)(k + 1) * G[k].x), fmaf(A.y, r2, (float)(k + 1) * G[k].y));
+                if (P_ >= 2) {
+                    c32 Bs = cscale(cconj(G[P_ - 1]), (float)(P_ - 1));
+#pragma unroll
+                    for (int k = P_ - 2; k >= 1; --k)
+                        Bs = make_float2(fmaf(Bs.x, r2, (float)k * G[k].x), fmaf(Bs.y, r2, -(float)k * G[k].y));
+                    A = cfma(cmul(x[q], x[q]), Bs, A);
+                }
+                gx[q] = A;
             }
         } else {
             const int P = g.n_orders, L = g.L, L1 = L + 1;
@@ -291,19 +300,27 @@ struct RowPa {
 template <int LOG2N>
 FD_HD constexpr int rows_per_cta_t() { return LOG2N >= 12 ? 1 : (1 << (12 - LOG2N)); }
 
-inline int rows_per_cta(int N) { return N >= 4096 ? 1 : 4096 / N; }
+FD_HD int rows_per_cta(int N) { return N >= 4096 ? 1 : 4096 / N; }
 
 // smem: per-pass twiddles, 2 buffers per row, coefficients per row
-inline size_t fftpa_smem_bytes_(const Geo &g) {
+// smem: per-pass twiddles, 2 buffers per row, coefficients per row, then the staging of
+// the next row group's inputs (stage_bytes per row)
+FD_HD size_t fftpa_smem_base_(const Geo &g) {
     const int N = g.N, padN = N + (N >> 4), r = rows_per_cta(N);
-    return sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * g.n_orders * (g.L + 1));
+    const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * g.n_orders * (g.L + 1));
+    return (b + 15) & ~size_t(15);
+}
+inline size_t fwd_stage_bytes(const Geo &g) { return sizeof(c32) * (size_t)((g.N_d + 1) & ~1); }   // x_hat row
+inline size_t adj_stage_bytes(const Geo &g) { return 4 * (size_t)(g.N + ((g.N_d + 3) & ~3)); }    // x(t), gX rows
+inline size_t fftpa_smem_bytes_(const Geo &g) {
+    return fftpa_smem_base_(g) + (size_t)rows_per_cta(g.N) * fwd_stage_bytes(g);
 }
 
 template <int LOG2N, int P_, int L_, typename TOut>
 __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows, const c32 *__restrict__ xh,
                                                                const c32 *__restrict__ pa,
                                                                const c32 *__restrict__ twp_g, TOut *__restrict__ Xout,
-                                                               double *__restrict__ metrics) {
+                                                               double *__restrict__ metrics, cbf16 *__restrict__ xt) {
     using F = Fft<LOG2N>;
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -313,6 +330,8 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
+    // x_hat rows of the next row group, in flight while this one is transformed
+    c32 *stage = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((g.N_d + 1) & ~1);
     __shared__ double red[32];
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     bool any_even = false;
@@ -320,23 +339,37 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     const float rs = rsqrtf((float)F::N);
     float gpow = 0.f, dpow = 0.f;
     const long ngroups = (rows + RPC - 1) / RPC;
+    auto prefetch = [&](long gg) {
+        const long r = gg * RPC + grp;
+        if (gg < ngroups && r < rows)
+            for (int i = t; i < g.N_d; i += F::T) cp_async_n<8>(stage + i, xh + r * g.N_d + i);
+        cp_async_commit_all();
+    };
+    prefetch(blockIdx.x);
 
     for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
         const int m = (int)(rowc % g.M);
-        __syncthreads();   // the previous row is done with coef and both buffers
+        cp_async_wait_none();
+        __syncthreads();   // this group's rows are staged; the previous row is done with coef and buffers
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
-        const c32 *xrow = xh + rowc * g.N_d;
         c32 x[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+            x[q] = (active && i >= 0) ? stage[i] : make_float2(0.f, 0.f);
         }
+        __syncthreads();   // the staged rows are read
+        prefetch(grp0 + gridDim.x);
         transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
+        if (xt && active) {   // the time-domain PA input, kept (BF16) for the adjoint
+            cbf16 *xrow_t = xt + row * F::N;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) xrow_t[t + q * F::T] = Operand<cbf16>::from(x[q]);
+        }
         __syncthreads();   // the last pass has read its buffer
 #pragma unroll
         for (int q = 0; q < 16; ++q) bufB[pidx(t + q * F::T)] = x[q];
@@ -371,7 +404,8 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
 template <int LOG2N, int P_, int L_, typename TIn, typename TOut>
 __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows, const c32 *__restrict__ xh,
                                                                const c32 *__restrict__ pa,
-                                                               const c32 *__restrict__ twp_g, const TIn *gX, TOut *gxh) {
+                                                               const c32 *__restrict__ twp_g, const TIn *gX, TOut *gxh,
+                                                               const cbf16 *__restrict__ xt) {
     using F = Fft<LOG2N>;
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -381,29 +415,68 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
+    // with a kept x(t) and BF16 gX: both rows of the next row group, in flight while this
+    // one is transformed ([N] then [N_d rounded to 4] 4-byte words per row)
+    constexpr bool STAGE = std::is_same<TIn, cbf16>::value;
+    const int ndp = (g.N_d + 3) & ~3;
+    uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw + fftpa_smem_base_(g)) + grp * (F::N + ndp);
+    uint32_t *sg = sx + F::N;
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     const float rs = rsqrtf((float)F::N);
     const long ngroups = (rows + RPC - 1) / RPC;
+    auto prefetch = [&](long gg) {
+        const long r = gg * RPC + grp;
+        if (gg < ngroups && r < rows) {
+            const uint4 *srcx = reinterpret_cast<const uint4 *>(xt + r * F::N);
+            for (int c = t; c < F::N / 4; c += F::T) cp_async_n<16>(sx + 4 * c, srcx + c);
+            const uint32_t *srcg = reinterpret_cast<const uint32_t *>(gX + r * g.N_d);
+            for (int i = t; i < g.N_d; i += F::T) cp_async_n<4>(sg + i, srcg + i);
+        }
+        cp_async_commit_all();
+    };
+    if (STAGE && xt) prefetch(blockIdx.x);
 
     for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
         const int m = (int)(rowc % g.M);
+        if (STAGE && xt) cp_async_wait_none();
         __syncthreads();
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
         const c32 *xrow = xh + rowc * g.N_d;
         const TIn *grow = gX + rowc * g.N_d;
         c32 x[16], gv[16];
+        if (STAGE && xt) {   // the forward kept the time-domain PA input; both rows staged
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-            x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
-            gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
+            for (int q = 0; q < 16; ++q) {
+                const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
+                x[q] = active ? Operand<cbf16>::load(reinterpret_cast<const cbf16 *>(sx + t + q * F::T))
+                              : make_float2(0.f, 0.f);
+                gv[q] = (active && i >= 0) ? Operand<cbf16>::load(reinterpret_cast<const cbf16 *>(sg + i))
+                                           : make_float2(0.f, 0.f);
+            }
+            __syncthreads();   // the staged rows are read
+            prefetch(grp0 + gridDim.x);
+        } else if (xt) {
+            const cbf16 *xrow_t = xt + rowc * F::N;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
+                x[q] = active ? Operand<cbf16>::load(xrow_t + t + q * F::T) : make_float2(0.f, 0.f);
+                gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
+                x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+                gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
+            }
+            transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
+            __syncthreads();
         }
-        transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
-        __syncthreads();
         transform<LOG2N, true>(gv, bufA, bufB, twp, t, rs);
         __syncthreads();
 #pragma unroll
@@ -440,25 +513,28 @@ inline cudaError_t persistent_blocks(Kern k, int N, long rows, int threads, size
 
 template <int LOG2N, int P_, int L_, typename TOut>
 inline cudaError_t fwd_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, TOut *X,
-                         double *metrics, cudaStream_t st) {
+                         double *metrics, cbf16 *xt, cudaStream_t st) {
     const int threads = 256;
     const size_t sm = fftpa_smem_bytes_(g);
     long blocks = 0;
     cudaError_t e = persistent_blocks(fftpa_forward_kernel<LOG2N, P_, L_, TOut>, g.N, rows, threads, sm, blocks);
     if (e != cudaSuccess) return e;
-    fftpa_forward_kernel<LOG2N, P_, L_, TOut><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, X, metrics);
+    fftpa_forward_kernel<LOG2N, P_, L_, TOut><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, X, metrics,
+                                                                                     xt);
     return cudaGetLastError();
 }
 
 template <int LOG2N, int P_, int L_, typename TA>
 inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const TA *gX,
-                         TA *gxh, cudaStream_t st) {
+                         TA *gxh, const cbf16 *xt, cudaStream_t st) {
     const int threads = 256;
-    const size_t sm = fftpa_smem_bytes_(g);
+    const size_t sm = fftpa_smem_base_(g) + (std::is_same<TA, cbf16>::value && xt
+                                                 ? (size_t)rows_per_cta(g.N) * adj_stage_bytes(g) : 0);
     long blocks = 0;
     cudaError_t e = persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA>, g.N, rows, threads, sm, blocks);
     if (e != cudaSuccess) return e;
-    fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, gX, gxh);
+    fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, gX, gxh,
+                                                                                       xt);
     return cudaGetLastError();
 }
 
@@ -475,46 +551,48 @@ inline int pa_shape(const Geo &g) {
 
 template <int LOG2N, typename TOut>
 inline cudaError_t fwd_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, TOut *X,
-                         double *metrics, cudaStream_t st) {
+                         double *metrics, cbf16 *xt, cudaStream_t st) {
     switch (pa_shape(g)) {
-        case 1: return fwd_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, X, metrics, st);
-        case 2: return fwd_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, X, metrics, st);
-        case 3: return fwd_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, X, metrics, st);
-        default: return fwd_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, X, metrics, st);
+        case 1: return fwd_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, X, metrics, xt, st);
+        case 2: return fwd_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, X, metrics, xt, st);
+        case 3: return fwd_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, X, metrics, xt, st);
+        default: return fwd_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, X, metrics, xt, st);
     }
 }
 
 template <int LOG2N, typename TA>
 inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const TA *gX, TA *gxh,
-                         cudaStream_t st) {
+                         const cbf16 *xt, cudaStream_t st) {
     switch (pa_shape(g)) {
-        case 1: return adj_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, gX, gxh, st);
-        case 2: return adj_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, gX, gxh, st);
-        case 3: return adj_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, gX, gxh, st);
-        default: return adj_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, gX, gxh, st);
+        case 1: return adj_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, gX, gxh, xt, st);
+        case 2: return adj_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, gX, gxh, xt, st);
+        case 3: return adj_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, gX, gxh, xt, st);
+        default: return adj_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, gX, gxh, xt, st);
     }
 }
 
 // Translation units per transform size instantiate these, the FP32-plane variants
 // (FD_FFTPA_SIZE) and the BF16-plane ones (FD_FFTPA_SIZE16: X out of the forward, gX in
-// and g_xhat out of the adjoint in BF16) separately, so they compile in parallel.
+// and g_xhat out of the adjoint in BF16; xt, when given, is the BF16 time-domain PA input
+// the forward keeps and the adjoint reads instead of transforming x_hat again) separately,
+// so they compile in parallel.
 #define FD_FFTPA_SIZE(LOG2N)                                                                                      \
     cudaError_t fftpa_fwd_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, c32 *X,  \
                                   double *metrics, cudaStream_t st) {                                            \
-        return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, st);                                               \
+        return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, nullptr, st);                                      \
     }                                                                                                            \
     cudaError_t fftpa_adj_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,         \
                                   const c32 *gX, c32 *gxh, cudaStream_t st) {                                    \
-        return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, st);                                                  \
+        return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, nullptr, st);                                         \
     }
 #define FD_FFTPA_SIZE16(LOG2N)                                                                                    \
     cudaError_t fftpa_fwd16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
-                                    cbf16 *X, double *metrics, cudaStream_t st) {                                \
-        return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, st);                                               \
+                                    cbf16 *X, double *metrics, cbf16 *xt, cudaStream_t st) {                     \
+        return fwd_n<LOG2N>(g, rows, xh, pa, twp, X, metrics, xt, st);                                           \
     }                                                                                                            \
     cudaError_t fftpa_adj16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
-                                    const cbf16 *gX, cbf16 *gxh, cudaStream_t st) {                              \
-        return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, st);                                                  \
+                                    const cbf16 *gX, cbf16 *gxh, const cbf16 *xt, cudaStream_t st) {             \
+        return adj_n<LOG2N>(g, rows, xh, pa, twp, gX, gxh, xt, st);                                              \
     }
 
 #define FD_FFTPA_DECL(LOG2N)                                                                                      \
@@ -523,9 +601,9 @@ inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     cudaError_t fftpa_adj_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,         \
                                   const c32 *gX, c32 *gxh, cudaStream_t st);                                     \
     cudaError_t fftpa_fwd16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
-                                    cbf16 *X, double *metrics, cudaStream_t st);                                 \
+                                    cbf16 *X, double *metrics, cbf16 *xt, cudaStream_t st);                      \
     cudaError_t fftpa_adj16_##LOG2N(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp,       \
-                                    const cbf16 *gX, cbf16 *gxh, cudaStream_t st);
+                                    const cbf16 *gX, cbf16 *gxh, const cbf16 *xt, cudaStream_t st);
 FD_FFTPA_DECL(6) FD_FFTPA_DECL(7) FD_FFTPA_DECL(8) FD_FFTPA_DECL(9) FD_FFTPA_DECL(10) FD_FFTPA_DECL(11) FD_FFTPA_DECL(12)
 
 }  // namespace fdk

@@ -70,10 +70,12 @@ cudaError_t to_16bit(long n, const c32 *in, void *out, int kind, cudaStream_t st
 
 // OFDM + PA rows
 size_t fftpa_smem_bytes(const Geo &g, bool adjoint);
+// xt (BF16 planes only, may be null): the forward stores the time-domain PA input there
+// [rows][N], and the adjoint reads it instead of transforming x_hat again
 cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, void *X, int out_kind,
-                          double *metrics, cudaStream_t st);
+                          double *metrics, void *xt, cudaStream_t st);
 cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const void *gX, void *gxh,
-                          int act_kind, cudaStream_t st);
+                          int act_kind, const void *xt, cudaStream_t st);
 
 // parameter updates and bookkeeping
 cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);
