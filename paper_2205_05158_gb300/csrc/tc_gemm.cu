@@ -114,18 +114,33 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
             (void)issued;
         }
     } else {
-        const bool ok = mbar_wait(&done, 0, err) && nkb > 0;
-        fence_after();
+        // epilogue: the operands the functor reads besides the accumulator (residual,
+        // activation) are fetched PRE chunks ahead, the first ones while the MMAs run
+        constexpr int PRE = 4, NCH = BN / 16;
         const int q = warp & 3;
         const int row = m0 + 32 * q + lane;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-            if (ok && row < Mdim) {
+        const bool rok = row < Mdim;
+        typename Epi::Pre pre[PRE];
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (n0 + c0 + j < Ndim) epi(row, n0 + c0 + j, v[j]);
+        for (int c = 0; c < PRE; ++c)
+            if (rok && n0 + 16 * c + 16 <= Ndim) epi.prefetch(row, n0 + 16 * c, pre[c]);
+        const bool ok = mbar_wait(&done, 0, err) && nkb > 0;
+        fence_after();
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * c), v);
+            const int n = n0 + 16 * c;
+            if (ok && rok && n < Ndim) {
+                if (n + 16 <= Ndim) {
+                    epi.chunk(row, n, v, pre[c % PRE]);   // 16 contiguous columns of the row
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n + j < Ndim) epi(row, n + j, v[j]);
+                }
             }
+            if (c + PRE < NCH && rok && n + 16 * PRE + 16 <= Ndim) epi.prefetch(row, n + 16 * PRE, pre[c % PRE]);
         }
     }
     fence_before();
@@ -189,39 +204,125 @@ static cudaError_t launch(const GemmArgs &g, const Epi &epi, int *err, cudaStrea
 }
 
 // --- epilogues --------------------------------------------------------------
+// operator()(m, n, v): one element; chunk(m, n, v[16], pre): columns n .. n + 15 of row m,
+// n a multiple of 16 -- whole 32-byte sectors where the row layout allows (vec) -- with
+// what prefetch(m, n, pre) loaded for those columns beforehand
+struct NoPre {};
 struct EpiStore {          // C[m][n] = acc (plain GEMM, ldc)
+    using Pre = NoPre;
     float *C;
     long ldc;
     FD_D void operator()(int m, int n, float v) const { C[(long)m * ldc + n] = v; }
+    FD_D void prefetch(int, int, Pre &) const {}
+    FD_D void chunk(int m, int n, const float (&v)[16], const Pre &) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
+    }
 };
 struct EpiAdd {            // C[m][n] += acc (split-K partial sums)
+    using Pre = NoPre;
     float *C;
     long ldc;
     FD_D void operator()(int m, int n, float v) const { atomicAdd(C + (long)m * ldc + n, v); }
+    FD_D void prefetch(int, int, Pre &) const {}
+    FD_D void chunk(int m, int n, const float (&v)[16], const Pre &) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
+    }
 };
 struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] + residual * s
+    struct Pre {
+        float4 r[4];
+    };
     float *st;
     const float *s, *fb;
-    int Nd, residual;
+    int Nd, residual, vec;  // vec: st and s rows 32-byte aligned
     FD_D void operator()(int m, int n, float v) const {
         const long idx = (long)m * 2 * Nd + n;
         st[idx] = v + fb[(n & 1) * Nd + (n >> 1)] + (residual ? s[idx] : 0.f);
     }
+    FD_D void prefetch(int m, int n, Pre &p) const {
+        if (vec && residual) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(s + (long)m * 2 * Nd + n);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) p.r[h] = s4[h];
+        }
+    }
+    FD_D void chunk(int m, int n, const float (&v)[16], const Pre &p) const {
+        if (!vec) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
+            return;
+        }
+        const long idx = (long)m * 2 * Nd + n;
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = v[j] + fb[(j & 1) * Nd + ((n + j) >> 1)];
+        if (residual) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                o[4 * h] += p.r[h].x;
+                o[4 * h + 1] += p.r[h].y;
+                o[4 * h + 2] += p.r[h].z;
+                o[4 * h + 3] += p.r[h].w;
+            }
+        }
+        st_global_v8(st + idx, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7]);
+        st_global_v8(st + idx + 8, o[8], o[9], o[10], o[11], o[12], o[13], o[14], o[15]);
+    }
 };
 struct EpiFcBwdData {      // gpre[m][f] = acc where act > 0
+    struct Pre {
+        uint4 a[2];
+    };
     float *gpre;
     const __nv_bfloat16 *act;
     long ld_act;
-    int F;
+    int F, vec;             // vec: gpre rows 32-byte and act rows 16-byte aligned
     FD_D void operator()(int m, int n, float v) const {
         gpre[(long)m * F + n] = __bfloat162float(act[(long)m * ld_act + n]) > 0.f ? v : 0.f;
     }
+    FD_D void prefetch(int m, int n, Pre &p) const {
+        if (vec) {
+            const uint4 *a4 = reinterpret_cast<const uint4 *>(act + (long)m * ld_act + n);
+            p.a[0] = a4[0];
+            p.a[1] = a4[1];
+        }
+    }
+    FD_D void chunk(int m, int n, const float (&v)[16], const Pre &p) const {
+        if (!vec) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
+            return;
+        }
+        float o[16];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t w[4] = {p.a[h].x, p.a[h].y, p.a[h].z, p.a[h].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[k]);
+                const float2 f2 = __bfloat1622float2(b2);
+                o[8 * h + 2 * k] = f2.x > 0.f ? v[8 * h + 2 * k] : 0.f;
+                o[8 * h + 2 * k + 1] = f2.y > 0.f ? v[8 * h + 2 * k + 1] : 0.f;
+            }
+        }
+        float *g = gpre + (long)m * F + n;
+        st_global_v8(g, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7]);
+        st_global_v8(g + 8, o[8], o[9], o[10], o[11], o[12], o[13], o[14], o[15]);
+    }
 };
 struct EpiFcBwdWeight {    // grad fc_w[pi(n')][f] += acc (split-K partial sums)
+    using Pre = NoPre;
     float *gfw;
     int Nd, F;
     FD_D void operator()(int m, int n, float v) const {
         atomicAdd(gfw + (long)((m & 1) * Nd + (m >> 1)) * F + n, v);
+    }
+    FD_D void prefetch(int, int, Pre &) const {}
+    FD_D void chunk(int m, int n, const float (&v)[16], const Pre &) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
     }
 };
 
@@ -232,14 +333,19 @@ cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaS
     return tc::launch<256>(g, tc::EpiStore{C, ldc}, err, st);
 }
 
+static bool al(const void *p, int b) { return !(reinterpret_cast<uintptr_t>(p) & (uintptr_t)(b - 1)); }
+
 cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
                           int *err, cudaStream_t st) {
-    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fb, Nd, residual}, err, st);
+    // rows of 2 N_d floats: whole sectors when that is a multiple of 8 and both bases align
+    const int vec = (2 * Nd) % 8 == 0 && al(st_out, 32) && (!residual || al(s, 16));
+    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fb, Nd, residual, vec}, err, st);
 }
 
 cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, const __nv_bfloat16 *act, long ld_act, int F, int *err,
                                 cudaStream_t st) {
-    return tc::launch<256>(g, tc::EpiFcBwdData{gpre, act, ld_act, F}, err, st);
+    const int vec = F % 8 == 0 && ld_act % 8 == 0 && al(gpre, 32) && al(act, 16);
+    return tc::launch<256>(g, tc::EpiFcBwdData{gpre, act, ld_act, F, vec}, err, st);
 }
 
 cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, int *err, cudaStream_t st) {
