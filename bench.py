@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--symbols", type=int, default=2000)
-    ap.add_argument("--cpu-sample", type=int, default=6, help="symbols in the oracle's cpu_baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=20, help="symbols in the oracle's cpu_baseline sample")
     ap.add_argument("--ref-sample", type=int, default=2, help="symbols per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

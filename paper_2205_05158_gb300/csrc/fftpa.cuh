@@ -163,8 +163,14 @@ FD_D void transform(c32 (&x)[16], c32 *bufA, c32 *bufB, const c32 *twp, int t, f
     for (int i = 1; i <= F::NP; ++i) {
         const int Ns = F::ns(i);
         const int k = t & (Ns - 1);
+        if constexpr ((F::T & 15) == 0) {   // pidx(t + r T) = pidx(t) + r (T + T / 16)
+            const c32 *s0 = src + pidx(t);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = src[pidx(t + r * F::T)];
+            for (int r = 0; r < 16; ++r) v[r] = s0[r * (F::T + F::T / 16)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = src[pidx(t + r * F::T)];
+        }
         const c32 *tw = twp + F::tw_off(i);
 #pragma unroll
         for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], tw[(r - 1) * Ns + k]);
@@ -212,9 +218,17 @@ struct RowPa {
 #pragma unroll
                 for (int p = 0; p < (P_ > 0 ? P_ : 1); ++p) c[p] = cp[p * L1 + l];
             }
+            // tap n - l of sample n = t + q T: with T a multiple of 16, pidx(i + q T) =
+            // pidx(i) + q (T + T / 16), so one base per tap and constant offsets; only q = 0
+            // can wrap around the row
+            const int stepq = T + (T >> 4);
+            const c32 *tap_q1 = xs + pidx(t - l + T) - stepq;   // + q stepq for q >= 1
+            const c32 *tap_q0 = xs + pidx((t - l) & (N - 1));
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const c32 xl = l == 0 ? x[q] : xs[pidx((t + q * T - l) & (N - 1))];
+                const c32 xl = l == 0 ? x[q]
+                                      : ((T & 15) == 0 ? (q == 0 ? *tap_q0 : tap_q1[q * stepq])
+                                                       : xs[pidx((t + q * T - l) & (N - 1))]);
                 const float r2 = cabs2(xl);
                 if (P_ > 0) {
                     c32 poly = c[(P_ > 0 ? P_ : 1) - 1];
@@ -245,6 +259,9 @@ struct RowPa {
             for (int k = 0; k < P_; ++k)
 #pragma unroll
                 for (int l = 0; l < L1; ++l) cc[k][l] = cconj(cp[k * L1 + l]);
+            // sample n + l of n = t + q T: one base per tap (T a multiple of 16), only q = 15
+            // can wrap around the row
+            const int stepq = T + (T >> 4);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 c32 G[P_];
@@ -252,7 +269,8 @@ struct RowPa {
                 for (int k = 0; k < P_; ++k) G[k] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int l = 0; l < L1; ++l) {
-                    const c32 gl = gs[pidx((t + q * T + l) & (N - 1))];
+                    const c32 gl = ((T & 15) == 0 && q < 15) ? gs[pidx(t + l) + q * stepq]
+                                                             : gs[pidx((t + q * T + l) & (N - 1))];
 #pragma unroll
                     for (int k = 0; k < P_; ++k) G[k] = cfma(cc[k][l], gl, G[k]);
                 }

@@ -233,6 +233,7 @@ struct EpiAdd {            // C[m][n] += acc (split-K partial sums)
 struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] + residual * s
     struct Pre {
         float4 r[4];
+        float b[16];
     };
     float *st;
     const float *s, *fb;
@@ -242,7 +243,10 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
         st[idx] = v + fb[(n & 1) * Nd + (n >> 1)] + (residual ? s[idx] : 0.f);
     }
     FD_D void prefetch(int m, int n, Pre &p) const {
-        if (vec && residual) {
+        if (!vec) return;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) p.b[j] = fb[(j & 1) * Nd + ((n + j) >> 1)];
+        if (residual) {
             const float4 *s4 = reinterpret_cast<const float4 *>(s + (long)m * 2 * Nd + n);
 #pragma unroll
             for (int h = 0; h < 4; ++h) p.r[h] = s4[h];
@@ -257,7 +261,7 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
         const long idx = (long)m * 2 * Nd + n;
         float o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] = v[j] + fb[(j & 1) * Nd + ((n + j) >> 1)];
+        for (int j = 0; j < 16; ++j) o[j] = v[j] + p.b[j];
         if (residual) {
 #pragma unroll
             for (int h = 0; h < 4; ++h) {

@@ -40,12 +40,14 @@ FD_D bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false (and *err set) on timeout.
+// Bounded wait for the phase with the given parity; false (and *err set) on timeout.  The
+// clock is read once per 256 polls, not after every one.
 FD_D bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
         if (globaltimer() - t0 > kWaitNs) {
             atomicOr(err, 2);
             return false;

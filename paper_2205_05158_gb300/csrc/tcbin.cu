@@ -52,7 +52,10 @@ constexpr int EX_A = 4 * 128 * 128, EX_B = 4 * 32 * 128;
 constexpr int EX_SMEM = EX_A + EX_B + 1024;
 // reduce: A (activations) [4 k-blocks][128 rows][128 B], B (H or W^H) [4 k-blocks][64
 // rows][128 B], then the staging of the results [16 t][16 u][4 subcarriers]
-constexpr int RD_A = 4 * 128 * 128, RD_B = 4 * 64 * 128, RD_Y = TS * 16 * RDB * 8;
+// result staging: symbol rows of 16 users x 4 subcarriers x (re, im) floats, padded to
+// 130 floats so the 16 symbols of a warp's write land in different banks
+constexpr int RD_YT = 16 * RDB * 2 + 2;
+constexpr int RD_A = 4 * 128 * 128, RD_B = 4 * 64 * 128, RD_Y = TS * RD_YT * 4;
 constexpr int RD_SMEM = RD_A + RD_B + RD_Y + 1024;
 
 template <typename T16> struct Pk;
@@ -117,9 +120,10 @@ FD_D uint32_t setup(uint64_t *bar, uint32_t *slot, uint32_t cols) {
     return *slot;
 }
 
-// Waits for the MMAs of this round; false in every thread of the CTA if any timed out.
+// Waits for the MMAs of this round (one thread polls, the CTA meets it at the barrier);
+// false in every thread of the CTA if the wait timed out.
 FD_D bool wait_mma(uint64_t *bar, uint32_t &phase, int *err) {
-    const bool ok = mbar_wait(bar, phase, err);
+    const bool ok = threadIdx.x == 0 ? mbar_wait(bar, phase, err) : true;
     phase ^= 1u;
     const bool all = __syncthreads_and(ok) != 0;
     fence_after();
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sA = align1024(smem_raw);          // activations [4 k-blocks][128 rows][128 B]
     uint8_t *sB = sA + RD_A;                    // H / W^H     [4 k-blocks][64 rows][128 B]
-    float *sY = reinterpret_cast<float *>(sB + RD_B);   // [t][u][b][re, im]
+    float *sY = reinterpret_cast<float *>(sB + RD_B);   // [t][u][b][re, im], rows of RD_YT floats
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_slot;
     __shared__ double red[32];
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                     if (b < nb && t < ns) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
-                            if (u < K) sY[((t * 16 + u) * RDB + b) * 2 + c] = v[u] * sc;
+                            if (u < K) sY[t * RD_YT + (u * RDB + b) * 2 + c] = v[u] * sc;
                     }
                 }
                 __syncthreads();
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                     const int e = tid + k * THREADS;
                     const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
                     if (e >= nout || b >= nb) continue;
-                    const c32 v = sYc[(t * 16 + u) * RDB + b];
+                    const c32 v = sYc[(t * RD_YT + (u * RDB + b) * 2) / 2];
                     const long idx = ((t0 + s0 + t) * K + u) * Nd + i0 + b;
                     if (COMB) {
                         const c32 sr = sref[k];
@@ -542,6 +546,348 @@ __global__ void __launch_bounds__(THREADS, 2)
             fence_before();
             __syncthreads();
         }
+    }
+    teardown(&bar, phase, alive, tmem, 64, err);
+    if (COMB && metrics) {
+        const double es = block_sum((double)err_acc, red);
+        const double ss = block_sum((double)sig_acc, red);
+        if (tid == 0) {
+            atomicAdd(metrics + 1, es);
+            atomicAdd(metrics + 2, ss);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The expand for the benchmark shape -- BF16 plans, M = 128, K = 16, one 16-symbol block
+// per realisation -- software-pipelined: as soon as an item's MMAs are complete, the next
+// item's A tile (cp.async) and activations (registers) go in flight, during this item's
+// store-heavy epilogue.
+template <bool CONJ, bool AT, typename TO>
+__global__ void __launch_bounds__(THREADS, 2)
+    expand_pipe_kernel(Geo g, int S, const uint32_t *__restrict__ A, const float *__restrict__ alpha,
+                       const c32 *__restrict__ B, TO *__restrict__ out, int inv_alpha, int vec_ok, int *err) {
+    constexpr int M = 128, K = 16, PER = TS * 16 * EXB / THREADS;   // B elements per thread
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sA = align1024(smem_raw);
+    uint8_t *sB = sA + EX_A;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Nd = g.N_d;
+    const int ngroups = (Nd + EXB - 1) / EXB;
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long nitems = (long)R * ngroups;
+    const uint32_t tmem = setup(&bar, &tmem_slot, 256);
+    const uint32_t idesc = instr_desc(1, 128, 32);
+    uint32_t phase = 0;
+    bool alive = true;
+
+    struct It {
+        long t0, bin0;
+        int i0, ns, nb;
+    };
+    auto info = [&](long item) {
+        It u;
+        const int r = (int)(item / ngroups);
+        u.i0 = (int)(item % ngroups) * EXB;
+        u.t0 = (long)r * g.S_per_real;
+        u.ns = (int)min((long)g.S_per_real, (long)S - u.t0);
+        u.bin0 = (long)r * Nd + u.i0;
+        u.nb = min(EXB, Nd - u.i0);
+        return u;
+    };
+    c32 bv[PER];   // the activations of the item being prepared
+    auto issue = [&](const It &u) {
+        // A by cp.async: direct (W16 rows m) or transposed (H16, lanes along m)
+        for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
+            if (!AT) {
+                const int ch = c & 7, m = (c >> 3) & 127, b = 2 * (c >> 10) + (ch >> 2);
+                const bool ok = b < u.nb;
+                cp_async16(sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8),
+                           ok ? A + ((u.bin0 + b) * M + m) * K + 4 * (ch & 3) : A, ok);
+            } else {
+                const int m = c & 127, ch = (c >> 7) & 7, b = 2 * (c >> 10) + (ch >> 2);
+                const int u0 = 4 * (ch & 3);
+                uint8_t *dst = sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8);
+                const bool ok = b < u.nb;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cp_async4(dst + 4 * j, ok ? A + ((u.bin0 + b) * K + u0 + j) * M + m : A, ok);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < PER; ++h) {
+            const int e = tid + h * THREADS, b = e & 7, uu = (e >> 3) & 15, t = e >> 7;
+            bv[h] = (t < u.ns && b < u.nb) ? B[((u.t0 + t) * K + uu) * Nd + u.i0 + b] : make_float2(0.f, 0.f);
+        }
+    };
+    if (blockIdx.x < nitems) issue(info(blockIdx.x));
+
+    for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
+        const It u = info(item);
+        float sc[EXB];
+#pragma unroll
+        for (int j = 0; j < EXB; ++j) {
+            const float al = j < u.nb ? alpha[u.bin0 + j] : 0.f;
+            sc[j] = inv_alpha ? 1.0f / al : al;
+        }
+        // B: rows 2t and 2t + 1 of pair tile b >> 1 at k = 32 (b & 1) + 2u
+#pragma unroll
+        for (int h = 0; h < PER; ++h) {
+            const int e = tid + h * THREADS, b = e & 7, uu = (e >> 3) & 15, t = e >> 7;
+            uint32_t w0, w1;
+            real_rows<cbf16, CONJ>(bv[h].x, bv[h].y, w0, w1);
+            uint8_t *tile = sB + (b >> 1) * 4096;
+            const int k = 32 * (b & 1) + 2 * uu;
+            st32(tile + sw128_offset(2 * t, k), w0);
+            st32(tile + sw128_offset(2 * t + 1, k), w1);
+        }
+        cp_async_wait_all();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            for (int b = 0; b < u.nb; ++b)
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t off = (b & 1) * 64 + ks * 32;
+                    mma_f16(tmem + 32 * b, smem_desc(sA + (b >> 1) * 16384 + off),
+                            smem_desc(sB + (b >> 1) * 4096 + off), idesc, ks ? 1u : 0u);
+                }
+            mma_commit(&bar);
+        }
+        alive = wait_mma(&bar, phase, err);
+        if (!alive) break;
+        // the operands are consumed: the next item's go in flight during this epilogue
+        if (item + gridDim.x < nitems) issue(info(item + gridDim.x));
+        const int q = warp & 3, m = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        if constexpr (std::is_same<TO, c32>::value) {
+            const int hb = 4 * (warp >> 2);
+            const bool vec = vec_ok && hb + 4 <= u.nb;
+            float sch[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sch[j] = hb ? sc[4 + j] : sc[j];
+            for (int tb = 0; 4 * tb < u.ns; ++tb) {
+                float v[4][8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tmem_ld8(trow + 32 * (hb + j) + 8 * tb, v[j]);
+#pragma unroll
+                for (int tt = 0; tt < 4; ++tt) {
+                    const int t = 4 * tb + tt;
+                    if (t >= u.ns) break;
+                    c32 *dst = out + ((u.t0 + t) * M + m) * Nd + u.i0 + hb;
+                    if (vec) {
+                        st_global_v8(dst, v[0][2 * tt] * sch[0], v[0][2 * tt + 1] * sch[0], v[1][2 * tt] * sch[1],
+                                     v[1][2 * tt + 1] * sch[1], v[2][2 * tt] * sch[2], v[2][2 * tt + 1] * sch[2],
+                                     v[3][2 * tt] * sch[3], v[3][2 * tt + 1] * sch[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (hb + j < u.nb) dst[j] = make_float2(v[j][2 * tt] * sch[j], v[j][2 * tt + 1] * sch[j]);
+                    }
+                }
+            }
+        } else {
+            const bool vec = vec_ok && u.nb == EXB;
+            for (int tb = warp >> 2; 4 * tb < u.ns; tb += 2) {
+                uint32_t w[4][EXB];
+#pragma unroll
+                for (int b = 0; b < EXB; ++b) {
+                    float v[8];
+                    tmem_ld8(trow + 32 * b + 8 * tb, v);
+#pragma unroll
+                    for (int tt = 0; tt < 4; ++tt) w[tt][b] = pack_bf16(v[2 * tt] * sc[b], v[2 * tt + 1] * sc[b]);
+                }
+#pragma unroll
+                for (int tt = 0; tt < 4; ++tt) {
+                    const int t = 4 * tb + tt;
+                    if (t >= u.ns) break;
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(out + ((u.t0 + t) * M + m) * Nd + u.i0);
+                    if (vec) {
+                        st_global_v8(dst, w[tt]);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < EXB; ++b)
+                            if (b < u.nb) dst[b] = w[tt][b];
+                    }
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();
+    }
+    teardown(&bar, phase, alive, tmem, 256, err);
+}
+
+// ---------------------------------------------------------------------------
+// The reduce for the benchmark shape -- BF16 activation planes, M = 128, K = 16, one
+// 16-symbol block per realisation -- software-pipelined: right after an item's A tile is
+// built, the activation loads of the CTA's next item are issued into the registers it
+// freed, so they are in flight during this item's MMAs and epilogue.
+template <bool CONJ, bool AT, bool COMB>
+__global__ void __launch_bounds__(THREADS, 2)
+    reduce_pipe_kernel(Geo g, int S, const uint32_t *__restrict__ Wt, const float *__restrict__ alpha,
+                       const cbf16 *__restrict__ X, c32 *__restrict__ out, const c32 *__restrict__ s_ref,
+                       c32 *__restrict__ gy, double *metrics, double inv_count, int inv_alpha, int vec_ok, int *err) {
+    constexpr int M = 128, K = 16, PER = TS * 128 / THREADS;   // (t, m) pairs per thread
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sA = align1024(smem_raw);
+    uint8_t *sB = sA + RD_A;
+    float *sY = reinterpret_cast<float *>(sB + RD_B);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double red[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Nd = g.N_d;
+    const int ngroups = (Nd + RDB - 1) / RDB;
+    const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    const long nitems = (long)R * ngroups;
+    const uint32_t tmem = setup(&bar, &tmem_slot, 64);
+    const uint32_t idesc = instr_desc(1, 128, 64);
+    const float gscale = (float)(2.0 * inv_count);
+    uint32_t phase = 0;
+    bool alive = true;
+    float err_acc = 0.f, sig_acc = 0.f;
+
+    struct It {
+        long t0, bin0;
+        int i0, ns, nb;
+    };
+    auto info = [&](long item) {
+        It u;
+        const int r = (int)(item / ngroups);
+        u.i0 = (int)(item % ngroups) * RDB;
+        u.t0 = (long)r * g.S_per_real;
+        u.ns = (int)min((long)g.S_per_real, (long)S - u.t0);
+        u.bin0 = (long)r * Nd + u.i0;
+        u.nb = min(RDB, Nd - u.i0);
+        return u;
+    };
+    uint32_t w[PER][RDB];   // the activations of the item being prepared
+    auto load_acts = [&](const It &u) {
+        const bool vec = vec_ok && u.nb == RDB;
+#pragma unroll
+        for (int h = 0; h < PER; ++h) {
+            const int e = tid + h * THREADS, m = e & 127, t = e >> 7;
+            const bool ok = t < u.ns;
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(X + ((u.t0 + (ok ? t : 0)) * M + m) * Nd + u.i0);
+            if (ok && vec) {
+                const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
+                w[h][0] = q4.x;
+                w[h][1] = q4.y;
+                w[h][2] = q4.z;
+                w[h][3] = q4.w;
+            } else {
+#pragma unroll
+                for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < u.nb) ? src[b] : 0u;
+            }
+        }
+    };
+    // B rows 16 b + u of an item by cp.async (into a tile no MMA is reading)
+    auto issue_b = [&](const It &u) {
+        if (!AT) {
+            for (int c = tid; c < RDB * K * 32; c += THREADS) {
+                const int mc = c & 31, uu = (c >> 5) & 15, b = c >> 9;
+                const bool ok = b < u.nb;
+                cp_async16(sB + (mc >> 3) * 8192 + sw128_offset(16 * b + uu, (mc & 7) * 8),
+                           ok ? Wt + ((u.bin0 + b) * K + uu) * M + 4 * mc : Wt, ok);
+            }
+        } else {
+            for (int c = tid; c < RDB * M * 4; c += THREADS) {
+                const int uq = c & 3, m = (c >> 2) & 127, b = c >> 9;
+                const bool ok = b < u.nb;
+                const uint32_t *src = ok ? Wt + ((u.bin0 + b) * M + m) * K + 4 * uq : Wt;
+                uint8_t *dst = sB + (m >> 5) * 8192;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    cp_async4(dst + sw128_offset(16 * b + 4 * uq + j, 2 * (m & 31)), ok ? src + j : Wt, ok);
+            }
+        }
+    };
+    if (blockIdx.x < nitems) {
+        load_acts(info(blockIdx.x));
+        issue_b(info(blockIdx.x));
+    }
+
+    for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
+        const It u = info(item);
+        float sc = 0.f;
+        if (warp < u.nb) {
+            const float al = alpha[u.bin0 + warp];
+            sc = inv_alpha ? 1.0f / al : al;
+        }
+        // A: the real form of this item's activations (loaded during the previous item)
+#pragma unroll
+        for (int h = 0; h < PER; ++h) {
+            const int e = tid + h * THREADS, m = e & 127, t = e >> 7;
+            uint8_t *tile = sA + (m >> 5) * 16384;
+            const int k = 2 * (m & 31);
+#pragma unroll
+            for (int b = 0; b < RDB; ++b) {
+                uint32_t w0, w1;
+                real_rows_packed<CONJ>(w[h][b], w0, w1);
+                st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
+                st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
+            }
+        }
+        // the next item's activations go in flight now
+        if (item + gridDim.x < nitems) load_acts(info(item + gridDim.x));
+        const int nout = u.ns * K * RDB;
+        c32 sref[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + k * THREADS;
+            const int b = e & (RDB - 1), uu = (e >> 2) & 15, t = e >> 6;
+            sref[k] = (COMB && e < nout && b < u.nb) ? s_ref[((u.t0 + t) * K + uu) * Nd + u.i0 + b]
+                                                     : make_float2(0.f, 0.f);
+        }
+        cp_async_wait_all();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks)
+                mma_f16(tmem, smem_desc(sA + (ks >> 2) * 16384 + (ks & 3) * 32),
+                        smem_desc(sB + (ks >> 2) * 8192 + (ks & 3) * 32), idesc, ks ? 1u : 0u);
+            mma_commit(&bar);
+        }
+        alive = wait_mma(&bar, phase, err);
+        // the tiles are consumed: the next item's B goes in flight during this epilogue
+        if (alive && item + gridDim.x < nitems) issue_b(info(item + gridDim.x));
+        if (alive) {
+            if (warp < RDB) {
+                const int b = warp, t = lane >> 1, c = lane & 1;
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
+                if (b < u.nb && t < u.ns) {
+#pragma unroll
+                    for (int uu = 0; uu < 16; ++uu) sY[t * RD_YT + (uu * RDB + b) * 2 + c] = v[uu] * sc;
+                }
+            }
+            __syncthreads();
+            const c32 *sYc = reinterpret_cast<const c32 *>(sY);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = tid + k * THREADS;
+                const int b = e & (RDB - 1), uu = (e >> 2) & 15, t = e >> 6;
+                if (e >= nout || b >= u.nb) continue;
+                const c32 v = sYc[(t * RD_YT + (uu * RDB + b) * 2) / 2];
+                const long idx = ((u.t0 + t) * K + uu) * Nd + u.i0 + b;
+                if (COMB) {
+                    const c32 d = csub(v, sref[k]);
+                    err_acc += cabs2(d);
+                    sig_acc += cabs2(sref[k]);
+                    if (out) out[idx] = v;
+                    if (gy) gy[idx] = cscale(d, gscale);
+                } else {
+                    out[idx] = v;
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();
     }
     teardown(&bar, phase, alive, tmem, 64, err);
     if (COMB && metrics) {
@@ -591,6 +937,20 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
     const uint32_t *a = static_cast<const uint32_t *>(A);
     unsigned blocks = 0;
     cudaError_t e;
+    if constexpr (std::is_same<T16, cbf16>::value) {
+        if (g.M == 128 && g.K == 16 && g.S_per_real <= TS && b_scale == 1.0f) {
+            if (mode == PRECODE) {
+                auto k = expand_pipe_kernel<false, false, TO>;
+                if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+                k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 0, vec_ok, err);
+            } else {
+                auto k = expand_pipe_kernel<true, true, TO>;
+                if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+                k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 1, vec_ok, err);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (mode == PRECODE) {
         auto k = expand_kernel<T16, false, false, TO>;
         if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
@@ -616,6 +976,20 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
     unsigned blocks = 0;
     cudaError_t e;
     const bool full = g.M == 128 && g.K == 16;
+    if constexpr (std::is_same<TX, cbf16>::value && std::is_same<T16, cbf16>::value) {
+        if (full && g.S_per_real <= TS && b_scale == 1.0f) {
+            if (mode == COMBINE) {
+                auto k = reduce_pipe_kernel<false, false, true>;
+                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, vec_ok, err);
+            } else {
+                auto k = reduce_pipe_kernel<true, true, false>;
+                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, vec_ok, err);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (mode == COMBINE) {
         auto k = full ? reduce_kernel<T16, false, false, true, TX, true> : reduce_kernel<T16, false, false, true, TX, false>;
         if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                 }
             mma_commit(&bar);
         }
-        const bool ok = mbar_wait(&bar, phase, err);
+        const bool ok = tid == 0 ? mbar_wait(&bar, phase, err) : true;   // one thread polls
         phase ^= 1u;
         alive = __syncthreads_and(ok) != 0;
         fence_after();
