@@ -86,12 +86,14 @@ def stage_work(cfg, S: int, prec: str):
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
         "precode": ("hbm", R * Nd * M * K * opb + S * K * Nd * c8 + S * M * Nd * c8),
-        # BF16 plans: the forward also keeps the time-domain PA input (4 bytes per sample)
-        # that the adjoint reads instead of transforming x_hat again
-        "fftpa_fwd": ("hbm", S * M * Nd * (c8 + ab) + (S * M * cfg.N * 4 if prec == "bf16" else 0)),
+        # the row kernels are bound by FP32 arithmetic: per row two N-point transforms at the
+        # conventional 5 N log2 N flops each, plus the PA (4 taps x 19 flops: |x|^2, the
+        # Horner polynomial in |x|^2, the complex multiply-add) or its adjoint (three 4-tap
+        # complex filters, 96 flops, plus ~26 for the two Horner evaluations and x^2)
+        "fftpa_fwd": ("alu", S * M * (2 * 5.0 * cfg.N * math.log2(cfg.N) + cfg.N * (cfg.L + 1) * 19.0)),
         "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * ab + 2 * S * K * Nd * c8),
         "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * ab),
-        "fftpa_adj": ("hbm", S * M * (cfg.N * 4 + 2 * Nd * ab) if prec == "bf16" else S * M * Nd * (c8 + 2 * ab)),
+        "fftpa_adj": ("alu", S * M * (2 * 5.0 * cfg.N * math.log2(cfg.N) + cfg.N * (24.0 * (cfg.L + 1) + 26.0))),
         "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * ab + S * K * Nd * c8),
         "fc_bwd_w": (fc_bound, 2.0 * 2 * Nd * F * cols),
         "fc_bwd_b": ("hbm", cols * 2 * Nd * 4),

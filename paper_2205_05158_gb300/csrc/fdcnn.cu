@@ -74,6 +74,159 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(Geo g, int cols_per_cta, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The benchmark's network (3 x 3 kernels, stride 1, 2 input channels -- the real and
+// imaginary parts of one user's symbols -- and 2 output channels) without a staged grid:
+// a thread owns output positions p = tid + 256 k for every column, whose 9-tap validity
+// masks (inside the G x G grid and below N_d) and base offsets are computed once; a tap
+// is one 8-byte complex load from the column's symbol row, which stays in L1, and the
+// weights live in registers.
+constexpr int CF_PPT = 5;   // positions per thread: G^2 <= 256 * 5
+
+FD_HD bool conv_fast(const Geo &g) {
+    return g.K_C == 3 && g.K_S == 1 && g.N_conv == 2 && g.Cin == 2 && g.pad == 1 && g.G * g.G <= 256 * CF_PPT;
+}
+
+struct ConvPos {
+    int base[CF_PPT];    // symbol index of tap (0, 0)
+    int mask[CF_PPT];    // bit 3a + b: tap (a, b) inside the grid and the data
+};
+FD_D ConvPos conv_positions(const Geo &g) {
+    ConvPos cp;
+    const int G = g.G, GG = G * G;
+#pragma unroll
+    for (int k = 0; k < CF_PPT; ++k) {
+        const int p = threadIdx.x + 256 * k;
+        const int i = p / G, j = p % G;
+        int m = 0;
+        if (p < GG) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int r = i + a - 1, q = j + b - 1;
+                    if (r >= 0 && r < G && q >= 0 && q < G && r * G + q < g.N_d) m |= 1 << (3 * a + b);
+                }
+        }
+        cp.base[k] = (i - 1) * G + (j - 1);
+        cp.mask[k] = m;
+    }
+    return cp;
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, const c32 *__restrict__ s,
+                                                            const float *__restrict__ theta, TOut *__restrict__ act,
+                                                            long ld) {
+    const int G = g.G, GG = G * G;
+    float w[2][2][9], bias[2];
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        bias[o] = theta[g.off_cb + o];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) w[o][c][k] = theta[(o * 2 + c) * 9 + k];   // conv_w at the start of theta
+    }
+    const ConvPos cp = conv_positions(g);
+    for (long col = blockIdx.x; col < cols; col += gridDim.x) {
+        const c32 *row = s + col * g.N_d;   // L_U = 1: the column's own user
+        TOut *out = act + col * ld;
+#pragma unroll
+        for (int k = 0; k < CF_PPT; ++k) {
+            const int p = threadIdx.x + 256 * k;
+            if (p >= GG) break;
+            float a0 = bias[0], a1 = bias[1];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int tap = 3 * a + b;
+                    if (cp.mask[k] >> tap & 1) {
+                        const c32 v = __ldg(row + cp.base[k] + a * G + b);
+                        a0 = fmaf(w[0][0][tap], v.x, fmaf(w[0][1][tap], v.y, a0));
+                        a1 = fmaf(w[1][0][tap], v.x, fmaf(w[1][1][tap], v.y, a1));
+                    }
+                }
+            a0 = fmaxf(a0, 0.f);
+            a1 = fmaxf(a1, 0.f);
+            if constexpr (sizeof(TOut) == 4) {
+                out[p] = a0;
+                out[GG + p] = a1;
+            } else {
+                out[p] = __float2bfloat16_rn(a0);
+                out[GG + p] = __float2bfloat16_rn(a1);
+            }
+        }
+    }
+}
+
+// parameter gradient: every thread accumulates the 36 weight and 2 bias partial sums of
+// its positions over the CTA's columns; one block reduction per CTA
+__global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, const c32 *__restrict__ s,
+                                                            const float *__restrict__ gpre,
+                                                            float *__restrict__ partials) {
+    constexpr int NW = 2 * 2 * 9 + 2;
+    const int G = g.G, GG = G * G;
+    float acc[2][2][9], accb[2] = {0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[o][c][k] = 0.f;
+    const ConvPos cp = conv_positions(g);
+    for (long col = blockIdx.x; col < cols; col += gridDim.x) {
+        const c32 *row = s + col * g.N_d;
+        const float *gp = gpre + col * g.F;
+#pragma unroll
+        for (int k = 0; k < CF_PPT; ++k) {
+            const int p = threadIdx.x + 256 * k;
+            if (p >= GG) break;
+            const float g0 = gp[p], g1 = gp[GG + p];
+            accb[0] += g0;
+            accb[1] += g1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int tap = 3 * a + b;
+                    if (cp.mask[k] >> tap & 1) {
+                        const c32 v = __ldg(row + cp.base[k] + a * G + b);
+                        acc[0][0][tap] = fmaf(g0, v.x, acc[0][0][tap]);
+                        acc[0][1][tap] = fmaf(g0, v.y, acc[0][1][tap]);
+                        acc[1][0][tap] = fmaf(g1, v.x, acc[1][0][tap]);
+                        acc[1][1][tap] = fmaf(g1, v.y, acc[1][1][tap]);
+                    }
+                }
+        }
+    }
+    __shared__ float red[8][NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float v = warp_sum(acc[o][c][k]);
+                if (lane == 0) red[warp][(o * 2 + c) * 9 + k] = v;
+            }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const float v = warp_sum(accb[o]);
+        if (lane == 0) red[warp][36 + o] = v;
+    }
+    __syncthreads();
+    for (int wi = threadIdx.x; wi < NW; wi += blockDim.x) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k][wi];
+        partials[(long)blockIdx.x * NW + wi] = t;
+    }
+}
+
+static long conv_fast_blocks(long cols) { return cols < 152L * 8 ? cols : 152L * 8; }
+
 static int conv_cols_per_cta(long cols) { return cols >= 152 * 64 ? 8 : 1; }
 
 template <typename TOut>
@@ -83,6 +236,10 @@ static cudaError_t conv_fwd_launch(const Geo &g, int S, const c32 *s, const floa
     if (!cols) return cudaSuccess;
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * (size_t)g.Cin * Gp * Gp;
+    if (conv_fast(g) && g.L_U == 1) {
+        conv_fwd_fast_kernel<TOut><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cols, s, theta, act, ld);
+        return cudaGetLastError();
+    }
     const int cpc = conv_cols_per_cta(cols);
     const unsigned blocks = (unsigned)((cols + cpc - 1) / cpc);
     if (g.K_C == 3) conv_fwd_kernel<3, TOut><<<blocks, 256, sm, st>>>(g, cpc, cols, s, theta, act, ld);
@@ -190,6 +347,7 @@ static bool conv_bwd_fast(const Geo &g) { return g.K_C == 3 && g.N_conv == 2 && 
 static const int kConvColsPerCta = 16;
 // rows of `partials` written by conv_backward for `cols` columns
 static long conv_partial_rows(const Geo &g, long cols) {
+    if (conv_fast(g) && g.L_U == 1) return conv_fast_blocks(cols);
     return conv_bwd_fast(g) ? (cols + kConvColsPerCta - 1) / kConvColsPerCta : cols;
 }
 
@@ -200,6 +358,10 @@ cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, 
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * ((size_t)g.Cin * Gp * Gp + g.F);
     cudaError_t e;
+    if (conv_fast(g) && g.L_U == 1) {
+        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cols, s, gpre, partials);
+        return cudaGetLastError();
+    }
     if (conv_bwd_fast(g)) {
         const int cpc = kConvColsPerCta;
         const unsigned blocks = (unsigned)conv_partial_rows(g, cols);
