@@ -414,9 +414,8 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {
         const long W2 = 2L * g.N_d;
-        FD_STAGE(p, FDDPD_STAGE_PACK, 4,
-                 (fdk::to_bf16(gd, cols, W2, W2, p->gd16, p->ld2N, st) == cudaSuccess &&
-                  fdk::transpose_bf16(gd, cols, W2, W2, p->gdT16, p->ldC, st) == cudaSuccess &&
+        FD_STAGE(p, FDDPD_STAGE_PACK, 3,
+                 (fdk::bf16_and_transpose(gd, cols, W2, W2, p->gd16, p->ld2N, p->gdT16, p->ldC, st) == cudaSuccess &&
                   fdk::transpose_bf16(p->act16, cols, g.F, p->ldF, p->actT16, p->ldC, st) == cudaSuccess)
                      ? fdk::pack_fcw_t(g, theta, p->fcwT16, p->ld2N, st)
                      : cudaGetLastError());

@@ -69,6 +69,60 @@ cudaError_t transpose_bf16(const __nv_bfloat16 *in, long rows, long cols, long l
     return run_transpose<__nv_bfloat16, false>(in, rows, cols, ld_in, 0, out, ld_out, st);
 }
 
+// One pass over an FP32 matrix in[rows][ld_in] (cols valid) writing both its BF16 copy
+// out[rows][ld_out] and its BF16 transpose outT[cols][ld_t]: 32 x 64 tiles, pairs of
+// elements (8-byte loads, 4-byte stores) on both sides, the transpose through shared memory.
+__global__ void __launch_bounds__(256) bf16_and_transpose_kernel(const float *__restrict__ in, long rows, long cols,
+                                                                 long ld_in, __nv_bfloat16 *__restrict__ out,
+                                                                 long ld_out, __nv_bfloat16 *__restrict__ outT,
+                                                                 long ld_t) {
+    __shared__ __nv_bfloat16 tile[64][34];   // [column][row], padded
+    const long r0 = (long)blockIdx.y * 32, c0 = (long)blockIdx.x * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 column pairs x 8 rows
+    for (int k = ty; k < 32; k += 8) {
+        const long r = r0 + k, c = c0 + 2 * tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows) {
+            if (c + 1 < cols) v = *reinterpret_cast<const float2 *>(in + r * ld_in + c);
+            else if (c < cols) v.x = in[r * ld_in + c];
+        }
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+        if (r < rows && c + 1 < cols) *reinterpret_cast<__nv_bfloat162 *>(out + r * ld_out + c) = b;
+        else if (r < rows && c < cols) out[r * ld_out + c] = b.x;
+        tile[2 * tx][k] = b.x;
+        tile[2 * tx + 1][k] = b.y;
+    }
+    __syncthreads();
+    // transpose: 64 columns x 16 row pairs
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+        const int cc = e >> 4, rp = e & 15;
+        const long c = c0 + cc, r = r0 + 2 * rp;
+        if (c >= cols || r >= rows) continue;
+        if (r + 1 < rows) {
+            __nv_bfloat162 b;
+            b.x = tile[cc][2 * rp];
+            b.y = tile[cc][2 * rp + 1];
+            *reinterpret_cast<__nv_bfloat162 *>(outT + c * ld_t + r) = b;
+        } else {
+            outT[c * ld_t + r] = tile[cc][2 * rp];
+        }
+    }
+}
+
+cudaError_t bf16_and_transpose(const float *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
+                               __nv_bfloat16 *outT, long ld_t, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    // pairs must stay 4-byte aligned: even leading dimensions and bases
+    if ((ld_in & 1) || (ld_out & 1) || (ld_t & 1) || (reinterpret_cast<uintptr_t>(in) & 7) ||
+        (reinterpret_cast<uintptr_t>(out) & 3) || (reinterpret_cast<uintptr_t>(outT) & 3)) {
+        cudaError_t e = to_bf16(in, rows, cols, ld_in, out, ld_out, st);
+        return e == cudaSuccess ? transpose_bf16(in, rows, cols, ld_in, outT, ld_t, st) : e;
+    }
+    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 31) / 32));
+    bf16_and_transpose_kernel<<<grid, 256, 0, st>>>(in, rows, cols, ld_in, out, ld_out, outT, ld_t);
+    return cudaGetLastError();
+}
+
 __global__ void to_bf16_kernel(const float *__restrict__ in, long rows, long cols, long ld_in,
                                __nv_bfloat16 *__restrict__ out, long ld_out) {
     const long r = blockIdx.y;

@@ -31,6 +31,9 @@ cudaError_t pack_fcw(const struct Geo &g, const float *theta, __nv_bfloat16 *out
 // transposed: out[f][n'] = bf16(fc_w[pi(n')][f]), ld_out
 cudaError_t pack_fcw_t(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st);
 // out[r][c] = bf16(in[r][c]) for a float matrix
+// bf16 copy and bf16 transpose of an FP32 matrix in one pass
+cudaError_t bf16_and_transpose(const float *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
+                               __nv_bfloat16 *outT, long ld_t, cudaStream_t st);
 cudaError_t to_bf16(const float *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
                     cudaStream_t st);
 // out[c][r] = in[r][c] (float or bf16 input)
