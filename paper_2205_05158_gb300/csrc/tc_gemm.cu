@@ -3,14 +3,16 @@
 // in tensor memory.  Used for the FD-CNN dense layer (forward, data gradient and
 // weight gradient) in 16-bit plans.
 //
-// One CTA computes one 128 x BN output tile (optionally a K slice of it, split-K):
+// A persistent CTA per SM walks 128 x BN output tiles (optionally K slices of them,
+// split-K), n fastest:
 //   warp 0 lane 0 : TMA producer, 128-byte-swizzled 128 x 64 / BN x 64 tiles into a
-//                   STAGES-deep shared-memory ring (mbarrier full / empty pairs);
-//   warp 1 lane 0 : issues tcgen05.mma (M = 128, N = BN, K = 16) into a TMEM
-//                   accumulator of BN columns, commits each stage back to its
-//                   producer barrier and the last one to `done`;
-//   warps 2..5    : epilogue, tcgen05.ld of the accumulator lanes of their quarter,
-//                   then a caller-supplied per-element functor.
+//                   STAGES-deep shared-memory ring (mbarrier full / empty pairs) that
+//                   runs on across tiles;
+//   warp 1 lane 0 : issues tcgen05.mma (M = 128, N = BN, K = 16) into one of two TMEM
+//                   accumulators of BN columns (tile j uses buffer j & 1), commits each
+//                   stage back to its producer barrier and the tile to tfull;
+//   warps 2..5    : epilogue of tile j while tile j + 1 accumulates: tcgen05.ld of the
+//                   lanes of their quarter, a caller-supplied functor, then tempty.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); a timeout sets the
 // error word, the waiting role stops, the MMA warp still drains its commits, and
 // TMEM is freed before the CTA exits.
@@ -33,37 +35,49 @@ struct Smem {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int BYTES = STAGES * STAGE + 1024;   // + alignment slack
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;   // per accumulator buffer (two are allocated)
 };
 
 template <int BN, class Epi>
 __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant__ CUtensorMap ta,
                                                           const __grid_constant__ CUtensorMap tb, int Mdim, int Ndim,
-                                                          int Kdim, int k_per_split, int ab_type, Epi epi, int *err) {
+                                                          int Kdim, int k_per_split, int ntn, int ntiles, int ab_type,
+                                                          Epi epi, int *err) {
     using L = Smem<BN>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = blockIdx.z * k_per_split;
-    const int kend = min(Kdim, kbeg + k_per_split);
-    const int nkb = (kend - kbeg + BK - 1) / BK;
+    const int ntm = (Mdim + BM - 1) / BM;
+    // tile t of this CTA: n fastest, so neighbouring CTAs share the A rows in L2
+    auto tile_of = [&](int t, int &m0, int &n0, int &kbeg, int &nkb) {
+        const int tn = t % ntn, tm = (t / ntn) % ntm, ks = t / (ntn * ntm);
+        m0 = tm * BM;
+        n0 = tn * BN;
+        kbeg = ks * k_per_split;
+        const int kend = min(Kdim, kbeg + k_per_split);
+        nkb = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 128);   // the four epilogue warps
+        }
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(L::TMEM_COLS)
+                     "r"(2 * L::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -74,80 +88,116 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t use = kb / STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty[s], (use & 1) ^ 1, err)) break;
-                uint8_t *sa = base + s * L::STAGE;
-                uint8_t *sb = sa + L::A_BYTES;
-                mbar_expect_tx(&full[s], L::STAGE);
-                const int kx = kbeg + kb * BK;
-                tma_load_2d(sa, &ta, &full[s], kx, m0);
-                tma_load_2d(sb, &tb, &full[s], kx, n0);
-                ++issued;
+            // producer: one ring of STAGES stages across all of this CTA's tiles
+            int g = 0;   // k-blocks issued so far
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+                int m0, n0, kbeg, nkb;
+                tile_of(t, m0, n0, kbeg, nkb);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t use = g / STAGES;
+                    if (g >= STAGES && !mbar_wait(&empty[s], (use & 1) ^ 1, err)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *sa = base + s * L::STAGE;
+                    uint8_t *sb = sa + L::A_BYTES;
+                    mbar_expect_tx(&full[s], L::STAGE);
+                    const int kx = kbeg + kb * BK;
+                    tma_load_2d(sa, &ta, &full[s], kx, m0);
+                    tma_load_2d(sb, &tb, &full[s], kx, n0);
+                }
             }
             // no copy may still be landing in shared memory when the CTA exits
-            for (int s = 0; s < STAGES && s < issued; ++s) {
-                const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
+            for (int s = 0; s < STAGES && s < g; ++s) {
+                const int last = s + ((g - 1 - s) / STAGES) * STAGES;
                 mbar_wait(&full[s], (uint32_t)(last / STAGES) & 1, err);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            // MMA: tile j of this CTA accumulates into TMEM buffer j & 1
             const uint32_t idesc = instr_desc(ab_type, BM, BN);
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t use = kb / STAGES;
-                if (!mbar_wait(&full[s], use & 1, err)) break;
+            int g = 0, j = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++j) {
+                int m0, n0, kbeg, nkb;
+                tile_of(t, m0, n0, kbeg, nkb);
+                const int buf = j & 1;
+                if (j >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((j >> 1) - 1) & 1, err)) {
+                    abort_flag = 1;
+                    break;
+                }
                 fence_after();
-                const uint64_t ad = smem_desc(base + s * L::STAGE);
-                const uint64_t bd = smem_desc(base + s * L::STAGE + L::A_BYTES);
+                const uint32_t d = tmem + (uint32_t)(buf * L::TMEM_COLS);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t use = g / STAGES;
+                    if (!mbar_wait(&full[s], use & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint64_t ad = smem_desc(base + s * L::STAGE);
+                    const uint64_t bd = smem_desc(base + s * L::STAGE + L::A_BYTES);
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
-                mma_commit(&empty[s]);
-                ++issued;
-            }
-            mma_commit(&done);   // arrives once every MMA issued above has completed
-            (void)issued;
-        }
-    } else {
-        // epilogue: the operands the functor reads besides the accumulator (residual,
-        // activation) are fetched PRE chunks ahead, the first ones while the MMAs run
-        constexpr int PRE = 4, NCH = BN / 16;
-        const int q = warp & 3;
-        const int row = m0 + 32 * q + lane;
-        const bool rok = row < Mdim;
-        typename Epi::Pre pre[PRE];
-#pragma unroll
-        for (int c = 0; c < PRE; ++c)
-            if (rok && n0 + 16 * c + 16 <= Ndim) epi.prefetch(row, n0 + 16 * c, pre[c]);
-        const bool ok = mbar_wait(&done, 0, err) && nkb > 0;
-        fence_after();
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * c), v);
-            const int n = n0 + 16 * c;
-            if (ok && rok && n < Ndim) {
-                if (n + 16 <= Ndim) {
-                    epi.chunk(row, n, v, pre[c % PRE]);   // 16 contiguous columns of the row
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (n + j < Ndim) epi(row, n + j, v[j]);
+                    for (int k = 0; k < BK / 16; ++k) mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[buf]);   // arrives once this tile's MMAs have completed
+                if (!ok) {
+                    abort_flag = 1;
+                    break;
                 }
             }
-            if (c + PRE < NCH && rok && n + 16 * PRE + 16 <= Ndim) epi.prefetch(row, n + 16 * PRE, pre[c % PRE]);
+        }
+    } else {
+        // epilogue: tile j from TMEM buffer j & 1; the operands the functor reads besides
+        // the accumulator (residual, activation) are fetched PRE chunks ahead, the first
+        // ones while the tile's MMAs run
+        constexpr int PRE = 4, NCH = BN / 16;
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            int m0, n0, kbeg, nkb;
+            tile_of(t, m0, n0, kbeg, nkb);
+            const int buf = j & 1;
+            const int row = m0 + 32 * q + lane;
+            const bool rok = row < Mdim;
+            typename Epi::Pre pre[PRE];
+#pragma unroll
+            for (int c = 0; c < PRE; ++c)
+                if (rok && n0 + 16 * c + 16 <= Ndim) epi.prefetch(row, n0 + 16 * c, pre[c]);
+            if (!mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1, err)) break;
+            fence_after();
+            const bool ok = nkb > 0 && !abort_flag;
+            const uint32_t trow = tmem + (uint32_t)(buf * L::TMEM_COLS) + ((uint32_t)(32 * q) << 16);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)(16 * c), v);
+                const int n = n0 + 16 * c;
+                if (ok && rok && n < Ndim) {
+                    if (n + 16 <= Ndim) {
+                        epi.chunk(row, n, v, pre[c % PRE]);   // 16 contiguous columns of the row
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj)
+                            if (n + jj < Ndim) epi(row, n + jj, v[jj]);
+                    }
+                }
+                if (c + PRE < NCH && rok && n + 16 * PRE + 16 <= Ndim) epi.prefetch(row, n + 16 * PRE, pre[c % PRE]);
+            }
+            fence_before();
+            mbar_arrive(&tempty[buf]);
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * L::TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -198,8 +248,12 @@ static cudaError_t launch(const GemmArgs &g, const Epi &epi, int *err, cudaStrea
     const int smem = Smem<BN>::BYTES;
     e = cudaFuncSetAttribute(gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
-    gemm_kernel<BN, Epi><<<grid, THREADS, smem, st>>>(ta, tb, g.M, g.N, g.K, kps, g.ab_type, epi, err);
+    const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM - 1) / BM, ntiles = ntn * ntm * splits;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ntiles < sms ? ntiles : sms;   // persistent: one CTA per SM
+    gemm_kernel<BN, Epi><<<grid, THREADS, smem, st>>>(ta, tb, g.M, g.N, g.K, kps, ntn, ntiles, g.ab_type, epi, err);
     return cudaGetLastError();
 }
 
@@ -233,7 +287,6 @@ struct EpiAdd {            // C[m][n] += acc (split-K partial sums)
 struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] + residual * s
     struct Pre {
         float4 r[4];
-        float b[16];
     };
     float *st;
     const float *s, *fb;
@@ -244,8 +297,6 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
     }
     FD_D void prefetch(int m, int n, Pre &p) const {
         if (!vec) return;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) p.b[j] = fb[(j & 1) * Nd + ((n + j) >> 1)];
         if (residual) {
             const float4 *s4 = reinterpret_cast<const float4 *>(s + (long)m * 2 * Nd + n);
 #pragma unroll
@@ -261,7 +312,7 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
         const long idx = (long)m * 2 * Nd + n;
         float o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] = v[j] + p.b[j];
+        for (int j = 0; j < 16; ++j) o[j] = v[j] + fb[(j & 1) * Nd + ((n + j) >> 1)];
         if (residual) {
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
