@@ -163,10 +163,28 @@ def fdcnn(d: Dims, s_sym, theta):
 
 
 # -- whole chain ---------------------------------------------------------------
+def _check_chain(d: Dims, s, H, W, alpha, pa_coef, theta):
+    """Shapes the C routines index without bounds checks: s [S][K][N_d], H [R][N_d][K][M],
+    W [R][N_d][M][K], alpha [R][N_d] with R covering the S symbols' realisations, the PA
+    coefficients [M][n_orders][L + 1] and theta."""
+    S = s.shape[0]
+    R = -(-S // d.S_per_real)
+    want = {"s": (s.shape, (S, d.K, d.N_d)), "pa": (pa_coef.shape, (d.M, d.n_orders, d.L + 1))}
+    for name, (got, exp) in want.items():
+        if tuple(got) != exp:
+            raise ValueError(f"{name} has shape {tuple(got)}, expected {exp}")
+    for name, a, tail in (("H", H, (d.N_d, d.K, d.M)), ("W", W, (d.N_d, d.M, d.K)), ("alpha", alpha, (d.N_d,))):
+        if tuple(a.shape[1:]) != tail or a.shape[0] < R:
+            raise ValueError(f"{name} has shape {tuple(a.shape)}, expected ({R}+, {', '.join(map(str, tail))})")
+    if theta.size != theta_len(d):
+        raise ValueError(f"theta has {theta.size} entries, expected {theta_len(d)}")
+
+
 def distort(d: Dims, s, H, W, alpha, pa_coef, theta):
     """Forward chain over S symbols -> (y_eq [S][K][N_d], metrics[5])."""
     s, H, W, pa_coef = _c128(s), _c128(H), _c128(W), _c128(pa_coef)
     alpha, th = _f64(alpha), _f64(theta)
+    _check_chain(d, s, H, W, alpha, pa_coef, th)
     y = np.empty_like(s)
     met = np.zeros(5)
     rc = lib().orc_distort(C.byref(d), s.shape[0], _p(s), _p(H), _p(W), _p(alpha), _p(pa_coef),
@@ -180,6 +198,7 @@ def backward(d: Dims, s, H, W, alpha, pa_coef, theta):
     """Gradient of the mean-squared symbol error w.r.t. theta -> (grad, metrics[5])."""
     s, H, W, pa_coef = _c128(s), _c128(H), _c128(W), _c128(pa_coef)
     alpha, th = _f64(alpha), _f64(theta)
+    _check_chain(d, s, H, W, alpha, pa_coef, th)
     g = np.zeros(theta_len(d))
     met = np.zeros(5)
     rc = lib().orc_backward(C.byref(d), s.shape[0], _p(s), _p(H), _p(W), _p(alpha), _p(pa_coef),
@@ -201,6 +220,7 @@ def update(d: Dims, s, H, W, alpha, pa_coef, theta, lr: float, iters: int, adam:
     s, H, W, pa_coef = _c128(s), _c128(H), _c128(W), _c128(pa_coef)
     alpha = _f64(alpha)
     th = _f64(theta).copy()
+    _check_chain(d, s, H, W, alpha, pa_coef, th)
     met = np.zeros(5)
     st = adam if adam is not None else AdamState(1)
     rc = lib().orc_update(C.byref(d), s.shape[0], _p(s), _p(H), _p(W), _p(alpha), _p(pa_coef),

@@ -12,6 +12,9 @@
 
 using fdk::Geo;
 
+static constexpr int kMaxRec = 4096;
+static constexpr int kCopyChunks = 8;   // H copies of fddpd_update_host, each followed by its ZF
+
 struct fddpd_plan {
     fddpd_dims d;
     fddpd_pa_desc pa;
@@ -49,10 +52,11 @@ struct fddpd_plan {
     c32 *hs, *hH, *hW, *hpa;
     float *hal, *htheta;
     double *hmet;
+    cudaStream_t cstream;                        // host-to-device copies, beside p->stream
+    cudaEvent_t cev[kCopyChunks + 2];            // [0] staging free, [1..kCopyChunks] H chunks, last: s, pa, theta
     char err[512];
 };
 
-static constexpr int kMaxRec = 4096;
 static const char *kStageNames[FDDPD_N_STAGES] = {
     "zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
     "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"};
@@ -233,6 +237,10 @@ extern "C" int fddpd_plan_destroy(fddpd_plan *p) {
     if (!p) return FDDPD_OK;
     if (p->base) cudaFree(p->base);
     if (p->stage_base) cudaFree(p->stage_base);
+    if (p->cstream) {
+        cudaStreamDestroy(p->cstream);
+        for (int i = 0; i < kCopyChunks + 2; ++i) cudaEventDestroy(p->cev[i]);
+    }
     if (p->status_host) cudaFreeHost(p->status_host);
     if (p->ev) {
         for (int i = 0; i < 2 * kMaxRec; ++i) cudaEventDestroy(p->ev[i]);
@@ -555,16 +563,54 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
         p->htheta = (float *)b; b += up(n_th);
         p->hmet = (double *)b;
     }
-    cudaStream_t st = p->stream;
-    FD_CK(p, cudaMemcpyAsync(p->hs, s, sizeof(c32) * (size_t)S * g.K * g.N_d, cudaMemcpyHostToDevice, st));
-    FD_CK(p, cudaMemcpyAsync(p->hH, H, sizeof(c32) * (size_t)R * g.N_d * g.K * g.M, cudaMemcpyHostToDevice, st));
-    FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, st));
-    FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, st));
-    int rc = fddpd_precode(p, (int)R, (const fddpd_c32 *)p->hH, (fddpd_c32 *)p->hW, p->hal);
-    if (rc) return rc;
-    rc = fddpd_update(p, S, (const fddpd_c32 *)p->hs, (const fddpd_c32 *)p->hH, (const fddpd_c32 *)p->hW, p->hal,
-                      (const fddpd_c32 *)p->hpa, p->htheta, lr, iters, optimizer, p->hmet);
-    if (rc) return rc;
+    if (!p->cstream) {
+        FD_CK(p, cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
+        for (int i = 0; i < kCopyChunks + 2; ++i) FD_CK(p, cudaEventCreateWithFlags(&p->cev[i], cudaEventDisableTiming));
+    }
+    // H crosses in chunks of realisations on the copy stream; the ZF of each chunk runs on
+    // the plan's stream as soon as its chunk has landed, under the copy of the next one.
+    cudaStream_t st = p->stream, cs = p->cstream;
+    const size_t h_real = sizeof(c32) * (size_t)g.N_d * g.K * g.M;   // one realisation of H (and of W)
+    const long rc = (R + kCopyChunks - 1) / kCopyChunks;
+    const int nch = (int)((R + rc - 1) / rc);
+    FD_CK(p, cudaEventRecord(p->cev[0], st));
+    FD_CK(p, cudaStreamWaitEvent(cs, p->cev[0], 0));
+    for (int c = 0; c < nch; ++c) {
+        const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        FD_CK(p, cudaMemcpyAsync((char *)p->hH + r0 * h_real, (const char *)H + r0 * h_real, (r1 - r0) * h_real,
+                                 cudaMemcpyHostToDevice, cs));
+        FD_CK(p, cudaEventRecord(p->cev[1 + c], cs));
+    }
+    FD_CK(p, cudaMemcpyAsync(p->hs, s, sizeof(c32) * (size_t)S * g.K * g.N_d, cudaMemcpyHostToDevice, cs));
+    FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, cs));
+    FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, cs));
+    FD_CK(p, cudaEventRecord(p->cev[kCopyChunks + 1], cs));
+    FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    const size_t h16_real = h_real / 2;
+    for (int c = 0; c < nch; ++c) {
+        const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        FD_CK(p, cudaStreamWaitEvent(st, p->cev[1 + c], 0));
+        for (int ph = 0; ph < 3; ++ph)
+            FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
+                     fdk::zf_phase(ph, g, (int)(r1 - r0), (const c32 *)((char *)p->hH + r0 * h_real),
+                                   (c32 *)((char *)p->hW + r0 * h_real), p->hal + r0 * g.N_d, p->status,
+                                   p->zf_scratch, p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
+                                   p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr, p->kind16, p->tc_bin,
+                                   p->status + 1, st));
+    }
+    if (p->p16) {
+        p->pk_H = p->hH;
+        p->pk_W = p->hW;
+        p->pk_R = (int)R;
+    }
+    FD_CK(p, cudaStreamWaitEvent(st, p->cev[kCopyChunks + 1], 0));
+    // a singular Gram matrix fails the call before the step, leaving theta as it was
+    FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FD_CK(p, cudaStreamSynchronize(st));
+    if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
+    int rc2 = fddpd_update(p, S, (const fddpd_c32 *)p->hs, (const fddpd_c32 *)p->hH, (const fddpd_c32 *)p->hW, p->hal,
+                           (const fddpd_c32 *)p->hpa, p->htheta, lr, iters, optimizer, p->hmet);
+    if (rc2) return rc2;
     FD_CK(p, cudaMemcpyAsync(theta, p->htheta, n_th, cudaMemcpyDeviceToHost, st));
     if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return fddpd_sync(p);

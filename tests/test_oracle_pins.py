@@ -322,3 +322,17 @@ def test_fig2_td_gmp_structure():
                    complexity.td_gmp(7, 3, 1, 4096, B, 8, per_sample=658) / 1205760)
     assert [round(v, 1) for v in r(32)] == [2.2, 8.9]
     assert [int(v) for v in r(1024)] == [26, 286]
+
+
+def test_chain_rejects_missing_realisations():
+    """The chain indexes H, W and alpha by realisation: too few for S symbols is an error."""
+    cfg = synth.CONFIGS["cfg1"]
+    w = synth.make_workload(cfg, S=2 * cfg.S_per_real)
+    d = oracle.dims_from_config(cfg, w.P_T)
+    W, al = oracle.precode(d, w.H[:1])
+    with pytest.raises(ValueError):
+        oracle.distort(d, w.s, w.H[:1], W, al, w.pa, w.theta)
+    with pytest.raises(ValueError):
+        oracle.backward(d, w.s, w.H[:1], W, al, w.pa, w.theta[:-1])
+    y, _ = oracle.distort(d, w.s[:cfg.S_per_real], w.H[:1], W, al, w.pa, w.theta)
+    assert y.shape == (cfg.S_per_real, cfg.K, cfg.N_d)
