@@ -165,10 +165,18 @@ int fddpd_reset_optimizer(fddpd_plan *plan);
 
 /* One training step from HOST memory (Sec. V-A with a new channel per mini-batch):
  * copies s [S][K][N_d], H [R][N_d][K][M] (R = ceil(S / S_per_real)), pa_coef and theta
- * to plan-owned device buffers (allocated on the first call), runs fddpd_precode and
- * fddpd_update(iters), and copies theta and metrics[5] back.  Host buffers should be
- * page-locked for full copy bandwidth.  Blocks until the step is complete.  Errors as
- * fddpd_precode / fddpd_update, NOMEM if the staging buffers cannot be allocated.   */
+ * to plan-owned device buffers (allocated on the first call) and copies theta and
+ * metrics[5] back; the result is that of fddpd_precode followed by fddpd_update(iters)
+ * up to the order of FP32 sums over symbols.  The first iteration is pipelined: the
+ * batch crosses in up to 8 chunks of whole realisations on a second, plan-owned stream,
+ * and each chunk's ZF, forward chain and adjoint run on the plan's stream while the
+ * next chunk is copied (the loss stays normalised by the whole batch; the gradient is
+ * summed over the chunks).  Further iterations run on the resident batch.  Host
+ * buffers should be page-locked for full copy bandwidth.  Blocks until the step is
+ * complete.  A singular Gram matrix anywhere in the batch returns FDDPD_ERR_SINGULAR
+ * before any step, with theta untouched.  iters = 0 only computes the precoders.
+ * Other errors as fddpd_precode / fddpd_update, NOMEM if the staging buffers cannot
+ * be allocated.                                                                   */
 int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
                       const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
                       double *metrics);

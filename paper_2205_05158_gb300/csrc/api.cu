@@ -368,19 +368,38 @@ static float grad_scale(const fddpd_plan *p, double inv_count) {
 }
 
 // Forward chain; gy (loss gradient at y) is written when non-null.
+// One pass of the chain over S symbols that may be part of a larger batch: the loss is
+// normalised by the whole batch (inv_count), the metric sums are cleared by the first
+// part and finalised by the last, parameter gradients are accumulated after the first,
+// and the plan's 16-bit H / W copies are read from realisation r0 on (the caller made
+// them for the whole batch).  A null Pass is a whole batch on its own.
+struct Pass {
+    double inv_count;
+    bool first, last;
+    int r0;
+};
+
+static int pass_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, const Pass *ps, BinOps &o) {
+    if (!ps || !p->p16) return bin_operands(p, S, H, W, o);
+    const size_t real16 = (size_t)p->g.N_d * p->g.K * p->g.M * 4;   // one realisation of a 16-bit copy
+    o = BinOps{(const char *)p->H16 + ps->r0 * real16, (const char *)p->W16 + ps->r0 * real16, p->kind16};
+    return FDDPD_OK;
+}
+
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
-                       const c32 *pa, const float *theta, c32 *y, c32 *gy) {
+                       const c32 *pa, const float *theta, c32 *y, c32 *gy, const Pass *ps = nullptr) {
     const Geo &g = p->g;
     cudaStream_t st = p->stream;
     const long cols = (long)S * g.K;
-    const double inv_count = 1.0 / ((double)cols * g.N_d);
+    const double inv_count = ps ? ps->inv_count : 1.0 / ((double)cols * g.N_d);
+    const bool first = !ps || ps->first, last = !ps || ps->last;
     BinOps ops;
-    int rc0 = bin_operands(p, S, H, W, ops);
+    int rc0 = pass_operands(p, S, H, W, ps, ops);
     if (rc0) return rc0;
-    FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
+    if (first) FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
     if (p->p16) {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, theta, p->act16, p->ldF, st));
-        FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, st));
+        if (first) FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, st));
         const fdk::GemmArgs ga{p->act16, p->fcw16, (int)cols, 2 * g.N_d, g.F, p->ldF, p->ldF, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
                  fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
@@ -396,22 +415,25 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
              fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, act_kind(p), p->met, xt, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
              reduce_op(p, fdk::COMBINE, S, ops, alpha, p->Xpa, y, s, gy, p->met, inv_count, 1.0f));
-    FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
-    p->launches += 1;
+    if (last) {
+        FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
+        p->launches += 1;
+    }
     return FDDPD_OK;
 }
 
 static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
-                        const c32 *pa, const float *theta, float *grad) {
+                        const c32 *pa, const float *theta, float *grad, const Pass *ps = nullptr) {
     const Geo &g = p->g;
     cudaStream_t st = p->stream;
     const int cols = S * g.K;
-    int rc = run_forward(p, S, s, H, W, alpha, pa, theta, nullptr, p->gy);
+    const bool first = !ps || ps->first;
+    int rc = run_forward(p, S, s, H, W, alpha, pa, theta, nullptr, p->gy, ps);
     if (rc) return rc;
     BinOps ops;
-    rc = bin_operands(p, S, H, W, ops);
+    rc = pass_operands(p, S, H, W, ps, ops);
     if (rc) return rc;
-    const float gsc = grad_scale(p, 1.0 / ((double)cols * g.N_d));
+    const float gsc = grad_scale(p, ps ? ps->inv_count : 1.0 / ((double)cols * g.N_d));
     FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
              fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, act_kind(p),
@@ -419,27 +441,31 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
              reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);
-    FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
+    if (first) FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {
         const long W2 = 2L * g.N_d;
-        FD_STAGE(p, FDDPD_STAGE_PACK, 3,
-                 (fdk::bf16_and_transpose(gd, cols, W2, W2, p->gd16, p->ld2N, p->gdT16, p->ldC, st) == cudaSuccess &&
-                  fdk::transpose_bf16(p->act16, cols, g.F, p->ldF, p->actT16, p->ldC, st) == cudaSuccess)
-                     ? fdk::pack_fcw_t(g, theta, p->fcwT16, p->ld2N, st)
+        FD_STAGE(p, FDDPD_STAGE_PACK, 2,
+                 fdk::bf16_and_transpose(gd, cols, W2, W2, p->gd16, p->ld2N, p->gdT16, p->ldC, st) == cudaSuccess
+                     ? fdk::transpose_bf16(p->act16, cols, g.F, p->ldF, p->actT16, p->ldC, st)
                      : cudaGetLastError());
-        FD_CK(p, cudaMemsetAsync(grad + g.off_fw, 0, sizeof(float) * W2 * g.F, st));
-        const fdk::GemmArgs gw{p->gdT16, p->actT16, (int)W2, g.F, cols, p->ldC, p->ldC, 1, 4};
+        if (first) {
+            FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw_t(g, theta, p->fcwT16, p->ld2N, st));
+            FD_CK(p, cudaMemsetAsync(grad + g.off_fw, 0, sizeof(float) * W2 * g.F, st));
+        }
+        // split-K partial sums are added into grad: enough splits to fill the GPU
+        const int splits = cols >= 16384 ? 4 : 2;
+        const fdk::GemmArgs gw{p->gdT16, p->actT16, (int)W2, g.F, cols, p->ldC, p->ldC, 1, splits};
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::tc_fc_backward_weight(gw, grad + g.off_fw, g.N_d, g.F, p->status + 1, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         const fdk::GemmArgs gdx{p->gd16, p->fcwT16, cols, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->act16, p->ldF, g.F, p->status + 1, st));
     } else {
-        FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, !first, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, cols, gd, theta, p->act, p->gpre, st));
     }
     FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, p->gpre, p->act, p->partials, st));
-    FD_CK(p, fdk::conv_reduce(g, cols, p->partials, grad, st));
+    FD_CK(p, fdk::conv_reduce(g, cols, p->partials, grad, !first, st));
     return FDDPD_OK;
 }
 
@@ -471,6 +497,18 @@ extern "C" int fddpd_backward(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
     return FDDPD_OK;
 }
 
+static int opt_step(fddpd_plan *p, float *theta, float lr, int optimizer) {
+    if (optimizer == FDDPD_GD) {
+        FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, p->grad, lr, p->stream));
+    } else {
+        const long t = ++p->adam_t;
+        const float c1 = (float)(1.0 - pow(0.9, (double)t)), c2 = (float)(1.0 - pow(0.999, (double)t));
+        FD_STAGE(p, FDDPD_STAGE_STEP, 1,
+                 fdk::adam_step(p->g.theta_len, theta, p->grad, p->adam_m, p->adam_v, lr, c1, c2, p->stream));
+    }
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_update(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
                             const float *alpha, const fddpd_c32 *pa_coef, float *theta, float lr, int iters,
                             int optimizer, double *metrics) {
@@ -484,13 +522,8 @@ extern "C" int fddpd_update(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
         rc = run_backward(p, S, (const c32 *)s, (const c32 *)H, (const c32 *)W, alpha, (const c32 *)pa_coef, theta,
                           p->grad);
         if (rc) return rc;
-        if (optimizer == FDDPD_GD) {
-            FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, p->grad, lr, p->stream));
-        } else {
-            const long t = ++p->adam_t;
-            const float c1 = (float)(1.0 - pow(0.9, (double)t)), c2 = (float)(1.0 - pow(0.999, (double)t));
-            FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::adam_step(p->g.theta_len, theta, p->grad, p->adam_m, p->adam_v, lr, c1, c2, p->stream));
-        }
+        rc = opt_step(p, theta, lr, optimizer);
+        if (rc) return rc;
     }
     if (metrics && iters > 0)
         FD_CK(p, cudaMemcpyAsync(metrics, p->met, sizeof(double) * 5, cudaMemcpyDeviceToDevice, p->stream));
@@ -539,6 +572,8 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     if (!p) return FDDPD_ERR_ARG;
     if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
     if (!s || !H || !pa_coef || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (iters < 0) return set_err(p, FDDPD_ERR_ARG, "iters < 0");
+    if (optimizer != FDDPD_GD && optimizer != FDDPD_ADAM) return set_err(p, FDDPD_ERR_ARG, "optimizer=%d", optimizer);
     const Geo &g = p->g;
     const long R = (S + g.S_per_real - 1) / g.S_per_real;
     const size_t n_s = sizeof(c32) * (size_t)p->d.max_symbols * g.K * g.N_d,
@@ -567,52 +602,73 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
         FD_CK(p, cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
         for (int i = 0; i < kCopyChunks + 2; ++i) FD_CK(p, cudaEventCreateWithFlags(&p->cev[i], cudaEventDisableTiming));
     }
-    // H crosses in chunks of realisations on the copy stream; the ZF of each chunk runs on
-    // the plan's stream as soon as its chunk has landed, under the copy of the next one.
+    // The batch crosses in chunks of whole realisations on the copy stream.  On the plan's
+    // stream each chunk's ZF, forward and adjoint run as soon as its H and s have landed,
+    // under the copy of the next chunk; the loss is normalised by the whole batch and the
+    // gradient accumulates over the chunks.  The step itself waits for the last chunk and
+    // for the check that every Gram matrix was positive definite.
     cudaStream_t st = p->stream, cs = p->cstream;
     const size_t h_real = sizeof(c32) * (size_t)g.N_d * g.K * g.M;   // one realisation of H (and of W)
+    const size_t s_sym = sizeof(c32) * (size_t)g.K * g.N_d;          // one symbol of s
     const long rc = (R + kCopyChunks - 1) / kCopyChunks;
     const int nch = (int)((R + rc - 1) / rc);
+    const double inv_count = 1.0 / ((double)S * g.K * g.N_d);
     FD_CK(p, cudaEventRecord(p->cev[0], st));
     FD_CK(p, cudaStreamWaitEvent(cs, p->cev[0], 0));
+    FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, cs));
+    FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, cs));
     for (int c = 0; c < nch; ++c) {
         const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        const long t0 = r0 * g.S_per_real, t1 = r1 * g.S_per_real < S ? r1 * g.S_per_real : S;
         FD_CK(p, cudaMemcpyAsync((char *)p->hH + r0 * h_real, (const char *)H + r0 * h_real, (r1 - r0) * h_real,
+                                 cudaMemcpyHostToDevice, cs));
+        FD_CK(p, cudaMemcpyAsync((char *)p->hs + t0 * s_sym, (const char *)s + t0 * s_sym, (t1 - t0) * s_sym,
                                  cudaMemcpyHostToDevice, cs));
         FD_CK(p, cudaEventRecord(p->cev[1 + c], cs));
     }
-    FD_CK(p, cudaMemcpyAsync(p->hs, s, sizeof(c32) * (size_t)S * g.K * g.N_d, cudaMemcpyHostToDevice, cs));
-    FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, cs));
-    FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, cs));
-    FD_CK(p, cudaEventRecord(p->cev[kCopyChunks + 1], cs));
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
     const size_t h16_real = h_real / 2;
     for (int c = 0; c < nch; ++c) {
         const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        const long t0 = r0 * g.S_per_real, t1 = r1 * g.S_per_real < S ? r1 * g.S_per_real : S;
+        const c32 *Hc = (const c32 *)((const char *)p->hH + r0 * h_real);
+        c32 *Wc = (c32 *)((char *)p->hW + r0 * h_real);
+        float *alc = p->hal + r0 * g.N_d;
         FD_CK(p, cudaStreamWaitEvent(st, p->cev[1 + c], 0));
         for (int ph = 0; ph < 3; ++ph)
             FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
-                     fdk::zf_phase(ph, g, (int)(r1 - r0), (const c32 *)((char *)p->hH + r0 * h_real),
-                                   (c32 *)((char *)p->hW + r0 * h_real), p->hal + r0 * g.N_d, p->status,
-                                   p->zf_scratch, p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
+                     fdk::zf_phase(ph, g, (int)(r1 - r0), Hc, Wc, alc, p->status, p->zf_scratch,
+                                   p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
                                    p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr, p->kind16, p->tc_bin,
                                    p->status + 1, st));
+        if (iters > 0) {
+            const Pass ps{inv_count, c == 0, c == nch - 1, (int)r0};
+            int rc1 = run_backward(p, (int)(t1 - t0), (const c32 *)((const char *)p->hs + t0 * s_sym), Hc, Wc, alc,
+                                   p->hpa, p->htheta, p->grad, &ps);
+            if (rc1) return rc1;
+        }
     }
     if (p->p16) {
         p->pk_H = p->hH;
         p->pk_W = p->hW;
         p->pk_R = (int)R;
     }
-    FD_CK(p, cudaStreamWaitEvent(st, p->cev[kCopyChunks + 1], 0));
     // a singular Gram matrix fails the call before the step, leaving theta as it was
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FD_CK(p, cudaStreamSynchronize(st));
     if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
-    int rc2 = fddpd_update(p, S, (const fddpd_c32 *)p->hs, (const fddpd_c32 *)p->hH, (const fddpd_c32 *)p->hW, p->hal,
-                           (const fddpd_c32 *)p->hpa, p->htheta, lr, iters, optimizer, p->hmet);
-    if (rc2) return rc2;
+    if (iters > 0) {
+        int rc2 = opt_step(p, p->htheta, lr, optimizer);
+        if (rc2) return rc2;
+        if (metrics) FD_CK(p, cudaMemcpyAsync(p->hmet, p->met, 5 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        // further iterations over the batch, now resident
+        rc2 = fddpd_update(p, S, (const fddpd_c32 *)p->hs, (const fddpd_c32 *)p->hH, (const fddpd_c32 *)p->hW,
+                           p->hal, (const fddpd_c32 *)p->hpa, p->htheta, lr, iters - 1, optimizer, p->hmet);
+        if (rc2) return rc2;
+    }
     FD_CK(p, cudaMemcpyAsync(theta, p->htheta, n_th, cudaMemcpyDeviceToHost, st));
-    if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (metrics && iters > 0)
+        FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return fddpd_sync(p);
 }
 

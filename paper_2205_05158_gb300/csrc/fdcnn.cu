@@ -376,18 +376,20 @@ cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, 
     return cudaGetLastError();
 }
 
-__global__ void conv_reduce_kernel(int rows, int nw, const float *__restrict__ partials, float *__restrict__ out) {
+__global__ void conv_reduce_kernel(int rows, int nw, const float *__restrict__ partials, float *__restrict__ out,
+                                   int accumulate) {
     __shared__ double red[32];
     const int w = blockIdx.x;
     double acc = 0;
     for (int c = threadIdx.x; c < rows; c += blockDim.x) acc += partials[(long)c * nw + w];
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) out[w] = (float)acc;
+    if (threadIdx.x == 0) out[w] = accumulate ? out[w] + (float)acc : (float)acc;
 }
 
-cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, cudaStream_t st) {
+cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, bool accumulate, cudaStream_t st) {
     const int nw = g.n_convw + g.N_conv;
-    conv_reduce_kernel<<<nw, 256, 0, st>>>((int)conv_partial_rows(g, cols), nw, partials, grad);   // conv_w, conv_b
+    conv_reduce_kernel<<<nw, 256, 0, st>>>((int)conv_partial_rows(g, cols), nw, partials, grad,
+                                           accumulate ? 1 : 0);   // conv_w, conv_b
     return cudaGetLastError();
 }
 
@@ -438,13 +440,16 @@ struct FcBwdData {   // A = gd [cols][2N_d]; B(f, n') = fc_w[pi(n')][f]; C -> gp
         gpre[idx] = act[idx] > 0.f ? v : 0.f;
     }
 };
-struct FcBwdWeight {   // A(n', c) = gd[c][n']; B(f, c) = act[c][f]; C -> grad fc_w[pi(n')][f]
+struct FcBwdWeight {   // A(n', c) = gd[c][n']; B(f, c) = act[c][f]; C -> grad fc_w[pi(n')][f] (= or +=)
     const float *gd, *act;
     float *gfw;
-    int F, Nd;
+    int F, Nd, accumulate;
     FD_D float a(long m, long k) const { return gd[k * 2 * Nd + m]; }
     FD_D float b(long n, long k) const { return act[k * F + n]; }
-    FD_D void store(long m, long n, float v) const { gfw[(long)((m & 1) * Nd + (m >> 1)) * F + n] = v; }
+    FD_D void store(long m, long n, float v) const {
+        float *dst = gfw + (long)((m & 1) * Nd + (m >> 1)) * F + n;
+        *dst = accumulate ? *dst + v : v;
+    }
 };
 
 template <class Op, bool A_K, bool B_K>
@@ -510,8 +515,8 @@ cudaError_t fc_backward_data_f32(const Geo &g, int cols, const float *gd, const 
 }
 
 cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, const float *act, float *grad,
-                                   cudaStream_t stm) {
-    FcBwdWeight op{gd, act, grad + g.off_fw, g.F, g.N_d};
+                                   bool accumulate, cudaStream_t stm) {
+    FcBwdWeight op{gd, act, grad + g.off_fw, g.F, g.N_d, accumulate ? 1 : 0};
     return run_sgemm<FcBwdWeight, false, false>(op, 2L * g.N_d, g.F, cols, stm);
 }
 

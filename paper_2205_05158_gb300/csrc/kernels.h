@@ -40,7 +40,8 @@ bool tc_bin_supported(const Geo &g);
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
 cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gact, const float *act, float *partials,
                           cudaStream_t st);
-cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, cudaStream_t st);
+// grad[conv_w, conv_b] = (accumulate ? grad + : ) the sum of the partial rows
+cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, bool accumulate, cudaStream_t st);
 cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st);
 
 // FP32 GEMM with the FD-CNN dense-layer layouts (rows of fc_w interleaved Re/Im)
@@ -49,7 +50,7 @@ cudaError_t fc_forward_f32(const Geo &g, int cols, const float *act, const float
 cudaError_t fc_backward_data_f32(const Geo &g, int cols, const float *gd, const float *theta, const float *act,
                                  float *gpre, cudaStream_t stm);
 cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, const float *act, float *grad,
-                                   cudaStream_t stm);
+                                   bool accumulate, cudaStream_t stm);
 
 // per-subcarrier complex contractions (FP32 operands)
 enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3 };

@@ -1,9 +1,12 @@
-"""fddpd_update_host: one training step from host buffers (H crosses in chunks of channel
-realisations, each chunk's ZF (Eq. 6) running while the next one is copied) against the
-same step through the device entry points fddpd_precode + fddpd_update.
+"""fddpd_update_host: a training step from host buffers, against the same step through the
+device entry points fddpd_precode + fddpd_update.
 
-Every subcarrier's ZF is computed on its own, so chunking changes no arithmetic: theta
-and the metrics must agree to FP32 rounding of order-independent reductions.
+The host path moves the batch in chunks of whole channel realisations and runs each
+chunk's ZF (Eq. 6), forward chain and adjoint while the next chunk is copied, with the
+loss normalised by the whole batch and the gradient summed over the chunks.  Every
+subcarrier's ZF and every symbol's chain are computed on their own, so only the order
+of the FP32 sums over symbols (gradient, metrics) differs: theta's step and the
+metrics agree to 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -48,7 +51,42 @@ def test_update_host_matches_device_path(name, cfg, prec):
     step_d, step_h = th_d - th0, th_h - th0
     assert np.abs(step_d).max() > 0
     assert np.linalg.norm(step_h - step_d) <= 1e-5 * np.linalg.norm(step_d)
-    assert np.allclose(met_h, met_d, rtol=1e-9, atol=0)
+    assert np.allclose(met_h, met_d, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("opt", ["gd", "adam"])
+def test_update_host_iterations(opt):
+    """iters = 3: the first pass is chunk-pipelined, the next two run on the resident batch."""
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    cfg = small_cfg(S=40, S_per_real=3)
+    o = fd.FDDPD_GD if opt == "gd" else fd.FDDPD_ADAM
+    c = Case(cfg, S=cfg.S, fc_scale=0.3)
+    met_d = T.zeros(5, dtype=T.float64, device="cuda")
+    c.gpu_zf()
+    c.plan.update(c.s, c.H, c.W, c.alpha, c.pa, c.theta, 1e-3, 3, o, met_d)
+    plan_h = fd.Plan.from_config(cfg, c.w.P_T, max_symbols=c.S)
+    th_h, met_h = _host(c.w.theta.copy()), _host(np.zeros(5))
+    plan_h.update_host(_host(c.w.s), _host(c.w.H), _host(c.w.pa), th_h, 1e-3, 3, o, met_h)
+    th0 = c.w.theta.astype(np.float64)
+    step_d = c.theta.cpu().numpy() - th0
+    diff = (th_h - th0) - step_d
+    if o == fd.FDDPD_GD:
+        assert np.linalg.norm(diff) <= 1e-4 * np.linalg.norm(step_d)
+    else:
+        # Adam's early steps are ~lr sign(g): a gradient within rounding of zero may differ
+        assert np.mean(np.abs(diff) > 0.1 * 1e-3) < 1e-3
+        assert np.linalg.norm(diff) <= 1e-2 * np.linalg.norm(step_d)
+    assert np.allclose(met_h, met_d.cpu().numpy(), rtol=1e-4, atol=0)
+
+
+def test_update_host_zero_iters_keeps_theta():
+    import paper_2205_05158_gb300 as fd
+    cfg = small_cfg(S=40, S_per_real=3)
+    c = Case(cfg, S=cfg.S, fc_scale=0.3)
+    th = _host(c.w.theta.copy())
+    c.plan.update_host(_host(c.w.s), _host(c.w.H), _host(c.w.pa), th, 1e-3, 0, fd.FDDPD_GD, None)
+    assert np.array_equal(th, c.w.theta)
 
 
 def test_update_host_twice_reuses_staging():
@@ -72,7 +110,7 @@ def test_update_host_twice_reuses_staging():
     th0 = c.w.theta.astype(np.float64)
     sr = th.cpu().numpy() - th0
     assert np.linalg.norm((th2 - th0) - sr) <= 1e-5 * np.linalg.norm(sr)
-    assert np.allclose(m2, met.cpu().numpy(), rtol=1e-9, atol=0)
+    assert np.allclose(m2, met.cpu().numpy(), rtol=1e-5, atol=0)
 
 
 @pytest.mark.parametrize("real", [0, 9, 13])
