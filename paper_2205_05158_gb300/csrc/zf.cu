@@ -174,6 +174,90 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel
     }
 }
 
+// K = 16 with M a multiple of 32 (the massive-MIMO shapes): the same warp-per-subcarrier
+// product with every index a compile-time constant.  Lane l < 30 takes block l % 10 over
+// antenna group l / 10 of each chunk: columns 11 g .. 11 g + 10, where the third group's
+// last column is the zero padding column 32 of the chunk buffer, so all three run the
+// same 11 steps.  The three groups' partial sums meet by warp shuffles.
+template <typename T16>
+__global__ void __launch_bounds__(32 * ZF_WARPS, 3)
+    zf_gram16_kernel(Geo g, long nbins, const c32 *__restrict__ H, c32 *__restrict__ Gs, T16 *__restrict__ H16) {
+    constexpr int K = 16, T = 136, LD = GR_LD, BUF = K * LD;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int M = g.M;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    c32 *wbuf = reinterpret_cast<c32 *>(sm) + (size_t)warp * 2 * BUF;
+    wbuf[(lane >> 4) * BUF + (lane & 15) * LD + GR_CHUNK] = make_float2(0.f, 0.f);   // padding columns
+    const int blk = lane % 10, grp = lane < 30 ? lane / 10 : 2;
+    const int bi = blk < 1 ? 0 : blk < 3 ? 1 : blk < 6 ? 2 : 3;
+    const int bj = blk - bi * (bi + 1) / 2;
+    const int ri = 4 * bi, rj = 4 * bj, col0 = 11 * grp;
+    const int nch = M / GR_CHUNK;
+    const long bstep = (long)gridDim.x * ZF_WARPS;
+    // chunk (b, ch) into buffer p: H rows u = 0..15, antennas 32 ch + lane
+    auto issue = [&](long b, int ch, int p) {
+        const c32 *src = H + b * K * M + ch * GR_CHUNK + lane;
+        c32 *dst = wbuf + p * BUF + lane;
+#pragma unroll
+        for (int u = 0; u < K; ++u) cp_async8z(dst + u * LD, src + (long)u * M, true);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    __syncwarp();
+    long b = (long)blockIdx.x * ZF_WARPS + warp;
+    if (b < nbins) issue(b, 0, 0);
+    int p = 0;
+    for (; b < nbins; b += bstep) {
+        c32 acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < nch; ++ch, p ^= 1) {
+            const c32 *sH = wbuf + p * BUF;
+            // the next chunk -- of this subcarrier, else of the next one -- goes in flight
+            const long bn = ch + 1 < nch ? b : b + bstep;
+            if (bn < nbins) {
+                issue(bn, ch + 1 < nch ? ch + 1 : 0, p ^ 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncwarp();
+            if (H16) {
+                T16 *dst = H16 + b * K * M + ch * GR_CHUNK + lane;
+#pragma unroll
+                for (int u = 0; u < K; ++u) dst[(long)u * M] = Operand<T16>::from(sH[u * LD + lane]);
+            }
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                c32 hi[4], hj[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    hi[a] = sH[(ri + a) * LD + col0 + k];
+                    hj[a] = sH[(rj + a) * LD + col0 + k];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] = cfmac(hj[c], hi[a], acc[a][c]);   // h_i conj(h_j)
+            }
+            __syncwarp();   // this buffer is free for the chunk after next
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                c32 v = acc[a][c];
+                const float x1 = __shfl_down_sync(0xffffffffu, v.x, 10), y1 = __shfl_down_sync(0xffffffffu, v.y, 10);
+                const float x2 = __shfl_down_sync(0xffffffffu, v.x, 20), y2 = __shfl_down_sync(0xffffffffu, v.y, 20);
+                v.x = (v.x + x1) + x2;
+                v.y = (v.y + y1) + y2;
+                const int i = ri + a, j = rj + c;
+                if (lane < 10 && j <= i) Gs[soa(b, tri(i) + j, T)] = v;
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Scalar type of the factor: FP64 for FP32 plans; FP32 for 16-bit plans, whose W is
 // rounded to 16 bits afterwards (the FP32 factor's relative error, about the Gram
@@ -420,7 +504,12 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
         const size_t smem = (size_t)ZF_WARPS * 2 * per_buf;
         long blocks = 0;
         cudaError_t e;
-        if (g.K <= 28) {
+        if (g.K == 16 && g.M % GR_CHUNK == 0) {
+            const size_t smem16 = (size_t)ZF_WARPS * 2 * 16 * GR_LD * sizeof(c32);
+            e = persistent_launch_dims(zf_gram16_kernel<T16>, 32 * ZF_WARPS, smem16, nbins, ZF_WARPS, blocks);
+            if (e != cudaSuccess) return e;
+            zf_gram16_kernel<T16><<<(unsigned)blocks, 32 * ZF_WARPS, smem16, st>>>(g, nbins, H, Gs, H16);
+        } else if (g.K <= 28) {
             e = persistent_launch_dims(zf_gram_kernel<T16, 1>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
             zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_buf);

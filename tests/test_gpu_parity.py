@@ -31,6 +31,8 @@ def _blocks(d, g):
 # --- ZF (Eq. 6) ---------------------------------------------------------------
 @pytest.mark.parametrize("cfg", [synth.CONFIGS["cfg1"], small_cfg(),
                                  synth.CONFIGS["cfg3"].with_(S=28),
+                                 small_cfg(M=96, K=16, S=6, S_per_real=2),      # K = 16 Gram, 3 chunks of 32
+                                 small_cfg(M=100, K=16, S=6, S_per_real=2),     # K = 16, ragged chunk
                                  small_cfg(M=256, K=32, N=512, N_d=300, S=2, S_per_real=1, G=18)])
 def test_zf_matches_oracle(cfg):
     c = Case(cfg, S=cfg.S)
