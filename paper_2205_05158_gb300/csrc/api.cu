@@ -1,5 +1,6 @@
 // C-ABI of the fddpd library: plan life cycle, argument checks, workspace layout and
 // the order in which the stage kernels run on the plan's stream.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -166,8 +167,8 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     const size_t o_st = take(sizeof(c32) * cols * g.N_d), o_gy = take(sizeof(c32) * cols * g.N_d),
-                 o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(sizeof(c32) * S * g.M * g.N_d),
-                 o_X = take(sizeof(c32) * S * g.M * g.N_d), o_tw = take(sizeof(c32) * g.N),
+                 o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))),
+                 o_X = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))), o_tw = take(sizeof(c32) * g.N),
                  o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * g.F),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
@@ -435,11 +436,14 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     if (rc) return rc;
     const float gsc = grad_scale(p, ps ? ps->inv_count : 1.0 / ((double)cols * g.N_d));
     FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
+    // BF16 planes: g_xhat goes to the blocked plane in x_hat's buffer (the adjoint reads
+    // the kept x(t), not x_hat); FP32 planes: in place over g_X
+    const bool a16 = act_kind(p) == fdk::OUT_BF16;
+    void *gxh = a16 ? (void *)p->xh : (void *)p->Xpa;
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
-             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, p->Xpa, act_kind(p),
-                                act_kind(p) == fdk::OUT_BF16 ? p->xt16 : nullptr, st));
+             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, gxh, act_kind(p), a16 ? p->xt16 : nullptr, st));
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
-             reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, p->Xpa, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
+             reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);
     if (first) FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {

@@ -56,6 +56,7 @@ cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, 
     if (xt_in && act_kind != OUT_BF16) return cudaErrorInvalidValue;
     const cbf16 *xt = static_cast<const cbf16 *>(xt_in);
     const bool a16 = act_kind == OUT_BF16;
+    if (a16 && gX == gxh) return cudaErrorInvalidValue;   // rows in, blocked plane out
     switch (g.log2N) {
         case 6:
             return a16 ? fftpa_adj16_6(g, rows, xh, pa, twp, static_cast<const cbf16 *>(gX), static_cast<cbf16 *>(gxh), xt, st)

@@ -334,6 +334,23 @@ inline size_t fftpa_smem_bytes_(const Geo &g) {
     return fftpa_smem_base_(g) + (size_t)rows_per_cta(g.N) * fwd_stage_bytes(g);
 }
 
+// BF16 outputs go to the blocked plane (BlkPlane): after a row group's last transform each
+// row's values are staged as BF16 in its (now free) buffer, and the CTA then writes 16-byte
+// pieces (4 subcarriers of one row), rows of the group fastest, so that the pieces of the
+// group's adjacent antennas land side by side.  Padding subcarriers past N_d are zero.
+template <int RPC>
+FD_D void store_blk_rows(const Geo &g, long row0, long rows, const uint32_t *stage, int stride, cbf16 *out) {
+    const BlkPlane bp(g);
+    const int ng4 = (g.N_d + 3) >> 2;
+    for (int idx = threadIdx.x; idx < RPC * ng4; idx += blockDim.x) {
+        const int rr = idx % RPC, j = idx / RPC;
+        const long row = row0 + rr;
+        if (row >= rows) continue;
+        const uint4 v = *reinterpret_cast<const uint4 *>(stage + rr * stride + 4 * j);
+        *reinterpret_cast<uint4 *>(out + bp.row(g, row / g.M, (int)(row % g.M)) + bp.sub(4 * j)) = v;
+    }
+}
+
 template <int LOG2N, int P_, int L_, typename TOut>
 __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows, const c32 *__restrict__ xh,
                                                                const c32 *__restrict__ pa,
@@ -396,6 +413,9 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
         RowPa<P_, L_>::forward(g, F::N, F::T, t, x, bufB, cp, any_even, y);
         __syncthreads();   // taps read; bufA / bufB are free
         transform<LOG2N, false>(y, bufA, bufB, twp, t, rs);
+        constexpr bool BLK = std::is_same<TOut, cbf16>::value;   // BF16: the blocked plane
+        uint32_t *so = reinterpret_cast<uint32_t *>(bufA);   // this row's BF16 values, by subcarrier
+        if (BLK) __syncthreads();   // the last pass has read bufA
         TOut *orow = Xout + rowc * g.N_d;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -403,10 +423,21 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
             const float p2 = active ? cabs2(y[q]) : 0.f;
             if (i >= 0) {
                 dpow += p2;
-                if (active) orow[i] = Operand<TOut>::from(y[q]);
+                if (BLK) {
+                    const cbf16 v = Operand<cbf16>::from(y[q]);
+                    so[i] = *reinterpret_cast<const uint32_t *>(&v);
+                } else if (active) {
+                    orow[i] = Operand<TOut>::from(y[q]);
+                }
             } else {
                 gpow += p2;
             }
+        }
+        if constexpr (BLK) {
+            for (int i = g.N_d + t; i < 4 * ((g.N_d + 3) >> 2); i += F::T) so[i] = 0u;
+            __syncthreads();
+            store_blk_rows<RPC>(g, grp0 * RPC, rows, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
+                                reinterpret_cast<cbf16 *>(Xout));
         }
     }
     if (metrics) {
@@ -503,7 +534,23 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
         RowPa<P_, L_>::adjoint(g, F::N, F::T, t, x, bufB, cp, gv);
         __syncthreads();
         transform<LOG2N, false>(gv, bufA, bufB, twp, t, rs);
-        if (active) {
+        constexpr bool BLK = std::is_same<TOut, cbf16>::value;   // BF16: the blocked plane (never gX's rows)
+        if constexpr (BLK) {
+            uint32_t *so = reinterpret_cast<uint32_t *>(bufA);   // this row's BF16 values, by subcarrier
+            __syncthreads();   // the last pass has read bufA
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
+                if (i >= 0) {
+                    const cbf16 v = Operand<cbf16>::from(gv[q]);
+                    so[i] = *reinterpret_cast<const uint32_t *>(&v);
+                }
+            }
+            for (int i = g.N_d + t; i < 4 * ((g.N_d + 3) >> 2); i += F::T) so[i] = 0u;
+            __syncthreads();
+            store_blk_rows<RPC>(g, grp0 * RPC, rows, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
+                                reinterpret_cast<cbf16 *>(gxh));
+        } else if (active) {
             TOut *orow = gxh + row * g.N_d;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {

@@ -20,6 +20,30 @@ struct Geo {
     double P_T;
 };
 
+// BF16 activation planes read by the tensor-core antenna -> user reductions (the FFT-PA
+// outputs X and g_xhat of BF16 plans): [realisation][subcarrier / 4][symbol of the
+// realisation][antenna][subcarrier % 4] of complex BF16, so that one reduction item -- 4
+// subcarriers of one realisation, all its symbols and antennas -- is one contiguous block.
+// The other planes (x_hat, g_X) keep rows [symbol][antenna][subcarrier].
+struct BlkPlane {
+    long per_group;   // elements of one subcarrier group: S_per_real x M x 4
+    long per_real;    // elements of one realisation
+    FD_HD explicit BlkPlane(const Geo &g)
+        : per_group((long)g.S_per_real * g.M * 4), per_real((long)((g.N_d + 3) >> 2) * g.S_per_real * g.M * 4) {}
+    // element of (symbol s, antenna m) at subcarrier 0 ...
+    FD_HD long row(const Geo &g, long s, int m) const {
+        return (s / g.S_per_real) * per_real + ((s % g.S_per_real) * g.M + m) * 4;
+    }
+    // ... plus this for subcarrier i
+    FD_HD long sub(int i) const { return (long)(i >> 2) * per_group + (i & 3); }
+    // first element of item (realisation r, subcarriers 4 j ..), then (slot t, antenna m) at 4 (t M + m)
+    FD_HD long item(long r, int j) const { return r * per_real + (long)j * per_group; }
+};
+inline size_t blk_plane_bytes(const Geo &g, long S) {
+    const long R = (S + g.S_per_real - 1) / g.S_per_real;
+    return (size_t)R * BlkPlane(g).per_real * 4;
+}
+
 // zero-forcing precoder (Eq. 6): FP32 Gram, Cholesky + triangular inverse (FP64, or FP32
 // when kind is 16-bit), W = H^H G^{-1}
 size_t zf_scratch_bytes(const Geo &g, long nbins);
@@ -72,7 +96,9 @@ cudaError_t to_16bit(long n, const c32 *in, void *out, int kind, cudaStream_t st
 // OFDM + PA rows
 size_t fftpa_smem_bytes(const Geo &g, bool adjoint);
 // xt (BF16 planes only, may be null): the forward stores the time-domain PA input there
-// [rows][N], and the adjoint reads it instead of transforming x_hat again
+// [rows][N], and the adjoint reads it instead of transforming x_hat again.  With BF16
+// planes, X (forward) and gxh (adjoint) are written in the blocked layout (BlkPlane);
+// x_hat and gX are rows, so gxh may not alias gX then.
 cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, void *X, int out_kind,
                           double *metrics, void *xt, cudaStream_t st);
 cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const void *gX, void *gxh,

@@ -464,21 +464,24 @@ __global__ void __launch_bounds__(THREADS, 2)
                     }
                 }
             } else {
-                // BF16 planes (BF16 plans, b_scale 1): every load of the unit in flight at once
+                // BF16 planes (BF16 plans, b_scale 1): every load of the unit in flight at once;
+                // subcarriers past N_d in the last group are padding, read as zero
                 constexpr int PER = TS * 128 / THREADS;
+                const bool b1 = nb > 1, b2 = nb > 2, b3 = nb > 3;
                 uint32_t w[PER][RDB];
 #pragma unroll
                 for (int h = 0; h < PER; ++h) {
                     const int e = tid + h * THREADS, m = e % MP, t = e / MP;
                     const bool ok = e < TS * MP && t < ns && m < M;
-                    const uint32_t *src =
-                        reinterpret_cast<const uint32_t *>(X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0);
-                    if (ok && vec) {
+                    // the blocked plane: the item's 4 subcarriers at (slot, antenna) are 16 bytes
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(
+                        X + BlkPlane(g).item(r, i0 / RDB) + ((long)(s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * RDB);
+                    if (ok && vec_ok) {
                         const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
                         w[h][0] = q4.x;
-                        w[h][1] = q4.y;
-                        w[h][2] = q4.z;
-                        w[h][3] = q4.w;
+                        w[h][1] = b1 ? q4.y : 0u;
+                        w[h][2] = b2 ? q4.z : 0u;
+                        w[h][3] = b3 ? q4.w : 0u;
                     } else {
 #pragma unroll
                         for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < nb) ? src[b] : 0u;
@@ -751,33 +754,36 @@ __global__ void __launch_bounds__(THREADS, 2)
     float err_acc = 0.f, sig_acc = 0.f;
 
     struct It {
-        long t0, bin0;
+        long t0, bin0, x0;
         int i0, ns, nb;
     };
+    const BlkPlane bp(g);
     auto info = [&](long item) {
         It u;
-        const int r = (int)(item / ngroups);
-        u.i0 = (int)(item % ngroups) * RDB;
+        const int r = (int)(item / ngroups), j = (int)(item % ngroups);
+        u.i0 = j * RDB;
         u.t0 = (long)r * g.S_per_real;
         u.ns = (int)min((long)g.S_per_real, (long)S - u.t0);
         u.bin0 = (long)r * Nd + u.i0;
         u.nb = min(RDB, Nd - u.i0);
+        u.x0 = bp.item(r, j);
         return u;
     };
     uint32_t w[PER][RDB];   // the activations of the item being prepared
+    // from the blocked plane: (slot t, antenna m) = element x0 + 4 (128 t + m), one 16-byte
+    // load each, consecutive across the CTA; padding subcarriers past N_d read as zero
     auto load_acts = [&](const It &u) {
-        const bool vec = vec_ok && u.nb == RDB;
 #pragma unroll
         for (int h = 0; h < PER; ++h) {
-            const int e = tid + h * THREADS, m = e & 127, t = e >> 7;
+            const int e = tid + h * THREADS, t = e >> 7;
             const bool ok = t < u.ns;
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(X + ((u.t0 + (ok ? t : 0)) * M + m) * Nd + u.i0);
-            if (ok && vec) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(X + u.x0 + (long)(ok ? e : 0) * RDB);
+            if (ok && vec_ok) {
                 const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
                 w[h][0] = q4.x;
-                w[h][1] = q4.y;
-                w[h][2] = q4.z;
-                w[h][3] = q4.w;
+                w[h][1] = u.nb > 1 ? q4.y : 0u;
+                w[h][2] = u.nb > 2 ? q4.z : 0u;
+                w[h][3] = u.nb > 3 ? q4.w : 0u;
             } else {
 #pragma unroll
                 for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < u.nb) ? src[b] : 0u;
@@ -970,8 +976,8 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long items = (long)R * ((g.N_d + RDB - 1) / RDB);
     if (items == 0) return cudaSuccess;
-    // 4 subcarriers: two 16-byte FP32 loads, or one of BF16
-    const int vec_ok = !(g.N_d & (std::is_same<TX, c32>::value ? 1 : 3)) && aligned16(B);
+    // 4 subcarriers: two 16-byte FP32 loads from rows, or one of BF16 from the blocked plane
+    const int vec_ok = (std::is_same<TX, c32>::value ? !(g.N_d & 1) : 1) && aligned16(B);
     const uint32_t *a = static_cast<const uint32_t *>(A);
     unsigned blocks = 0;
     cudaError_t e;
