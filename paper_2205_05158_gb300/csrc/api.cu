@@ -169,7 +169,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     const size_t o_st = take(sizeof(c32) * cols * g.N_d), o_gy = take(sizeof(c32) * cols * g.N_d),
                  o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))),
                  o_X = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))), o_tw = take(sizeof(c32) * g.N),
-                 o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * g.F),
+                 o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * ((g.F + 7) / 8 * 8)),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
                  o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int));
@@ -462,13 +462,13 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::tc_fc_backward_weight(gw, grad + g.off_fw, g.N_d, g.F, p->status + 1, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         const fdk::GemmArgs gdx{p->gd16, p->fcwT16, cols, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
-        FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->act16, p->ldF, g.F, p->status + 1, st));
+        FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->ldF, p->act16, p->ldF, p->status + 1, st));
     } else {
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, !first, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, cols, gd, theta, p->act, p->gpre, st));
     }
-    FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, p->gpre, p->act, p->partials, st));
+    FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, p->gpre, p->p16 ? p->ldF : g.F, p->partials, st));
     FD_CK(p, fdk::conv_reduce(g, cols, p->partials, grad, !first, st));
     return FDDPD_OK;
 }

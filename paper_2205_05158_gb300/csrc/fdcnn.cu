@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, co
 // parameter gradient: every thread accumulates the 36 weight and 2 bias partial sums of
 // its positions over the CTA's columns; one block reduction per CTA
 __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, const c32 *__restrict__ s,
-                                                            const float *__restrict__ gpre,
+                                                            const float *__restrict__ gpre, long ldg,
                                                             float *__restrict__ partials) {
     constexpr int NW = 2 * 2 * 9 + 2;
     const int G = g.G, GG = G * G;
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, co
     const ConvPos cp = conv_positions(g);
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
         const c32 *row = s + col * g.N_d;
-        const float *gp = gpre + col * g.F;
+        const float *gp = gpre + col * ldg;
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -262,7 +262,7 @@ cudaError_t conv_forward_bf16(const Geo &g, int S, const c32 *s, const float *th
 template <int KC, int NCONV, int CIN>
 __global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, long cols,
                                                        const c32 *__restrict__ s, const float *__restrict__ gpre,
-                                                       float *__restrict__ partials) {
+                                                       long ldg, float *__restrict__ partials) {
     extern __shared__ float smf[];
     constexpr int NW = NCONV * CIN * KC * KC + NCONV;
     const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, 
     for (long col = c0; col < min(cols, c0 + cols_per_cta); ++col) {
         __syncthreads();
         load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
-        for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * g.F + f];
+        for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * ldg + f];
         __syncthreads();
         for (int p = threadIdx.x; p < GoGo; p += blockDim.x) {
             const int i = p / g.Go, j = p % g.Go;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, 
 
 // generic fallback (any kernel size / channel count): one warp per parameter, lanes
 // over positions, one column per CTA
-__global__ void conv_bwd_generic_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ gpre,
+__global__ void conv_bwd_generic_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ gpre, long ldg,
                                         float *__restrict__ partials) {
     extern __shared__ float smf[];
     const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go, KC = g.K_C;
@@ -323,7 +323,7 @@ __global__ void conv_bwd_generic_kernel(Geo g, const c32 *__restrict__ s, const 
     float *gp = Xp + g.Cin * GpGp;
     const long col = blockIdx.x;
     load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
-    for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * g.F + f];
+    for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * ldg + f];
     __syncthreads();
     const int nw = g.n_convw + g.N_conv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -351,15 +351,15 @@ static long conv_partial_rows(const Geo &g, long cols) {
     return conv_bwd_fast(g) ? (cols + kConvColsPerCta - 1) / kConvColsPerCta : cols;
 }
 
-cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, const float * /*act*/,
-                          float *partials, cudaStream_t st) {
+cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, long ldg, float *partials,
+                          cudaStream_t st) {
     const long cols = (long)S * g.K;
     if (!cols) return cudaSuccess;
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * ((size_t)g.Cin * Gp * Gp + g.F);
     cudaError_t e;
     if (conv_fast(g) && g.L_U == 1) {
-        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cols, s, gpre, partials);
+        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cols, s, gpre, ldg, partials);
         return cudaGetLastError();
     }
     if (conv_bwd_fast(g)) {
@@ -367,11 +367,11 @@ cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, 
         const unsigned blocks = (unsigned)conv_partial_rows(g, cols);
         e = cudaFuncSetAttribute(conv_bwd_kernel<3, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        conv_bwd_kernel<3, 2, 2><<<blocks, 256, sm, st>>>(g, cpc, cols, s, gpre, partials);
+        conv_bwd_kernel<3, 2, 2><<<blocks, 256, sm, st>>>(g, cpc, cols, s, gpre, ldg, partials);
     } else {
         e = cudaFuncSetAttribute(conv_bwd_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        conv_bwd_generic_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, gpre, partials);
+        conv_bwd_generic_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, gpre, ldg, partials);
     }
     return cudaGetLastError();
 }

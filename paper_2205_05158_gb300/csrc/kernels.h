@@ -62,7 +62,8 @@ bool tc_bin_supported(const Geo &g);
 
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
-cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gact, const float *act, float *partials,
+// gact: gradient at the pre-activations, [S K][ldg] FP32
+cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gact, long ldg, float *partials,
                           cudaStream_t st);
 // grad[conv_w, conv_b] = (accumulate ? grad + : ) the sum of the partial rows
 cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, bool accumulate, cudaStream_t st);

@@ -332,10 +332,10 @@ struct EpiFcBwdData {      // gpre[m][f] = acc where act > 0
     };
     float *gpre;
     const __nv_bfloat16 *act;
-    long ld_act;
-    int F, vec;             // vec: gpre rows 32-byte and act rows 16-byte aligned
+    long ld_g, ld_act;
+    int vec;                // vec: gpre rows 32-byte and act rows 16-byte aligned
     FD_D void operator()(int m, int n, float v) const {
-        gpre[(long)m * F + n] = __bfloat162float(act[(long)m * ld_act + n]) > 0.f ? v : 0.f;
+        gpre[(long)m * ld_g + n] = __bfloat162float(act[(long)m * ld_act + n]) > 0.f ? v : 0.f;
     }
     FD_D void prefetch(int m, int n, Pre &p) const {
         if (vec) {
@@ -362,7 +362,7 @@ struct EpiFcBwdData {      // gpre[m][f] = acc where act > 0
                 o[8 * h + 2 * k + 1] = f2.y > 0.f ? v[8 * h + 2 * k + 1] : 0.f;
             }
         }
-        float *g = gpre + (long)m * F + n;
+        float *g = gpre + (long)m * ld_g + n;
         st_global_v8(g, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7]);
         st_global_v8(g + 8, o[8], o[9], o[10], o[11], o[12], o[13], o[14], o[15]);
     }
@@ -397,10 +397,10 @@ cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, cons
     return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fb, Nd, residual, vec}, err, st);
 }
 
-cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, const __nv_bfloat16 *act, long ld_act, int F, int *err,
-                                cudaStream_t st) {
-    const int vec = F % 8 == 0 && ld_act % 8 == 0 && al(gpre, 32) && al(act, 16);
-    return tc::launch<256>(g, tc::EpiFcBwdData{gpre, act, ld_act, F, vec}, err, st);
+cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,
+                                int *err, cudaStream_t st) {
+    const int vec = ld_g % 8 == 0 && ld_act % 8 == 0 && al(gpre, 32) && al(act, 16);
+    return tc::launch<256>(g, tc::EpiFcBwdData{gpre, act, ld_g, ld_act, vec}, err, st);
 }
 
 cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, int *err, cudaStream_t st) {

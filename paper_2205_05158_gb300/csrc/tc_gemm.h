@@ -19,8 +19,9 @@ struct GemmArgs {
 cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st);
 cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
                           int *err, cudaStream_t st);
-cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, const __nv_bfloat16 *act, long ld_act, int F, int *err,
-                                cudaStream_t st);
+// gpre [rows][ld_g] FP32 (ld_g a multiple of 8 for whole-sector stores)
+cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,
+                                int *err, cudaStream_t st);
 cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, int *err, cudaStream_t st);
 
 // 16-bit operand preparation (pack16.cu)
