@@ -117,8 +117,12 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *       MMAs on BF16 high / low splits of H and (H H^H)^{-1} (relative error near
  *       2^-16); 0: CUDA-core kernels with FP32 activations and an FP32 W.
  *       Ignored by FP32 plans.
+ *   FDDPD_OPT_HOST_CHUNKS  1..16 (default 7): the number of realisation chunks in which
+ *       fddpd_update_host moves a batch and overlaps its copies with the step; 1 copies
+ *       everything first.  The result does not depend on it beyond the order of FP32
+ *       sums over symbols.
  * Returns FDDPD_ERR_ARG for an unknown option or value. */
-enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1 };
+enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
 
 /* Eq. (6): zero-forcing precoder for R channel realisations (Sec. II-A).
@@ -168,10 +172,12 @@ int fddpd_reset_optimizer(fddpd_plan *plan);
  * to plan-owned device buffers (allocated on the first call) and copies theta and
  * metrics[5] back; the result is that of fddpd_precode followed by fddpd_update(iters)
  * up to the order of FP32 sums over symbols.  The first iteration is pipelined: the
- * batch crosses in up to 8 chunks of whole realisations on a second, plan-owned stream,
- * and each chunk's ZF, forward chain and adjoint run on the plan's stream while the
- * next chunk is copied (the loss stays normalised by the whole batch; the gradient is
- * summed over the chunks).  Further iterations run on the resident batch.  Host
+ * batch crosses in chunks of whole realisations (FDDPD_OPT_HOST_CHUNKS of them, the
+ * first half the size of the others) on a second, plan-owned stream, and each chunk's
+ * ZF, forward chain and adjoint run on the plan's stream while the next chunk is
+ * copied (the loss stays normalised by the whole batch; the gradient is summed over
+ * the chunks).  16-bit plans keep only the 16-bit copy of W here.  Further iterations
+ * run on the resident batch.  Host
  * buffers should be page-locked for full copy bandwidth.  Blocks until the step is
  * complete.  A singular Gram matrix anywhere in the batch returns FDDPD_ERR_SINGULAR
  * before any step, with theta untouched.  iters = 0 only computes the precoders.

@@ -20,6 +20,7 @@ FDDPD_ERR_CUDA, FDDPD_ERR_TIMEOUT, FDDPD_ERR_UNSUPPORTED, FDDPD_ERR_NOMEM = -4, 
 FDDPD_FP32, FDDPD_BF16, FDDPD_FP16 = 0, 1, 2
 FDDPD_GD, FDDPD_ADAM = 0, 1
 FDDPD_OPT_TENSOR_CONTRACTIONS = 1
+FDDPD_OPT_HOST_CHUNKS = 2
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",

@@ -14,7 +14,7 @@
 using fdk::Geo;
 
 static constexpr int kMaxRec = 4096;
-static constexpr int kCopyChunks = 8;   // H copies of fddpd_update_host, each followed by its ZF
+static constexpr int kCopyChunks = 16;   // most chunks of fddpd_update_host
 
 struct fddpd_plan {
     fddpd_dims d;
@@ -53,6 +53,7 @@ struct fddpd_plan {
     c32 *hs, *hH, *hW, *hpa;
     float *hal, *htheta;
     double *hmet;
+    int host_chunks;                             // chunks of fddpd_update_host (FDDPD_OPT_HOST_CHUNKS)
     cudaStream_t cstream;                        // host-to-device copies, beside p->stream
     cudaEvent_t cev[kCopyChunks + 2];            // [0] staging free, [1..kCopyChunks] H chunks, last: s, pa, theta
     char err[512];
@@ -176,6 +177,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     const size_t o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N_d));
     p->p16 = d->precision != FDDPD_FP32;
     p->tc_bin = true;
+    p->host_chunks = 7;
     auto r8 = [](long v) { return (v + 7) / 8 * 8; };
     p->ldF = r8(g.F);
     p->ld2N = r8(2L * g.N_d);
@@ -265,6 +267,10 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
     if (!p) return FDDPD_ERR_ARG;
     if (option == FDDPD_OPT_TENSOR_CONTRACTIONS && (value == 0 || value == 1)) {
         p->tc_bin = value != 0;
+        return FDDPD_OK;
+    }
+    if (option == FDDPD_OPT_HOST_CHUNKS && value >= 1 && value <= kCopyChunks) {
+        p->host_chunks = value;
         return FDDPD_OK;
     }
     return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
@@ -614,15 +620,25 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     cudaStream_t st = p->stream, cs = p->cstream;
     const size_t h_real = sizeof(c32) * (size_t)g.N_d * g.K * g.M;   // one realisation of H (and of W)
     const size_t s_sym = sizeof(c32) * (size_t)g.K * g.N_d;          // one symbol of s
-    const long rc = (R + kCopyChunks - 1) / kCopyChunks;
-    const int nch = (int)((R + rc - 1) / rc);
+    // chunk c holds realisations [rb[c], rb[c + 1]): the first is half the size of the
+    // others, so the step starts after a short copy; the rest split the remainder evenly
+    long rb[kCopyChunks + 1];
+    int nch = (int)std::min<long>(p->host_chunks, R);
+    rb[0] = 0;
+    if (nch > 1) {
+        const long first = std::max<long>(1, R / (2 * nch - 1));
+        rb[1] = first;
+        for (int c = 2; c <= nch; ++c) rb[c] = first + (R - first) * (c - 1) / (nch - 1);
+    } else {
+        rb[1] = R;
+    }
     const double inv_count = 1.0 / ((double)S * g.K * g.N_d);
     FD_CK(p, cudaEventRecord(p->cev[0], st));
     FD_CK(p, cudaStreamWaitEvent(cs, p->cev[0], 0));
     FD_CK(p, cudaMemcpyAsync(p->hpa, pa_coef, n_pa, cudaMemcpyHostToDevice, cs));
     FD_CK(p, cudaMemcpyAsync(p->htheta, theta, n_th, cudaMemcpyHostToDevice, cs));
     for (int c = 0; c < nch; ++c) {
-        const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        const long r0 = rb[c], r1 = rb[c + 1];
         const long t0 = r0 * g.S_per_real, t1 = r1 * g.S_per_real < S ? r1 * g.S_per_real : S;
         FD_CK(p, cudaMemcpyAsync((char *)p->hH + r0 * h_real, (const char *)H + r0 * h_real, (r1 - r0) * h_real,
                                  cudaMemcpyHostToDevice, cs));
@@ -633,7 +649,7 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
     const size_t h16_real = h_real / 2;
     for (int c = 0; c < nch; ++c) {
-        const long r0 = c * rc, r1 = r0 + rc < R ? r0 + rc : R;
+        const long r0 = rb[c], r1 = rb[c + 1];
         const long t0 = r0 * g.S_per_real, t1 = r1 * g.S_per_real < S ? r1 * g.S_per_real : S;
         const c32 *Hc = (const c32 *)((const char *)p->hH + r0 * h_real);
         c32 *Wc = (c32 *)((char *)p->hW + r0 * h_real);
@@ -644,7 +660,7 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
                      fdk::zf_phase(ph, g, (int)(r1 - r0), Hc, Wc, alc, p->status, p->zf_scratch,
                                    p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
                                    p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr, p->kind16, p->tc_bin,
-                                   p->status + 1, st));
+                                   p->status + 1, st, !p->p16));   // 16-bit plans read only W's copy
         if (iters > 0) {
             const Pass ps{inv_count, c == 0, c == nch - 1, (int)r0};
             int rc1 = run_backward(p, (int)(t1 - t0), (const c32 *)((const char *)p->hs + t0 * s_sym), Hc, Wc, alc,

@@ -52,8 +52,9 @@ cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, in
                      void *H16, void *W16, int kind, cudaStream_t st);
 // one of the three ZF kernels: 0 = Gram, 1 = factor / inverse, 2 = W (-1: all three).
 // tc: W on the tensor cores when kind is 16-bit and M <= 128, K <= 16 (err: timeout word)
+// keep_w32 = false: with the tensor-core apply, only the 16-bit copy of W is written
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st);
+                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st, bool keep_w32 = true);
 // W = H^H Z (Z = G^{-1}, lower triangle in the factor's scratch layout) with BF16 hi / lo
 // operand splits on the tensor cores; W16 of the given 16-bit kind beside it
 cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,

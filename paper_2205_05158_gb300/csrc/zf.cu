@@ -539,9 +539,11 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
 }
 
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st) {
-    // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128
+                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st, bool keep_w32) {
+    // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128;
+    // it may leave the FP32 W out when only the copy is wanted
     const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_bin_supported(g);
+    if (tc_apply && !keep_w32) W = nullptr;
     if (kind == OUT_F16)
         return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, false, tc_apply, err,
                           st);

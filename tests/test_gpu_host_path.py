@@ -130,3 +130,24 @@ def test_update_host_singular_leaves_theta(real):
     # the plan stays usable
     c.plan.update_host(hs, _host(c.w.H), hpa, th, 1e-3, 1, fd.FDDPD_GD, None)
     assert not np.array_equal(th, c.w.theta)
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 16])
+def test_update_host_chunk_counts(chunks):
+    """FDDPD_OPT_HOST_CHUNKS changes only how the batch is pipelined."""
+    import paper_2205_05158_gb300 as fd
+    cfg = small_cfg(S=40, S_per_real=3)
+    c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=1)
+    args = (_host(c.w.s), _host(c.w.H), _host(c.w.pa))
+    th_ref, m_ref = _host(c.w.theta.copy()), _host(np.zeros(5))
+    c.plan.update_host(*args, th_ref, 1e-3, 1, fd.FDDPD_GD, m_ref)
+    plan = fd.Plan.from_config(cfg, c.w.P_T, max_symbols=c.S, precision=1)
+    plan.set_option(fd.FDDPD_OPT_HOST_CHUNKS, chunks)
+    th, m = _host(c.w.theta.copy()), _host(np.zeros(5))
+    plan.update_host(*args, th, 1e-3, 1, fd.FDDPD_GD, m)
+    th0 = c.w.theta.astype(np.float64)
+    assert np.linalg.norm((th - th0) - (th_ref - th0)) <= 1e-5 * np.linalg.norm(th_ref - th0)
+    assert np.allclose(m, m_ref, rtol=1e-5, atol=0)
+    for bad in (0, 17):
+        with pytest.raises(fd.FddpdError):
+            plan.set_option(fd.FDDPD_OPT_HOST_CHUNKS, bad)
