@@ -46,6 +46,25 @@ template <int BYTES> FD_D void cp_async_n(void *dst, const void *src) {
 FD_D void cp_async_commit_all() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 FD_D void cp_async_wait_none() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Sum and difference of complex values as one packed FP32-pair instruction each
+// (add / sub .f32x2, sm_100 and later): the same IEEE results as two scalar adds.
+FD_D c32 padd(c32 a, c32 b) {
+    c32 r;
+    asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tadd.rn.f32x2 z, x, y;\n\t"
+        "mov.b64 {%0, %1}, z;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+FD_D c32 psub(c32 a, c32 b) {
+    c32 r;
+    asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tsub.rn.f32x2 z, x, y;\n\t"
+        "mov.b64 {%0, %1}, z;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 template <bool INV> FD_D c32 mul_mi(c32 a) {      // a * (-i) forward, a * (+i) inverse
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
@@ -73,15 +92,15 @@ template <bool INV, int MM> FD_D c32 w16(c32 a) {
 
 template <bool INV> FD_D void dft2(c32 *v) {
     c32 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
 }
 template <bool INV> FD_D void dft4s(c32 &x0, c32 &x1, c32 &x2, c32 &x3) {
-    c32 a0 = cadd(x0, x2), a2 = csub(x0, x2);
-    c32 a1 = cadd(x1, x3), a3 = mul_mi<INV>(csub(x1, x3));
-    x0 = cadd(a0, a1);
-    x2 = csub(a0, a1);
-    x1 = cadd(a2, a3);
+    c32 a0 = padd(x0, x2), a2 = psub(x0, x2);
+    c32 a1 = padd(x1, x3), a3 = mul_mi<INV>(psub(x1, x3));
+    x0 = padd(a0, a1);
+    x2 = psub(a0, a1);
+    x1 = cadd(a2, a3);   // a3 is a swapped pair: two scalar adds
     x3 = csub(a2, a3);
 }
 template <bool INV> FD_D void dft4(c32 *v) { dft4s<INV>(v[0], v[1], v[2], v[3]); }
@@ -90,10 +109,10 @@ template <bool INV> FD_D void dft8(c32 *v) {
     dft4<INV>(e);
     dft4<INV>(o);
     c32 o1 = w16<INV, 2>(o[1]), o2 = w16<INV, 4>(o[2]), o3 = w16<INV, 6>(o[3]);
-    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+    v[0] = padd(e[0], o[0]); v[4] = psub(e[0], o[0]);
+    v[1] = padd(e[1], o1);   v[5] = psub(e[1], o1);
+    v[2] = padd(e[2], o2);   v[6] = psub(e[2], o2);
+    v[3] = padd(e[3], o3);   v[7] = psub(e[3], o3);
 }
 // 16-point DFT, natural order in and out: n = 4 n1 + n2, k = k1 + 4 k2.
 template <bool INV> FD_D void dft16(c32 *v) {
