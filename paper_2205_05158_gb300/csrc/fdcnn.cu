@@ -87,6 +87,13 @@ FD_HD bool conv_fast(const Geo &g) {
     return g.K_C == 3 && g.K_S == 1 && g.N_conv == 2 && g.Cin == 2 && g.pad == 1 && g.G * g.G <= 256 * CF_PPT;
 }
 
+// L1 warm-up of the next column's symbol row: one 128-byte line per thread
+FD_D void prefetch_row_l1(const c32 *row, int n) {
+    const int lines = (n * (int)sizeof(c32) + 127) / 128;
+    if ((int)threadIdx.x < lines)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char *>(row) + 128 * threadIdx.x));
+}
+
 struct ConvPos {
     int base[CF_PPT];    // symbol index of tap (0, 0)
     int mask[CF_PPT];    // bit 3a + b: tap (a, b) inside the grid and the data
@@ -132,6 +139,7 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, co
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
         const c32 *row = s + col * g.N_d;   // L_U = 1: the column's own user
         TOut *out = act + col * ld;
+        if (col + gridDim.x < cols) prefetch_row_l1(row + gridDim.x * g.N_d, g.N_d);
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -176,14 +184,34 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, co
 #pragma unroll
             for (int k = 0; k < 9; ++k) acc[o][c][k] = 0.f;
     const ConvPos cp = conv_positions(g);
-    for (long col = blockIdx.x; col < cols; col += gridDim.x) {
-        const c32 *row = s + col * g.N_d;
+    // this thread's gradient values of the next column, loaded one column ahead
+    float gn[2][CF_PPT];
+    auto load_g = [&](long col) {
         const float *gp = gpre + col * ldg;
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
+            const bool ok = col < cols && p < GG;
+            gn[0][k] = ok ? gp[p] : 0.f;
+            gn[1][k] = ok ? gp[GG + p] : 0.f;
+        }
+    };
+    load_g(blockIdx.x);
+    for (long col = blockIdx.x; col < cols; col += gridDim.x) {
+        const c32 *row = s + col * g.N_d;
+        float gc[2][CF_PPT];
+#pragma unroll
+        for (int k = 0; k < CF_PPT; ++k) {
+            gc[0][k] = gn[0][k];
+            gc[1][k] = gn[1][k];
+        }
+        load_g(col + gridDim.x);
+        if (col + gridDim.x < cols) prefetch_row_l1(row + gridDim.x * g.N_d, g.N_d);
+#pragma unroll
+        for (int k = 0; k < CF_PPT; ++k) {
+            const int p = threadIdx.x + 256 * k;
             if (p >= GG) break;
-            const float g0 = gp[p], g1 = gp[GG + p];
+            const float g0 = gc[0][k], g1 = gc[1][k];
             accb[0] += g0;
             accb[1] += g1;
 #pragma unroll
