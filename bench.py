@@ -34,6 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "DPD'd OFDM symbols/s at M=128,K=16,N=2048; % roofline; EVM vs FP64 oracle"
 UNIT = "symbols/s"
+WORKLOAD = ("cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, orders 1,3,5 taps 0..3, "
+            "FD-CNN G=35 N_conv=2 K_C=3")
 LR = 1e-4
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
@@ -225,7 +227,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation",
+           "config": {"workload": WORKLOAD,
                       "sample": f"{n} symbols per step"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": f"ZF of the {-(-n // cfg.S_per_real)} 1200-subcarrier realisation(s) of "
@@ -349,8 +351,7 @@ def run_ours(args):
            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec_name == "fp32" else f"{prec_name}+f32",
            "data": "synthetic",
-           "config": {"workload": "cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, "
-                                  "orders 1,3,5 taps 0..3, FD-CNN G=35 N_conv=2 K_C=3",
+           "config": {"workload": WORKLOAD,
                       "symbols_per_step": S, "realisations_per_step": R, "precision": prec_name,
                       "step": "ZF + FD-CNN + precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
                       "l2": "inputs larger than L2 (H 2.8 GB), no flush",

@@ -35,6 +35,7 @@ struct fddpd_plan {
     bool p16;
     long ldF, ld2N, ldC;
     __nv_bfloat16 *act16, *actT16, *gd16, *gdT16, *fcw16, *fcwT16;
+    float *fbi;                    // fc_b in the dense layer's interleaved output order
     int kind16;                    // OUT_BF16 or OUT_F16: storage of the H / W copies
     bool tc_bin;                   // per-subcarrier contractions on the tensor cores
     void *H16, *W16;               // [R_max][N_d][K][M] and [R_max][N_d][M][K]
@@ -182,7 +183,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->ldF = r8(g.F);
     p->ld2N = r8(2L * g.N_d);
     p->ldC = r8(cols);
-    size_t o_a16 = 0, o_aT = 0, o_g16 = 0, o_gT = 0, o_w16 = 0, o_wT = 0;
+    size_t o_a16 = 0, o_aT = 0, o_g16 = 0, o_gT = 0, o_w16 = 0, o_wT = 0, o_fbi = 0;
     if (p->p16) {
         o_a16 = take(2 * (size_t)cols * p->ldF);
         o_aT = take(2 * (size_t)g.F * p->ldC);
@@ -190,6 +191,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_gT = take(2 * (size_t)2 * g.N_d * p->ldC);
         o_w16 = take(2 * (size_t)2 * g.N_d * p->ldF);
         o_wT = take(2 * (size_t)g.F * p->ld2N);
+        o_fbi = take(sizeof(float) * 2 * (size_t)g.N_d);
     }
     size_t o_h16 = 0, o_wq16 = 0, o_xt = 0;
     if (p->p16) {
@@ -215,6 +217,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
         p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
         p->fcw16 = (__nv_bfloat16 *)(b + o_w16); p->fcwT16 = (__nv_bfloat16 *)(b + o_wT);
+        p->fbi = (float *)(b + o_fbi);
         p->H16 = b + o_h16;
         p->W16 = b + o_wq16;
         p->kind16 = d->precision == FDDPD_FP16 ? fdk::OUT_F16 : fdk::OUT_BF16;
@@ -406,11 +409,11 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
     if (first) FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
     if (p->p16) {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, theta, p->act16, p->ldF, st));
-        if (first) FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, st));
+        if (first) FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, p->fbi, st));
         const fdk::GemmArgs ga{p->act16, p->fcw16, (int)cols, 2 * g.N_d, g.F, p->ldF, p->ldF, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
                  fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
-                                    theta + g.off_fb, g.N_d, g.residual, p->status + 1, st));
+                                    p->fbi, g.N_d, g.residual, p->status + 1, st));
     } else {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));

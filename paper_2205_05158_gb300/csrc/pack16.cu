@@ -8,16 +8,18 @@
 namespace fdk {
 
 // out[n'][f] = bf16(fc_w[pi(n')][f])
-__global__ void pack_fcw_kernel(Geo g, const float *__restrict__ fw, __nv_bfloat16 *__restrict__ out, long ld) {
+__global__ void pack_fcw_kernel(Geo g, const float *__restrict__ fw, const float *__restrict__ fb,
+                                __nv_bfloat16 *__restrict__ out, long ld, float *__restrict__ fbi) {
     const long n = blockIdx.y;
     const long src = (n & 1) * g.N_d + (n >> 1);
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.F; f += gridDim.x * blockDim.x)
         out[n * ld + f] = __float2bfloat16_rn(fw[src * g.F + f]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) fbi[n] = fb[src];
 }
 
-cudaError_t pack_fcw(const Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st) {
+cudaError_t pack_fcw(const Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, float *fbi, cudaStream_t st) {
     dim3 grid((g.F + 255) / 256, 2 * g.N_d);
-    pack_fcw_kernel<<<grid, 256, 0, st>>>(g, theta + g.off_fw, out, ld_out);
+    pack_fcw_kernel<<<grid, 256, 0, st>>>(g, theta + g.off_fw, theta + g.off_fb, out, ld_out, fbi);
     return cudaGetLastError();
 }
 

@@ -289,11 +289,11 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
         float4 r[4];
     };
     float *st;
-    const float *s, *fb;
-    int Nd, residual, vec;  // vec: st and s rows 32-byte aligned
+    const float *s, *fbi;   // fbi: the bias in output order
+    int Nd, residual, vec;  // vec: st and s rows 32-byte aligned, fbi 16-byte aligned
     FD_D void operator()(int m, int n, float v) const {
         const long idx = (long)m * 2 * Nd + n;
-        st[idx] = v + fb[(n & 1) * Nd + (n >> 1)] + (residual ? s[idx] : 0.f);
+        st[idx] = v + fbi[n] + (residual ? s[idx] : 0.f);
     }
     FD_D void prefetch(int m, int n, Pre &p) const {
         if (!vec) return;
@@ -311,8 +311,15 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
         }
         const long idx = (long)m * 2 * Nd + n;
         float o[16];
+        const float4 *b4 = reinterpret_cast<const float4 *>(fbi + n);   // the same for every row
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] = v[j] + fb[(j & 1) * Nd + ((n + j) >> 1)];
+        for (int h = 0; h < 4; ++h) {
+            const float4 b = b4[h];
+            o[4 * h] = v[4 * h] + b.x;
+            o[4 * h + 1] = v[4 * h + 1] + b.y;
+            o[4 * h + 2] = v[4 * h + 2] + b.z;
+            o[4 * h + 3] = v[4 * h + 3] + b.w;
+        }
         if (residual) {
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -390,11 +397,11 @@ cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaS
 
 static bool al(const void *p, int b) { return !(reinterpret_cast<uintptr_t>(p) & (uintptr_t)(b - 1)); }
 
-cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
+cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fbi, int Nd, int residual,
                           int *err, cudaStream_t st) {
     // rows of 2 N_d floats: whole sectors when that is a multiple of 8 and both bases align
-    const int vec = (2 * Nd) % 8 == 0 && al(st_out, 32) && (!residual || al(s, 16));
-    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fb, Nd, residual, vec}, err, st);
+    const int vec = (2 * Nd) % 8 == 0 && al(st_out, 32) && (!residual || al(s, 16)) && al(fbi, 16);
+    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fbi, Nd, residual, vec}, err, st);
 }
 
 cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,

@@ -17,7 +17,8 @@ struct GemmArgs {
 };
 
 cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st);
-cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fb, int Nd, int residual,
+// fbi: fc_b in the output's interleaved order [2 N_d] (as pack_fcw writes it)
+cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fbi, int Nd, int residual,
                           int *err, cudaStream_t st);
 // gpre [rows][ld_g] FP32 (ld_g a multiple of 8 for whole-sector stores)
 cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,
@@ -27,8 +28,10 @@ cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, 
 // 16-bit operand preparation (pack16.cu)
 cudaError_t conv_forward_bf16(const struct Geo &g, int S, const float2 *s, const float *theta, __nv_bfloat16 *act,
                               long ld, cudaStream_t st);
-// fc_w rows in interleaved order: out[n'][f] = bf16(fc_w[pi(n')][f]), ld_out
-cudaError_t pack_fcw(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st);
+// fc_w rows in interleaved order: out[n'][f] = bf16(fc_w[pi(n')][f]), ld_out; and the
+// bias in the same order, fbi[n'] = fc_b[pi(n')] (FP32)
+cudaError_t pack_fcw(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, float *fbi,
+                     cudaStream_t st);
 // transposed: out[f][n'] = bf16(fc_w[pi(n')][f]), ld_out
 cudaError_t pack_fcw_t(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, cudaStream_t st);
 // out[r][c] = bf16(in[r][c]) for a float matrix

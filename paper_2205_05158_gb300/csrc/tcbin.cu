@@ -823,6 +823,16 @@ __global__ void __launch_bounds__(THREADS, 2)
             const float al = alpha[u.bin0 + warp];
             sc = inv_alpha ? 1.0f / al : al;
         }
+        // the reference symbols of the epilogue, in flight from the start of the item
+        const int nout = u.ns * K * RDB;
+        c32 sref[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + k * THREADS;
+            const int b = e & (RDB - 1), uu = (e >> 2) & 15, t = e >> 6;
+            sref[k] = (COMB && e < nout && b < u.nb) ? s_ref[((u.t0 + t) * K + uu) * Nd + u.i0 + b]
+                                                     : make_float2(0.f, 0.f);
+        }
         // A: the real form of this item's activations (loaded during the previous item)
 #pragma unroll
         for (int h = 0; h < PER; ++h) {
@@ -839,15 +849,6 @@ __global__ void __launch_bounds__(THREADS, 2)
         }
         // the next item's activations go in flight now
         if (item + gridDim.x < nitems) load_acts(info(item + gridDim.x));
-        const int nout = u.ns * K * RDB;
-        c32 sref[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = tid + k * THREADS;
-            const int b = e & (RDB - 1), uu = (e >> 2) & 15, t = e >> 6;
-            sref[k] = (COMB && e < nout && b < u.nb) ? s_ref[((u.t0 + t) * K + uu) * Nd + u.i0 + b]
-                                                     : make_float2(0.f, 0.f);
-        }
         cp_async_wait_all();
         fence_proxy_async();
         __syncthreads();
