@@ -66,9 +66,48 @@ cudaError_t transpose_bf16(const float *in, long rows, long cols, long ld_in, __
     return run_transpose<float, false>(in, rows, cols, ld_in, 0, out, ld_out, st);
 }
 
+// BF16 to BF16 transpose in 64 x 64 tiles, two elements per 4-byte access on both sides
+// (a warp reads and writes 128 contiguous bytes); needs even leading dimensions and
+// 4-byte aligned bases
+__global__ void __launch_bounds__(256) transpose16_kernel(const __nv_bfloat16 *__restrict__ in, long rows, long cols,
+                                                          long ld_in, __nv_bfloat16 *__restrict__ out, long ld_out) {
+    __shared__ __nv_bfloat16 tile[64][66];   // [column][row], padded
+    const long r0 = (long)blockIdx.y * 64, c0 = (long)blockIdx.x * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 column pairs x 8 rows
+    for (int k = ty; k < 64; k += 8) {
+        const long r = r0 + k, c = c0 + 2 * tx;
+        __nv_bfloat162 b = __floats2bfloat162_rn(0.f, 0.f);
+        if (r < rows) {
+            if (c + 1 < cols) b = *reinterpret_cast<const __nv_bfloat162 *>(in + r * ld_in + c);
+            else if (c < cols) b.x = in[r * ld_in + c];
+        }
+        tile[2 * tx][k] = b.x;
+        tile[2 * tx + 1][k] = b.y;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 32; e += 256) {   // 64 columns x 32 row pairs
+        const int cc = e >> 5, rp = e & 31;
+        const long c = c0 + cc, r = r0 + 2 * rp;
+        if (c >= cols || r >= rows) continue;
+        if (r + 1 < rows) {
+            __nv_bfloat162 b;
+            b.x = tile[cc][2 * rp];
+            b.y = tile[cc][2 * rp + 1];
+            *reinterpret_cast<__nv_bfloat162 *>(out + c * ld_out + r) = b;
+        } else {
+            out[c * ld_out + r] = tile[cc][2 * rp];
+        }
+    }
+}
+
 cudaError_t transpose_bf16(const __nv_bfloat16 *in, long rows, long cols, long ld_in, __nv_bfloat16 *out, long ld_out,
                            cudaStream_t st) {
-    return run_transpose<__nv_bfloat16, false>(in, rows, cols, ld_in, 0, out, ld_out, st);
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if ((ld_in | ld_out) & 1 || (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 3)
+        return run_transpose<__nv_bfloat16, false>(in, rows, cols, ld_in, 0, out, ld_out, st);
+    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
+    transpose16_kernel<<<grid, 256, 0, st>>>(in, rows, cols, ld_in, out, ld_out);
+    return cudaGetLastError();
 }
 
 // One pass over an FP32 matrix in[rows][ld_in] (cols valid) writing both its BF16 copy
