@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 
 METRIC = "DPD'd OFDM symbols/s at M=128,K=16,N=2048; % roofline; EVM vs FP64 oracle"
 UNIT = "symbols/s"
+SER_SNR_DB = 30.0   # mean per-subcarrier SNR at the users for the SER line
 WORKLOAD = ("cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, orders 1,3,5 taps 0..3, "
             "FD-CNN G=35 N_conv=2 K_C=3")
 LR = 1e-4
@@ -322,6 +323,22 @@ def run_ours(args):
     evm_db = 10 * math.log10(m[1] / m[2])
     acpr_db = 10 * math.log10(m[3] / m[4])
 
+    # symbol errors at the users: forward chain, receiver noise at a mean per-subcarrier
+    # SNR of SER_SNR_DB, nearest-point decisions (informational)
+    y_ser = torch.empty_like(s)
+    ser_counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    N0 = float((al.double() ** 2).mean()) * 10 ** (-SER_SNR_DB / 10)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for it in range(args.steps):
+        plan.distort(s, H, W, al, pa, theta, y_ser, None)
+        plan.ser(y_ser, s, al, cfg.Q, N0, 1000 + it, ser_counts)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    ser_ms = q0.elapsed_time(q1) / args.steps
+    sc = ser_counts.cpu().numpy()
+
     # roofline of the dominant stage
     mp, src = peaks()
     work = stage_work(cfg, S, prec_name)
@@ -362,6 +379,8 @@ def run_ours(args):
            "stages": stages_out,
            "forward_only": {"value": world * S / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
            "quality": {"evm_db": evm_db, "acpr_db": acpr_db},
+           "ser": {"value": world * S / (ser_ms / 1e3), "unit": UNIT, "ms": ser_ms, "snr_db": SER_SNR_DB,
+                   "ser": float(sc[0]) / max(1, int(sc[1])), "symbols": int(sc[1])},
            "gpu_launches": launches,
            "clocks": clk}
 

@@ -187,6 +187,23 @@ int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c
                       const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
                       double *metrics);
 
+/* Symbol errors at the users (Sec. V-B, the setting of Fig. 3).  To the equalised
+ * symbols y of fddpd_distort it adds the receiver noise of Eq. (4)-(5) -- w ~ CN(0, N0)
+ * per (symbol, user, data subcarrier); the unitary DFT keeps the variance N0 -- scaled
+ * by the user's equaliser, z = y + w / alpha_k, decides z to the nearest point of the
+ * unit-power square Q-QAM constellation (per component) and compares with s.
+ *   y, s   [S][K][N_d]  in (device)   alpha [R][N_d] in (device), R = ceil(S / S_per_real)
+ *   Q      4, 16, 64, 256 or 1024      N0 >= 0 (0: no noise)
+ *   counts [2] (device, 8-byte aligned): errors and symbols compared are ADDED to it
+ *          (subcarriers with alpha <= 0, i.e. singular, are not compared)
+ * Noise: Philox-4x32-10 (Salmon et al., SC'11) with key = seed (low word first) and
+ * counter = (flat index s K N_d + k N_d + i, low word first, 0, 0); its first two
+ * outputs x1, x2 give u = (x + 1/2) 2^-32 and w = sqrt(N0) sqrt(-ln u1) e^{j 2 pi u2}.
+ * Imperfect CSI (Sec. II-A) is the caller's choice of the H given to fddpd_precode.
+ * Asynchronous on the plan's stream.  Errors: ARG, LAYOUT.                         */
+int fddpd_ser(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
+              float N0, unsigned long long seed, unsigned long long *counts);
+
 /* Stage tracing.  Stages of the chain, in execution order. */
 enum fddpd_stage {
     FDDPD_STAGE_ZF_GRAM = 0, FDDPD_STAGE_ZF_FACTOR, FDDPD_STAGE_ZF_APPLY, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,

@@ -56,7 +56,9 @@ def lib():
         L.orc_backward.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, P, P, P, P, P]
         L.orc_update.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, P, P, P, C.c_double, C.c_int,
                                  C.c_int, P, P, C.POINTER(C.c_int), P]
-        for f in ("orc_zf", "orc_precode_all", "orc_distort", "orc_backward", "orc_update"):
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_ser.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, C.c_int, C.c_double, C.c_ulonglong, P, P, P]
+        for f in ("orc_zf", "orc_precode_all", "orc_distort", "orc_backward", "orc_update", "orc_ser"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -229,6 +231,36 @@ def update(d: Dims, s, H, W, alpha, pa_coef, theta, lr: float, iters: int, adam:
     if rc:
         raise ValueError("bad dims")
     return th, met
+
+
+# -- symbol errors at the users (Sec. V-B) -------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """The oracle's own Philox-4x32-10 (C): ctr uint32[4], key uint32[2] -> uint32[4]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def ser(d: Dims, y, s, alpha, Q: int, N0: float, seed: int):
+    """Noisy equalised symbols z = y + w / alpha (w ~ CN(0, N0) from Philox-4x32-10),
+    nearest-point Q-QAM decisions against s -> (errors, compared, z, wrong[S][K][N_d])."""
+    y, s = _c128(y), _c128(s)
+    alpha = _f64(alpha)
+    if y.shape != s.shape or y.ndim != 3 or y.shape[1:] != (d.K, d.N_d):
+        raise ValueError(f"y / s shapes {y.shape} / {s.shape}, expected (S, {d.K}, {d.N_d})")
+    R = -(-y.shape[0] // d.S_per_real)
+    if alpha.shape[0] < R or alpha.shape[1:] != (d.N_d,):
+        raise ValueError(f"alpha has shape {alpha.shape}, expected ({R}+, {d.N_d})")
+    z = np.empty_like(y)
+    wrong = np.zeros(y.shape, dtype=np.int32)
+    counts = np.zeros(2, dtype=np.int64)
+    rc = lib().orc_ser(C.byref(d), y.shape[0], _p(y), _p(s), _p(alpha), int(Q), float(N0), int(seed) & (2**64 - 1),
+                       _p(z), _p(wrong), _p(counts))
+    if rc:
+        raise ValueError("Q must be a square")
+    return int(counts[0]), int(counts[1]), z, wrong
 
 
 def evm_db(met) -> float:

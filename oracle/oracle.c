@@ -486,3 +486,78 @@ int orc_update(const orc_dims *d, int S, const cplx *s, const cplx *H, const cpl
     free(g);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11): ten rounds; each multiplies counter words 0 and  */
+/* 2 by 0xD2511F53 and 0xCD9E8D57 (64-bit products), XORs the high halves     */
+/* with words 1 and 3 and the key, and permutes; the key is bumped by the     */
+/* Weyl constants 0x9E3779B9 and 0xBB67AE85 between rounds.                   */
+void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4])
+{
+    unsigned long long c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    unsigned int k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * c0, p1 = 0xCD9E8D57ull * c2;
+        const unsigned long long n0 = (p1 >> 32) ^ c1 ^ k0, n1 = p1 & 0xFFFFFFFFull;
+        const unsigned long long n2 = (p0 >> 32) ^ c3 ^ k1, n3 = p0 & 0xFFFFFFFFull;
+        c0 = n0 & 0xFFFFFFFFull; c1 = n1; c2 = n2 & 0xFFFFFFFFull; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = (unsigned int)c0; out[1] = (unsigned int)c1; out[2] = (unsigned int)c2; out[3] = (unsigned int)c3;
+}
+
+/* nearest level index of the side-point PAM with levels (2 i - side + 1) / scale */
+static int pam_nearest(double v, double scale, int side)
+{
+    int best = 0;
+    double bd = INFINITY;
+    for (int i = 0; i < side; ++i) {
+        const double d = fabs(v - (2.0 * i - side + 1) / scale);
+        if (d < bd) { bd = d; best = i; }
+    }
+    return best;
+}
+
+/* Sec. V-B (SER at the users) with the noise of Eq. (4)-(5) under the unitary DFT:  */
+/* the per-subcarrier noise is CN(0, N0), and the user equalises by 1 / alpha_k.    */
+int orc_ser(const orc_dims *d, int S, const cplx *y, const cplx *s, const double *alpha, int Q, double N0,
+            unsigned long long seed, cplx *z, int *wrong, long long *counts)
+{
+    int side = 1;
+    while (side * side < Q) ++side;
+    if (side * side != Q || S < 0) return -1;
+    const double scale = sqrt(2.0 * (Q - 1) / 3.0);          /* unit mean power */
+    const unsigned int key[2] = {(unsigned int)seed, (unsigned int)(seed >> 32)};
+    const long long n = (long long)S * d->K * d->N_d;
+    long long errors = 0, compared = 0;
+    for (long long e = 0; e < n; ++e) {
+        const long long t = e / ((long long)d->K * d->N_d);
+        const int i = (int)(e % d->N_d);
+        const double al = alpha[(t / d->S_per_real) * d->N_d + i];
+        if (wrong) wrong[e] = 0;
+        if (!(al > 0.0)) {
+            if (z) z[e] = y[e];
+            continue;
+        }
+        cplx w = 0.0;
+        if (N0 > 0.0) {
+            const unsigned int ctr[4] = {(unsigned int)e, (unsigned int)((unsigned long long)e >> 32), 0u, 0u};
+            unsigned int r[4];
+            orc_philox4x32_10(ctr, key, r);
+            const double u1 = ((double)r[0] + 0.5) / 4294967296.0, u2 = ((double)r[1] + 0.5) / 4294967296.0;
+            w = sqrt(N0) * sqrt(-log(u1)) * (cos(2.0 * M_PI * u2) + I * sin(2.0 * M_PI * u2));
+        }
+        const cplx zz = y[e] + w / al;
+        if (z) z[e] = zz;
+        const int bad = pam_nearest(creal(zz), scale, side) != pam_nearest(creal(s[e]), scale, side) ||
+                        pam_nearest(cimag(zz), scale, side) != pam_nearest(cimag(s[e]), scale, side);
+        if (wrong) wrong[e] = bad;
+        errors += bad;
+        ++compared;
+    }
+    counts[0] = errors;
+    counts[1] = compared;
+    return 0;
+}

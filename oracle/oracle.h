@@ -46,4 +46,15 @@ int  orc_update(const orc_dims *d, int S, const double complex *s, const double 
                 const double complex *W, const double *alpha, const double complex *pa,
                 double *theta, double lr, int iters, int adam, double *adam_m, double *adam_v,
                 int *adam_t, double *metrics);
+/* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ctr[4], key[2] -> out[4]. */
+void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);
+/* Symbol errors at the users (Sec. V-B; noise of Eq. 4-5): z = y + w / alpha with
+ * w ~ CN(0, N0) drawn by Philox-4x32-10 (key = seed, counter = (flat index, 0, 0), first
+ * two outputs u = (x + 1/2) 2^-32, w = sqrt(N0) sqrt(-ln u1) e^{j 2 pi u2}), decided to the
+ * nearest unit-power square Q-QAM point.  Subcarriers with alpha <= 0 are skipped.
+ *   z [S][K][N_d] out (may be NULL), wrong [S][K][N_d] out 0/1 (may be NULL)
+ *   counts[2] out: errors, symbols compared                                       */
+int  orc_ser(const orc_dims *d, int S, const double complex *y, const double complex *s,
+             const double *alpha, int Q, double N0, unsigned long long seed, double complex *z,
+             int *wrong, long long *counts);
 #endif

@@ -26,7 +26,7 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
-            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option"]
+            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_tc_gemm.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P]
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     L.fddpd_set_option.argtypes = [P, I, I]
+    L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
@@ -212,6 +213,15 @@ class Plan:
         """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
         self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
+
+    def ser(self, y, s, alpha, Q: int, N0: float, seed: int, counts, S: Optional[int] = None):
+        """fddpd_ser: adds (errors, symbols compared) of the noisy, equalised symbols
+        y + w / alpha against s to `counts` (a device int64[2] tensor; asynchronous)."""
+        import torch
+        S = y.shape[0] if S is None else S
+        self._check(self._lib.fddpd_ser(self._h, S, _ptr(y, torch.complex64), _ptr(s, torch.complex64),
+                                        _ptr(alpha, torch.float32), int(Q), float(N0),
+                                        int(seed) & (2 ** 64 - 1), _ptr(counts, torch.int64)))
 
     def update_host(self, s, H, pa, theta, lr: float, iters: int = 1, optimizer: int = FDDPD_GD, metrics=None,
                     S: Optional[int] = None):

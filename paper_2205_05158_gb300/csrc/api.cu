@@ -695,6 +695,21 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     return fddpd_sync(p);
 }
 
+extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
+                         float N0, unsigned long long seed, unsigned long long *counts) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
+    if (!y || !s || !alpha || !counts) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (Q != 4 && Q != 16 && Q != 64 && Q != 256 && Q != 1024) return set_err(p, FDDPD_ERR_ARG, "Q=%d", Q);
+    if (!(N0 >= 0.0f)) return set_err(p, FDDPD_ERR_ARG, "N0 must be >= 0");
+    if (!aligned(y, 8) || !aligned(s, 8) || !aligned(alpha, 4) || !aligned(counts, 8))
+        return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    FD_CK(p, fdk::ser_count(p->g, S, reinterpret_cast<const c32 *>(y), reinterpret_cast<const c32 *>(s), alpha, Q, N0,
+                            seed, counts, p->stream));
+    p->launches += 1;
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_sync(fddpd_plan *p) {
     if (!p) return FDDPD_ERR_ARG;
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));

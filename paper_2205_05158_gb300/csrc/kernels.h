@@ -61,6 +61,10 @@ cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, c
                         int kind, int *err, cudaStream_t st);
 bool tc_bin_supported(const Geo &g);
 
+// symbol errors at the users: counts[0] += errors, counts[1] += symbols compared
+cudaError_t ser_count(const Geo &g, int S, const c32 *y, const c32 *s, const float *alpha, int Q, float N0,
+                      unsigned long long seed, unsigned long long *counts, cudaStream_t st);
+
 // FD-CNN
 cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
 // gact: gradient at the pre-activations, [S K][ldg] FP32

@@ -158,6 +158,26 @@ def channel_taps(seed: int, R: int, T: int, K: int, M: int, rho: float = 0.0,
     return out
 
 
+def channel_estimate(cfg: "Config", eta: float, S: Optional[int] = None, symbol_offset: int = 0) -> np.ndarray:
+    """Imperfect CSI at the base station (Sec. II-A): taps H_t^est = sqrt(1 - eta) H_t +
+    sqrt(eta) H_t^err with H_t^err entries CN(0, 1), as the per-subcarrier response of the
+    data bins [R][N_d][K][M] (complex64) of the same realisations make_workload draws."""
+    if not 0.0 <= eta <= 1.0:
+        raise ValueError("eta outside [0, 1]")
+    S = cfg.S if S is None else S
+    r0 = symbol_offset // cfg.S_per_real
+    R = (S + cfg.S_per_real - 1) // cfg.S_per_real
+    bins = data_bins(cfg.N, cfg.N_d)
+    out = np.empty((R, cfg.N_d, cfg.K, cfg.M), dtype=np.complex64)
+    for r in range(R):
+        taps = channel_taps(cfg.seed, 1, cfg.T, cfg.K, cfg.M, cfg.rho, first_real=r0 + r)
+        st = Stream(cfg.seed, f"taps_err/{r0 + r}")
+        g = st.normal(2 * cfg.T * cfg.K * cfg.M).reshape(1, cfg.T, cfg.K, cfg.M, 2)
+        err = (g[..., 0] + 1j * g[..., 1]) * math.sqrt(0.5)
+        out[r] = channel_fd(math.sqrt(1.0 - eta) * taps + math.sqrt(eta) * err, cfg.N, bins)[0]
+    return out
+
+
 def channel_fd(taps: np.ndarray, N: int, bins: np.ndarray) -> np.ndarray:
     """Per-subcarrier channel of the data bins: H_k = sum_t H_t exp(-j 2 pi k t / N).
     taps [R][T][K][M] -> [R][N_d][K][M]."""

@@ -336,3 +336,60 @@ def test_chain_rejects_missing_realisations():
         oracle.backward(d, w.s, w.H[:1], W, al, w.pa, w.theta[:-1])
     y, _ = oracle.distort(d, w.s[:cfg.S_per_real], w.H[:1], W, al, w.pa, w.theta)
     assert y.shape == (cfg.S_per_real, cfg.K, cfg.N_d)
+
+
+# --- symbol errors at the users (Sec. V-B; noise of Eq. 4-5) ------------------------
+def test_oracle_philox_known_answers():
+    """The oracle's own Philox-4x32-10 against the published Random123 vectors."""
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert list(oracle.philox4x32_10(w[:4], w[4:6])) == w[6:10]
+
+
+def _ser_dims(K=2, N_d=48, Spr=5):
+    return oracle.make_dims(M=4, K=K, N=64, N_d=N_d, orders=[1], L=0, G=7, P_T=1.0, S_per_real=Spr)
+
+
+def test_oracle_ser_noiseless_and_one_step_off():
+    d = _ser_dims()
+    s = synth.qam_symbols(3, 16, (10, d.K, d.N_d)).astype(np.complex128)
+    al = np.ones((2, d.N_d))
+    e, n, _, _ = oracle.ser(d, s, s, al, 16, 0.0, 7)
+    assert (e, n) == (0, s.size)
+    step = 2.0 / math.sqrt(2.0 * 15 / 3.0)                  # one level of unit-power 16-QAM
+    y = s + np.where(s.real < 0, step, -step)              # every real part moves to the next level inwards
+    e, n, _, _ = oracle.ser(d, y, s, al, 16, 0.0, 7)
+    assert (e, n) == (s.size, s.size)
+    al[1, 5] = 0.0                                          # a singular subcarrier carries no symbol
+    e, n, _, _ = oracle.ser(d, s, s, al, 16, 0.0, 7)
+    assert n == s.size - 5 * d.K
+
+
+def test_oracle_ser_matches_awgn_closed_form():
+    """y = s, alpha = 1: square 16-QAM in AWGN, P_s = 1 - (1 - p)^2 with
+    p = 2 (1 - 1/4) Q(sqrt(3 SNR / 15)), SNR = E_s / N0 (a textbook closed form)."""
+    d = _ser_dims(K=4, N_d=500, Spr=10)
+    S = 100
+    s = synth.qam_symbols(5, 16, (S, d.K, d.N_d)).astype(np.complex128)
+    al = np.ones((10, d.N_d))
+    for snr_db in (12.0, 15.0):
+        N0 = 10 ** (-snr_db / 10)
+        e, n, z, _ = oracle.ser(d, s, s, al, 16, N0, 1234)
+        w = z - s
+        assert abs(np.mean(np.abs(w) ** 2) / N0 - 1.0) < 0.01        # E|w|^2 = N0
+        assert abs(np.mean(w.real ** 2) - np.mean(w.imag ** 2)) < 0.01 * N0
+        p = 2 * (1 - 1 / 4) * 0.5 * math.erfc(math.sqrt(3 * 10 ** (snr_db / 10) / 15) / math.sqrt(2))
+        ps = 1 - (1 - p) ** 2
+        sd = math.sqrt(ps * (1 - ps) / n)
+        assert abs(e / n - ps) < 4 * sd, (snr_db, e / n, ps)
+
+
+def test_oracle_ser_noise_scales_with_alpha():
+    """z = y + w / alpha: alpha 2 with 4 N0 reproduces the same z as alpha 1 with N0."""
+    d = _ser_dims()
+    s = synth.qam_symbols(9, 64, (10, d.K, d.N_d)).astype(np.complex128)
+    _, _, z1, w1 = oracle.ser(d, s, s, np.ones((2, d.N_d)), 64, 0.02, 99)
+    _, _, z2, w2 = oracle.ser(d, s, s, 2 * np.ones((2, d.N_d)), 64, 0.08, 99)
+    assert np.allclose(z1, z2, rtol=0, atol=1e-15) and np.array_equal(w1, w2)

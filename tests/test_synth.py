@@ -86,3 +86,15 @@ def test_workload_shapes():
     w2 = synth.make_workload(synth.CONFIGS["cfg2"], S=28, symbol_offset=14)
     w3 = synth.make_workload(synth.CONFIGS["cfg2"], S=42)
     assert np.array_equal(w2.s, w3.s[14:]) and np.array_equal(w2.H, w3.H[1:])
+
+
+def test_channel_estimate_imperfect_csi():
+    """Sec. II-A: H_est = sqrt(1 - eta) H + sqrt(eta) H_err, H_err taps CN(0, 1), so the
+    per-subcarrier error has variance eta T; eta = 0 returns the true channel."""
+    cfg = synth.CONFIGS["cfg2"].with_(S=28)
+    w = synth.make_workload(cfg, S=28)
+    assert np.array_equal(synth.channel_estimate(cfg, 0.0, S=28), w.H)
+    eta = 0.2
+    d = synth.channel_estimate(cfg, eta, S=28).astype(np.complex128) - math.sqrt(1 - eta) * w.H
+    assert abs(np.mean(np.abs(d) ** 2) / (eta * cfg.T) - 1) < 0.02
+    assert abs(np.mean(d)) < 0.02 * math.sqrt(eta * cfg.T)
