@@ -74,7 +74,9 @@ typedef struct {
 
 typedef struct {
     int n_orders;     /* 1..8                                                            */
-    int orders[8];    /* nonlinear orders p >= 1 of the basis x |x|^{p-1} (e.g. 1, 3, 5) */
+    int orders[8];    /* nonlinear orders p >= 1 of the basis x |x|^{p-1} (e.g. 1, 3, 5); */
+                      /* or {0} with n_orders = 1, L = 0: the ideal linear-clipping PA of  */
+                      /* Sec. V-B, y = x for |x| <= A, A x / |x| above, A = Re c^b_{0,0}   */
     int L;            /* memory: taps l = 0..L, 0..7                                     */
 } fddpd_pa_desc;
 

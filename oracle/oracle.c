@@ -141,6 +141,14 @@ int orc_precode_all(const orc_dims *d, int R, const cplx *H, cplx *W, double *al
 /* ------------------------------------------------------------------------ */
 void orc_pa(int N, const cplx *x, int n_orders, const int *orders, int L, const cplx *c, cplx *y)
 {
+    if (n_orders == 1 && orders[0] == 0) {   /* ideal linear-clipping PA (Sec. V-B), A = Re c */
+        const double A = creal(c[0]);
+        for (int n = 0; n < N; ++n) {
+            const double r = cabs(x[n]);
+            y[n] = r > A ? x[n] * (A / r) : x[n];
+        }
+        return;
+    }
     for (int n = 0; n < N; ++n) {
         cplx acc = 0;
         for (int pi = 0; pi < n_orders; ++pi)
@@ -369,7 +377,14 @@ static void backward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr
         orc_dft(N, gX, gpa, 1);                 /* adjoint of the unitary DFT      */
         const cplx *x = st->x + (long)m * N;
         const cplx *c = pa + (long)m * P * L1;
-        for (int n = 0; n < N; ++n) {           /* adjoint of the PA               */
+        const int clip = P == 1 && d->orders[0] == 0;
+        for (int n = 0; n < N && clip; ++n) {   /* adjoint of the clipping PA:      */
+            const double A = creal(c[0]), r = cabs(x[n]);   /* above A, df/dx = A/(2r),  */
+            gx[n] = r > A ? (A / (2 * r)) * gpa[n]          /* df/dx* = -A x^2/(2 r^3)  */
+                              - (A / (2 * r * r * r)) * x[n] * x[n] * conj(gpa[n])
+                          : gpa[n];
+        }
+        for (int n = 0; n < N && !clip; ++n) {  /* adjoint of the PA               */
             cplx acc = 0;
             for (int pi = 0; pi < P; ++pi) {
                 cplx h = 0;

@@ -11,7 +11,9 @@
  *   H      [R][N_d][K][M]       per-subcarrier channel, R = ceil(S / S_per_real)
  *   W      [R][N_d][M][K]       unnormalised ZF precoder H^H (H H^H)^{-1}
  *   alpha  [R][N_d]             per-subcarrier power normalisation
- *   pa     [M][P][L+1]          memory-polynomial coefficients c^b_{p,l}
+ *   pa     [M][P][L+1]          memory-polynomial coefficients c^b_{p,l}; orders = {0}
+ *                               with L = 0 is the ideal linear-clipping PA of clipping
+ *                               amplitude A = Re c^b_{0,0}
  *   theta  flat: conv_w[N_conv][2L_U][K_C][K_C], conv_b[N_conv],
  *                fc_w[2N_d][N_conv*Go*Go], fc_b[2N_d]   (Go = ceil(G/K_S))
  * metrics[5] = { loss, sum|y/alpha - s|^2, sum|s|^2, guard-bin power, data-bin power }

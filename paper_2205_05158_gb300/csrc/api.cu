@@ -117,7 +117,9 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (!(d->P_T > 0)) return set_err(nullptr, FDDPD_ERR_ARG, "P_T must be positive");
     if (pa->n_orders < 1 || pa->n_orders > 8 || pa->L < 0 || pa->L > 7) return set_err(nullptr, FDDPD_ERR_ARG, "PA orders / memory out of range");
     for (int i = 0; i < pa->n_orders; ++i)
-        if (pa->orders[i] < 1 || pa->orders[i] > 15) return set_err(nullptr, FDDPD_ERR_ARG, "PA order %d outside 1..15", pa->orders[i]);
+        if (pa->orders[i] < 0 || pa->orders[i] > 15 || (pa->orders[i] == 0 && (pa->n_orders != 1 || pa->L != 0)))
+            return set_err(nullptr, FDDPD_ERR_ARG, "PA order %d: 1..15, or 0 (linear clipping) alone with L = 0",
+                           pa->orders[i]);
     if (dpd->G < 1 || dpd->G * dpd->G < d->N_d || dpd->G > 128) return set_err(nullptr, FDDPD_ERR_ARG, "grid G=%d cannot hold N_d", dpd->G);
     if (dpd->L_U < 1 || dpd->L_U > d->K) return set_err(nullptr, FDDPD_ERR_ARG, "L_U=%d outside 1..K", dpd->L_U);
     if (dpd->K_C < 1 || !(dpd->K_C & 1) || dpd->K_C > 15) return set_err(nullptr, FDDPD_ERR_ARG, "K_C=%d must be odd in 1..15", dpd->K_C);

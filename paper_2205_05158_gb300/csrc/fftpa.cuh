@@ -255,6 +255,9 @@ struct RowPa {
                     for (int p = (P_ > 0 ? P_ : 1) - 2; p >= 0; --p)
                         poly = make_float2(fmaf(poly.x, r2, c[p].x), fmaf(poly.y, r2, c[p].y));
                     y[q] = cfma(xl, poly, y[q]);
+                } else if (g.orders[0] == 0) {   // linear clipping (L = 0): x min(1, A / |x|), A = Re c
+                    const float A = cp[0].x, mg = sqrtf(r2);
+                    y[q] = mg > A ? cscale(xl, A / mg) : xl;
                 } else {
                     const float mg = any_even ? sqrtf(r2) : 0.f;
                     for (int p = 0; p < P; ++p)
@@ -306,6 +309,16 @@ struct RowPa {
                     A = cfma(cmul(x[q], x[q]), Bs, A);
                 }
                 gx[q] = A;
+            }
+        } else if (g.orders[0] == 0) {
+            // linear clipping: above A, d y / d x = A / (2 |x|), d y / d x* = -A x^2 / (2 |x|^3)
+            const float A = cp[0].x;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const c32 gl = gs[pidx((t + q * T) & (N - 1))];
+                const float r2 = cabs2(x[q]), mg = sqrtf(r2);
+                gx[q] = mg > A ? cfma(cscale(cmul(x[q], x[q]), -A / (2.0f * mg * r2)), cconj(gl), cscale(gl, A / (2.0f * mg)))
+                               : gl;
             }
         } else {
             const int P = g.n_orders, L = g.L, L1 = L + 1;

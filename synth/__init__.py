@@ -206,11 +206,18 @@ def pa_coefficients(seed: int, M: int, nominal: Dict[int, List[complex]], spread
     return base[None] * (1.0 + delta)
 
 
+# The ideal linear-clipping PA of Sec. V-B (Fig. 3): order 0 with one coefficient, the
+# clipping amplitude A (y = x for |x| <= A, A x / |x| above).
+PA_LINEAR_CLIP = {0: [1.0]}
+
+
 def saturation_amplitude(nominal: Dict[int, List[complex]]) -> float:
     """Drive-level reference: the first local maximum over A > 0 of the nominal
     static AM/AM curve |sum_p (sum_l c_{p,l}) A^p| (found on a fine grid, then
     refined by golden-section search)."""
     orders = sorted(nominal)
+    if orders == [0]:   # the linear-clipping PA saturates at its clipping amplitude
+        return float(abs(nominal[0][0]))
     cs = [sum(nominal[p]) for p in orders]
 
     def f(a):

@@ -68,7 +68,9 @@ def _create(lib, **over):
     (dict(precision=7), binding.FDDPD_ERR_ARG), (dict(G=6), binding.FDDPD_ERR_ARG),
     (dict(L_U=3), binding.FDDPD_ERR_ARG), (dict(K_C=2), binding.FDDPD_ERR_ARG),
     (dict(N_conv=0), binding.FDDPD_ERR_ARG), (dict(residual=2), binding.FDDPD_ERR_ARG),
-    (dict(orders=[0]), binding.FDDPD_ERR_ARG), (dict(L=9), binding.FDDPD_ERR_ARG),
+    (dict(orders=[-1]), binding.FDDPD_ERR_ARG), (dict(L=9), binding.FDDPD_ERR_ARG),
+    # order 0 is the linear-clipping PA: alone and memoryless only
+    (dict(orders=[0, 3]), binding.FDDPD_ERR_ARG), (dict(orders=[0], L=1), binding.FDDPD_ERR_ARG),
 ])
 def test_plan_rejects_bad_descriptors(lib, over, code):
     rc, h = _create(lib, **over)

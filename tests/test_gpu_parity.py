@@ -68,6 +68,9 @@ FWD_CASES = [
     ("pa13_mem3", lambda: Case(small_cfg(N=512, pa_nominal=PA_13_MEM), fc_scale=0.3)),
     ("pa_general_even", lambda: Case(small_cfg(N=128, N_d=100, G=10, pa_nominal=PA_EVEN), fc_scale=0.3)),
     ("pa_general_1357", lambda: Case(small_cfg(N=2048, N_d=1200, M=12, G=35, pa_nominal=PA_1357), fc_scale=0.1)),
+    # the ideal linear-clipping PA of Sec. V-B driven into clipping (IBO 0 dB)
+    ("pa_clip", lambda: Case(small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0),
+                             fc_scale=0.3)),
 ]
 
 
@@ -118,6 +121,8 @@ BWD_CASES = [
     ("ragged", lambda: Case(small_cfg(), fc_scale=0.3)),
     ("ragged_literal", lambda: Case(small_cfg(L_U=1, K_S=1), fc_scale=0.5, residual=0)),
     ("cfg2_14", lambda: Case(synth.CONFIGS["cfg2"], S=14, fc_scale=0.2)),
+    ("pa_clip", lambda: Case(small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0),
+                             fc_scale=0.3)),
 ]
 
 

@@ -133,3 +133,23 @@ def test_imperfect_csi_chain(prec):
     yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
     assert nmse(y.cpu().numpy(), yo) <= (1e-9 if prec == 0 else 1e-4)
     assert abs(oracle.evm_db(met.cpu().numpy()) - oracle.evm_db(meto)) <= (1e-3 if prec == 0 else 0.1)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16"])
+def test_clipping_pa_ser_pipeline(prec):
+    """The Fig. 3 reference PA (linear clipping) through forward, noise and decisions:
+    GPU counts against the oracle's on the oracle's own forward output."""
+    T = torch()
+    cfg = small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=3.0, S=20, S_per_real=4)
+    c = Case(cfg, S=cfg.S, fc_scale=0.0, precision=prec)
+    c.use_oracle_zf_on_gpu()
+    y, met = c.gpu_distort()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    from gpu_common import nmse
+    assert nmse(y, yo) <= (1e-9 if prec == 0 else 1e-4)
+    assert meto[3] > 0                                    # clipping spreads power into the guard bins
+    N0 = float(np.mean(alo ** 2)) * 10 ** (-12 / 10)
+    e_g, n_g = _gpu_ser(c.plan, dev(y.astype(np.complex64)), c.s, c.alpha, cfg.Q, N0, 9)
+    e_o, n_o, z, _ = oracle.ser(c.d, y, c.w.s, c.alpha.cpu().numpy(), cfg.Q, N0, 9)
+    assert n_g == n_o and abs(e_g - e_o) <= _near_boundary(z, cfg.Q)

@@ -393,3 +393,36 @@ def test_oracle_ser_noise_scales_with_alpha():
     _, _, z1, w1 = oracle.ser(d, s, s, np.ones((2, d.N_d)), 64, 0.02, 99)
     _, _, z2, w2 = oracle.ser(d, s, s, 2 * np.ones((2, d.N_d)), 64, 0.08, 99)
     assert np.allclose(z1, z2, rtol=0, atol=1e-15) and np.array_equal(w1, w2)
+
+
+# --- the ideal linear-clipping PA (Sec. V-B, Fig. 3) --------------------------------
+def test_clip_pa_definition():
+    """|y| = min(|x|, A) with the phase of x; a clipping level above every sample is the
+    identity; the drive-level reference is the clipping amplitude."""
+    rng = np.random.default_rng(4)
+    x = (rng.standard_normal(64) + 1j * rng.standard_normal(64)) * 0.8
+    y = oracle.pa(x, [0], np.array([[0.9]]))
+    assert np.allclose(np.abs(y), np.minimum(np.abs(x), 0.9), atol=1e-15)
+    assert np.allclose(np.angle(y), np.angle(x), atol=1e-12)
+    assert np.array_equal(oracle.pa(x, [0], np.array([[1e9]])), x)
+    assert synth.saturation_amplitude({0: [1.3]}) == 1.3
+
+
+def test_clip_pa_adjoint_central_differences():
+    """The chain with a clipping PA driven into clipping: hand-derived adjoint (Wirtinger
+    derivatives A/(2|x|), -A x^2/(2|x|^3) above A) against central differences."""
+    cfg = _small_cfg(pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0)
+    w, d, W, al = _setup(cfg, fc_scale=0.5)
+    th = w.theta.astype(np.float64)
+    g, _ = oracle.backward(d, w.s, w.H, W, al, w.pa, th)
+    rng = np.random.default_rng(5)
+    gmax = np.abs(g).max()
+    for j in rng.choice(len(th), 60, replace=False):
+        tp, tm = th.copy(), th.copy()
+        tp[j] += 1e-6
+        tm[j] -= 1e-6
+        fd = (_loss(d, w, W, al, tp) - _loss(d, w, W, al, tm)) / 2e-6
+        assert abs(fd - g[j]) <= 1e-5 * gmax, (j, fd, g[j])
+    # the PA clips a good share of the time-domain samples at this drive level
+    y, met = oracle.distort(d, w.s, w.H, W, al, w.pa, th)
+    assert met[3] > 1e-4 * met[4]
