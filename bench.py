@@ -207,7 +207,7 @@ def oracle_step(cfg, w, n_sym: int):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    rank, _, _ = rank_env()
     if rank != 0:
         return
     import oracle
@@ -238,6 +238,35 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# ranks: one process per GPU running an independent replica (symbols and channel
+# realisations are independent units, so the data path exchanges nothing); a rank draws
+# its own symbols and channels, the timing is the maximum over ranks, and the value
+# counts every rank's symbols
+# ---------------------------------------------------------------------------
+def rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_config(rank: int, symbols: int):
+    import synth
+    return synth.CONFIGS["cfg3"].with_(seed=rank, S=symbols)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, symbols: int, seconds: float) -> float:
+    return world * symbols / seconds
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -247,9 +276,7 @@ def run_ours(args):
     import synth
     import paper_2205_05158_gb300 as fd
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -262,7 +289,7 @@ def run_ours(args):
 
     prec_name = args.precision or "bf16"
     prec = {"fp32": fd.FDDPD_FP32, "bf16": fd.FDDPD_BF16, "fp16": fd.FDDPD_FP16}[prec_name]
-    cfg = synth.CONFIGS["cfg3"].with_(seed=rank, S=args.symbols)
+    cfg = rank_config(rank, args.symbols)
     S = cfg.S
     w = synth.make_workload(cfg, fc_scale=0.05)
     R = w.H.shape[0]
@@ -303,12 +330,8 @@ def run_ours(args):
     plan.profile(False)
     launches = plan.launch_count - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * S / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    value = job_rate(world, S, ms / 1e3)
 
     # forward-only (running mode) throughput on the same inputs, informational
     torch.cuda.synchronize()
@@ -398,12 +421,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
-        sec = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([sec], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        out["e2e"] = {"value": world * S / sec, "unit": UNIT,
+        sec = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
+        out["e2e"] = {"value": job_rate(world, S, sec), "unit": UNIT,
                       "h2d_bytes_per_step": int(hs.nbytes + hH.nbytes + hpa.nbytes + hth.nbytes),
                       "d2h_bytes_per_step": int(hth.nbytes + 5 * 8)}
 
