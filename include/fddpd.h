@@ -78,6 +78,11 @@ typedef struct {
                       /* or {0} with n_orders = 1, L = 0: the ideal linear-clipping PA of  */
                       /* Sec. V-B, y = x for |x| <= A, A x / |x| above, A = Re c^b_{0,0}   */
     int L;            /* memory: taps l = 0..L, 0..7                                     */
+    int G;            /* cross-term length of Eq. (9), 0..2: with G > 0 each antenna's   */
+                      /* coefficients are a [n_orders][L+1] (the memory polynomial), then */
+                      /* the lagging b [n_orders][L+1][G] of x_{n-l} |x_{n-l-g}|^{p-1} and */
+                      /* the leading c [n_orders][L+1][G] of x_{n-l} |x_{n-l+g}|^{p-1}     */
+                      /* (order-1 slots unused), n_orders (L+1)(1+2G) values per antenna */
 } fddpd_pa_desc;
 
 typedef struct {
@@ -142,7 +147,8 @@ int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, flo
 /* Forward chain over S symbols (running mode of the FD-DPD, Sec. III-A and IV).
  *   s       [S][K][N_d]       in : unit-power QAM symbols of the data bins
  *   H, W, alpha               in : as produced for realisations 0..ceil(S/S_per_real)-1
- *   pa_coef [M][n_orders][L+1] in: per-antenna PA coefficients c^b_{p,l}
+ *   pa_coef [M][n_orders][L+1] in: per-antenna PA coefficients c^b_{p,l} (with cross
+ *           terms, G > 0: [M][n_orders (L+1) (1 + 2G)] as fddpd_pa_desc describes)
  *   theta                     in : FD-CNN parameters (layout above)
  *   y       [S][K][N_d]       out: equalised received symbols y_k / alpha_k (may be NULL)
  *   metrics double[5]         out: see above (may be NULL)                         */

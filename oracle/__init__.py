@@ -37,7 +37,7 @@ class Dims(C.Structure):
                 ("first_bin", C.c_int), ("S_per_real", C.c_int),
                 ("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int),
                 ("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int),
-                ("N_conv", C.c_int), ("residual", C.c_int), ("P_T", C.c_double)]
+                ("N_conv", C.c_int), ("residual", C.c_int), ("P_T", C.c_double), ("Gx", C.c_int)]
 
 
 def lib():
@@ -51,6 +51,7 @@ def lib():
         L.orc_zf.argtypes = [C.c_int, C.c_int, P, C.c_double, P, P]
         L.orc_precode_all.argtypes = [C.POINTER(Dims), C.c_int, P, P, P]
         L.orc_pa.argtypes = [C.c_int, P, C.c_int, P, C.c_int, P, P]
+        L.orc_pa_gmp.argtypes = [C.c_int, P, C.c_int, P, C.c_int, C.c_int, P, P]
         L.orc_fdcnn.argtypes = [C.POINTER(Dims), P, P, P, P, P]
         L.orc_distort.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, P, P, P, P, P]
         L.orc_backward.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, P, P, P, P, P]
@@ -81,7 +82,7 @@ def _p(a: Optional[np.ndarray]):
 
 
 def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, first_bin=None,
-              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1) -> Dims:
+              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, Gx=0) -> Dims:
     d = Dims()
     d.M, d.K, d.N, d.N_d = M, K, N, N_d
     d.first_bin = N - N_d // 2 if first_bin is None else first_bin
@@ -91,13 +92,14 @@ def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, firs
         d.orders[i] = p
     d.L, d.G, d.L_U, d.K_C, d.K_S, d.N_conv, d.residual = L, G, L_U, K_C, K_S, N_conv, residual
     d.P_T = P_T
+    d.Gx = Gx
     return d
 
 
 def dims_from_config(cfg, P_T: float, residual: int = 1) -> Dims:
     return make_dims(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.orders, cfg.L, cfg.grid, P_T,
                      S_per_real=cfg.S_per_real, first_bin=cfg.first_bin, L_U=cfg.L_U,
-                     K_C=cfg.K_C, K_S=cfg.K_S, N_conv=cfg.N_conv, residual=residual)
+                     K_C=cfg.K_C, K_S=cfg.K_S, N_conv=cfg.N_conv, residual=residual, Gx=cfg.pa_G)
 
 
 # -- single stages -----------------------------------------------------------
@@ -145,6 +147,18 @@ def pa(x, orders: Sequence[int], coef) -> np.ndarray:
     return y
 
 
+def pa_gmp(x, orders: Sequence[int], coef, Gx: int) -> np.ndarray:
+    """Eq. (9) with cross terms on one N-sample row; coef [P][(L+1)(1 + 2 Gx)] laid out as
+    a [P][L+1], then b [P][L+1][Gx], then c [P][L+1][Gx] (flattened per antenna)."""
+    x = _c128(x)
+    coef = _c128(coef).reshape(-1)
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    L1 = coef.size // (len(o) * (1 + 2 * Gx))
+    y = np.empty_like(x)
+    lib().orc_pa_gmp(x.shape[-1], _p(x), len(o), _p(o), L1 - 1, int(Gx), _p(coef), _p(y))
+    return y
+
+
 def theta_len(d: Dims) -> int:
     Go = -(-d.G // d.K_S)
     F = d.N_conv * Go * Go
@@ -171,7 +185,8 @@ def _check_chain(d: Dims, s, H, W, alpha, pa_coef, theta):
     coefficients [M][n_orders][L + 1] and theta."""
     S = s.shape[0]
     R = -(-S // d.S_per_real)
-    want = {"s": (s.shape, (S, d.K, d.N_d)), "pa": (pa_coef.shape, (d.M, d.n_orders, d.L + 1))}
+    pa_shape = (d.M, d.n_orders, d.L + 1) if d.Gx == 0 else (d.M, d.n_orders * (d.L + 1) * (1 + 2 * d.Gx))
+    want = {"s": (s.shape, (S, d.K, d.N_d)), "pa": (pa_coef.shape, pa_shape)}
     for name, (got, exp) in want.items():
         if tuple(got) != exp:
             raise ValueError(f"{name} has shape {tuple(got)}, expected {exp}")

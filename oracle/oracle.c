@@ -160,6 +160,30 @@ void orc_pa(int N, const cplx *x, int n_orders, const int *orders, int L, const 
     }
 }
 
+/* Eq. (9) with its cross terms (the GMP): the lagging and leading envelope    */
+/* |x_{n-l-+g}|^{p-1} multiplies x_{n-l}, for orders p >= 2 and g = 1..Gx.     */
+static int wrapi(int i, int N) { return ((i % N) + N) % N; }
+
+void orc_pa_gmp(int N, const cplx *x, int n_orders, const int *orders, int L, int Gx, const cplx *c, cplx *y)
+{
+    const int L1 = L + 1, PL = n_orders * L1;
+    orc_pa(N, x, n_orders, orders, L, c, y);
+    if (Gx <= 0) return;
+    const cplx *cb = c + PL, *cc = c + PL + (long)PL * Gx;    /* b [P][L1][Gx], c [P][L1][Gx] */
+    for (int n = 0; n < N; ++n)
+        for (int pi = 0; pi < n_orders; ++pi) {
+            const int e = orders[pi] - 1;
+            if (e < 1) continue;
+            for (int l = 0; l <= L; ++l)
+                for (int g = 1; g <= Gx; ++g) {
+                    const int k = (pi * L1 + l) * Gx + (g - 1);
+                    const cplx v = x[wrapi(n - l, N)];
+                    y[n] += cb[k] * v * pow(cabs(x[wrapi(n - l - g, N)]), e)
+                          + cc[k] * v * pow(cabs(x[wrapi(n - l + g, N)]), e);
+                }
+        }
+}
+
 /* Wirtinger derivatives of phi_p(x) = x |x|^{p-1}:                          */
 /* d phi / dx = (p+1)/2 |x|^{p-1},  d phi / dx* = (p-1)/2 x^2 |x|^{p-3}.      */
 static void phi_derivs(int p, cplx x, double *a, cplx *b)
@@ -276,7 +300,8 @@ static void forward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr,
             xh[bin_of(d, i)] = al[i] * acc;
         }
         orc_dft(N, xh, st->x + (long)m * N, 1);
-        orc_pa(N, st->x + (long)m * N, P, d->orders, d->L, pa + (long)m * P * L1, xpa);
+        orc_pa_gmp(N, st->x + (long)m * N, P, d->orders, d->L, d->Gx,
+                   pa + (long)m * P * L1 * (1 + 2 * (d->Gx > 0 ? d->Gx : 0)), xpa);
         orc_dft(N, xpa, X + (long)m * N, 0);
         double gsum = 0, dat = 0;
         for (int k = 0; k < N; ++k) {
@@ -376,7 +401,8 @@ static void backward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr
         }
         orc_dft(N, gX, gpa, 1);                 /* adjoint of the unitary DFT      */
         const cplx *x = st->x + (long)m * N;
-        const cplx *c = pa + (long)m * P * L1;
+        const int Gx = d->Gx > 0 ? d->Gx : 0;
+        const cplx *c = pa + (long)m * P * L1 * (1 + 2 * Gx);
         const int clip = P == 1 && d->orders[0] == 0;
         for (int n = 0; n < N && clip; ++n) {   /* adjoint of the clipping PA:      */
             const double A = creal(c[0]), r = cabs(x[n]);   /* above A, df/dx = A/(2r),  */
@@ -395,6 +421,26 @@ static void backward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr
             }
             gx[n] = acc;
         }
+        /* adjoint of the cross terms T = b x_j e(x_i), e = |x_i|^E, i = j -+ g, j = n - l:
+         * to x_j: conj(b e(x_i)) g_n; to x_i (de/dx = E/2 |x|^{E-2} x*, de/dx* = E/2 |x|^{E-2} x):
+         * E/2 |x_i|^{E-2} (conj(b x_j) x_i g_n + b x_j x_i conj(g_n))                       */
+        const cplx *cb = c + P * L1, *cc = c + P * L1 + (long)P * L1 * Gx;
+        for (int n = 0; n < N && Gx > 0; ++n)
+            for (int pi = 0; pi < P; ++pi) {
+                const int E = d->orders[pi] - 1;
+                if (E < 1) continue;
+                for (int l = 0; l <= d->L; ++l)
+                    for (int gg = 1; gg <= Gx; ++gg)
+                        for (int side = 0; side < 2; ++side) {
+                            const cplx b = side ? cc[(pi * L1 + l) * Gx + gg - 1] : cb[(pi * L1 + l) * Gx + gg - 1];
+                            const int j = wrapi(n - l, N), i = wrapi(side ? n - l + gg : n - l - gg, N);
+                            const double r = cabs(x[i]);
+                            gx[j] += conj(b * pow(r, E)) * gpa[n];
+                            if (r > 0.0)
+                                gx[i] += 0.5 * E * pow(r, E - 2) *
+                                         (conj(b * x[j]) * x[i] * gpa[n] + b * x[j] * x[i] * conj(gpa[n]));
+                        }
+            }
         orc_dft(N, gx, gxh + (long)m * N, 0);   /* adjoint of the unitary IDFT     */
         free(gX); free(gpa); free(gx);
     }

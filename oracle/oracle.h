@@ -11,7 +11,10 @@
  *   H      [R][N_d][K][M]       per-subcarrier channel, R = ceil(S / S_per_real)
  *   W      [R][N_d][M][K]       unnormalised ZF precoder H^H (H H^H)^{-1}
  *   alpha  [R][N_d]             per-subcarrier power normalisation
- *   pa     [M][P][L+1]          memory-polynomial coefficients c^b_{p,l}; orders = {0}
+ *   pa     [M][P][L+1]          memory-polynomial coefficients c^b_{p,l} when Gx = 0;
+ *                               with Gx > 0 each antenna holds a [P][L+1], then the lagging
+ *                               b [P][L+1][Gx] and the leading c [P][L+1][Gx] of Eq. (9)
+ *                               (order-1 cross slots unused); orders = {0}
  *                               with L = 0 is the ideal linear-clipping PA of clipping
  *                               amplitude A = Re c^b_{0,0}
  *   theta  flat: conv_w[N_conv][2L_U][K_C][K_C], conv_b[N_conv],
@@ -28,6 +31,7 @@ typedef struct {
     int n_orders, orders[8], L;
     int G, L_U, K_C, K_S, N_conv, residual;
     double P_T;
+    int Gx;   /* PA cross-term length (Eq. 9): 0 = memory polynomial */
 } orc_dims;
 
 int  orc_num_threads(void);
@@ -36,6 +40,11 @@ int  orc_zf(int K, int M, const double complex *Hk, double P_T, double complex *
 int  orc_precode_all(const orc_dims *d, int R, const double complex *H, double complex *W, double *alpha);
 void orc_pa(int N, const double complex *x, int n_orders, const int *orders, int L,
             const double complex *c, double complex *y);
+/* Eq. (9) with cross terms: y_n = sum_p sum_l a_{p,l} x_{n-l} |x_{n-l}|^{p-1}
+ *   + sum_{p>=2} sum_l sum_{g=1..Gx} (b_{p,l,g} x_{n-l} |x_{n-l-g}|^{p-1} + c_{p,l,g} x_{n-l} |x_{n-l+g}|^{p-1}),
+ * indices circular in n; coefficients as described for pa above.                 */
+void orc_pa_gmp(int N, const double complex *x, int n_orders, const int *orders, int L, int Gx,
+                const double complex *c, double complex *y);
 void orc_fdcnn(const orc_dims *d, const double complex *s_sym, const double *theta,
                double complex *s_tilde, double *pre, double *act);
 int  orc_distort(const orc_dims *d, int S, const double complex *s, const double complex *H,

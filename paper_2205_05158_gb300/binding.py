@@ -38,7 +38,7 @@ class Dims(C.Structure):
 
 
 class PaDesc(C.Structure):
-    _fields_ = [("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int)]
+    _fields_ = [("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int), ("G", C.c_int)]
 
 
 class DpdDesc(C.Structure):
@@ -133,7 +133,8 @@ class Plan:
 
     def __init__(self, M: int, K: int, N: int, N_d: int, S_per_real: int, max_symbols: int, P_T: float,
                  orders: Sequence[int], L: int, G: int, L_U: int = 1, K_C: int = 3, K_S: int = 1, N_conv: int = 2,
-                 residual: int = 1, precision: int = FDDPD_FP32, first_bin: int = -1, stream=None):
+                 residual: int = 1, precision: int = FDDPD_FP32, first_bin: int = -1, stream=None,
+                 pa_G: int = 0):
         self._lib = load()
         d = Dims(M, K, N, N_d, first_bin, S_per_real, max_symbols, precision, float(P_T))
         pa = PaDesc()
@@ -141,6 +142,7 @@ class Plan:
         for i, p in enumerate(orders):
             pa.orders[i] = int(p)
         pa.L = L
+        pa.G = pa_G
         dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual)
         h = C.c_void_p()
         rc = self._lib.fddpd_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(dpd), _stream_ptr(stream))
@@ -154,7 +156,8 @@ class Plan:
     def from_config(cls, cfg, P_T: float, max_symbols: Optional[int] = None, precision: int = FDDPD_FP32,
                     residual: int = 1, stream=None) -> "Plan":
         return cls(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.S_per_real, max_symbols or cfg.S, P_T, cfg.orders, cfg.L,
-                   cfg.grid, cfg.L_U, cfg.K_C, cfg.K_S, cfg.N_conv, residual, precision, cfg.first_bin, stream)
+                   cfg.grid, cfg.L_U, cfg.K_C, cfg.K_S, cfg.N_conv, residual, precision, cfg.first_bin, stream,
+                   getattr(cfg, "pa_G", 0))
 
     def _check(self, rc: int):
         if rc:

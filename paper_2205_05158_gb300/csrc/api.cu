@@ -115,7 +115,9 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (d->precision != FDDPD_FP32 && d->precision != FDDPD_BF16 && d->precision != FDDPD_FP16)
         return set_err(nullptr, FDDPD_ERR_ARG, "precision=%d", d->precision);
     if (!(d->P_T > 0)) return set_err(nullptr, FDDPD_ERR_ARG, "P_T must be positive");
-    if (pa->n_orders < 1 || pa->n_orders > 8 || pa->L < 0 || pa->L > 7) return set_err(nullptr, FDDPD_ERR_ARG, "PA orders / memory out of range");
+    if (pa->n_orders < 1 || pa->n_orders > 8 || pa->L < 0 || pa->L > 7 || pa->G < 0 || pa->G > 2)
+        return set_err(nullptr, FDDPD_ERR_ARG, "PA orders / memory / cross-term length out of range");
+    if (pa->G > 0 && pa->orders[0] == 0) return set_err(nullptr, FDDPD_ERR_ARG, "the clipping PA has no cross terms");
     for (int i = 0; i < pa->n_orders; ++i)
         if (pa->orders[i] < 0 || pa->orders[i] > 15 || (pa->orders[i] == 0 && (pa->n_orders != 1 || pa->L != 0)))
             return set_err(nullptr, FDDPD_ERR_ARG, "PA order %d: 1..15, or 0 (linear clipping) alone with L = 0",
@@ -140,6 +142,7 @@ static Geo make_geo(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     g.n_orders = pa->n_orders;
     for (int i = 0; i < 8; ++i) g.orders[i] = i < pa->n_orders ? pa->orders[i] : 0;
     g.L = pa->L;
+    g.pa_G = pa->G;
     g.G = dpd->G; g.K_S = dpd->K_S; g.Go = (dpd->G + dpd->K_S - 1) / dpd->K_S;
     g.L_U = dpd->L_U; g.Cin = 2 * dpd->L_U; g.K_C = dpd->K_C; g.pad = dpd->K_C / 2;
     g.N_conv = dpd->N_conv; g.F = dpd->N_conv * g.Go * g.Go; g.residual = dpd->residual;
@@ -594,7 +597,7 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     const size_t n_s = sizeof(c32) * (size_t)p->d.max_symbols * g.K * g.N_d,
                  n_H = sizeof(c32) * (size_t)p->R_max * g.N_d * g.K * g.M,
                  n_al = sizeof(float) * (size_t)p->R_max * g.N_d,
-                 n_pa = sizeof(c32) * (size_t)g.M * g.n_orders * (g.L + 1),
+                 n_pa = sizeof(c32) * (size_t)g.M * g.n_orders * (g.L + 1) * (1 + 2 * g.pa_G),
                  n_th = sizeof(float) * (size_t)g.theta_len;
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     if (!p->stage_base) {

@@ -262,13 +262,31 @@ struct RowPa {
                     const float mg = any_even ? sqrtf(r2) : 0.f;
                     for (int p = 0; p < P; ++p)
                         y[q] = cfma(cp[p * L1 + l], cscale(xl, powabs(r2, mg, g.orders[p] - 1)), y[q]);
+                    // cross terms of Eq. 9 (P_ < 0 only): x_{n-l} times the envelope of
+                    // x_{n-l-g} (lagging, b) and of x_{n-l+g} (leading, c), orders p >= 2
+                    const int Gx = P_ < 0 ? g.pa_G : 0, PL1 = P * L1;
+                    for (int gg = 1; gg <= Gx; ++gg) {
+                        const int n = t + q * T;
+                        const c32 xa = xs[pidx((n - l - gg) & (N - 1))], xb = xs[pidx((n - l + gg) & (N - 1))];
+                        const float ra = cabs2(xa), rb = cabs2(xb), ma = sqrtf(ra), mb = sqrtf(rb);
+                        c32 env = make_float2(0.f, 0.f);
+                        for (int p = 0; p < P; ++p) {
+                            const int e = g.orders[p] - 1;
+                            if (e < 1) continue;
+                            const int k = (p * L1 + l) * Gx + gg - 1;
+                            env = cfma(cp[PL1 + k], make_float2(powabs(ra, ma, e), 0.f), env);
+                            env = cfma(cp[PL1 + PL1 * Gx + k], make_float2(powabs(rb, mb, e), 0.f), env);
+                        }
+                        y[q] = cfma(xl, env, y[q]);
+                    }
                 }
             }
         }
     }
     // gx_n = sum_l A_l(x_n) g_{n+l} + B_l(x_n) conj(g_{n+l}); gs holds g in natural order
+    // xs: x in natural order (read by the cross terms of the general path only)
     static FD_D void adjoint(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *gs, const c32 *cp,
-                             c32 (&gx)[16]) {
+                             c32 (&gx)[16], const c32 *xs) {
         if constexpr (P_ > 0) {
             // odd orders 2k+1, k < P_, r = |x_n|^2:
             //   sum_l A_l g_{n+l} = sum_k (k+1) r^k G_k(n),  G_k(n) = sum_l conj(c_{k,l}) g_{n+l}
@@ -343,6 +361,44 @@ struct RowPa {
                     gx[q] = cfma(B, cconj(gl), gx[q]);
                 }
             }
+            // cross terms T = b x_j e(x_i), e = |x_i|^E, i = j -+ g (lagging b, leading c):
+            // as the signal x_j (output j + l): conj(b e(x_i)) g; as the envelope sample x_i
+            // (de/dx = E/2 |x|^{E-2} x*): E/2 |x_i|^{E-2} (conj(b x_j) x_i g + b x_j x_i conj(g))
+            if constexpr (P_ < 0) {
+            const int Gx = g.pa_G, PL1 = P * L1;
+            for (int gg = 1; gg <= Gx; ++gg)
+                for (int l = 0; l <= L; ++l)
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int n = t + q * T;
+                        const c32 xn = x[q];
+                        const float rn = cabs2(xn), mn = sqrtf(rn);
+                        const c32 g0 = gs[pidx((n + l) & (N - 1))];               // n as the signal sample
+                        const c32 xa = xs[pidx((n - gg) & (N - 1))], xb = xs[pidx((n + gg) & (N - 1))];
+                        const float ra = cabs2(xa), rb = cabs2(xb), ma = sqrtf(ra), mb = sqrtf(rb);
+                        const c32 xj1 = xs[pidx((n + gg) & (N - 1))], g1 = gs[pidx((n + gg + l) & (N - 1))];
+                        const c32 xj2 = xs[pidx((n - gg) & (N - 1))], g2 = gs[pidx((n - gg + l) & (N - 1))];
+                        for (int p = 0; p < P; ++p) {
+                            const int e = g.orders[p] - 1;
+                            if (e < 1) continue;
+                            const int k = (p * L1 + l) * Gx + gg - 1;
+                            const c32 b = cp[PL1 + k], c = cp[PL1 + PL1 * Gx + k];
+                            // signal: envelopes at n - g (b) and n + g (c)
+                            gx[q] = cfma(cconj(cadd(cscale(b, powabs(ra, ma, e)), cscale(c, powabs(rb, mb, e)))), g0,
+                                         gx[q]);
+                            if (mn > 0.f) {
+                                const float h = 0.5f * (float)e * powabs(rn, mn, e) / rn;   // E/2 |x_n|^{E-2}
+                                // envelope of the lagging term of signal j = n + g (output n + g + l)
+                                const c32 bx1 = cmul(b, xj1), cx2 = cmul(c, xj2);
+                                gx[q] = cfma(cscale(cmul(cconj(bx1), xn), h), g1, gx[q]);
+                                gx[q] = cfma(cscale(cmul(bx1, xn), h), cconj(g1), gx[q]);
+                                // envelope of the leading term of signal j = n - g (output n - g + l)
+                                gx[q] = cfma(cscale(cmul(cconj(cx2), xn), h), g2, gx[q]);
+                                gx[q] = cfma(cscale(cmul(cx2, xn), h), cconj(g2), gx[q]);
+                            }
+                        }
+                    }
+            }
         }
     }
 };
@@ -352,12 +408,15 @@ FD_HD constexpr int rows_per_cta_t() { return LOG2N >= 12 ? 1 : (1 << (12 - LOG2
 
 FD_HD int rows_per_cta(int N) { return N >= 4096 ? 1 : 4096 / N; }
 
-// smem: per-pass twiddles, 2 buffers per row, coefficients per row
+// PA coefficients of one antenna: the memory polynomial [P][L+1], then with cross terms
+// (Eq. 9) the lagging [P][L+1][G] and the leading [P][L+1][G]
+FD_HD int pa_coef_count(const Geo &g) { return g.n_orders * (g.L + 1) * (1 + 2 * g.pa_G); }
+
 // smem: per-pass twiddles, 2 buffers per row, coefficients per row, then the staging of
 // the next row group's inputs (stage_bytes per row)
 FD_HD size_t fftpa_smem_base_(const Geo &g) {
     const int N = g.N, padN = N + (N >> 4), r = rows_per_cta(N);
-    const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * g.n_orders * (g.L + 1));
+    const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * pa_coef_count(g));
     return (b + 15) & ~size_t(15);
 }
 inline size_t fwd_stage_bytes(const Geo &g) { return sizeof(c32) * (size_t)((g.N_d + 1) & ~1); }   // x_hat row
@@ -392,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1);
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1) * (1 + 2 * g.pa_G);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
@@ -491,7 +550,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1);
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1) * (1 + 2 * g.pa_G);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
@@ -562,8 +621,12 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < 16; ++q) bufB[pidx(t + q * F::T)] = gv[q];
+        if (P_ < 0) {   // the cross terms read x's neighbours
+#pragma unroll
+            for (int q = 0; q < 16; ++q) bufA[pidx(t + q * F::T)] = x[q];
+        }
         __syncthreads();
-        RowPa<P_, L_>::adjoint(g, F::N, F::T, t, x, bufB, cp, gv);
+        RowPa<P_, L_>::adjoint(g, F::N, F::T, t, x, bufB, cp, gv, bufA);
         __syncthreads();
         transform<LOG2N, false>(gv, bufA, bufB, twp, t, rs);
         constexpr bool BLK = std::is_same<TOut, cbf16>::value;   // BF16: the blocked plane (never gX's rows)
@@ -638,6 +701,7 @@ inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
 // PA shapes with a compiled fast path: orders 1,3,5 with taps 0..3, orders 1,3 with
 // taps 0..3, and the memoryless 1,3.  Anything else takes the general path.
 inline int pa_shape(const Geo &g) {
+    if (g.pa_G > 0) return 4;   // cross terms: the general path with the GMP terms compiled in
     for (int p = 0; p < g.n_orders; ++p)
         if (g.orders[p] != 2 * p + 1) return 0;
     if (g.n_orders == 3 && g.L == 3) return 1;
@@ -653,6 +717,7 @@ inline cudaError_t fwd_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
         case 1: return fwd_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, X, metrics, xt, st);
         case 2: return fwd_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, X, metrics, xt, st);
         case 3: return fwd_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, X, metrics, xt, st);
+        case 4: return fwd_t<LOG2N, -1, 0>(g, rows, xh, pa, twp, X, metrics, xt, st);
         default: return fwd_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, X, metrics, xt, st);
     }
 }
@@ -664,6 +729,7 @@ inline cudaError_t adj_n(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
         case 1: return adj_t<LOG2N, 3, 3>(g, rows, xh, pa, twp, gX, gxh, xt, st);
         case 2: return adj_t<LOG2N, 2, 3>(g, rows, xh, pa, twp, gX, gxh, xt, st);
         case 3: return adj_t<LOG2N, 2, 0>(g, rows, xh, pa, twp, gX, gxh, xt, st);
+        case 4: return adj_t<LOG2N, -1, 0>(g, rows, xh, pa, twp, gX, gxh, xt, st);
         default: return adj_t<LOG2N, 0, 0>(g, rows, xh, pa, twp, gX, gxh, xt, st);
     }
 }

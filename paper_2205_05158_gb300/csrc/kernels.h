@@ -14,6 +14,7 @@ enum OutKind { OUT_F32 = 0, OUT_BF16 = 1, OUT_F16 = 2 };
 struct Geo {
     int M, K, N, N_d, first_bin, S_per_real, log2N;
     int n_orders, orders[8], L;
+    int pa_G;                // PA cross-term length of Eq. 9 (0: memory polynomial)
     int G, Go, L_U, Cin, K_C, K_S, pad, N_conv, F, residual;
     int n_convw;             // N_conv * Cin * K_C * K_C
     long off_cb, off_fw, off_fb, theta_len;

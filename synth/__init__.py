@@ -47,6 +47,7 @@ class Config:
     pa_nominal: Dict[int, List[complex]]
     pa_spread: float = 0.10     # real multiplicative spread, uniform in [-spread, spread]
     pa_spread_orders: Optional[Sequence[int]] = None   # None: every coefficient
+    pa_G: int = 0               # PA cross-term length of Eq. 9 (0: memory polynomial)
     ibo_db: float = 6.0
     T: int = 10                 # channel taps
     rho: float = 0.0            # exponential antenna correlation

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def _create(lib, **over):
     d = dict(M=16, K=2, N=64, N_d=48, first_bin=-1, S_per_real=10, max_symbols=10, precision=0, P_T=10.0)
-    pa = dict(orders=[1, 3], L=0)
+    pa = dict(orders=[1, 3], L=0, G_pa=0)
     dpd = dict(G=7, L_U=1, K_C=3, K_S=1, N_conv=2, residual=1)
     for k, v in over.items():
         (d if k in d else pa if k in pa else dpd)[k] = v
@@ -53,6 +53,7 @@ def _create(lib, **over):
     for i, p in enumerate(pa["orders"]):
         pad.orders[i] = p
     pad.L = pa["L"]
+    pad.G = pa["G_pa"]
     dd = binding.DpdDesc(dpd["G"], dpd["L_U"], dpd["K_C"], dpd["K_S"], dpd["N_conv"], dpd["residual"])
     h = C.c_void_p()
     rc = lib.fddpd_plan_create(C.byref(h), C.byref(dims), C.byref(pad), C.byref(dd), None)
@@ -71,6 +72,9 @@ def _create(lib, **over):
     (dict(orders=[-1]), binding.FDDPD_ERR_ARG), (dict(L=9), binding.FDDPD_ERR_ARG),
     # order 0 is the linear-clipping PA: alone and memoryless only
     (dict(orders=[0, 3]), binding.FDDPD_ERR_ARG), (dict(orders=[0], L=1), binding.FDDPD_ERR_ARG),
+    # cross terms of Eq. 9: G in 0..2, none for the clipping PA
+    (dict(G_pa=3), binding.FDDPD_ERR_ARG), (dict(G_pa=-1), binding.FDDPD_ERR_ARG),
+    (dict(orders=[0], G_pa=1), binding.FDDPD_ERR_ARG),
 ])
 def test_plan_rejects_bad_descriptors(lib, over, code):
     rc, h = _create(lib, **over)

@@ -57,6 +57,23 @@ def test_zf_singular_flagged():
 
 
 # --- forward chain ----------------------------------------------------------------
+# the paper's PA model (Sec. V-A): the GMP of Eq. 9 with orders 1..7, memory 3, G = 1
+PA_GMP_1TO7 = {1: [1.0, 0.05 - 0.02j, 0.01, 0.002], 2: [0.02j, 0.004, 0.0, 0.0],
+               3: [-0.08 + 0.02j, 0.01j, -0.003, 0.001], 4: [0.005, 0.0, 0.0, 0.0],
+               5: [-0.002 + 0.0005j, 3e-4, -1e-4, 0.0], 6: [1e-4, 0.0, 0.0, 0.0], 7: [1e-5j, 0.0, 0.0, 0.0]}
+
+
+def _gmp_case(**kw):
+    """A ragged system with the GMP PA: the memory polynomial of PA_GMP_1TO7 per antenna
+    plus seeded lagging / leading cross terms, flattened per antenna."""
+    cfg = small_cfg(N=256, pa_nominal=PA_GMP_1TO7, pa_G=1, ibo_db=10.0)
+    a = synth.pa_coefficients(cfg.seed, cfg.M, cfg.pa_nominal, cfg.pa_spread)
+    rng = np.random.default_rng(11)
+    bc = 0.01 * (rng.standard_normal((2,) + a.shape + (1,)) + 1j * rng.standard_normal((2,) + a.shape + (1,)))
+    pa = np.concatenate([a.reshape(cfg.M, -1), bc[0].reshape(cfg.M, -1), bc[1].reshape(cfg.M, -1)], axis=1)
+    return Case(cfg, pa=pa, **kw)
+
+
 FWD_CASES = [
     ("cfg1", lambda: Case(synth.CONFIGS["cfg1"], fc_scale=0.3)),
     ("ragged", lambda: Case(small_cfg(), fc_scale=0.3)),
@@ -71,6 +88,7 @@ FWD_CASES = [
     # the ideal linear-clipping PA of Sec. V-B driven into clipping (IBO 0 dB)
     ("pa_clip", lambda: Case(small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0),
                              fc_scale=0.3)),
+    ("pa_gmp_G1", lambda: _gmp_case(fc_scale=0.3)),
 ]
 
 
@@ -123,6 +141,7 @@ BWD_CASES = [
     ("cfg2_14", lambda: Case(synth.CONFIGS["cfg2"], S=14, fc_scale=0.2)),
     ("pa_clip", lambda: Case(small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0),
                              fc_scale=0.3)),
+    ("pa_gmp_G1", lambda: _gmp_case(fc_scale=0.3)),
 ]
 
 

@@ -426,3 +426,71 @@ def test_clip_pa_adjoint_central_differences():
     # the PA clips a good share of the time-domain samples at this drive level
     y, met = oracle.distort(d, w.s, w.H, W, al, w.pa, th)
     assert met[3] > 1e-4 * met[4]
+
+
+# --- the GMP of Eq. (9) with cross terms (the paper's PA model, Sec. V-A: K = 7, L = 3, G = 1)
+def _gmp_coef(a, G, scale, seed):
+    """[M][P][L+1] memory-polynomial part a plus random lagging / leading cross terms,
+    flattened per antenna as a [P][L+1], b [P][L+1][G], c [P][L+1][G]."""
+    M, P, L1 = a.shape
+    rng = np.random.default_rng(seed)
+    bc = scale * (rng.standard_normal((2, M, P, L1, G)) + 1j * rng.standard_normal((2, M, P, L1, G)))
+    return np.concatenate([a.reshape(M, -1), bc[0].reshape(M, -1), bc[1].reshape(M, -1)], axis=1)
+
+
+def test_gmp_single_cross_terms_by_hand():
+    """One lagging term b x_{n-1} |x_{n-2}|^2 and one leading term c x_{n-1} |x_n|^2
+    (order 3, l = 1, g = 1), circular in n."""
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(16) + 1j * rng.standard_normal(16)
+    orders, L, G = [1, 3], 1, 1
+    a = np.zeros((1, 2, 2), complex)
+    for side, ref in ((0, np.roll(x, 1) * np.abs(np.roll(x, 2)) ** 2), (1, np.roll(x, 1) * np.abs(x) ** 2)):
+        coef = _gmp_coef(a, G, 0.0, 0)
+        # a [2][2] at 0..3, b [2][2][1] at 4..7, c at 8..11: order index 1 (p = 3), l = 1, g = 1
+        coef[0, 4 + 4 * side + (1 * 2 + 1) * G + 0] = 0.3 - 0.2j
+        y = oracle.pa_gmp(x, orders, coef[0], G)
+        assert np.allclose(y, (0.3 - 0.2j) * ref, atol=1e-13), side
+
+
+def test_gmp_constant_envelope_reduces_to_memory_polynomial():
+    """With |x_n| = r for every n the envelope of every cross term is r^{p-1}: the GMP
+    equals the memory polynomial with a'_{p,l} = a_{p,l} + sum_g (b_{p,l,g} + c_{p,l,g})."""
+    rng = np.random.default_rng(7)
+    x = 0.7 * np.exp(2j * np.pi * rng.random(32))
+    orders, L, G = [1, 2, 3, 5], 3, 2
+    a = rng.standard_normal((1, 4, 4)) + 1j * rng.standard_normal((1, 4, 4))
+    coef = _gmp_coef(a, G, 0.2, 8)[0]
+    b = coef[16:16 + 32].reshape(4, 4, G)
+    c = coef[48:].reshape(4, 4, G)
+    a2 = a[0] + np.where(np.array(orders)[:, None] >= 2, (b + c).sum(axis=2), 0)
+    assert np.allclose(oracle.pa_gmp(x, orders, coef, G), oracle.pa(x, orders, a2), atol=1e-12)
+
+
+def test_gmp_adjoint_central_differences():
+    """The whole chain with a GMP PA (orders 1..7, L = 3, G = 1): the hand-derived adjoint
+    of the cross terms against central differences."""
+    cfg = _small_cfg(pa_nominal={1: [1.0, 0.05 - 0.02j, 0.01, 0.002], 2: [0.02j, 0.004, 0.0, 0.0],
+                                 3: [-0.08 + 0.02j, 0.01j, -0.003, 0.001], 4: [0.005, 0.0, 0.0, 0.0],
+                                 5: [-0.002 + 0.0005j, 3e-4, -1e-4, 0.0], 6: [1e-4, 0.0, 0.0, 0.0],
+                                 7: [1e-5j, 0.0, 0.0, 0.0]}, pa_G=1)
+    w = synth.make_workload(cfg, fc_scale=0.5)
+    pa = _gmp_coef(w.pa.astype(complex), 1, 0.01, 9)
+    d = oracle.dims_from_config(cfg, w.P_T)
+    W, al = oracle.precode(d, w.H)
+    th = w.theta.astype(np.float64)
+    loss = lambda t: oracle.distort(d, w.s, w.H, W, al, pa, t)[1][0]
+    g, met = oracle.backward(d, w.s, w.H, W, al, pa, th)
+    assert abs(met[0] - loss(th)) < 1e-15
+    rng = np.random.default_rng(10)
+    gmax = np.abs(g).max()
+    for j in rng.choice(len(th), 60, replace=False):
+        tp, tm = th.copy(), th.copy()
+        tp[j] += 1e-5
+        tm[j] -= 1e-5
+        assert abs((loss(tp) - loss(tm)) / 2e-5 - g[j]) <= 1e-6 * gmax, j
+    # the cross terms matter: without them the output differs
+    y1, _ = oracle.distort(d, w.s, w.H, W, al, pa, th)
+    d0 = oracle.dims_from_config(cfg.with_(pa_G=0), w.P_T)
+    y0, _ = oracle.distort(d0, w.s, w.H, W, al, w.pa, th)
+    assert np.abs(y1 - y0).max() > 1e-4
