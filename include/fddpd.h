@@ -212,6 +212,20 @@ int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c
 int fddpd_ser(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
               float N0, unsigned long long seed, unsigned long long *counts);
 
+/* Batched launch of many plans (uneven M, K, N) as one CUDA graph.  Between
+ * fddpd_graph_begin and fddpd_graph_end every fddpd_distort / fddpd_backward /
+ * fddpd_update / fddpd_ser call of plans whose stream is `stream` (fddpd_set_stream) is
+ * recorded instead of run; fddpd_graph_launch then runs the whole recorded sequence as
+ * one graph launch on `stream`, as often as wanted, with the pointers and sizes given at
+ * recording time (the data behind them may change between launches).  fddpd_precode and
+ * fddpd_update_host synchronise and cannot be recorded (they fail with FDDPD_ERR_CUDA).
+ * Errors: ARG, CUDA (a call that cannot be recorded ends the recording).            */
+typedef struct fddpd_graph fddpd_graph;
+int fddpd_graph_begin(void *stream);
+int fddpd_graph_end(void *stream, fddpd_graph **out);
+int fddpd_graph_launch(fddpd_graph *graph, void *stream);
+int fddpd_graph_destroy(fddpd_graph *graph);
+
 /* Stage tracing.  Stages of the chain, in execution order. */
 enum fddpd_stage {
     FDDPD_STAGE_ZF_GRAM = 0, FDDPD_STAGE_ZF_FACTOR, FDDPD_STAGE_ZF_APPLY, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,

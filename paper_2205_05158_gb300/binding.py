@@ -26,7 +26,8 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
-            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser"]
+            "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
+            "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -97,6 +98,10 @@ def load(build_if_missing: bool = True):
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     L.fddpd_set_option.argtypes = [P, I, I]
     L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
+    L.fddpd_graph_begin.argtypes = [P]
+    L.fddpd_graph_end.argtypes = [P, C.POINTER(C.c_void_p)]
+    L.fddpd_graph_launch.argtypes = [P, P]
+    L.fddpd_graph_destroy.argtypes = [P]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
@@ -302,3 +307,45 @@ def precode_noalloc(H, W, alpha, P_T: float, stream=None):
                                  _ptr(alpha, torch.float32), _stream_ptr(stream))
     if rc:
         raise FddpdError(rc, L.fddpd_last_error(None).decode())
+
+
+class Graph:
+    """A CUDA graph of recorded library calls (fddpd_graph_*): calls of plans on `stream`
+    made inside ``with Graph.record(stream) as g:`` are recorded, then ``g.launch()``
+    replays them as one launch."""
+
+    def __init__(self, stream):
+        self._lib = load()
+        self._stream = _stream_ptr(stream)
+        self._h = C.c_void_p()
+
+    @classmethod
+    def record(cls, stream):
+        return _Recording(cls(stream))
+
+    def launch(self):
+        rc = self._lib.fddpd_graph_launch(self._h, self._stream)
+        if rc:
+            raise FddpdError(rc, self._lib.fddpd_last_error(None).decode())
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fddpd_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+
+class _Recording:
+    def __init__(self, g: Graph):
+        self.g = g
+
+    def __enter__(self) -> Graph:
+        rc = self.g._lib.fddpd_graph_begin(self.g._stream)
+        if rc:
+            raise FddpdError(rc, self.g._lib.fddpd_last_error(None).decode())
+        return self.g
+
+    def __exit__(self, exc_type, exc, tb):
+        rc = self.g._lib.fddpd_graph_end(self.g._stream, C.byref(self.g._h))
+        if rc and exc_type is None:
+            raise FddpdError(rc, self.g._lib.fddpd_last_error(None).decode())
+        return False

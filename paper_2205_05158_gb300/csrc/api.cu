@@ -715,6 +715,60 @@ extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c
     return FDDPD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CUDA graphs over recorded calls of many plans (batched uneven workloads)
+struct fddpd_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" int fddpd_graph_begin(void *stream) {
+    if (!stream) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_begin: the default stream cannot record");
+    const cudaError_t e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_begin: %s", cudaGetErrorString(e));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_graph_end(void *stream, fddpd_graph **out) {
+    if (!stream || !out) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_end: null argument");
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_end: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_end: instantiate: %s", cudaGetErrorString(e));
+    }
+    fddpd_graph *r = new (std::nothrow) fddpd_graph{g, x};
+    if (!r) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return set_err(nullptr, FDDPD_ERR_NOMEM, "fddpd_graph_end: host allocation failed");
+    }
+    *out = r;
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_graph_launch(fddpd_graph *graph, void *stream) {
+    if (!graph) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_launch: null graph");
+    const cudaError_t e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_launch: %s", cudaGetErrorString(e));
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_graph_destroy(fddpd_graph *graph) {
+    if (!graph) return FDDPD_OK;
+    cudaGraphExecDestroy(graph->exec);
+    cudaGraphDestroy(graph->graph);
+    delete graph;
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_sync(fddpd_plan *p) {
     if (!p) return FDDPD_ERR_ARG;
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));

@@ -1,0 +1,89 @@
+"""Batched uneven workload: independent downlink instances of different (M, K, N) recorded
+into one CUDA graph (fddpd_graph_*) and replayed as one launch.  The replay must give what
+the same calls give one by one (the same kernels on the same inputs), and each instance
+stays within the 16-bit tolerances of the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import Case, nmse, rel_l2, small_cfg, torch
+
+pytestmark = pytest.mark.gpu
+
+# (M, K, N, orders): K <= M / 4, about 58 % of the bins occupied, odd-order PAs with memory
+SHAPES = [(32, 4, 512, {1: [1.0, 0.05 - 0.02j, 0.01, 0.002], 3: [-0.08 + 0.02j, 0.01j, -0.003, 0.001]}),
+          (64, 8, 1024, synth.PA_NOMINAL_MP135),
+          (32, 8, 512, synth.PA_NOMINAL_MP135),
+          (128, 16, 512, {1: [1.0, 0.05 - 0.02j, 0.01, 0.002], 3: [-0.08 + 0.02j, 0.01j, -0.003, 0.001]}),
+          (64, 16, 2048, synth.PA_NOMINAL_MP135),
+          (128, 32, 1024, synth.PA_NOMINAL_MP135)]
+
+
+def _instance(i, shape, S=10):
+    M, K, N, pa = shape
+    N_d = int(round(N * 600 / 1024))
+    cfg = small_cfg(name=f"inst{i}", M=M, K=K, N=N, N_d=N_d, Q=64, S=S, S_per_real=5, pa_nominal=pa,
+                    G=math.ceil(math.sqrt(N_d)), L_U=1, K_S=1, seed=100 + i)
+    c = Case(cfg, S=S, fc_scale=0.2, precision=1)
+    c.gpu_zf()
+    return c
+
+
+def test_graph_replays_uneven_instances():
+    T = torch()
+    cases = [_instance(i, sh) for i, sh in enumerate(SHAPES)]
+    # one by one on the default stream
+    ref = []
+    for c in cases:
+        ref.append(c.gpu_distort())
+    # recorded on a side stream, replayed as one graph launch (twice)
+    stream = T.cuda.Stream()
+    ys = [T.empty_like(c.s) for c in cases]
+    mets = [T.zeros(5, dtype=T.float64, device="cuda") for c in cases]
+    for c in cases:
+        c.plan.set_stream(stream)
+    import paper_2205_05158_gb300 as fd
+    T.cuda.synchronize()
+    with fd.Graph.record(stream) as g:
+        for c, y, m in zip(cases, ys, mets):
+            c.plan.distort(c.s, c.H, c.W, c.alpha, c.pa, c.theta, y, m)
+    for _ in range(2):
+        g.launch()
+    T.cuda.synchronize()
+    for c, y, m, (y0, m0) in zip(cases, ys, mets, ref):
+        assert np.array_equal(y.cpu().numpy(), y0)
+        assert np.allclose(m.cpu().numpy(), m0, rtol=1e-12, atol=0)
+    # two instances against the oracle (16-bit tolerances)
+    for c, (y0, m0) in list(zip(cases, ref))[:2]:
+        Wo, alo = c.oracle_zf()
+        yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+        assert nmse(y0, yo) <= 1e-4
+        assert abs(oracle.evm_db(m0) - oracle.evm_db(meto)) <= 0.1
+
+
+def test_graph_replays_training_steps():
+    """One GD step of three uneven instances recorded and replayed from the same theta:
+    the same step as one by one (up to the order of the split-K sums)."""
+    T = torch()
+    import paper_2205_05158_gb300 as fd
+    cases = [_instance(i, sh) for i, sh in enumerate(SHAPES[:3])]
+    th0 = [c.theta.clone() for c in cases]
+    for c in cases:
+        c.plan.update(c.s, c.H, c.W, c.alpha, c.pa, c.theta, 1e-3, 1, fd.FDDPD_GD)
+    T.cuda.synchronize()
+    step_ref = [(c.theta - t).cpu().numpy() for c, t in zip(cases, th0)]
+    stream = T.cuda.Stream()
+    for c, t in zip(cases, th0):
+        c.theta.copy_(t)
+        c.plan.set_stream(stream)
+    T.cuda.synchronize()
+    with fd.Graph.record(stream) as g:
+        for c in cases:
+            c.plan.update(c.s, c.H, c.W, c.alpha, c.pa, c.theta, 1e-3, 1, fd.FDDPD_GD)
+    g.launch()
+    T.cuda.synchronize()
+    for c, t, sr in zip(cases, th0, step_ref):
+        assert rel_l2((c.theta - t).cpu().numpy(), sr) <= 1e-5
