@@ -451,7 +451,9 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1) * (1 + 2 * g.pa_G);
+    // coefficients per antenna: compile-time for the fixed shapes (which have no cross terms)
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L;
+    const int PL = P_ > 0 ? P_ * (L_ + 1) : pa_coef_count(g);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
@@ -550,7 +552,9 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     constexpr int RPC = rows_per_cta_t<LOG2N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
-    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L, PL = P * (L + 1) * (1 + 2 * g.pa_G);
+    // coefficients per antenna: compile-time for the fixed shapes (which have no cross terms)
+    const int P = P_ > 0 ? P_ : g.n_orders, L = P_ > 0 ? L_ : g.L;
+    const int PL = P_ > 0 ? P_ * (L_ + 1) : pa_coef_count(g);
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
