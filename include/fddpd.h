@@ -212,6 +212,17 @@ int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c
 int fddpd_ser(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
               float N0, unsigned long long seed, unsigned long long *counts);
 
+/* Per-shape implementation choice (for batches of uneven plans): times `reps` forward
+ * passes (fddpd_distort) of each implementation of the per-subcarrier contractions the
+ * plan's shape admits -- tcgen05 (16-bit plans with M <= 128, K <= 16) and CUDA cores --
+ * with CUDA events on the plan's stream, and keeps the faster set
+ * (FDDPD_OPT_TENSOR_CONTRACTIONS).  Arguments as fddpd_distort; ms[2] (host, may be NULL)
+ * receives the mean times (tensor-core first; -1 where not admitted).  Synchronises,
+ * so it cannot be recorded into a graph (call it before fddpd_graph_begin).  On an error
+ * the previous choice is kept.  Errors as fddpd_distort, ARG for reps < 1.          */
+int fddpd_autotune(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
+                   const float *alpha, const fddpd_c32 *pa_coef, const float *theta, int reps, float *ms);
+
 /* Batched launch of many plans (uneven M, K, N) as one CUDA graph.  Between
  * fddpd_graph_begin and fddpd_graph_end every fddpd_distort / fddpd_backward /
  * fddpd_update / fddpd_ser call of plans whose stream is `stream` (fddpd_set_stream) is

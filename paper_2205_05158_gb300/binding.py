@@ -27,7 +27,7 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
-            "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy"]
+            "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     L.fddpd_set_option.argtypes = [P, I, I]
     L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
+    L.fddpd_autotune.argtypes = [P, I, P, P, P, P, P, P, I, P]
     L.fddpd_graph_begin.argtypes = [P]
     L.fddpd_graph_end.argtypes = [P, C.POINTER(C.c_void_p)]
     L.fddpd_graph_launch.argtypes = [P, P]
@@ -221,6 +222,17 @@ class Plan:
         """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
         self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
+
+    def autotune(self, s, H, W, alpha, pa, theta, reps: int = 3, S: Optional[int] = None):
+        """fddpd_autotune: keeps the faster contraction implementation for this shape;
+        returns the mean forward times (tensor-core, CUDA-core) in ms (-1: not admitted)."""
+        import torch
+        S = s.shape[0] if S is None else S
+        ms = (C.c_float * 2)()
+        self._check(self._lib.fddpd_autotune(self._h, S, _ptr(s, torch.complex64), _ptr(H, torch.complex64),
+                                             _ptr(W, torch.complex64), _ptr(alpha, torch.float32),
+                                             _ptr(pa, torch.complex64), _ptr(theta, torch.float32), int(reps), ms))
+        return float(ms[0]), float(ms[1])
 
     def ser(self, y, s, alpha, Q: int, N0: float, seed: int, counts, S: Optional[int] = None):
         """fddpd_ser: adds (errors, symbols compared) of the noisy, equalised symbols

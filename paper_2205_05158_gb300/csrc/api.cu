@@ -715,6 +715,52 @@ extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c
     return FDDPD_OK;
 }
 
+extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
+                              const float *alpha, const fddpd_c32 *pa_coef, const float *theta, int reps,
+                              float *ms) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (reps < 1) return set_err(p, FDDPD_ERR_ARG, "reps < 1");
+    float t[2] = {-1.0f, -1.0f};
+    const bool was = p->tc_bin;
+    const bool tc_ok = p->p16 && fdk::tc_bin_supported(p->g);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FD_CK(p, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_err(p, FDDPD_ERR_CUDA, "event creation failed");
+    }
+    int rc = FDDPD_OK;
+    for (int v = 0; v < 2 && rc == FDDPD_OK; ++v) {
+        if (v == 0 && !tc_ok) continue;
+        p->tc_bin = v == 0;
+        rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);   // warm-up (and re-pack)
+        if (rc) break;
+        if (cudaEventRecord(e0, p->stream) != cudaSuccess) { rc = set_err(p, FDDPD_ERR_CUDA, "event record"); break; }
+        for (int r = 0; r < reps && rc == FDDPD_OK; ++r)
+            rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);
+        if (rc) break;
+        float el = 0.0f;
+        if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
+            rc = set_err(p, FDDPD_ERR_CUDA, "event timing");
+            break;
+        }
+        t[v] = el / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        p->tc_bin = was;
+        return rc;
+    }
+    p->tc_bin = tc_ok && t[0] <= t[1];
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    return fddpd_sync(p);
+}
+
 // ---------------------------------------------------------------------------
 // CUDA graphs over recorded calls of many plans (batched uneven workloads)
 struct fddpd_graph {

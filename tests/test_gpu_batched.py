@@ -87,3 +87,29 @@ def test_graph_replays_training_steps():
     T.cuda.synchronize()
     for c, t, sr in zip(cases, th0, step_ref):
         assert rel_l2((c.theta - t).cpu().numpy(), sr) <= 1e-5
+
+
+@pytest.mark.parametrize("shape_i", [1, 5], ids=["m64_k8", "m128_k32"])
+def test_autotune_picks_an_admitted_implementation(shape_i):
+    """fddpd_autotune times the admitted contraction implementations and keeps the faster:
+    K = 32 admits only the CUDA-core one; the result stays within the 16-bit tolerances."""
+    c = _instance(shape_i, SHAPES[shape_i])
+    t_tc, t_cc = c.plan.autotune(c.s, c.H, c.W, c.alpha, c.pa, c.theta, reps=2)
+    assert t_cc > 0
+    if SHAPES[shape_i][1] > 16:
+        assert t_tc == -1.0
+    else:
+        assert t_tc > 0
+    y, met = c.gpu_distort()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert nmse(y, yo) <= 1e-4
+    assert abs(oracle.evm_db(met) - oracle.evm_db(meto)) <= 0.1
+
+
+def test_autotune_fp32_plan_has_one_choice():
+    cfg = small_cfg()
+    c = Case(cfg, S=cfg.S)
+    c.gpu_zf()
+    t_tc, t_cc = c.plan.autotune(c.s, c.H, c.W, c.alpha, c.pa, c.theta, reps=1)
+    assert t_tc == -1.0 and t_cc > 0
