@@ -132,14 +132,22 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
 enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
 
+/* Transmit power P_T of Eq. (6) for the plan's next fddpd_precode / fddpd_update_host
+ * calls (the ZF normalisation alpha_k = sqrt(P_T / tr((H_k H_k^H)^{-1})); W does not
+ * depend on it).  The PA drive level of an SER-versus-power sweep (Sec. V-B, Fig. 3):
+ * the PA sees alpha W s, so P_T sets its input back-off.  Host-side only; it changes no
+ * array already produced.  Errors: ARG unless 0 < P_T < inf.                     */
+int fddpd_set_power(fddpd_plan *plan, double P_T);
+
 /* Eq. (6): zero-forcing precoder for R channel realisations (Sec. II-A).
  *   H     [R][N_d][K][M]  in : per-subcarrier channel of the data bins
  *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}
  *   alpha [R][N_d]        out: sqrt(P_T / tr((H_k H_k^H)^{-1}))
  * The Gram matrix is accumulated in FP32 and factorised (Cholesky) and inverted in
- * FP64.  16-bit plans also cache packed 16-bit copies of alpha W and H / alpha for the
- * next distort / backward / update calls with these same H, W and alpha pointers
- * (calls with other pointers re-pack from the FP32 arrays).  R <= ceil(max_symbols /
+ * FP64.  16-bit plans also keep 16-bit copies of W and H for the next distort /
+ * backward / update calls with these same H and W pointers (calls with other pointers
+ * re-pack from the FP32 arrays; H or W rewritten in place by other means than this
+ * call must be passed through it again).  R <= ceil(max_symbols /
  * S_per_real).  Errors: ARG, LAYOUT, SINGULAR (reported after the kernel completes:
  * this call synchronises the stream once to read the status word).              */
 int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha);

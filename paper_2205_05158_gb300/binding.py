@@ -27,7 +27,8 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
-            "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune"]
+            "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune",
+            "fddpd_set_power"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_tc_gemm.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P]
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     L.fddpd_set_option.argtypes = [P, I, I]
+    L.fddpd_set_power.argtypes = [P, C.c_double]
     L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
     L.fddpd_autotune.argtypes = [P, I, P, P, P, P, P, P, I, P]
     L.fddpd_graph_begin.argtypes = [P]
@@ -106,7 +108,7 @@ def load(build_if_missing: bool = True):
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
-              "fddpd_precode_noalloc", "fddpd_set_option"):
+              "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -157,6 +159,7 @@ class Plan:
         self._h = h
         self.M, self.K, self.N, self.N_d, self.S_per_real = M, K, N, N_d, S_per_real
         self.precision = precision
+        self.P_T = float(P_T)
 
     @classmethod
     def from_config(cls, cfg, P_T: float, max_symbols: Optional[int] = None, precision: int = FDDPD_FP32,
@@ -222,6 +225,46 @@ class Plan:
         """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
         self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
+
+    def set_power(self, P_T: float):
+        """fddpd_set_power: the transmit power P_T of the next precode / update_host calls."""
+        self._check(self._lib.fddpd_set_power(self._h, float(P_T)))
+        self.P_T = float(P_T)
+
+    def ser_sweep(self, s, H, pa, theta, P_T_values, Q: int, N0: float, seed: int, S: Optional[int] = None):
+        """SER versus drive level (Sec. V-B, the structure of Fig. 3).  For each P_T the plan
+        runs the ZF precoder (fddpd_precode), the forward chain (fddpd_distort) and the
+        symbol errors under receiver noise N0 (fddpd_ser); the plan's P_T is restored
+        afterwards.  Returns one dict per P_T: P_T, P_PA (mean PA output power per antenna
+        sample: the data- plus guard-bin power of the unitary DFT of x^PA over M S N
+        samples), errors, symbols and SER."""
+        import torch
+        S = s.shape[0] if S is None else S
+        R = (S + self.S_per_real - 1) // self.S_per_real
+        dev = s.device
+        W = torch.empty((R, self.N_d, self.M, self.K), dtype=torch.complex64, device=dev)
+        alpha = torch.empty((R, self.N_d), dtype=torch.float32, device=dev)
+        y = torch.empty_like(s)
+        n = len(P_T_values)
+        metrics = torch.zeros((n, 5), dtype=torch.float64, device=dev)
+        counts = torch.zeros((n, 2), dtype=torch.int64, device=dev)
+        P_T0 = self.P_T
+        try:
+            for i, P_T in enumerate(P_T_values):
+                self.set_power(P_T)
+                self.precode(H[:R], W, alpha, R)
+                self.distort(s, H, W, alpha, pa, theta, y, metrics[i], S)
+                self.ser(y, s, alpha, Q, N0, seed, counts[i], S)
+        finally:
+            self.set_power(P_T0)
+        self._check(self._lib.fddpd_sync(self._h))
+        m, c = metrics.cpu().numpy(), counts.cpu().numpy()
+        out = []
+        for i, P_T in enumerate(P_T_values):
+            e, k = int(c[i, 0]), int(c[i, 1])
+            out.append(dict(P_T=float(P_T), P_PA=float(m[i, 3] + m[i, 4]) / (self.M * S * self.N), errors=e,
+                            symbols=k, SER=e / k if k else float("nan")))
+        return out
 
     def autotune(self, s, H, W, alpha, pa, theta, reps: int = 3, S: Optional[int] = None):
         """fddpd_autotune: keeps the faster contraction implementation for this shape;

@@ -1,6 +1,7 @@
 // C-ABI of the fddpd library: plan life cycle, argument checks, workspace layout and
 // the order in which the stage kernels run on the plan's stream.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -282,6 +283,14 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
         return FDDPD_OK;
     }
     return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
+}
+
+extern "C" int fddpd_set_power(fddpd_plan *p, double P_T) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (!(P_T > 0) || !std::isfinite(P_T)) return set_err(p, FDDPD_ERR_ARG, "P_T must be positive and finite");
+    p->d.P_T = P_T;
+    p->g.P_T = P_T;
+    return FDDPD_OK;
 }
 
 extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {

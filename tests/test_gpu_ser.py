@@ -18,8 +18,8 @@ from gpu_common import Case, dev, small_cfg, torch
 pytestmark = pytest.mark.gpu
 
 
-def _near_boundary(z, Q):
-    """Oracle symbols whose real or imaginary part is within 1e-4 level steps of a
+def _near_boundary(z, Q, tol=1e-4):
+    """Oracle symbols whose real or imaginary part is within `tol` level steps of a
     decision boundary (midpoints between levels, in the constellation's range)."""
     side = int(round(math.sqrt(Q)))
     inv_step = math.sqrt(2.0 * (Q - 1) / 3.0) / 2.0
@@ -28,7 +28,7 @@ def _near_boundary(z, Q):
         x = comp * inv_step + 0.5 * (side - 1)
         frac = x - np.floor(x)
         inside = (x > 0) & (x < side - 1)
-        near |= inside & (np.abs(frac - 0.5) < 1e-4)
+        near |= inside & (np.abs(frac - 0.5) < tol)
     return int(near.sum())
 
 
@@ -153,3 +153,45 @@ def test_clipping_pa_ser_pipeline(prec):
     e_g, n_g = _gpu_ser(c.plan, dev(y.astype(np.complex64)), c.s, c.alpha, cfg.Q, N0, 9)
     e_o, n_o, z, _ = oracle.ser(c.d, y, c.w.s, c.alpha.cpu().numpy(), cfg.Q, N0, 9)
     assert n_g == n_o and abs(e_g - e_o) <= _near_boundary(z, cfg.Q)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16"])
+def test_ser_sweep_over_drive(prec):
+    """SER versus PA drive (the structure of Fig. 3) with the linear-clipping PA and fixed
+    N0: at each P_T the GPU's PA output power and error count against the oracle's own
+    precoder, forward chain and noise; the curve falls while noise dominates and rises
+    again once clipping dominates.  The slack counts the oracle's symbols within the
+    forward chain's error of a decision boundary (2e-3 level steps in FP32, 0.05 in BF16)."""
+    import paper_2205_05158_gb300 as fd
+    cfg = small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, S=20, S_per_real=4, Q=16, ibo_db=0.0)
+    c = Case(cfg, S=cfg.S, fc_scale=0.0, precision=prec)
+    P0 = synth.transmit_power(cfg)
+    P_Ts = [P0 * 10 ** (-ibo / 10) for ibo in (18, 12, 6, 0)]
+    N0 = 1.0
+    res = c.plan.ser_sweep(c.s, c.H, c.pa, c.theta, P_Ts, cfg.Q, N0, 5)
+    assert c.plan.P_T == c.w.P_T
+    tol = 2e-3 if prec == 0 else 0.05
+    ser_o = []
+    for r, P_T in zip(res, P_Ts):
+        d = oracle.dims_from_config(cfg, P_T, 1)
+        Wo, alo = oracle.precode(d, c.w.H)
+        yo, meto = oracle.distort(d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+        e_o, n_o, z, _ = oracle.ser(d, yo, c.w.s, alo, cfg.Q, N0, 5)
+        P_PA_o = (meto[3] + meto[4]) / (cfg.M * cfg.S * cfg.N)
+        assert r["symbols"] == n_o == c.w.s.size
+        assert abs(r["P_PA"] - P_PA_o) <= (1e-4 if prec == 0 else 1e-2) * P_PA_o
+        assert abs(r["errors"] - e_o) <= _near_boundary(z, cfg.Q, tol), (P_T, r["errors"], e_o)
+        ser_o.append(e_o / n_o)
+    ser = [r["SER"] for r in res]
+    assert ser_o[0] > ser_o[1] > ser_o[2] and ser_o[3] > ser_o[2]
+    assert ser[0] > ser[1] > ser[2] and ser[3] > ser[2]
+    # the plan's own precoder is back at its P_T
+    W = torch().empty_like(c.W)
+    al = torch().empty_like(c.alpha)
+    c.plan.precode(c.H, W, al)
+    Wo, alo = c.oracle_zf()
+    assert np.allclose(al.cpu().numpy(), alo, rtol=1e-4)
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(fd.FddpdError) as ei:
+            c.plan.set_power(bad)
+        assert ei.value.code == fd.FDDPD_ERR_ARG
