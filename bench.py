@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "DPD'd OFDM symbols/s at M=128,K=16,N=2048; % roofline; EVM vs FP64 oracle"
 UNIT = "symbols/s"
 SER_SNR_DB = 30.0   # mean per-subcarrier SNR at the users for the SER line
-WORKLOAD = ("cfg3: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, orders 1,3,5 taps 0..3, "
+WORKLOAD = ("m128_k16_n2048: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, orders 1,3,5 taps 0..3, "
             "FD-CNN G=35 N_conv=2 K_C=3")
 LR = 1e-4
 FP32_LANES_PER_SM = 128
@@ -212,7 +212,7 @@ def run_reference(args):
         return
     import oracle
     import synth
-    cfg = synth.CONFIGS["cfg3"]
+    cfg = synth.CONFIGS["m128_k16_n2048"]
     n = max(1, args.ref_sample)
     w = synth.make_workload(cfg, S=n, fc_scale=0.05)
     oracle.build()
@@ -250,7 +250,7 @@ def rank_env():
 
 def rank_config(rank: int, symbols: int):
     import synth
-    return synth.CONFIGS["cfg3"].with_(seed=rank, S=symbols)
+    return synth.CONFIGS["m128_k16_n2048"].with_(seed=rank, S=symbols)
 
 
 def max_over_ranks(x: float, dist, device) -> float:

@@ -48,7 +48,7 @@ enum fddpd_status {
     FDDPD_ERR_SINGULAR = -3,     /* a Gram matrix H_k H_k^H not positive definite          */
     FDDPD_ERR_CUDA = -4,         /* a CUDA runtime error (launch, allocation on create)     */
     FDDPD_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up                      */
-    FDDPD_ERR_UNSUPPORTED = -6,  /* a configuration this build does not implement           */
+    FDDPD_ERR_UNSUPPORTED = -6,  /* a configuration the library does not implement             */
     FDDPD_ERR_NOMEM = -7         /* workspace allocation failed                             */
 };
 

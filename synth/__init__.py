@@ -26,7 +26,7 @@ from .philox import Stream, philox4x32_10, splitmix64  # noqa: F401
 
 # Nominal memory-polynomial sets (rows: odd orders, columns: taps 0..L).  The
 # paper's measured coefficient set is not public, so these stand in for it.
-PA_NOMINAL_CFG1 = {1: [1.0 + 0j], 3: [-0.08 + 0.02j]}
+PA_NOMINAL_TOY = {1: [1.0 + 0j], 3: [-0.08 + 0.02j]}
 PA_NOMINAL_MP135 = {
     1: [1.0, 0.08 - 0.04j, -0.02 + 0.01j, 0.005],
     3: [-0.08 + 0.02j, 0.012 - 0.006j, -0.004 + 0.002j, 0.001],
@@ -86,13 +86,13 @@ class Config:
 # The five workloads: a 16x2 toy system, paper scale, the 128x16 mixed-precision
 # system, the same system for training, and a small instance of the uneven batch.
 CONFIGS = {
-    "cfg1": Config("cfg1", M=16, K=2, N=64, N_d=48, Q=16, S=10, S_per_real=10,
-                   pa_nominal=PA_NOMINAL_CFG1, pa_spread_orders=(3,), iters=3, G=7),
-    "cfg2": Config("cfg2", M=64, K=8, N=1024, N_d=600, Q=64, S=1000, S_per_real=14,
+    "m16_k2_n64": Config("m16_k2_n64", M=16, K=2, N=64, N_d=48, Q=16, S=10, S_per_real=10,
+                   pa_nominal=PA_NOMINAL_TOY, pa_spread_orders=(3,), iters=3, G=7),
+    "m64_k8_n1024": Config("m64_k8_n1024", M=64, K=8, N=1024, N_d=600, Q=64, S=1000, S_per_real=14,
                    pa_nominal=PA_NOMINAL_MP135, iters=4, G=25),
-    "cfg3": Config("cfg3", M=128, K=16, N=2048, N_d=1200, Q=256, S=2000, S_per_real=14,
+    "m128_k16_n2048": Config("m128_k16_n2048", M=128, K=16, N=2048, N_d=1200, Q=256, S=2000, S_per_real=14,
                    pa_nominal=PA_NOMINAL_MP135, rho=0.5, iters=1, G=35),
-    "cfg4": Config("cfg4", M=128, K=16, N=2048, N_d=1200, Q=256, S=256, S_per_real=14,
+    "m128_k16_n2048_train": Config("m128_k16_n2048_train", M=128, K=16, N=2048, N_d=1200, Q=256, S=256, S_per_real=14,
                    pa_nominal=PA_NOMINAL_MP135, rho=0.5, iters=500, G=35),
 }
 

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 def test_autograd_gradient_is_library_adjoint():
     import paper_2205_05158_gb300 as fd
     T = torch()
-    c = Case(synth.CONFIGS["cfg1"], fc_scale=0.3)
+    c = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
     c.gpu_zf()
     th = T.nn.Parameter(c.theta.clone())
     loss = fd.fddpd_loss(th, c.plan, c.s, c.H, c.W, c.alpha, c.pa)
@@ -25,7 +25,7 @@ def test_autograd_gradient_is_library_adjoint():
 def test_torch_adam_loop_matches_library_adam():
     import paper_2205_05158_gb300 as fd
     T = torch()
-    c = Case(synth.CONFIGS["cfg1"], fc_scale=0.3)
+    c = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
     c.gpu_zf()
     th0 = c.theta.clone()
     th = T.nn.Parameter(th0.clone())

@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
 @pytest.mark.parametrize("name,mk", [
     ("ragged", lambda p: Case(small_cfg(), fc_scale=0.3, precision=p)),
-    ("cfg2_28", lambda p: Case(synth.CONFIGS["cfg2"], S=28, fc_scale=0.2, precision=p)),
-    ("cfg3_28", lambda p: Case(synth.CONFIGS["cfg3"].with_(S=28), fc_scale=0.05, precision=p)),
+    ("m64_k8_n1024_28", lambda p: Case(synth.CONFIGS["m64_k8_n1024"], S=28, fc_scale=0.2, precision=p)),
+    ("m128_k16_n2048_28", lambda p: Case(synth.CONFIGS["m128_k16_n2048"].with_(S=28), fc_scale=0.05, precision=p)),
 ])
 def test_mixed_forward_quality(name, mk, prec):
     c = mk(prec)
@@ -41,7 +41,7 @@ def test_mixed_backward(prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
-@pytest.mark.parametrize("cfg", [small_cfg(), synth.CONFIGS["cfg3"].with_(S=28)], ids=["ragged", "cfg3_28"])
+@pytest.mark.parametrize("cfg", [small_cfg(), synth.CONFIGS["m128_k16_n2048"].with_(S=28)], ids=["ragged", "m128_k16_n2048_28"])
 def test_mixed_zf_fp32_factor(cfg, prec):
     """16-bit plans factor the Gram matrix in FP32: W and alpha (Eq. 6) still agree with
     the FP64 oracle far inside the 16-bit rounding that W undergoes afterwards."""
@@ -57,7 +57,7 @@ def test_mixed_zf_fp32_factor(cfg, prec):
 def test_mixed_zf_singular_flagged(prec):
     import paper_2205_05158_gb300 as fd
     from gpu_common import dev
-    c = Case(synth.CONFIGS["cfg1"], precision=prec)
+    c = Case(synth.CONFIGS["m16_k2_n64"], precision=prec)
     H = c.w.H.copy()
     H[0, 5, 1] = H[0, 5, 0]          # two identical users on one subcarrier
     with pytest.raises(fd.FddpdError) as e:

@@ -29,8 +29,8 @@ def _blocks(d, g):
 
 
 # --- ZF (Eq. 6) ---------------------------------------------------------------
-@pytest.mark.parametrize("cfg", [synth.CONFIGS["cfg1"], small_cfg(),
-                                 synth.CONFIGS["cfg3"].with_(S=28),
+@pytest.mark.parametrize("cfg", [synth.CONFIGS["m16_k2_n64"], small_cfg(),
+                                 synth.CONFIGS["m128_k16_n2048"].with_(S=28),
                                  small_cfg(M=96, K=16, S=6, S_per_real=2),      # K = 16 Gram, 3 chunks of 32
                                  small_cfg(M=100, K=16, S=6, S_per_real=2),     # K = 16, ragged chunk
                                  small_cfg(M=256, K=32, N=512, N_d=300, S=2, S_per_real=1, G=18)])
@@ -47,7 +47,7 @@ def test_zf_matches_oracle(cfg):
 
 def test_zf_singular_flagged():
     import paper_2205_05158_gb300 as fd
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     c = Case(cfg)
     H = c.w.H.copy()
     H[0, 5, 1] = H[0, 5, 0]          # two identical users on one subcarrier
@@ -75,10 +75,10 @@ def _gmp_case(**kw):
 
 
 FWD_CASES = [
-    ("cfg1", lambda: Case(synth.CONFIGS["cfg1"], fc_scale=0.3)),
+    ("m16_k2_n64", lambda: Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)),
     ("ragged", lambda: Case(small_cfg(), fc_scale=0.3)),
     ("ragged_literal", lambda: Case(small_cfg(L_U=1, K_S=1), fc_scale=0.5, residual=0)),
-    ("cfg2_28", lambda: Case(synth.CONFIGS["cfg2"], S=28, fc_scale=0.2)),
+    ("m64_k8_n1024_28", lambda: Case(synth.CONFIGS["m64_k8_n1024"], S=28, fc_scale=0.2)),
     ("n4096_nd_full", lambda: Case(small_cfg(M=8, K=2, N=4096, N_d=4096, S=3, S_per_real=2, G=64, L_U=1, K_S=1),
                                    fc_scale=0.05)),
     ("n64_siso", lambda: Case(small_cfg(M=1, K=1, N=64, N_d=40, S=5, S_per_real=5, G=7, L_U=1, K_S=1), fc_scale=0.3)),
@@ -131,14 +131,14 @@ def test_linear_pa_is_identity():
 
 # --- adjoint -----------------------------------------------------------------------
 BWD_CASES = [
-    ("cfg1", lambda: Case(synth.CONFIGS["cfg1"], fc_scale=0.3)),
+    ("m16_k2_n64", lambda: Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)),
     ("pa13_mem3", lambda: Case(small_cfg(N=512, pa_nominal=PA_13_MEM), fc_scale=0.3)),
     ("pa_general_even", lambda: Case(small_cfg(N=128, N_d=100, G=10, pa_nominal=PA_EVEN), fc_scale=0.3)),
     ("n4096", lambda: Case(small_cfg(M=8, K=2, N=4096, N_d=2400, S=3, S_per_real=2, G=49, L_U=1, K_S=1),
                            fc_scale=0.05)),
     ("ragged", lambda: Case(small_cfg(), fc_scale=0.3)),
     ("ragged_literal", lambda: Case(small_cfg(L_U=1, K_S=1), fc_scale=0.5, residual=0)),
-    ("cfg2_14", lambda: Case(synth.CONFIGS["cfg2"], S=14, fc_scale=0.2)),
+    ("m64_k8_n1024_14", lambda: Case(synth.CONFIGS["m64_k8_n1024"], S=14, fc_scale=0.2)),
     ("pa_clip", lambda: Case(small_cfg(N=512, N_d=300, G=18, pa_nominal=synth.PA_LINEAR_CLIP, ibo_db=0.0),
                              fc_scale=0.3)),
     ("pa_gmp_G1", lambda: _gmp_case(fc_scale=0.3)),
@@ -161,7 +161,7 @@ def test_backward_matches_oracle(name, mk):
 def test_gd_update_matches_oracle():
     import paper_2205_05158_gb300 as fd
     T = torch()
-    c = Case(synth.CONFIGS["cfg1"], fc_scale=0.3)
+    c = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
     c.use_oracle_zf_on_gpu()
     Wo, alo = c.oracle_zf()
     th0 = c.w.theta.astype(np.float64)
@@ -175,7 +175,7 @@ def test_gd_update_matches_oracle():
 
 def test_adam_update_matches_oracle():
     import paper_2205_05158_gb300 as fd
-    c = Case(synth.CONFIGS["cfg1"], fc_scale=0.3)
+    c = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
     c.use_oracle_zf_on_gpu()
     Wo, alo = c.oracle_zf()
     th0 = c.w.theta.astype(np.float64)
@@ -194,7 +194,7 @@ def test_adam_update_matches_oracle():
 def test_call_argument_errors():
     import paper_2205_05158_gb300 as fd
     T = torch()
-    c = Case(synth.CONFIGS["cfg1"])
+    c = Case(synth.CONFIGS["m16_k2_n64"])
     c.gpu_zf()
     with pytest.raises(fd.FddpdError) as e:
         c.plan.distort(c.s, c.H, c.W, c.alpha, c.pa, c.theta, S=c.S + 1)
@@ -207,8 +207,8 @@ def test_call_argument_errors():
 
 # --- full-size 128 x 16 x 2048 workload (the benchmark's launch shape) ----------------------
 @pytest.mark.slow
-def test_cfg3_full_size_sampled_symbols():
-    cfg = synth.CONFIGS["cfg3"]
+def test_m128_k16_n2048_full_size_sampled_symbols():
+    cfg = synth.CONFIGS["m128_k16_n2048"]
     c = Case(cfg, fc_scale=0.05)
     c.gpu_zf()
     y, met = c.gpu_distort()

@@ -44,10 +44,10 @@ def _gpu_ser(plan, y, s, alpha, Q, N0, seed):
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16"])
 @pytest.mark.parametrize("snr_db", [10.0, 16.0, None], ids=["snr10", "snr16", "noiseless"])
 def test_ser_matches_oracle(prec, snr_db):
-    """Distorted symbols of a 16-QAM system (cfg1 with 60 symbols) through the noise and
+    """Distorted symbols of a 16-QAM system (m16_k2_n64 with 60 symbols) through the noise and
     the decisions on both sides: equal counts up to the near-boundary symbols."""
     T = torch()
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     c = Case(cfg, S=60, fc_scale=0.3, precision=prec)
     c.gpu_zf()
     y = T.empty_like(c.s)
@@ -83,7 +83,7 @@ def test_ser_awgn_closed_form(Q, snr_db):
 def test_ser_counts_accumulate_and_errors():
     import paper_2205_05158_gb300 as fd
     T = torch()
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     c = Case(cfg, S=20)
     c.gpu_zf()
     counts = T.zeros(2, dtype=T.int64, device="cuda")
@@ -106,7 +106,7 @@ def test_ser_counts_accumulate_and_errors():
 
 def test_ser_singular_subcarriers_skipped():
     T = torch()
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     c = Case(cfg, S=20)
     al = T.ones((c.R, cfg.N_d), dtype=T.float32, device="cuda")
     al[1, 3] = 0.0
@@ -120,7 +120,7 @@ def test_imperfect_csi_chain(prec):
     against the oracle given the same two channels."""
     from gpu_common import nmse
     T = torch()
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     c = Case(cfg, S=30, fc_scale=0.3, precision=prec)
     He = synth.channel_estimate(cfg, 0.1, S=30)
     W = T.empty_like(c.W)

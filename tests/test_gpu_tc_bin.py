@@ -19,7 +19,7 @@ CFGS = [
     ("ragged", small_cfg()),                                           # M 40, K 3, realisations of 3
     ("pad", small_cfg(M=100, K=13, S=45, S_per_real=20)),               # M % 8 = 4, K % 4 = 1, 2 symbol chunks
     ("full", small_cfg(M=128, K=16, S=33, S_per_real=14)),             # full tiles, ragged subcarrier groups
-    ("cfg3_140", synth.CONFIGS["cfg3"].with_(S=140)),                   # several items per CTA
+    ("m128_k16_n2048_140", synth.CONFIGS["m128_k16_n2048"].with_(S=140)),                   # several items per CTA
 ]
 
 
@@ -74,7 +74,7 @@ def test_option_ignored_by_fp32_plans():
 
 def test_option_rejects_unknown():
     import paper_2205_05158_gb300 as fd
-    c = Case(synth.CONFIGS["cfg1"], precision=1)
+    c = Case(synth.CONFIGS["m16_k2_n64"], precision=1)
     with pytest.raises(fd.FddpdError) as e:
         c.plan.set_option(99, 1)
     assert e.value.code == fd.FDDPD_ERR_ARG
@@ -83,8 +83,8 @@ def test_option_rejects_unknown():
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
-@pytest.mark.parametrize("name,cfg", [CFGS[0], CFGS[1], ("cfg3_28", synth.CONFIGS["cfg3"].with_(S=28))],
-                         ids=["ragged", "pad", "cfg3_28"])
+@pytest.mark.parametrize("name,cfg", [CFGS[0], CFGS[1], ("m128_k16_n2048_28", synth.CONFIGS["m128_k16_n2048"].with_(S=28))],
+                         ids=["ragged", "pad", "m128_k16_n2048_28"])
 def test_tc_zf_apply(name, cfg, prec):
     """W = H^H (H H^H)^{-1} (Eq. 6) from the tensor-core apply (BF16 hi / lo splits)
     against the oracle and against the CUDA-core apply; alpha comes from the same factor."""

@@ -174,7 +174,7 @@ def _setup(cfg, fc_scale=0.0, pa=None):
 
 
 def test_identity_for_linear_pa():
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     w, d, W, al = _setup(cfg, pa=synth.linear_pa(cfg))
     y, met = oracle.distort(d, w.s, w.H, W, al, w.pa, w.theta)
     assert np.abs(y - w.s).max() < 1e-12
@@ -326,7 +326,7 @@ def test_fig2_td_gmp_structure():
 
 def test_chain_rejects_missing_realisations():
     """The chain indexes H, W and alpha by realisation: too few for S symbols is an error."""
-    cfg = synth.CONFIGS["cfg1"]
+    cfg = synth.CONFIGS["m16_k2_n64"]
     w = synth.make_workload(cfg, S=2 * cfg.S_per_real)
     d = oracle.dims_from_config(cfg, w.P_T)
     W, al = oracle.precode(d, w.H[:1])

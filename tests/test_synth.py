@@ -61,13 +61,13 @@ def test_channel_statistics():
 
 
 def test_pa_spread_and_linear():
-    cfg = synth.CONFIGS["cfg2"]
+    cfg = synth.CONFIGS["m64_k8_n1024"]
     pa = synth.pa_coefficients(0, 64, cfg.pa_nominal, 0.1)
     nom = np.array([cfg.pa_nominal[p] for p in cfg.orders])
     ratio = pa / nom[None]
     assert np.allclose(ratio.imag, 0, atol=1e-12)
     assert ratio.real.min() >= 0.9 - 1e-12 and ratio.real.max() <= 1.1 + 1e-12
-    c1 = synth.CONFIGS["cfg1"]
+    c1 = synth.CONFIGS["m16_k2_n64"]
     p1 = synth.pa_coefficients(0, 16, c1.pa_nominal, 0.1, (3,))
     assert np.all(p1[:, 0, 0] == 1.0) and np.ptp(p1[:, 1, 0].real) > 0
 
@@ -80,18 +80,18 @@ def test_saturation_amplitude_closed_form():
 
 
 def test_workload_shapes():
-    w = synth.make_workload(synth.CONFIGS["cfg1"])
+    w = synth.make_workload(synth.CONFIGS["m16_k2_n64"])
     assert w.s.shape == (10, 2, 48) and w.H.shape == (1, 48, 2, 16) and w.pa.shape == (16, 2, 1)
     assert w.theta.dtype == np.float32 and w.s.dtype == np.complex64
-    w2 = synth.make_workload(synth.CONFIGS["cfg2"], S=28, symbol_offset=14)
-    w3 = synth.make_workload(synth.CONFIGS["cfg2"], S=42)
+    w2 = synth.make_workload(synth.CONFIGS["m64_k8_n1024"], S=28, symbol_offset=14)
+    w3 = synth.make_workload(synth.CONFIGS["m64_k8_n1024"], S=42)
     assert np.array_equal(w2.s, w3.s[14:]) and np.array_equal(w2.H, w3.H[1:])
 
 
 def test_channel_estimate_imperfect_csi():
     """Sec. II-A: H_est = sqrt(1 - eta) H + sqrt(eta) H_err, H_err taps CN(0, 1), so the
     per-subcarrier error has variance eta T; eta = 0 returns the true channel."""
-    cfg = synth.CONFIGS["cfg2"].with_(S=28)
+    cfg = synth.CONFIGS["m64_k8_n1024"].with_(S=28)
     w = synth.make_workload(cfg, S=28)
     assert np.array_equal(synth.channel_estimate(cfg, 0.0, S=28), w.H)
     eta = 0.2

@@ -18,7 +18,7 @@ def test_noalloc_precode_matches_plan_precode_twice():
     import paper_2205_05158_gb300 as fd
     from paper_2205_05158_gb300 import binding
     T = torch()
-    cfg = synth.CONFIGS["cfg3"].with_(S=28)            # 2 realisations x 1200 subcarriers
+    cfg = synth.CONFIGS["m128_k16_n2048"].with_(S=28)            # 2 realisations x 1200 subcarriers
     outs = []
     for seed in (0, 5):
         w = synth.make_workload(cfg.with_(seed=seed))
