@@ -139,6 +139,12 @@ int fddpd_set_option(fddpd_plan *plan, int option, int value);
  * array already produced.  Errors: ARG unless 0 < P_T < inf.                     */
 int fddpd_set_power(fddpd_plan *plan, double P_T);
 
+/* Drops a 16-bit plan's copies of H and W (see fddpd_precode), so that the next
+ * distort / backward / update call re-packs them from the FP32 arrays it is given: for
+ * H or W rewritten in place under the same pointers (fddpd_precode_noalloc, a copy).
+ * Host-side only; no effect on FP32 plans.  Errors: ARG for a null plan.           */
+int fddpd_invalidate_operands(fddpd_plan *plan);
+
 /* Eq. (6): zero-forcing precoder for R channel realisations (Sec. II-A).
  *   H     [R][N_d][K][M]  in : per-subcarrier channel of the data bins
  *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}
@@ -146,8 +152,8 @@ int fddpd_set_power(fddpd_plan *plan, double P_T);
  * The Gram matrix is accumulated in FP32 and factorised (Cholesky) and inverted in
  * FP64.  16-bit plans also keep 16-bit copies of W and H for the next distort /
  * backward / update calls with these same H and W pointers (calls with other pointers
- * re-pack from the FP32 arrays; H or W rewritten in place by other means than this
- * call must be passed through it again).  R <= ceil(max_symbols /
+ * re-pack from the FP32 arrays; after H or W is rewritten in place by other means than
+ * this call, call fddpd_invalidate_operands).  R <= ceil(max_symbols /
  * S_per_real).  Errors: ARG, LAYOUT, SINGULAR (reported after the kernel completes:
  * this call synchronises the stream once to read the status word).              */
 int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha);

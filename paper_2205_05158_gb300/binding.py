@@ -28,7 +28,7 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
             "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune",
-            "fddpd_set_power"]
+            "fddpd_set_power", "fddpd_invalidate_operands"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_precode_noalloc.argtypes = [I, I, I, I, C.c_double, P, P, P, P]
     L.fddpd_set_option.argtypes = [P, I, I]
     L.fddpd_set_power.argtypes = [P, C.c_double]
+    L.fddpd_invalidate_operands.argtypes = [P]
     L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
     L.fddpd_autotune.argtypes = [P, I, P, P, P, P, P, P, I, P]
     L.fddpd_graph_begin.argtypes = [P]
@@ -108,7 +109,8 @@ def load(build_if_missing: bool = True):
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
-              "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power"):
+              "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power",
+              "fddpd_invalidate_operands"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -225,6 +227,11 @@ class Plan:
         """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
         self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
+
+    def invalidate_operands(self):
+        """fddpd_invalidate_operands: the next call re-packs H and W (16-bit plans) --
+        needed after H or W was rewritten in place other than by ``precode``."""
+        self._check(self._lib.fddpd_invalidate_operands(self._h))
 
     def set_power(self, P_T: float):
         """fddpd_set_power: the transmit power P_T of the next precode / update_host calls."""

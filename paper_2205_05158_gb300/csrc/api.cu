@@ -293,6 +293,14 @@ extern "C" int fddpd_set_power(fddpd_plan *p, double P_T) {
     return FDDPD_OK;
 }
 
+extern "C" int fddpd_invalidate_operands(fddpd_plan *p) {
+    if (!p) return FDDPD_ERR_ARG;
+    p->pk_H = nullptr;
+    p->pk_W = nullptr;
+    p->pk_R = 0;
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {
     if (!p) return FDDPD_ERR_ARG;
     p->adam_t = 0;
