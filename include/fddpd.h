@@ -204,7 +204,8 @@ int fddpd_reset_optimizer(fddpd_plan *plan);
  * complete.  A singular Gram matrix anywhere in the batch returns FDDPD_ERR_SINGULAR
  * before any step, with theta untouched.  iters = 0 only computes the precoders.
  * Other errors as fddpd_precode / fddpd_update, NOMEM if the staging buffers cannot
- * be allocated.                                                                   */
+ * be allocated; a failed call still waits for its copies, so the host arrays are free
+ * for reuse whenever it returns.                                                  */
 int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
                       const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
                       double *metrics);

@@ -601,10 +601,9 @@ extern "C" const char *fddpd_stage_name(int stage) {
 
 extern "C" long long fddpd_launch_count(const fddpd_plan *p) { return p ? p->launches : 0; }
 
-extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H,
-                                 const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
-                                 double *metrics) {
-    if (!p) return FDDPD_ERR_ARG;
+static int update_host_impl(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                            const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
+                            double *metrics) {
     if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
     if (!s || !H || !pa_coef || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
     if (iters < 0) return set_err(p, FDDPD_ERR_ARG, "iters < 0");
@@ -715,6 +714,18 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     if (metrics && iters > 0)
         FD_CK(p, cudaMemcpyAsync(metrics, p->hmet, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return fddpd_sync(p);
+}
+
+extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H,
+                                 const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
+                                 double *metrics) {
+    if (!p) return FDDPD_ERR_ARG;
+    const int rc = update_host_impl(p, S, s, H, pa_coef, theta, lr, iters, optimizer, metrics);
+    // a call that fails part-way may have copies of the caller's host arrays in flight:
+    // they end before the call returns, so the caller may reuse or free the arrays
+    if (rc != FDDPD_OK && p->cstream) cudaStreamSynchronize(p->cstream);
+    if (rc != FDDPD_OK) cudaStreamSynchronize(p->stream);
+    return rc;
 }
 
 extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
