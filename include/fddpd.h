@@ -67,7 +67,7 @@ typedef struct {
     int N_d;          /* data subcarriers, 1..N                                          */
     int first_bin;    /* FFT bin of data subcarrier 0; -1 selects N - N_d/2 (DC-centred) */
     int S_per_real;   /* OFDM symbols per channel realisation, >= 1                      */
-    int max_symbols;  /* the largest S any call on this plan passes (sizes the workspace)*/
+    int max_symbols;  /* the largest S any call passes (sizes the workspace); x M < 2^31 */
     int precision;    /* enum fddpd_precision                                            */
     double P_T;       /* transmit power of the ZF normalisation, E||x_hat_k||^2 = P_T    */
 } fddpd_dims;

@@ -2,6 +2,7 @@
 // the order in which the stage kernels run on the plan's stream.
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -113,6 +114,9 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (d->N_d < 1 || d->N_d > d->N) return set_err(nullptr, FDDPD_ERR_ARG, "N_d=%d outside 1..N", d->N_d);
     if (d->first_bin < -1 || d->first_bin >= d->N) return set_err(nullptr, FDDPD_ERR_ARG, "first_bin=%d", d->first_bin);
     if (d->S_per_real < 1 || d->max_symbols < 1) return set_err(nullptr, FDDPD_ERR_ARG, "S_per_real / max_symbols < 1");
+    // symbol x antenna rows and symbol x user columns are counted in 32 bits by the launchers
+    if ((long)d->max_symbols * d->M > INT_MAX)
+        return set_err(nullptr, FDDPD_ERR_ARG, "max_symbols x M above 2^31 - 1");
     if (d->precision != FDDPD_FP32 && d->precision != FDDPD_BF16 && d->precision != FDDPD_FP16)
         return set_err(nullptr, FDDPD_ERR_ARG, "precision=%d", d->precision);
     if (!(d->P_T > 0)) return set_err(nullptr, FDDPD_ERR_ARG, "P_T must be positive");

@@ -65,7 +65,8 @@ def _create(lib, **over):
     (dict(N=100), binding.FDDPD_ERR_UNSUPPORTED), (dict(N=8192), binding.FDDPD_ERR_UNSUPPORTED),
     (dict(N_d=65), binding.FDDPD_ERR_ARG), (dict(N_d=0), binding.FDDPD_ERR_ARG),
     (dict(first_bin=64), binding.FDDPD_ERR_ARG), (dict(S_per_real=0), binding.FDDPD_ERR_ARG),
-    (dict(max_symbols=0), binding.FDDPD_ERR_ARG), (dict(P_T=0.0), binding.FDDPD_ERR_ARG),
+    (dict(max_symbols=0), binding.FDDPD_ERR_ARG), (dict(max_symbols=2 ** 31 // 16 + 1), binding.FDDPD_ERR_ARG),
+    (dict(P_T=0.0), binding.FDDPD_ERR_ARG),
     (dict(precision=7), binding.FDDPD_ERR_ARG), (dict(G=6), binding.FDDPD_ERR_ARG),
     (dict(L_U=3), binding.FDDPD_ERR_ARG), (dict(K_C=2), binding.FDDPD_ERR_ARG),
     (dict(N_conv=0), binding.FDDPD_ERR_ARG), (dict(residual=2), binding.FDDPD_ERR_ARG),
