@@ -83,8 +83,9 @@ class Config:
         return dataclasses.replace(self, **kw)
 
 
-# The five workloads: a 16x2 toy system, paper scale, the 128x16 mixed-precision
-# system, the same system for training, and a small instance of the uneven batch.
+# The workloads, named by their sizes: a 16x2 toy system, a 64x8 N=1024 system, the
+# 128x16 N=2048 system of the benchmark, and the same system with 256 symbols for long
+# training runs (500 iterations).
 CONFIGS = {
     "m16_k2_n64": Config("m16_k2_n64", M=16, K=2, N=64, N_d=48, Q=16, S=10, S_per_real=10,
                    pa_nominal=PA_NOMINAL_TOY, pa_spread_orders=(3,), iters=3, G=7),
