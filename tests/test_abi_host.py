@@ -89,3 +89,38 @@ def test_null_plan_calls(lib):
     assert lib.fddpd_precode(None, 1, None, None, None) == binding.FDDPD_ERR_ARG
     assert lib.fddpd_distort(None, 1, *([None] * 8)) == binding.FDDPD_ERR_ARG
     assert lib.fddpd_theta_len(None) == 0
+
+
+PLAN_CALLS = ["fddpd_set_stream", "fddpd_precode", "fddpd_distort", "fddpd_backward", "fddpd_update",
+              "fddpd_reset_optimizer", "fddpd_update_host", "fddpd_profile_enable", "fddpd_profile_read",
+              "fddpd_sync", "fddpd_set_option", "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_ser",
+              "fddpd_autotune"]
+
+
+@pytest.mark.parametrize("name", PLAN_CALLS)
+def test_every_plan_call_rejects_a_null_plan(lib, name):
+    """Every entry point that takes a plan returns FDDPD_ERR_ARG for NULL before any
+    device work (the remaining arguments are placeholders of their declared types)."""
+    f = getattr(lib, name)
+    args = [None]
+    for t in f.argtypes[1:]:
+        if t in (C.c_float, C.c_double):
+            args.append(1.0)
+        elif t in (C.c_int, C.c_ulonglong):
+            args.append(1)
+        else:
+            args.append(None)
+    assert f(*args) == binding.FDDPD_ERR_ARG
+
+
+def test_plan_free_calls_reject_bad_arguments(lib):
+    out = C.c_void_p()
+    assert lib.fddpd_graph_begin(None) == binding.FDDPD_ERR_ARG      # the default stream cannot record
+    assert lib.fddpd_graph_end(None, C.byref(out)) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_graph_launch(None, None) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_graph_destroy(None) == 0
+    assert lib.fddpd_precode_noalloc(0, 1, 1, 1, 1.0, None, None, None, None) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_precode_noalloc(8, 2, 4, 1, 0.0, None, None, None, None) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_tc_gemm(-1, 1, 1, None, 1, None, 1, None, 1, 0, 1, None) == binding.FDDPD_ERR_ARG
+    assert lib.fddpd_stage_name(-1) is None and lib.fddpd_stage_name(10 ** 6) is None
+    assert lib.fddpd_launch_count(None) == 0 and lib.fddpd_workspace_bytes(None) == 0
