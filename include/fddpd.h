@@ -6,7 +6,7 @@
  *   s_tilde = s + FD-CNN_theta(s)            (Sec. IV-A; residual form, see residual)
  *   x_hat_k = alpha_k W_k s_tilde_k          (Eq. 1 with the ZF precoder of Eq. 6)
  *   x_b     = IDFT_N(x_hat_{.,b})            (Eq. 2, unitary; guard bins zero)
- *   x^PA_b  = PA_b(x_b)                      (Eq. 7 with the memory polynomial of Eq. 9)
+ *   x^PA_b  = PA_b(x_b)                      (Eq. 7: the GMP of Eq. 9, or the clipping PA)
  *   y_k     = H_k DFT_N(x^PA)_k / alpha_k    (Eq. 4-5, noise free, then equalised)
  *   loss    = mean |y - s|^2                 (training criterion, Sec. V-A)
  * and its adjoint with respect to theta, and gradient-descent / Adam updates.
@@ -48,7 +48,7 @@ enum fddpd_status {
     FDDPD_ERR_SINGULAR = -3,     /* a Gram matrix H_k H_k^H not positive definite          */
     FDDPD_ERR_CUDA = -4,         /* a CUDA runtime error (launch, allocation on create)     */
     FDDPD_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up                      */
-    FDDPD_ERR_UNSUPPORTED = -6,  /* a configuration the library does not implement             */
+    FDDPD_ERR_UNSUPPORTED = -6,  /* a configuration the library does not implement          */
     FDDPD_ERR_NOMEM = -7         /* workspace allocation failed                             */
 };
 
@@ -86,11 +86,11 @@ typedef struct {
 } fddpd_pa_desc;
 
 typedef struct {
-    int G;            /* grid side, G*G >= N_d (the paper's ceil(sqrt(N_d)))             */
+    int G;            /* grid side, G*G >= N_d, <= 128 (the paper's ceil(sqrt(N_d)))     */
     int L_U;          /* users per FD-CNN input, 1..K (users u, u+1, ... mod K)          */
-    int K_C;          /* odd kernel size                                                 */
-    int K_S;          /* stride                                                          */
-    int N_conv;       /* number of kernels                                               */
+    int K_C;          /* kernel size, odd, 1..15                                         */
+    int K_S;          /* stride, 1..G                                                    */
+    int N_conv;       /* number of kernels, 1..64                                        */
     int residual;     /* 1: s_tilde = s + FC(.); 0: s_tilde = FC(.) as printed           */
 } fddpd_dpd_desc;
 
@@ -122,7 +122,8 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *       adjoints) run as tcgen05 MMAs with 16-bit B operands (the activations rounded
  *       to the plan's 16-bit type), and the ZF matrix W = H^H (H H^H)^{-1} as tcgen05
  *       MMAs on BF16 high / low splits of H and (H H^H)^{-1} (relative error near
- *       2^-16); 0: CUDA-core kernels with FP32 activations and an FP32 W.
+ *       2^-16); 0: CUDA-core contractions on the same 16-bit copies of H and W with
+ *       FP32 activations, and W computed on CUDA cores in FP32 before its rounding.
  *       Ignored by FP32 plans.
  *   FDDPD_OPT_HOST_CHUNKS  1..16 (default 7): the number of realisation chunks in which
  *       fddpd_update_host moves a batch and overlaps its copies with the step; 1 copies
@@ -150,7 +151,7 @@ int fddpd_invalidate_operands(fddpd_plan *plan);
  *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}
  *   alpha [R][N_d]        out: sqrt(P_T / tr((H_k H_k^H)^{-1}))
  * The Gram matrix is accumulated in FP32 and factorised (Cholesky) and inverted in
- * FP64.  16-bit plans also keep 16-bit copies of W and H for the next distort /
+ * FP64 (in FP32 in 16-bit plans, whose W is rounded to 16 bits).  16-bit plans also keep 16-bit copies of W and H for the next distort /
  * backward / update calls with these same H and W pointers (calls with other pointers
  * re-pack from the FP32 arrays; after H or W is rewritten in place by other means than
  * this call, call fddpd_invalidate_operands).  R <= ceil(max_symbols /
@@ -171,8 +172,10 @@ int fddpd_distort(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *
                   const float *theta, fddpd_c32 *y, double *metrics);
 
 /* Gradient of the loss over the S symbols with respect to theta (Sec. V-A), by the
- * hand-written adjoint of the whole chain; the time-domain PA inputs are recomputed
- * from x_hat, not stored.  grad [theta_len] out (overwritten).  metrics as distort. */
+ * hand-written adjoint of the whole chain, after a forward pass of its own; the
+ * time-domain PA inputs of the adjoint are recomputed from x_hat, or, in BF16 plans
+ * on the tensor-core path, kept by that forward pass in BF16.
+ * grad [theta_len] out (overwritten).  metrics as distort.                        */
 int fddpd_backward(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
                    const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
                    const float *theta, float *grad, double *metrics);
@@ -199,9 +202,8 @@ int fddpd_reset_optimizer(fddpd_plan *plan);
  * ZF, forward chain and adjoint run on the plan's stream while the next chunk is
  * copied (the loss stays normalised by the whole batch; the gradient is summed over
  * the chunks).  16-bit plans keep only the 16-bit copy of W here.  Further iterations
- * run on the resident batch.  Host
- * buffers should be page-locked for full copy bandwidth.  Blocks until the step is
- * complete.  A singular Gram matrix anywhere in the batch returns FDDPD_ERR_SINGULAR
+ * run on the resident batch.  Host buffers should be page-locked for full copy
+ * bandwidth.  Blocks until the step is complete.  A singular Gram matrix anywhere in the batch returns FDDPD_ERR_SINGULAR
  * before any step, with theta untouched.  iters = 0 only computes the precoders.
  * Other errors as fddpd_precode / fddpd_update, NOMEM if the staging buffers cannot
  * be allocated; a failed call still waits for its copies, so the host arrays are free
@@ -243,8 +245,9 @@ int fddpd_autotune(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 
  * fddpd_update / fddpd_ser call of plans whose stream is `stream` (fddpd_set_stream) is
  * recorded instead of run; fddpd_graph_launch then runs the whole recorded sequence as
  * one graph launch on `stream`, as often as wanted, with the pointers and sizes given at
- * recording time (the data behind them may change between launches).  fddpd_precode and
- * fddpd_update_host synchronise and cannot be recorded (they fail with FDDPD_ERR_CUDA).
+ * recording time (the data behind them may change between launches).  fddpd_precode,
+ * fddpd_update_host, fddpd_autotune and fddpd_sync synchronise and cannot be recorded
+ * (they fail with FDDPD_ERR_CUDA).
  * Errors: ARG, CUDA (a call that cannot be recorded ends the recording).            */
 typedef struct fddpd_graph fddpd_graph;
 int fddpd_graph_begin(void *stream);
