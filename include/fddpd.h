@@ -272,7 +272,7 @@ int fddpd_profile_enable(fddpd_plan *plan, int enable);
  * the last read, and clear them.  Either pointer may be NULL.                        */
 int fddpd_profile_read(fddpd_plan *plan, double *ms, long long *count);
 
-/* Name of a stage ("zf", "fc_fwd", ...), or NULL. */
+/* Name of a stage ("zf_gram", "fc_fwd", "fftpa_adj", ...), or NULL. */
 const char *fddpd_stage_name(int stage);
 
 /* Number of kernels this plan has launched since it was created. */
