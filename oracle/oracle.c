@@ -124,6 +124,7 @@ int orc_zf(int K, int M, const cplx *Hk, double P_T, cplx *Wk, double *alpha)
     return rc;
 }
 
+/* Eq. (6) for every data subcarrier of R realisations; nonzero if any is singular. */
 int orc_precode_all(const orc_dims *d, int R, const cplx *H, cplx *W, double *alpha)
 {
     const long nb = (long)R * d->N_d;
@@ -228,6 +229,7 @@ static void cnn_input(const orc_dims *d, const cnn_geo *g, const cplx *s_sym, in
     }
 }
 
+/* Sec. IV-A: the FD-CNN of one symbol for every user (pre / act: the conv layer). */
 void orc_fdcnn(const orc_dims *d, const cplx *s_sym, const double *theta, cplx *s_tilde,
                double *pre, double *act)
 {
@@ -353,6 +355,7 @@ static int check_dims(const orc_dims *d)
     return 0;
 }
 
+/* The forward chain above over S symbols (symbol t on realisation t / S_per_real). */
 int orc_distort(const orc_dims *d, int S, const cplx *s, const cplx *H, const cplx *W,
                 const double *alpha, const cplx *pa, const double *theta, cplx *y, double *metrics)
 {
@@ -494,6 +497,7 @@ static long theta_len(const orc_dims *d)
     return g.o_fb + 2L * d->N_d;
 }
 
+/* Sec. V-A: gradient of the symbol MSE over S symbols by the adjoint above.     */
 int orc_backward(const orc_dims *d, int S, const cplx *s, const cplx *H, const cplx *W,
                  const double *alpha, const cplx *pa, const double *theta, double *grad, double *metrics)
 {
