@@ -726,9 +726,17 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     if (!p) return FDDPD_ERR_ARG;
     const int rc = update_host_impl(p, S, s, H, pa_coef, theta, lr, iters, optimizer, metrics);
     // a call that fails part-way may have copies of the caller's host arrays in flight:
-    // they end before the call returns, so the caller may reuse or free the arrays
-    if (rc != FDDPD_OK && p->cstream) cudaStreamSynchronize(p->cstream);
-    if (rc != FDDPD_OK) cudaStreamSynchronize(p->stream);
+    // they end before the call returns, so the caller may reuse or free the arrays (a
+    // stream being recorded into a graph runs nothing, and is left alone)
+    auto drain = [](cudaStream_t q) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(q, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone)
+            cudaStreamSynchronize(q);
+    };
+    if (rc != FDDPD_OK) {
+        if (p->cstream) drain(p->cstream);
+        drain(p->stream);
+    }
     return rc;
 }
 
