@@ -37,7 +37,8 @@ class Dims(C.Structure):
                 ("first_bin", C.c_int), ("S_per_real", C.c_int),
                 ("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int),
                 ("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int),
-                ("N_conv", C.c_int), ("residual", C.c_int), ("P_T", C.c_double), ("Gx", C.c_int)]
+                ("N_conv", C.c_int), ("residual", C.c_int), ("P_T", C.c_double), ("Gx", C.c_int),
+                ("per_user", C.c_int)]
 
 
 def lib():
@@ -82,7 +83,7 @@ def _p(a: Optional[np.ndarray]):
 
 
 def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, first_bin=None,
-              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, Gx=0) -> Dims:
+              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, Gx=0, per_user=0) -> Dims:
     d = Dims()
     d.M, d.K, d.N, d.N_d = M, K, N, N_d
     d.first_bin = N - N_d // 2 if first_bin is None else first_bin
@@ -93,13 +94,15 @@ def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, firs
     d.L, d.G, d.L_U, d.K_C, d.K_S, d.N_conv, d.residual = L, G, L_U, K_C, K_S, N_conv, residual
     d.P_T = P_T
     d.Gx = Gx
+    d.per_user = per_user
     return d
 
 
 def dims_from_config(cfg, P_T: float, residual: int = 1) -> Dims:
     return make_dims(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.orders, cfg.L, cfg.grid, P_T,
                      S_per_real=cfg.S_per_real, first_bin=cfg.first_bin, L_U=cfg.L_U,
-                     K_C=cfg.K_C, K_S=cfg.K_S, N_conv=cfg.N_conv, residual=residual, Gx=cfg.pa_G)
+                     K_C=cfg.K_C, K_S=cfg.K_S, N_conv=cfg.N_conv, residual=residual, Gx=cfg.pa_G,
+                     per_user=getattr(cfg, "per_user", 0))
 
 
 # -- single stages -----------------------------------------------------------
@@ -162,13 +165,16 @@ def pa_gmp(x, orders: Sequence[int], coef, Gx: int) -> np.ndarray:
 def theta_len(d: Dims) -> int:
     Go = -(-d.G // d.K_S)
     F = d.N_conv * Go * Go
-    return d.N_conv * 2 * d.L_U * d.K_C * d.K_C + d.N_conv + 2 * d.N_d * F + 2 * d.N_d
+    one = d.N_conv * 2 * d.L_U * d.K_C * d.K_C + d.N_conv + 2 * d.N_d * F + 2 * d.N_d
+    return one * (d.K if d.per_user else 1)
 
 
 def fdcnn(d: Dims, s_sym, theta):
     """FD-CNN of one symbol: s_sym [K][N_d] -> (s_tilde [K][N_d], pre [K][F], act [K][F])."""
     s_sym = _c128(s_sym)
     th = _f64(theta)
+    if th.size != theta_len(d):
+        raise ValueError(f"theta has {th.size} entries, expected {theta_len(d)}")
     Go = -(-d.G // d.K_S)
     F = d.N_conv * Go * Go
     st = np.empty_like(s_sym)

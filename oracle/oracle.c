@@ -234,11 +234,13 @@ void orc_fdcnn(const orc_dims *d, const cplx *s_sym, const double *theta, cplx *
                double *pre, double *act)
 {
     cnn_geo g = geometry(d);
-    const double *cw = theta, *cb = theta + g.o_cb, *fw = theta + g.o_fw, *fb = theta + g.o_fb;
     double *X = malloc(sizeof(double) * (size_t)g.Cin * g.G * g.G);
     double *a = malloc(sizeof(double) * (size_t)g.F);
     double *dd = malloc(sizeof(double) * 2 * (size_t)d->N_d);
     for (int u = 0; u < d->K; ++u) {
+        /* one parameter set for all users, or user u's own (theta_u, stacked by user) */
+        const double *th = theta + (d->per_user ? (long)u * (g.o_fb + 2L * d->N_d) : 0);
+        const double *cw = th, *cb = th + g.o_cb, *fw = th + g.o_fw, *fb = th + g.o_fb;
         cnn_input(d, &g, s_sym, u, X);
         for (int o = 0; o < d->N_conv; ++o)
             for (int i = 0; i < g.Go; ++i)
@@ -451,9 +453,11 @@ static void backward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr
     double *gd = malloc(sizeof(double) * 2 * (size_t)Nd);
     double *ga = malloc(sizeof(double) * (size_t)g.F);
     double *X = malloc(sizeof(double) * (size_t)g.Cin * g.G * g.G);
-    double *gcw = grad, *gcb = grad + g.o_cb, *gfw = grad + g.o_fw, *gfb = grad + g.o_fb;
-    const double *fw = theta + g.o_fw;
+    const long len1 = g.o_fb + 2L * Nd;   /* one parameter set */
     for (int u = 0; u < K; ++u) {
+        const long off = d->per_user ? (long)u * len1 : 0;
+        double *gcw = grad + off, *gcb = grad + off + g.o_cb, *gfw = grad + off + g.o_fw, *gfb = grad + off + g.o_fb;
+        const double *fw = theta + off + g.o_fw;
         for (int i = 0; i < Nd; ++i) {
             cplx acc = 0;
             for (int m = 0; m < M; ++m) acc += conj(Wr[((long)i * M + m) * K + u]) * gxh[(long)m * N + bin_of(d, i)];
@@ -494,7 +498,7 @@ static void backward_symbol(const orc_dims *d, const cplx *s_sym, const cplx *Hr
 static long theta_len(const orc_dims *d)
 {
     cnn_geo g = geometry(d);
-    return g.o_fb + 2L * d->N_d;
+    return (g.o_fb + 2L * d->N_d) * (d->per_user ? d->K : 1);
 }
 
 /* Sec. V-A: gradient of the symbol MSE over S symbols by the adjoint above.     */

@@ -32,6 +32,7 @@ typedef struct {
     int G, L_U, K_C, K_S, N_conv, residual;
     double P_T;
     int Gx;   /* PA cross-term length (Eq. 9): 0 = memory polynomial */
+    int per_user;  /* 1: every user u has its own FD-CNN parameters theta_u (Sec. IV-A) */
 } orc_dims;
 
 int  orc_num_threads(void);

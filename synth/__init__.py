@@ -48,6 +48,7 @@ class Config:
     pa_spread: float = 0.10     # real multiplicative spread, uniform in [-spread, spread]
     pa_spread_orders: Optional[Sequence[int]] = None   # None: every coefficient
     pa_G: int = 0               # PA cross-term length of Eq. 9 (0: memory polynomial)
+    per_user: int = 0           # 1: each user its own FD-CNN parameters theta_u (Sec. IV-A)
     ibo_db: float = 6.0
     T: int = 10                 # channel taps
     rho: float = 0.0            # exponential antenna correlation
@@ -266,9 +267,15 @@ def theta_sizes(cfg: Config) -> Dict[str, int]:
 def theta_init(cfg: Config, seed: int, fc_scale: float = 0.0) -> np.ndarray:
     """conv ~ U(+-1/sqrt(fan_in)), conv bias ~ U(+-1/sqrt(fan_in)); the FC weight is
     fc_scale * U(+-1/sqrt(fan_in_fc)) (0 gives the identity predistorter with
-    the residual form) and the FC bias is fc_scale * 0.01 * U(+-1)."""
+    the residual form) and the FC bias is fc_scale * 0.01 * U(+-1).  With per-user
+    parameters the K sets are stacked by user, user u's drawn from its own stream."""
+    if cfg.per_user:
+        return np.concatenate([_theta_one(cfg, Stream(seed, f"theta/user{u}"), fc_scale) for u in range(cfg.K)])
+    return _theta_one(cfg, Stream(seed, "theta"), fc_scale)
+
+
+def _theta_one(cfg: Config, st: "Stream", fc_scale: float) -> np.ndarray:
     sz = theta_sizes(cfg)
-    st = Stream(seed, "theta")
     fan = 2 * cfg.L_U * cfg.K_C * cfg.K_C
     b = 1.0 / math.sqrt(fan)
     cw = b * (2 * st.uniform(sz["conv_w"]) - 1)

@@ -494,3 +494,57 @@ def test_gmp_adjoint_central_differences():
     d0 = oracle.dims_from_config(cfg.with_(pa_G=0), w.P_T)
     y0, _ = oracle.distort(d0, w.s, w.H, W, al, w.pa, th)
     assert np.abs(y1 - y0).max() > 1e-4
+
+
+# --- per-user FD-CNN parameters theta_u (Sec. IV-A) ------------------------------
+def test_per_user_equal_parameters_reduce_to_shared():
+    """K copies of one theta: the same forward chain as the shared network, and the
+    per-user gradient slices add up to the shared gradient (the shared gradient is the
+    sum of every user's contribution)."""
+    cfg = _small_cfg(L_U=1)
+    w, d, W, al = _setup(cfg, fc_scale=0.5)
+    th = w.theta.astype(np.float64)
+    dp = oracle.dims_from_config(cfg.with_(per_user=1), w.P_T)
+    thK = np.tile(th, cfg.K)
+    assert oracle.theta_len(dp) == cfg.K * th.size
+    y, m = oracle.distort(d, w.s, w.H, W, al, w.pa, th)
+    yp, mp = oracle.distort(dp, w.s, w.H, W, al, w.pa, thK)
+    assert np.array_equal(y, yp) and np.array_equal(m, mp)
+    g, _ = oracle.backward(d, w.s, w.H, W, al, w.pa, th)
+    gp, _ = oracle.backward(dp, w.s, w.H, W, al, w.pa, thK)
+    assert np.abs(gp.reshape(cfg.K, -1).sum(axis=0) - g).max() <= 1e-12 * np.abs(g).max()
+
+
+def test_per_user_outputs_follow_their_own_parameters():
+    """A linear PA and perfect CSI pass s_tilde through unchanged (y = s_tilde), so with
+    per-user parameters user u receives exactly the FD-CNN of theta_u applied to its own
+    symbols (L_U = 1), whatever the other users' parameters are."""
+    cfg = _small_cfg(L_U=1, per_user=1)
+    w, d, W, al = _setup(cfg, fc_scale=0.5, pa=synth.linear_pa(cfg))
+    thK = w.theta.astype(np.float64).reshape(cfg.K, -1)
+    assert not np.allclose(thK[0], thK[1])
+    y, _ = oracle.distort(d, w.s, w.H, W, al, w.pa, thK.ravel())
+    d1 = oracle.dims_from_config(cfg.with_(per_user=0), w.P_T)
+    for t in range(cfg.S):
+        for u in range(cfg.K):
+            st, _, _ = oracle.fdcnn(d1, w.s[t], thK[u])
+            assert np.abs(y[t, u] - st[u]).max() < 1e-12
+
+
+def test_per_user_adjoint_central_differences():
+    cfg = _small_cfg(L_U=1, per_user=1)
+    w, d, W, al = _setup(cfg, fc_scale=0.5)
+    th = w.theta.astype(np.float64)
+    g, _ = oracle.backward(d, w.s, w.H, W, al, w.pa, th)
+    one = th.size // cfg.K
+    n_conv = d.N_conv * 2 * d.K_C * d.K_C + d.N_conv
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([u * one + np.arange(n_conv) for u in range(cfg.K)] +
+                         [rng.choice(np.arange(th.size), 60, replace=False)])
+    gmax, eps = np.abs(g).max(), 1e-5
+    for j in idx:
+        tp, tm = th.copy(), th.copy()
+        tp[j] += eps
+        tm[j] -= eps
+        fd = (_loss(d, w, W, al, tp) - _loss(d, w, W, al, tm)) / (2 * eps)
+        assert abs(fd - g[j]) <= 1e-6 * gmax, (j, fd, g[j])
