@@ -20,7 +20,8 @@
  *   - theta is one flat FP32 vector:
  *       conv_w [N_conv][2 L_U][K_C][K_C], conv_b [N_conv],
  *       fc_w   [2 N_d][N_conv Go Go],     fc_b   [2 N_d]        (Go = ceil(G / K_S));
- *     fc rows 0..N_d-1 give the real parts, rows N_d..2N_d-1 the imaginary parts.
+ *     fc rows 0..N_d-1 give the real parts, rows N_d..2N_d-1 the imaginary parts;
+ *     with per-user parameters (fddpd_dpd_desc.per_user) K such vectors, user 0 first.
  *   - metrics (device, double[5]) receive { loss, sum |y - s|^2, sum |s|^2,
  *     guard-bin power of DFT(x^PA), data-bin power of DFT(x^PA) } summed over the call.
  *   - Ownership: the caller owns every data pointer; the plan owns its workspace.
@@ -92,6 +93,9 @@ typedef struct {
     int K_S;          /* stride, 1..G                                                    */
     int N_conv;       /* number of kernels, 1..64                                        */
     int residual;     /* 1: s_tilde = s + FC(.); 0: s_tilde = FC(.) as printed           */
+    int per_user;     /* 0: one theta for all users; 1: user u has its own theta_u (the  */
+                      /* K sets stacked by user; FP32 plans with L_U = 1, else           */
+                      /* FDDPD_ERR_UNSUPPORTED)                                          */
 } fddpd_dpd_desc;
 
 /* Create a plan on `stream` (a cudaStream_t; NULL = legacy default stream).  Validates

@@ -45,7 +45,7 @@ class PaDesc(C.Structure):
 
 class DpdDesc(C.Structure):
     _fields_ = [("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int), ("N_conv", C.c_int),
-                ("residual", C.c_int)]
+                ("residual", C.c_int), ("per_user", C.c_int)]
 
 
 class FddpdError(RuntimeError):
@@ -144,7 +144,7 @@ class Plan:
     def __init__(self, M: int, K: int, N: int, N_d: int, S_per_real: int, max_symbols: int, P_T: float,
                  orders: Sequence[int], L: int, G: int, L_U: int = 1, K_C: int = 3, K_S: int = 1, N_conv: int = 2,
                  residual: int = 1, precision: int = FDDPD_FP32, first_bin: int = -1, stream=None,
-                 pa_G: int = 0):
+                 pa_G: int = 0, per_user: int = 0):
         self._lib = load()
         d = Dims(M, K, N, N_d, first_bin, S_per_real, max_symbols, precision, float(P_T))
         pa = PaDesc()
@@ -153,7 +153,7 @@ class Plan:
             pa.orders[i] = int(p)
         pa.L = L
         pa.G = pa_G
-        dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual)
+        dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual, per_user)
         h = C.c_void_p()
         rc = self._lib.fddpd_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(dpd), _stream_ptr(stream))
         if rc:
@@ -168,7 +168,7 @@ class Plan:
                     residual: int = 1, stream=None) -> "Plan":
         return cls(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.S_per_real, max_symbols or cfg.S, P_T, cfg.orders, cfg.L,
                    cfg.grid, cfg.L_U, cfg.K_C, cfg.K_S, cfg.N_conv, residual, precision, cfg.first_bin, stream,
-                   getattr(cfg, "pa_G", 0))
+                   getattr(cfg, "pa_G", 0), getattr(cfg, "per_user", 0))
 
     def _check(self, rc: int):
         if rc:

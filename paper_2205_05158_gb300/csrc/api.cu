@@ -30,6 +30,7 @@ struct fddpd_plan {
     c32 *st, *gy, *gst, *xh, *Xpa, *tw;
     void *zf_scratch;
     float *act, *gpre, *partials, *grad, *adam_m, *adam_v;
+    c32 *pu_s, *pu_st;  // per-user parameters: one user's symbols and FD-CNN output [S][N_d]
     double *met;
     int *status;        // [0] singular subcarriers of the last precode, [1] sticky device timeouts
     int *status_host;
@@ -133,6 +134,9 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (dpd->K_S < 1 || dpd->K_S > dpd->G) return set_err(nullptr, FDDPD_ERR_ARG, "K_S=%d", dpd->K_S);
     if (dpd->N_conv < 1 || dpd->N_conv > 64) return set_err(nullptr, FDDPD_ERR_ARG, "N_conv=%d outside 1..64", dpd->N_conv);
     if (dpd->residual != 0 && dpd->residual != 1) return set_err(nullptr, FDDPD_ERR_ARG, "residual must be 0 or 1");
+    if (dpd->per_user != 0 && dpd->per_user != 1) return set_err(nullptr, FDDPD_ERR_ARG, "per_user must be 0 or 1");
+    if (dpd->per_user && (d->precision != FDDPD_FP32 || dpd->L_U != 1))
+        return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "per-user parameters need an FP32 plan and L_U = 1");
     return FDDPD_OK;
 }
 
@@ -155,7 +159,7 @@ static Geo make_geo(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     g.off_cb = g.n_convw;
     g.off_fw = g.off_cb + g.N_conv;
     g.off_fb = g.off_fw + 2L * g.N_d * g.F;
-    g.theta_len = g.off_fb + 2L * g.N_d;
+    g.theta_len = (g.off_fb + 2L * g.N_d) * (dpd->per_user ? g.K : 1);   // per user: K sets stacked by user
     g.P_T = d->P_T;
     return g;
 }
@@ -209,6 +213,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
     }
     if (d->precision == FDDPD_BF16) o_xt = take(4 * (size_t)S * g.M * g.N);
+    const size_t o_pu = dpd->per_user ? take(2 * sizeof(c32) * (size_t)S * g.N_d) : 0;
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
     if (e != cudaSuccess) {
@@ -223,6 +228,10 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
     p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
     p->zf_scratch = b + o_zf;
+    if (dpd->per_user) {
+        p->pu_s = (c32 *)(b + o_pu);
+        p->pu_st = p->pu_s + (size_t)S * g.N_d;
+    }
     if (p->p16) {
         p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
         p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
@@ -422,6 +431,14 @@ static int pass_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, const
     return FDDPD_OK;
 }
 
+// The geometry of one user's FD-CNN (per-user parameters): the same network, K = 1.
+static Geo one_user(const Geo &g) {
+    Geo g1 = g;
+    g1.K = 1;
+    g1.theta_len = g.theta_len / g.K;
+    return g1;
+}
+
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
                        const c32 *pa, const float *theta, c32 *y, c32 *gy, const Pass *ps = nullptr) {
     const Geo &g = p->g;
@@ -440,6 +457,20 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
                  fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
                                     p->fbi, g.N_d, g.residual, p->status + 1, st));
+    } else if (p->dpd.per_user) {
+        // user u's own network theta_u on its own symbols (L_U = 1): the one-user kernels
+        // on user u's column of s, gathered and scattered by strided copies
+        const Geo g1 = one_user(g);
+        const long len1 = g.theta_len / g.K;
+        const size_t row = sizeof(c32) * g.N_d, pitch = row * g.K;
+        for (int u = 0; u < g.K; ++u) {
+            const float *th = theta + u * len1;
+            float *act = p->act + (long)u * S * g.F;
+            FD_CK(p, cudaMemcpy2DAsync(p->pu_s, row, s + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
+            FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g1, S, p->pu_s, th, act, st));
+            FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g1, S, act, th, p->pu_s, p->pu_st, st));
+            FD_CK(p, cudaMemcpy2DAsync(p->st + (long)u * g.N_d, pitch, p->pu_st, row, row, S, cudaMemcpyDeviceToDevice, st));
+        }
     } else {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
@@ -498,6 +529,28 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         const fdk::GemmArgs gdx{p->gd16, p->fcwT16, cols, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->ldF, p->act16, p->ldF, p->status + 1, st));
+    } else if (p->dpd.per_user) {
+        // per user: user u's slices of the activations and of theta / grad (the bias
+        // gradients were cleared above for user 0 only)
+        const Geo g1 = one_user(g);
+        const long len1 = g.theta_len / g.K;
+        const size_t row = sizeof(c32) * g.N_d, pitch = row * g.K;
+        for (int u = 0; u < g.K; ++u) {
+            const float *th = theta + u * len1;
+            float *gr = grad + u * len1;
+            const float *act = p->act + (long)u * S * g.F;
+            float *gpre = p->gpre + (long)u * S * g.F;
+            const float *gdu = reinterpret_cast<const float *>(p->pu_st);
+            if (first && u > 0) FD_CK(p, cudaMemsetAsync(gr + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
+            FD_CK(p, cudaMemcpy2DAsync(p->pu_st, row, p->gst + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
+            FD_CK(p, cudaMemcpy2DAsync(p->pu_s, row, s + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
+            FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g1, S, gdu, act, gr, !first, st));
+            FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g1, S, gdu, gr, st));
+            FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g1, S, gdu, th, act, gpre, st));
+            FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g1, S, p->pu_s, gpre, g.F, p->partials, st));
+            FD_CK(p, fdk::conv_reduce(g1, S, p->partials, gr, !first, st));
+        }
+        return FDDPD_OK;
     } else {
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, !first, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));

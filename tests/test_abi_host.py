@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 def _create(lib, **over):
     d = dict(M=16, K=2, N=64, N_d=48, first_bin=-1, S_per_real=10, max_symbols=10, precision=0, P_T=10.0)
     pa = dict(orders=[1, 3], L=0, G_pa=0)
-    dpd = dict(G=7, L_U=1, K_C=3, K_S=1, N_conv=2, residual=1)
+    dpd = dict(G=7, L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, per_user=0)
     for k, v in over.items():
         (d if k in d else pa if k in pa else dpd)[k] = v
     dims = binding.Dims(d["M"], d["K"], d["N"], d["N_d"], d["first_bin"], d["S_per_real"], d["max_symbols"],
@@ -54,7 +54,8 @@ def _create(lib, **over):
         pad.orders[i] = p
     pad.L = pa["L"]
     pad.G = pa["G_pa"]
-    dd = binding.DpdDesc(dpd["G"], dpd["L_U"], dpd["K_C"], dpd["K_S"], dpd["N_conv"], dpd["residual"])
+    dd = binding.DpdDesc(dpd["G"], dpd["L_U"], dpd["K_C"], dpd["K_S"], dpd["N_conv"], dpd["residual"],
+                         dpd["per_user"])
     h = C.c_void_p()
     rc = lib.fddpd_plan_create(C.byref(h), C.byref(dims), C.byref(pad), C.byref(dd), None)
     return rc, h
@@ -76,6 +77,9 @@ def _create(lib, **over):
     # cross terms of Eq. 9: G in 0..2, none for the clipping PA
     (dict(G_pa=3), binding.FDDPD_ERR_ARG), (dict(G_pa=-1), binding.FDDPD_ERR_ARG),
     (dict(orders=[0], G_pa=1), binding.FDDPD_ERR_ARG),
+    # per-user FD-CNN parameters: 0 or 1, FP32 plans with one input user each
+    (dict(per_user=2), binding.FDDPD_ERR_ARG), (dict(per_user=1, precision=1), binding.FDDPD_ERR_UNSUPPORTED),
+    (dict(per_user=1, L_U=2), binding.FDDPD_ERR_UNSUPPORTED),
 ])
 def test_plan_rejects_bad_descriptors(lib, over, code):
     rc, h = _create(lib, **over)
