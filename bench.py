@@ -38,8 +38,11 @@ SER_SNR_DB = 30.0   # mean per-subcarrier SNR at the users for the SER line
 WORKLOAD = ("m128_k16_n2048: M=128 K=16 N=2048 N_d=1200 256-QAM rho=0.5, 14 symbols/realisation, orders 1,3,5 taps 0..3, "
             "FD-CNN G=35 N_conv=2 K_C=3")
 LR = 1e-4
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
+ARITHMETIC = ("ZF Gram FP32, Cholesky + triangular inverse FP64; FD-CNN dense layer, precoding and combining "
+              "on tcgen05 with BF16 operands and FP32 accumulation; FFT, PA and its adjoint FP32 with x(t) "
+              "recomputed in the adjoint")
+FAST_ARITHMETIC = ("as the headline but Cholesky + triangular inverse FP32 and x(t) kept from the forward in BF16 "
+                   "(FDDPD_OPT_FACTOR_FP64 = 0, FDDPD_OPT_KEEP_PA_INPUT = 1)")
 
 
 def parse():
@@ -55,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-fast-variant", action="store_true")
     return ap.parse_args()
 
 
@@ -67,10 +71,18 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def alu_peaks(fd, stream):
+    """FP32 and FP64 pipe peaks measured now by the library's FMA loop (TFLOP/s): the
+    FP32 peak is the better of the scalar and the packed-pair fma loops."""
+    p = {k: fd.alu_peak(k, stream) for k in ("fp32", "fp32x2", "fp64")}
+    p["fp32_peak"] = max(p["fp32"], p["fp32x2"])
+    return p
+
+
 # ---------------------------------------------------------------------------
 # algorithmic work per launch of each stage (bytes or flops)
 # ---------------------------------------------------------------------------
-def stage_work(cfg, S: int, prec: str):
+def stage_work(cfg, S: int, prec: str, fp64_factor: bool = True, kept_xt: bool = False):
     M, K, Nd, F, L_U = cfg.M, cfg.K, cfg.N_d, cfg.N_conv * (-(-cfg.grid // cfg.K_S)) ** 2, cfg.L_U
     R = -(-S // cfg.S_per_real)
     cols = S * K
@@ -84,7 +96,7 @@ def stage_work(cfg, S: int, prec: str):
         # (Cholesky + triangular inverse, 4 FMA = 8 flop each), FP64 in FP32 plans and FP32
         # in 16-bit plans; apply: read H, write W
         "zf_gram": ("hbm", R * Nd * K * M * (c8 + (0 if prec == "fp32" else 4))),
-        "zf_factor": ("fp64" if prec == "fp32" else "alu", R * Nd * 8.0 * (K ** 3 / 3.0)),
+        "zf_factor": ("fp64" if (prec == "fp32" or fp64_factor) else "alu", R * Nd * 8.0 * (K ** 3 / 3.0)),
         "zf_apply": ("hbm", R * Nd * K * M * (2 * c8 + (0 if prec == "fp32" else 4)) + R * Nd * 4),
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),
         "fc_fwd": (fc_bound, 2.0 * cols * 2 * Nd * F),
@@ -96,7 +108,10 @@ def stage_work(cfg, S: int, prec: str):
         "fftpa_fwd": ("alu", S * M * (2 * 5.0 * cfg.N * math.log2(cfg.N) + cfg.N * (cfg.L + 1) * 19.0)),
         "combine": ("hbm", R * Nd * K * M * opb + S * M * Nd * ab + 2 * S * K * Nd * c8),
         "adj_combine": ("hbm", R * Nd * K * M * opb + S * K * Nd * c8 + S * M * Nd * ab),
-        "fftpa_adj": ("alu", S * M * (2 * 5.0 * cfg.N * math.log2(cfg.N) + cfg.N * (24.0 * (cfg.L + 1) + 26.0))),
+        # adjoint: the transform of g_X and the final one, plus (x(t) recomputed) the inverse
+        # transform of x_hat
+        "fftpa_adj": ("alu", S * M * ((2 if kept_xt else 3) * 5.0 * cfg.N * math.log2(cfg.N)
+                                      + cfg.N * (24.0 * (cfg.L + 1) + 26.0))),
         "adj_precode": ("hbm", R * Nd * M * K * opb + S * M * Nd * ab + S * K * Nd * c8),
         "fc_bwd_w": (fc_bound, 2.0 * 2 * Nd * F * cols),
         "fc_bwd_b": ("hbm", cols * 2 * Nd * 4),
@@ -104,6 +119,31 @@ def stage_work(cfg, S: int, prec: str):
         "conv_bwd": ("hbm", cols * (Nd * c8 * L_U + F * 4)),
         "step": ("hbm", 3 * theta_len * 4),
     }
+
+
+def roofline_of(bound, amount, per_launch_ms, mp, src, alu):
+    """(achieved, peak, unit, peak source) of `amount` bytes / flops done in per_launch_ms."""
+    sec = per_launch_ms / 1e3
+    if bound == "hbm":
+        return amount / sec / 1e9, mp["hbm_gbs"], "GB/s", f"{src} hbm_gbs (copy)"
+    if bound == "tensor":
+        return amount / sec / 1e12, mp["bf16_tflops_sustained"], "TFLOP/s", f"{src} bf16_tflops_sustained"
+    if bound == "fp64":
+        return amount / sec / 1e12, alu["fp64"], "TFLOP/s", "measured now: FP64 fma loop (fddpd_alu_peak)"
+    return (amount / sec / 1e12, alu["fp32_peak"], "TFLOP/s",
+            "measured now: FP32 fma loop, the better of scalar and packed-pair (fddpd_alu_peak)")
+
+
+def step_lower_bounds(work, mp, alu):
+    """Milliseconds each resource needs for the whole step's algorithmic work (the stages'
+    bytes through HBM as this staged design moves them; flops per pipe)."""
+    tot = {"hbm": 0.0, "tensor": 0.0, "alu": 0.0, "fp64": 0.0}
+    for bound, amount in work.values():
+        tot[bound] += amount
+    return {"hbm": tot["hbm"] / (mp["hbm_gbs"] * 1e9) * 1e3,
+            "tensor": tot["tensor"] / (mp["bf16_tflops_sustained"] * 1e12) * 1e3,
+            "fp32_alu": tot["alu"] / (alu["fp32_peak"] * 1e12) * 1e3,
+            "fp64": tot["fp64"] / (alu["fp64"] * 1e12) * 1e3}
 
 
 def source_files(stage: str, prec: str):
@@ -294,6 +334,7 @@ def run_ours(args):
     w = synth.make_workload(cfg, fc_scale=0.05)
     R = w.H.shape[0]
     stream = torch.cuda.current_stream()
+    alu = alu_peaks(fd, stream)
     plan = fd.Plan.from_config(cfg, w.P_T, max_symbols=S, precision=prec, stream=stream)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     s, H, pa, theta0 = dev(w.s), dev(w.H), dev(w.pa), dev(w.theta)
@@ -368,24 +409,19 @@ def run_ours(args):
     stage, (tot_ms, cnt) = max(((k, v) for k, v in prof.items() if k in work and v[1] > 0), key=lambda kv: kv[1][0])
     bound, amount = work[stage]
     per_launch_ms = tot_ms / cnt
-    if bound == "hbm":
-        achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e9, mp["hbm_gbs"], "GB/s"
-        peak_src = f"{src} hbm_gbs (copy)"
-    elif bound == "fp64":
-        peak = NUM_SMS * 2 * 2 * mp.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved, unit = amount / (per_launch_ms / 1e3) / 1e12, "TFLOP/s"
-        peak_src = f"derived: {NUM_SMS} SMs x 2 FP64 FMA/clk x 2 x {mp.get('sm_max_mhz', 2070.0):.0f} MHz"
-    elif bound == "tensor":
-        achieved, peak, unit = amount / (per_launch_ms / 1e3) / 1e12, mp["bf16_tflops_sustained"], "TFLOP/s"
-        peak_src = f"{src} bf16_tflops_sustained"
-    else:
-        clk_mhz = mp.get("sm_max_mhz", 2070.0)
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
-        achieved, unit = amount / (per_launch_ms / 1e3) / 1e12, "TFLOP/s"
-        peak_src = f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz"
+    achieved, peak, unit, peak_src = roofline_of(bound, amount, per_launch_ms, mp, src, alu)
     traffic = measured_traffic(stage, prec_name)
-    stages_out = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                  for k, v in prof.items() if v[1] > 0}
+    stages_out = {}
+    for k, v in prof.items():
+        if v[1] <= 0:
+            continue
+        stages_out[k] = {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+        if k in work:
+            a, pk, u, _ = roofline_of(work[k][0], work[k][1], v[0] / v[1], mp, src, alu)
+            stages_out[k].update({"bound": work[k][0], "achieved": a, "unit": u, "frac": a / pk})
+    # step-level roofline: the largest resource lower bound of the whole step over its time
+    lb = step_lower_bounds(work, mp, alu)
+    zf_res = plan.zf_residual(H, W, 1)   # the final FP64 check of H_k W_k = I, all subcarriers
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -393,12 +429,17 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": WORKLOAD,
                       "symbols_per_step": S, "realisations_per_step": R, "precision": prec_name,
+                      "arithmetic": ARITHMETIC if prec_name == "bf16" else "default options of the plan",
                       "step": "ZF + FD-CNN + precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
                       "l2": "inputs larger than L2 (H 2.8 GB), no flush",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": {"kernel": stage, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                         "work_per_launch": amount},
+           "step_roofline": {"lower_bounds_ms": lb, "binding": max(lb, key=lb.get),
+                             "frac": max(lb.values()) / ms},
+           "alu_peaks_tflops": alu,
+           "zf_residual_fp64": zf_res,
            "stages": stages_out,
            "forward_only": {"value": world * S / (fwd_ms / 1e3), "unit": UNIT, "ms": fwd_ms},
            "quality": {"evm_db": evm_db, "acpr_db": acpr_db},
@@ -406,6 +447,40 @@ def run_ours(args):
                    "ser": float(sc[0]) / max(1, int(sc[1])), "symbols": int(sc[1])},
            "gpu_launches": launches,
            "clocks": clk}
+
+    # the faster arithmetic beside the headline: FP32 Gram factor and x(t) kept in BF16
+    if prec_name == "bf16" and not args.no_fast_variant:
+        plan.set_option(fd.FDDPD_OPT_FACTOR_FP64, 0)
+        plan.set_option(fd.FDDPD_OPT_KEEP_PA_INPUT, 1)
+        thf = theta0.clone()
+        metf = torch.zeros(5, dtype=torch.float64, device="cuda")
+
+        def stepf():
+            plan.precode(H, W, al)
+            plan.update(s, H, W, al, pa, thf, LR, 1, fd.FDDPD_GD, metf)
+
+        for _ in range(max(3, args.warmup)):
+            stepf()
+        torch.cuda.synchronize()
+        plan.profile(True)
+        plan.profile_read()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            stepf()
+        v1.record(stream)
+        torch.cuda.synchronize()
+        proff = plan.profile_read()
+        plan.profile(False)
+        msf = max_over_ranks(v0.elapsed_time(v1) / args.steps, dist, "cuda")
+        plan.distort(s, H, W, al, pa, theta0, None, metf)
+        mf = metf.cpu().numpy()
+        out["fast_variant"] = {"arithmetic": FAST_ARITHMETIC, "value": job_rate(world, S, msf / 1e3), "unit": UNIT,
+                               "ms_per_step": msf, "evm_db": 10 * math.log10(mf[1] / mf[2]),
+                               "acpr_db": 10 * math.log10(mf[3] / mf[4]),
+                               "stages_ms": {k: v[0] / args.steps for k, v in proff.items() if v[1] > 0}}
+        plan.set_option(fd.FDDPD_OPT_FACTOR_FP64, 1)
+        plan.set_option(fd.FDDPD_OPT_KEEP_PA_INPUT, 0)
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     if not args.no_e2e:

@@ -133,8 +133,19 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *       fddpd_update_host moves a batch and overlaps its copies with the step; 1 copies
  *       everything first.  The result does not depend on it beyond the order of FP32
  *       sums over symbols.
+ *   FDDPD_OPT_KEEP_PA_INPUT  0 (default): the adjoint recomputes the time-domain PA input
+ *       x(t) = IDFT(x_hat) in FP32 from x_hat, so the PA derivative is evaluated at the
+ *       FP32 signal and nothing time-domain is stored between the passes; 1: BF16 plans
+ *       on the tensor-core path keep x(t) from the forward of a training pass as BF16
+ *       [max_symbols][M][N] (allocated by this call; NOMEM if that fails) and the
+ *       adjoint reads it instead of a third transform (faster; the PA derivative then
+ *       sees x rounded to 8 significant bits).  Ignored by FP32 and FP16 plans.
+ *   FDDPD_OPT_FACTOR_FP64  1 (default): the Cholesky factor and triangular inverse of
+ *       every Gram matrix run in FP64; 0: in FP32 in 16-bit plans (whose W is rounded to
+ *       16 bits afterwards; faster).  FP32 plans always factor in FP64.
  * Returns FDDPD_ERR_ARG for an unknown option or value. */
-enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2 };
+enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2, FDDPD_OPT_KEEP_PA_INPUT = 3,
+       FDDPD_OPT_FACTOR_FP64 = 4 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
 
 /* Transmit power P_T of Eq. (6) for the plan's next fddpd_precode / fddpd_update_host
@@ -155,13 +166,22 @@ int fddpd_invalidate_operands(fddpd_plan *plan);
  *   W     [R][N_d][M][K]  out: H_k^H (H_k H_k^H)^{-1}
  *   alpha [R][N_d]        out: sqrt(P_T / tr((H_k H_k^H)^{-1}))
  * The Gram matrix is accumulated in FP32 and factorised (Cholesky) and inverted in
- * FP64 (in FP32 in 16-bit plans, whose W is rounded to 16 bits).  16-bit plans also keep 16-bit copies of W and H for the next distort /
+ * FP64 (in FP32 in 16-bit plans set so by FDDPD_OPT_FACTOR_FP64 = 0).  16-bit plans also
+ * keep 16-bit copies of W and H for the next distort /
  * backward / update calls with these same H and W pointers (calls with other pointers
  * re-pack from the FP32 arrays; after H or W is rewritten in place by other means than
  * this call, call fddpd_invalidate_operands).  R <= ceil(max_symbols /
  * S_per_real).  Errors: ARG, LAYOUT, SINGULAR (reported after the kernel completes:
  * this call synchronises the stream once to read the status word).              */
 int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha);
+
+/* FP64 check of the zero-forcing identity of Eq. (6) on precoders already produced:
+ *   out (device double, 8-byte aligned) = max over the subcarriers b = 0, every,
+ *   2 every, ... of the R N_d ones of max_{i,j} |(H_b W_b - I_K)_{ij}|,
+ * with H, W laid out as for fddpd_precode and every product and sum in FP64.  About
+ * K^2 M complex FP64 multiply-adds per checked subcarrier (the final check of a run,
+ * not a per-step stage).  Asynchronous on the plan's stream.  Errors: ARG, LAYOUT.  */
+int fddpd_zf_residual(fddpd_plan *plan, int R, const fddpd_c32 *H, const fddpd_c32 *W, int every, double *out);
 
 /* Forward chain over S symbols (running mode of the FD-DPD, Sec. III-A and IV).
  *   s       [S][K][N_d]       in : unit-power QAM symbols of the data bins
@@ -177,8 +197,8 @@ int fddpd_distort(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *
 
 /* Gradient of the loss over the S symbols with respect to theta (Sec. V-A), by the
  * hand-written adjoint of the whole chain, after a forward pass of its own; the
- * time-domain PA inputs of the adjoint are recomputed from x_hat, or, in BF16 plans
- * on the tensor-core path, kept by that forward pass in BF16.
+ * time-domain PA inputs of the adjoint are recomputed from x_hat (or, in BF16 plans set
+ * so by FDDPD_OPT_KEEP_PA_INPUT, kept by that forward pass in BF16).
  * grad [theta_len] out (overwritten).  metrics as distort.                        */
 int fddpd_backward(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
                    const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
@@ -195,6 +215,15 @@ int fddpd_update(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H
 
 /* Zero the Adam moments and step counter. */
 int fddpd_reset_optimizer(fddpd_plan *plan);
+
+/* Checkpoint / resume of a training run (Sec. V-A trains theta over many steps): the
+ * Adam first and second moments m, v [theta_len] FP32 and the step counter t.  theta
+ * itself is the caller's array.  m, v may be host or device memory (any pointer the CUDA
+ * runtime can address); both calls synchronise the plan's stream.  Restoring a state
+ * and continuing gives the steps an uninterrupted run would take (up to the order of
+ * FP32 sums).  Errors: ARG (null pointer, t < 0), LAYOUT, CUDA.                      */
+int fddpd_get_optimizer_state(fddpd_plan *plan, float *m, float *v, long long *t);
+int fddpd_set_optimizer_state(fddpd_plan *plan, const float *m, const float *v, long long t);
 
 /* One training step from HOST memory (Sec. V-A with a new channel per mini-batch):
  * copies s [S][K][N_d], H [R][N_d][K][M] (R = ceil(S / S_per_real)), pa_coef and theta
@@ -296,10 +325,16 @@ int fddpd_sync(fddpd_plan *plan);
 int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
                   int ab_type, int splits, void *stream);
 
+/* Arithmetic peak of this GPU's FP32 or FP64 pipe in TFLOP/s (*tflops, host), measured by
+ * an FMA loop over a grid of resident CTAs on every SM and timed with CUDA events on
+ * `stream` (synchronised): kind 0 scalar FP32 fma, 1 packed FP32-pair fma (fma.rn.f32x2),
+ * 2 FP64 fma.  Each measurement runs for some tens of milliseconds.  No counterpart in
+ * the paper: the denominator of the FP32 / FP64 rooflines.  Errors: ARG, CUDA.       */
+int fddpd_alu_peak(int kind, double *tflops, void *stream);
+
 /* Zero-forcing precoder (same result as fddpd_precode) for callers that cannot allocate
  * device memory, e.g. a real-time baseband pipeline that reserves all device memory up
- * front and forbids cudaMalloc on its processing path.  The paper has no counterpart;
- * this is a deployment variant of Eq. (6).
+ * front and forbids cudaMalloc on its processing path.  The paper has no counterpart.
  *   H [R][N_d][K][M] in, W [R][N_d][M][K] out, alpha [R][N_d] out: device memory owned by
  *   the caller, as for fddpd_precode (data subcarriers only; no plan is needed).
  * No device memory is allocated: the scratch of the ZF kernels is one static device

@@ -21,6 +21,8 @@ FDDPD_FP32, FDDPD_BF16, FDDPD_FP16 = 0, 1, 2
 FDDPD_GD, FDDPD_ADAM = 0, 1
 FDDPD_OPT_TENSOR_CONTRACTIONS = 1
 FDDPD_OPT_HOST_CHUNKS = 2
+FDDPD_OPT_KEEP_PA_INPUT = 3
+FDDPD_OPT_FACTOR_FP64 = 4
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
@@ -28,7 +30,8 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_profile_enable", "fddpd_profile_read", "fddpd_stage_name", "fddpd_launch_count",
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
             "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune",
-            "fddpd_set_power", "fddpd_invalidate_operands"]
+            "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak",
+            "fddpd_get_optimizer_state", "fddpd_set_optimizer_state"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
@@ -106,11 +109,16 @@ def load(build_if_missing: bool = True):
     L.fddpd_graph_end.argtypes = [P, C.POINTER(C.c_void_p)]
     L.fddpd_graph_launch.argtypes = [P, P]
     L.fddpd_graph_destroy.argtypes = [P]
+    L.fddpd_zf_residual.argtypes = [P, I, P, P, I, P]
+    L.fddpd_alu_peak.argtypes = [I, C.POINTER(C.c_double), P]
+    L.fddpd_get_optimizer_state.argtypes = [P, P, P, C.POINTER(C.c_longlong)]
+    L.fddpd_set_optimizer_state.argtypes = [P, P, P, C.c_longlong]
     for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
               "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power",
-              "fddpd_invalidate_operands"):
+              "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak", "fddpd_get_optimizer_state",
+              "fddpd_set_optimizer_state"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -223,6 +231,41 @@ class Plan:
     def reset_optimizer(self):
         self._check(self._lib.fddpd_reset_optimizer(self._h))
 
+    def checkpoint(self, theta) -> dict:
+        """Training state for a later resume: theta (copied from the caller's tensor) and
+        the plan's Adam moments and step counter (fddpd_get_optimizer_state), as numpy."""
+        import numpy as np
+        n = self.theta_len
+        m = np.empty(n, dtype=np.float32)
+        v = np.empty(n, dtype=np.float32)
+        t = C.c_longlong(0)
+        self._check(self._lib.fddpd_get_optimizer_state(self._h, m.ctypes.data, v.ctypes.data, C.byref(t)))
+        return {"theta": theta.detach().cpu().numpy().copy(), "adam_m": m, "adam_v": v, "adam_t": int(t.value)}
+
+    def restore(self, ckpt: dict, theta):
+        """Resume from `checkpoint`: theta is overwritten in place, the moments and the
+        step counter go back into the plan (fddpd_set_optimizer_state)."""
+        import numpy as np
+        import torch
+        m = np.ascontiguousarray(ckpt["adam_m"], dtype=np.float32)
+        v = np.ascontiguousarray(ckpt["adam_v"], dtype=np.float32)
+        if m.size != self.theta_len or v.size != self.theta_len or ckpt["theta"].size != self.theta_len:
+            raise ValueError("checkpoint of a plan with another theta length")
+        self._check(self._lib.fddpd_set_optimizer_state(self._h, m.ctypes.data, v.ctypes.data, int(ckpt["adam_t"])))
+        theta.copy_(torch.from_numpy(np.ascontiguousarray(ckpt["theta"], dtype=np.float32)))
+
+    @staticmethod
+    def save_checkpoint(path: str, ckpt: dict):
+        import numpy as np
+        np.savez(path, theta=ckpt["theta"], adam_m=ckpt["adam_m"], adam_v=ckpt["adam_v"],
+                 adam_t=np.int64(ckpt["adam_t"]))
+
+    @staticmethod
+    def load_checkpoint(path: str) -> dict:
+        import numpy as np
+        with np.load(path) as z:
+            return {"theta": z["theta"], "adam_m": z["adam_m"], "adam_v": z["adam_v"], "adam_t": int(z["adam_t"])}
+
     def set_option(self, option: int, value: int):
         """fddpd_set_option, e.g. FDDPD_OPT_TENSOR_CONTRACTIONS = 0 to run the per-subcarrier
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
@@ -284,6 +327,16 @@ class Plan:
                                              _ptr(pa, torch.complex64), _ptr(theta, torch.float32), int(reps), ms))
         return float(ms[0]), float(ms[1])
 
+    def zf_residual(self, H, W, every: int = 1, out=None, R: Optional[int] = None):
+        """fddpd_zf_residual: max over every `every`-th subcarrier of max |H_k W_k - I| in
+        FP64; returns the host float (or writes the device float64[1] `out`, async)."""
+        import torch
+        R = H.shape[0] if R is None else R
+        o = torch.zeros(1, dtype=torch.float64, device=H.device) if out is None else out
+        self._check(self._lib.fddpd_zf_residual(self._h, R, _ptr(H, torch.complex64), _ptr(W, torch.complex64),
+                                                int(every), _ptr(o, torch.float64)))
+        return float(o.item()) if out is None else None
+
     def ser(self, y, s, alpha, Q: int, N0: float, seed: int, counts, S: Optional[int] = None):
         """fddpd_ser: adds (errors, symbols compared) of the noisy, equalised symbols
         y + w / alpha against s to `counts` (a device int64[2] tensor; asynchronous)."""
@@ -329,6 +382,17 @@ class Plan:
         """Synchronise the plan's stream; raises on a recorded device-side timeout."""
         self._check(self._lib.fddpd_sync(self._h))
 
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fddpd_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 def tc_gemm(A, B, C, splits: int = 1, stream=None):
     """C (+)= A @ B.T on the tensor cores; A [M][lda], B [N][ldb] bf16/fp16 CUDA tensors
@@ -346,16 +410,19 @@ def tc_gemm(A, B, C, splits: int = 1, stream=None):
     if rc:
         raise FddpdError(rc, L.fddpd_last_error(None).decode())
 
-    def close(self):
-        if getattr(self, "_h", None) is not None and self._h.value:
-            self._lib.fddpd_plan_destroy(self._h)
-            self._h = C.c_void_p()
 
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+ALU_PEAK_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def alu_peak(kind: str, stream=None) -> float:
+    """fddpd_alu_peak: measured FMA-loop peak in TFLOP/s of the FP32 pipe (kind "fp32",
+    scalar fma; "fp32x2", packed pair fma) or of the FP64 pipe ("fp64")."""
+    L = load()
+    out = C.c_double(0.0)
+    rc = L.fddpd_alu_peak(ALU_PEAK_KINDS[kind], C.byref(out), _stream_ptr(stream))
+    if rc:
+        raise FddpdError(rc, L.fddpd_last_error(None).decode())
+    return out.value
 
 
 def precode_noalloc(H, W, alpha, P_T: float, stream=None):

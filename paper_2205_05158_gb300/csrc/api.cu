@@ -41,8 +41,11 @@ struct fddpd_plan {
     float *fbi;                    // fc_b in the dense layer's interleaved output order
     int kind16;                    // OUT_BF16 or OUT_F16: storage of the H / W copies
     bool tc_bin;                   // per-subcarrier contractions on the tensor cores
+    bool keep_xt;                  // BF16 planes: the forward keeps x(t) for the adjoint (FDDPD_OPT_KEEP_PA_INPUT)
+    bool fp64_factor;              // Cholesky + triangular inverse in FP64 (FDDPD_OPT_FACTOR_FP64)
     void *H16, *W16;               // [R_max][N_d][K][M] and [R_max][N_d][M][K]
-    void *xt16;                    // BF16 plans: time-domain PA input [S][M][N], forward -> adjoint
+    void *xt16;                    // kept time-domain PA input [S][M][N] (BF16), allocated by the option
+    size_t gxh_off;                // BF16 planes, recomputed x(t): g_xhat's offset in the X^PA buffer
     const void *pk_H, *pk_W;       // the FP32 arrays the copies were made from
     int pk_R;
     long adam_t;
@@ -184,7 +187,11 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     const size_t o_st = take(sizeof(c32) * cols * g.N_d), o_gy = take(sizeof(c32) * cols * g.N_d),
                  o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))),
-                 o_X = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))), o_tw = take(sizeof(c32) * g.N),
+                 // X^PA buffer: the FP32 plane, or (BF16 planes) the blocked X^PA, or the BF16 rows
+                 // of g_X followed by the blocked g_xhat of an adjoint that recomputes x(t)
+                 gxh_off = (4 * (size_t)S * g.M * g.N_d + 255) & ~size_t(255),
+                 o_X = take(std::max(sizeof(c32) * S * g.M * g.N_d, gxh_off + fdk::blk_plane_bytes(g, S))),
+                 o_tw = take(sizeof(c32) * g.N),
                  o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * ((g.F + 7) / 8 * 8)),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
@@ -192,6 +199,9 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     const size_t o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N_d));
     p->p16 = d->precision != FDDPD_FP32;
     p->tc_bin = true;
+    p->keep_xt = false;
+    p->fp64_factor = true;
+    p->gxh_off = gxh_off;
     p->host_chunks = 7;
     auto r8 = [](long v) { return (v + 7) / 8 * 8; };
     p->ldF = r8(g.F);
@@ -207,12 +217,11 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_wT = take(2 * (size_t)g.F * p->ld2N);
         o_fbi = take(sizeof(float) * 2 * (size_t)g.N_d);
     }
-    size_t o_h16 = 0, o_wq16 = 0, o_xt = 0;
+    size_t o_h16 = 0, o_wq16 = 0;
     if (p->p16) {
         o_h16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
         o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
     }
-    if (d->precision == FDDPD_BF16) o_xt = take(4 * (size_t)S * g.M * g.N);
     const size_t o_pu = dpd->per_user ? take(2 * sizeof(c32) * (size_t)S * g.N_d) : 0;
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
@@ -241,7 +250,6 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         p->W16 = b + o_wq16;
         p->kind16 = d->precision == FDDPD_FP16 ? fdk::OUT_F16 : fdk::OUT_BF16;
     }
-    if (d->precision == FDDPD_BF16) p->xt16 = b + o_xt;
     e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
     if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
     p->launches = 1;
@@ -261,6 +269,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
 extern "C" int fddpd_plan_destroy(fddpd_plan *p) {
     if (!p) return FDDPD_OK;
     if (p->base) cudaFree(p->base);
+    if (p->xt16) cudaFree(p->xt16);
     if (p->stage_base) cudaFree(p->stage_base);
     if (p->cstream) {
         cudaStreamDestroy(p->cstream);
@@ -295,6 +304,23 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
         p->host_chunks = value;
         return FDDPD_OK;
     }
+    if (option == FDDPD_OPT_KEEP_PA_INPUT && (value == 0 || value == 1)) {
+        // BF16 plans only: the BF16 copy of x(t), [max_symbols][M][N], allocated once
+        if (value && p->d.precision == FDDPD_BF16 && !p->xt16) {
+            const size_t n = 4 * (size_t)p->d.max_symbols * p->g.M * p->g.N;
+            if (cudaMalloc(&p->xt16, n) != cudaSuccess) {
+                cudaGetLastError();
+                p->xt16 = nullptr;
+                return set_err(p, FDDPD_ERR_NOMEM, "kept PA input (%zu bytes)", n);
+            }
+        }
+        p->keep_xt = value != 0;
+        return FDDPD_OK;
+    }
+    if (option == FDDPD_OPT_FACTOR_FP64 && (value == 0 || value == 1)) {
+        p->fp64_factor = value != 0 || !p->p16;   // FP32 plans always factor in FP64
+        return FDDPD_OK;
+    }
     return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
 }
 
@@ -322,6 +348,30 @@ extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {
     return FDDPD_OK;
 }
 
+extern "C" int fddpd_get_optimizer_state(fddpd_plan *p, float *m, float *v, long long *t) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (!m || !v || !t) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (!aligned(m, 4) || !aligned(v, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    const size_t n = sizeof(float) * (size_t)p->g.theta_len;
+    FD_CK(p, cudaMemcpyAsync(m, p->adam_m, n, cudaMemcpyDefault, p->stream));
+    FD_CK(p, cudaMemcpyAsync(v, p->adam_v, n, cudaMemcpyDefault, p->stream));
+    FD_CK(p, cudaStreamSynchronize(p->stream));
+    *t = p->adam_t;
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_set_optimizer_state(fddpd_plan *p, const float *m, const float *v, long long t) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (!m || !v || t < 0) return set_err(p, FDDPD_ERR_ARG, "null pointer or negative step count");
+    if (!aligned(m, 4) || !aligned(v, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    const size_t n = sizeof(float) * (size_t)p->g.theta_len;
+    FD_CK(p, cudaMemcpyAsync(p->adam_m, m, n, cudaMemcpyDefault, p->stream));
+    FD_CK(p, cudaMemcpyAsync(p->adam_v, v, n, cudaMemcpyDefault, p->stream));
+    FD_CK(p, cudaStreamSynchronize(p->stream));
+    p->adam_t = (long)t;
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha) {
     if (!p) return FDDPD_ERR_ARG;
     if (R < 0 || R > p->R_max) return set_err(p, FDDPD_ERR_ARG, "R=%d outside 0..%d", R, p->R_max);
@@ -334,7 +384,7 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
         FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
                  fdk::zf_phase(ph, p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha,
                                p->status, p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr,
-                               p->kind16, p->tc_bin, p->status + 1, st));
+                               p->kind16, p->tc_bin, p->fp64_factor, p->status + 1, st));
     if (p->p16) {
         p->pk_H = H;
         p->pk_W = W;
@@ -408,6 +458,8 @@ static cudaError_t reduce_op(fddpd_plan *p, int mode, int S, const BinOps &o, co
     return fdk::bin_reduce(p->g, mode, S, o.W_or_H(mode), o.kind, alpha, static_cast<const c32 *>(B), out, s_ref, gy,
                            metrics, inv_count, p->stream);
 }
+// BF16 planes with FDDPD_OPT_KEEP_PA_INPUT: the forward of a training pass stores x(t)
+static bool keeps_xt(const fddpd_plan *p) { return p->keep_xt && p->xt16 && act_kind(p) == fdk::OUT_BF16; }
 static float grad_scale(const fddpd_plan *p, double inv_count) {
     return p->kind16 == fdk::OUT_F16 ? exp2f(rintf(log2f((float)(0.5 / inv_count)))) : 1.0f;
 }
@@ -477,7 +529,8 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
     }
     FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
     // a backward follows when gy is wanted: keep the time-domain PA input for its adjoint
-    void *xt = (gy && act_kind(p) == fdk::OUT_BF16) ? p->xt16 : nullptr;
+    // when the plan is set to (FDDPD_OPT_KEEP_PA_INPUT); by default the adjoint recomputes it
+    void *xt = keeps_xt(p) && gy ? p->xt16 : nullptr;
     FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1,
              fdk::fftpa_forward(g, S * g.M, p->xh, pa, p->tw, p->Xpa, act_kind(p), p->met, xt, st));
     FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
@@ -502,12 +555,13 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     if (rc) return rc;
     const float gsc = grad_scale(p, ps ? ps->inv_count : 1.0 / ((double)cols * g.N_d));
     FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
-    // BF16 planes: g_xhat goes to the blocked plane in x_hat's buffer (the adjoint reads
-    // the kept x(t), not x_hat); FP32 planes: in place over g_X
-    const bool a16 = act_kind(p) == fdk::OUT_BF16;
-    void *gxh = a16 ? (void *)p->xh : (void *)p->Xpa;
+    // BF16 planes: g_xhat goes to a blocked plane -- in x_hat's buffer when the adjoint
+    // reads the kept x(t), else behind the rows of g_X (x_hat is read to recompute x(t));
+    // FP32 planes: in place over g_X
+    const bool a16 = act_kind(p) == fdk::OUT_BF16, kept = keeps_xt(p);
+    void *gxh = !a16 ? (void *)p->Xpa : kept ? (void *)p->xh : (void *)((char *)p->Xpa + p->gxh_off);
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
-             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, gxh, act_kind(p), a16 ? p->xt16 : nullptr, st));
+             fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, gxh, act_kind(p), kept ? p->xt16 : nullptr, st));
     FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
              reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
     const float *gd = reinterpret_cast<const float *>(p->gst);
@@ -741,7 +795,7 @@ static int update_host_impl(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
                      fdk::zf_phase(ph, g, (int)(r1 - r0), Hc, Wc, alc, p->status, p->zf_scratch,
                                    p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
                                    p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr, p->kind16, p->tc_bin,
-                                   p->status + 1, st, !p->p16));   // 16-bit plans read only W's copy
+                                   p->fp64_factor, p->status + 1, st, !p->p16));   // 16-bit plans read only W's copy
         if (iters > 0) {
             const Pass ps{inv_count, c == 0, c == nch - 1, (int)r0};
             int rc1 = run_backward(p, (int)(t1 - t0), (const c32 *)((const char *)p->hs + t0 * s_sym), Hc, Wc, alc,
@@ -938,6 +992,26 @@ extern "C" int fddpd_tc_gemm(int M, int N, int K, const void *A, int lda, const 
     if (err) cudaFree(err);
     if (e != cudaSuccess) return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_tc_gemm: %s", cudaGetErrorString(e));
     if (herr) return set_err(nullptr, FDDPD_ERR_TIMEOUT, "fddpd_tc_gemm: bounded wait timed out");
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_zf_residual(fddpd_plan *p, int R, const fddpd_c32 *H, const fddpd_c32 *W, int every,
+                                 double *out) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (R < 0 || R > p->R_max) return set_err(p, FDDPD_ERR_ARG, "R=%d outside 0..%d", R, p->R_max);
+    if (every < 1) return set_err(p, FDDPD_ERR_ARG, "every=%d < 1", every);
+    if (!H || !W || !out) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (!aligned(H, 8) || !aligned(W, 8) || !aligned(out, 8)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    FD_CK(p, fdk::zf_residual(p->g, (long)R * p->g.N_d, every, reinterpret_cast<const c32 *>(H),
+                              reinterpret_cast<const c32 *>(W), out, p->stream));
+    p->launches += 1;
+    return FDDPD_OK;
+}
+
+extern "C" int fddpd_alu_peak(int kind, double *tflops, void *stream) {
+    if (kind < 0 || kind > 2 || !tflops) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_alu_peak: bad argument");
+    const cudaError_t e = fdk::alu_peak(kind, tflops, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_alu_peak: %s", cudaGetErrorString(e));
     return FDDPD_OK;
 }
 

@@ -45,8 +45,7 @@ inline size_t blk_plane_bytes(const Geo &g, long S) {
     return (size_t)R * BlkPlane(g).per_real * 4;
 }
 
-// zero-forcing precoder (Eq. 6): FP32 Gram, Cholesky + triangular inverse (FP64, or FP32
-// when kind is 16-bit), W = H^H G^{-1}
+// zero-forcing precoder (Eq. 6): FP32 Gram, Cholesky + triangular inverse (FP64), W = H^H G^{-1}
 size_t zf_scratch_bytes(const Geo &g, long nbins);
 // H16 / W16 (optional, kind OUT_BF16 / OUT_F16): 16-bit copies of H and W written on the way
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
@@ -54,8 +53,10 @@ cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, in
 // one of the three ZF kernels: 0 = Gram, 1 = factor / inverse, 2 = W (-1: all three).
 // tc: W on the tensor cores when kind is 16-bit and M <= 128, K <= 16 (err: timeout word)
 // keep_w32 = false: with the tensor-core apply, only the 16-bit copy of W is written
+// fp64: Cholesky and triangular inverse in FP64 (else FP32; FP32 kinds always FP64)
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st, bool keep_w32 = true);
+                     void *H16, void *W16, int kind, bool tc, bool fp64, int *err, cudaStream_t st,
+                     bool keep_w32 = true);
 // W = H^H Z (Z = G^{-1}, lower triangle in the factor's scratch layout) with BF16 hi / lo
 // operand splits on the tensor cores; W16 of the given 16-bit kind beside it
 cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,
@@ -110,6 +111,13 @@ cudaError_t fftpa_forward(const Geo &g, int rows, const c32 *xh, const c32 *pa, 
                           double *metrics, void *xt, cudaStream_t st);
 cudaError_t fftpa_adjoint(const Geo &g, int rows, const c32 *xh, const c32 *pa, const c32 *tw, const void *gX, void *gxh,
                           int act_kind, const void *xt, cudaStream_t st);
+
+// FP64 check of H_k W_k = I on every `every`-th of nbins subcarriers: *out (device) =
+// max over them of max_ij |(H_k W_k - I)_ij|
+cudaError_t zf_residual(const Geo &g, long nbins, long every, const c32 *H, const c32 *W, double *out,
+                        cudaStream_t st);
+// FMA-loop peak of the FP32 (kind 0 scalar, 1 packed pairs) or FP64 (kind 2) pipe, TFLOP/s
+cudaError_t alu_peak(int kind, double *tflops, cudaStream_t st);
 
 // parameter updates and bookkeeping
 cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);

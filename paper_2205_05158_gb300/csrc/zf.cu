@@ -9,9 +9,9 @@
 //            array laid out [bin / 32][entry][bin % 32].
 //   factor : one bin per LANE, so every instruction is a full-warp instruction:
 //            Cholesky G = L L^H (left-looking) and the in-place triangular inverse
-//            Y = L^{-1}; tr(G^{-1}) = ||Y||_F^2.  FP64 for FP32 plans (1/sqrt(d) from
-//            the FP32 rsqrtf and two Newton-Raphson steps y <- y (3 - d y^2) / 2 in
-//            FP64), FP32 for 16-bit plans (one Newton step).  Y (FP32) and alpha go out;
+//            Y = L^{-1}; tr(G^{-1}) = ||Y||_F^2.  FP64 (1/sqrt(d) from the FP32
+//            rsqrtf and two Newton-Raphson steps y <- y (3 - d y^2) / 2 in FP64), or
+//            FP32 in 16-bit plans that select it (one Newton step).  Y (FP32) and alpha go out;
 //            a pivot <= 1e-9 (FP64) or 1e-5 (FP32) of its Gram diagonal marks the bin
 //            singular (alpha = 0, W = 0, status bit 0).
 //   apply  : one warp per bin, W^H = Y^H (Y H) in FP32 (one antenna per lane), staged
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, 3)
 }
 
 // ---------------------------------------------------------------------------
-// Scalar type of the factor: FP64 for FP32 plans; FP32 for 16-bit plans, whose W is
+// Scalar type of the factor: FP64; or FP32 where a 16-bit plan selects it, since its W is
 // rounded to 16 bits afterwards (the FP32 factor's relative error, about the Gram
 // condition number times 2^-24, stays far below that rounding).
 template <typename Real> struct Fac;
@@ -539,21 +539,21 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
 }
 
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, bool tc, int *err, cudaStream_t st, bool keep_w32) {
+                     void *H16, void *W16, int kind, bool tc, bool fp64, int *err, cudaStream_t st, bool keep_w32) {
     // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128;
     // it may leave the FP32 W out when only the copy is wanted
     const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_bin_supported(g);
     if (tc_apply && !keep_w32) W = nullptr;
     if (kind == OUT_F16)
-        return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, false, tc_apply, err,
+        return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, fp64, tc_apply, err,
                           st);
-    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, kind == OUT_F32,
+    return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, fp64 || kind == OUT_F32,
                       tc_apply, err, st);
 }
 
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st) {
-    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, false, nullptr, st);
+    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, false, true, nullptr, st);
 }
 
 }  // namespace fdk

@@ -21,13 +21,20 @@ def test_stage_work_of_the_benchmark_step():
     realisations, F = 2 x 35^2 = 2450 dense inputs, BF16 plan: figures worked out by hand
     from the per-stage formulas (dense layer 2 x cols x 2N_d x F; row kernels two
     5 N log2 N transforms plus 19 flops per tap and sample forward, 24 per tap and 26 per
-    sample for the adjoint; the contractions' operand and plane bytes)."""
+    sample for the adjoint, which transforms three times when it recomputes x(t); the
+    contractions' operand and plane bytes)."""
     w = bench.stage_work(synth.CONFIGS["m128_k16_n2048"], 2000, "bf16")
     assert set(w) == set(STAGES)
     assert w["fc_fwd"] == ("tensor", 376_320_000_000)
     assert w["fc_bwd_w"][1] == w["fc_bwd_d"][1] == w["fc_fwd"][1]
     assert w["fftpa_fwd"] == ("alu", 2000 * 128 * (10 * 2048 * 11 + 2048 * 4 * 19))
-    assert w["fftpa_adj"] == ("alu", 121_634_816_000)
+    # the adjoint recomputes x(t) (three transforms); with x(t) kept, two
+    assert w["fftpa_adj"] == ("alu", 2000 * 128 * (3 * 5 * 2048 * 11 + 2048 * (24 * 4 + 26)))
+    assert bench.stage_work(synth.CONFIGS["m128_k16_n2048"], 2000, "bf16", kept_xt=True)["fftpa_adj"] == \
+        ("alu", 121_634_816_000)
+    # the Gram factor in FP64 by default, FP32 when the plan selects it
+    assert w["zf_factor"][0] == "fp64"
+    assert bench.stage_work(synth.CONFIGS["m128_k16_n2048"], 2000, "bf16", fp64_factor=False)["zf_factor"][0] == "alu"
     # alpha W s: W's 16-bit copy per realisation, s_tilde in, x_hat out (FP32)
     assert w["precode"] == ("hbm", 143 * 1200 * 128 * 16 * 4 + 2000 * 16 * 1200 * 8 + 2000 * 128 * 1200 * 8)
     # H's copy, the BF16 X^PA plane, s in and y out

@@ -43,14 +43,31 @@ def test_mixed_backward(prec):
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
 @pytest.mark.parametrize("cfg", [small_cfg(), synth.CONFIGS["m128_k16_n2048"].with_(S=28)], ids=["ragged", "m128_k16_n2048_28"])
 def test_mixed_zf_fp32_factor(cfg, prec):
-    """16-bit plans factor the Gram matrix in FP32: W and alpha (Eq. 6) still agree with
-    the FP64 oracle far inside the 16-bit rounding that W undergoes afterwards."""
+    """16-bit plans set to factor the Gram matrix in FP32 (FDDPD_OPT_FACTOR_FP64 = 0): W
+    and alpha (Eq. 6) still agree with the FP64 oracle far inside the 16-bit rounding
+    that W undergoes afterwards."""
+    import paper_2205_05158_gb300 as fd
     c = Case(cfg, S=cfg.S, precision=prec)
+    c.plan.set_option(fd.FDDPD_OPT_FACTOR_FP64, 0)
     W, al = c.gpu_zf()
     Wo, alo = c.oracle_zf()
     Wg, alg = W.cpu().numpy().astype(np.complex128), al.cpu().numpy().astype(np.float64)
     assert np.abs(Wg - Wo).max() <= 1e-4 * np.abs(Wo).max()
     assert np.abs(alg - alo).max() <= 1e-4 * alo.max()
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("cfg", [small_cfg(), synth.CONFIGS["m128_k16_n2048"].with_(S=28)], ids=["ragged", "m128_k16_n2048_28"])
+def test_mixed_zf_fp64_factor(cfg, prec):
+    """16-bit plans factor in FP64 by default: alpha (from tr(G^-1) of the FP64 inverse
+    and the FP32 Gram) within 1e-5 of the oracle's, W (split-BF16 tensor-core apply or
+    FP32 CUDA-core apply of Z) within 1e-4, and the 16-bit copy only rounded after."""
+    c = Case(cfg, S=cfg.S, precision=prec)
+    W, al = c.gpu_zf()
+    Wo, alo = c.oracle_zf()
+    Wg, alg = W.cpu().numpy().astype(np.complex128), al.cpu().numpy().astype(np.float64)
+    assert np.abs(Wg - Wo).max() <= 1e-4 * np.abs(Wo).max()
+    assert np.abs(alg - alo).max() <= 1e-5 * alo.max()
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])

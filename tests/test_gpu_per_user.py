@@ -1,7 +1,7 @@
 """Per-user FD-CNN parameters theta_u (Sec. IV-A; fddpd_dpd_desc.per_user, FP32 plans with
 L_U = 1) against the FP64 oracle: the forward chain, the gradient of every user's slice
 and a GD step, at the FP32 tolerances of the shared network; and K copies of one theta
-against the shared network.  Collected after the other GPU tests."""
+against the shared network."""
 import numpy as np
 import pytest
 
