@@ -38,7 +38,7 @@ class Dims(C.Structure):
                 ("n_orders", C.c_int), ("orders", C.c_int * 8), ("L", C.c_int),
                 ("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int),
                 ("N_conv", C.c_int), ("residual", C.c_int), ("P_T", C.c_double), ("Gx", C.c_int),
-                ("per_user", C.c_int)]
+                ("per_user", C.c_int), ("nn_L4", C.c_int), ("nn_D", C.c_int), ("nn_layers", C.c_int)]
 
 
 def lib():
@@ -60,7 +60,10 @@ def lib():
                                  C.c_int, P, P, C.POINTER(C.c_int), P]
         L.orc_philox4x32_10.argtypes = [P, P, P]
         L.orc_ser.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, C.c_int, C.c_double, C.c_ulonglong, P, P, P]
-        for f in ("orc_zf", "orc_precode_all", "orc_distort", "orc_backward", "orc_update", "orc_ser"):
+        L.orc_fdnn.argtypes = [C.POINTER(Dims), P, P, P]
+        L.orc_fdnn_distort.argtypes = [C.POINTER(Dims), C.c_int, P, P, P, P, P, P, P, P]
+        for f in ("orc_zf", "orc_precode_all", "orc_distort", "orc_backward", "orc_update", "orc_ser",
+                  "orc_fdnn_distort"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -83,7 +86,8 @@ def _p(a: Optional[np.ndarray]):
 
 
 def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, first_bin=None,
-              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, Gx=0, per_user=0) -> Dims:
+              L_U=1, K_C=3, K_S=1, N_conv=2, residual=1, Gx=0, per_user=0, nn_L4=3, nn_D=15,
+              nn_layers=1) -> Dims:
     d = Dims()
     d.M, d.K, d.N, d.N_d = M, K, N, N_d
     d.first_bin = N - N_d // 2 if first_bin is None else first_bin
@@ -95,6 +99,7 @@ def make_dims(M, K, N, N_d, orders: Sequence[int], L, G, P_T, S_per_real=1, firs
     d.P_T = P_T
     d.Gx = Gx
     d.per_user = per_user
+    d.nn_L4, d.nn_D, d.nn_layers = nn_L4, nn_D, nn_layers
     return d
 
 
@@ -102,7 +107,8 @@ def dims_from_config(cfg, P_T: float, residual: int = 1) -> Dims:
     return make_dims(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.orders, cfg.L, cfg.grid, P_T,
                      S_per_real=cfg.S_per_real, first_bin=cfg.first_bin, L_U=cfg.L_U,
                      K_C=cfg.K_C, K_S=cfg.K_S, N_conv=cfg.N_conv, residual=residual, Gx=cfg.pa_G,
-                     per_user=getattr(cfg, "per_user", 0))
+                     per_user=getattr(cfg, "per_user", 0), nn_L4=cfg.nn_L4, nn_D=cfg.nn_D,
+                     nn_layers=cfg.nn_layers)
 
 
 # -- single stages -----------------------------------------------------------
@@ -252,6 +258,58 @@ def update(d: Dims, s, H, W, alpha, pa_coef, theta, lr: float, iters: int, adam:
     if rc:
         raise ValueError("bad dims")
     return th, met
+
+
+# -- the FD-NN comparison workload (Sec. III-C) -----------------------------------
+def fdnn_theta_len(d: Dims) -> int:
+    """W_0 [D][2U(L_4+1)], b_0 [D], (W_k [D][D], b_k [D]) x (K^NN - 1), W_o [2U][D], b_o [2U]."""
+    U, L1, D = d.K, d.nn_L4 + 1, d.nn_D
+    return D * 2 * U * L1 + D + (d.nn_layers - 1) * (D * D + D) + 2 * U * D + 2 * U
+
+
+def all_bins_dims(d: Dims) -> Dims:
+    """The same system with every one of the N subcarriers taken as a data bin (in FFT bin
+    order): the geometry of the ZF precoder of all bins that the FD-NN chain needs."""
+    e = Dims.from_buffer_copy(d)
+    e.N_d, e.first_bin = d.N, 0
+    return e
+
+
+def fdnn(d: Dims, s_sym, theta) -> np.ndarray:
+    """FD-NN of one symbol (Sec. III-C): s_sym [K][N_d] -> predistorted [K][N] on every bin."""
+    s_sym = _c128(s_sym)
+    th = _f64(theta)
+    if s_sym.shape != (d.K, d.N_d):
+        raise ValueError(f"s_sym has shape {s_sym.shape}, expected ({d.K}, {d.N_d})")
+    if th.size != fdnn_theta_len(d):
+        raise ValueError(f"theta has {th.size} entries, expected {fdnn_theta_len(d)}")
+    out = np.empty((d.K, d.N), dtype=np.complex128)
+    lib().orc_fdnn(C.byref(d), _p(s_sym), _p(th), _p(out))
+    return out
+
+
+def fdnn_distort(d: Dims, s, H, W_all, alpha_all, pa_coef, theta):
+    """FD-NN chain over S symbols: FD-NN, ZF precoding of every subcarrier (W_all
+    [R][N][M][K], alpha_all [R][N] by FFT bin), IDFT, PA, DFT, combining at the data bins
+    (H [R][N_d][K][M]) -> (y [S][K][N_d], metrics[5])."""
+    s, H, W_all, pa_coef = _c128(s), _c128(H), _c128(W_all), _c128(pa_coef)
+    alpha_all, th = _f64(alpha_all), _f64(theta)
+    S = s.shape[0]
+    R = -(-S // d.S_per_real)
+    if s.shape[1:] != (d.K, d.N_d) or H.shape[1:] != (d.N_d, d.K, d.M) or H.shape[0] < R:
+        raise ValueError("s / H shapes")
+    if W_all.shape[1:] != (d.N, d.M, d.K) or W_all.shape[0] < R or alpha_all.shape[1:] != (d.N,) \
+            or alpha_all.shape[0] < R:
+        raise ValueError("W_all / alpha_all must cover every bin of the symbols' realisations")
+    if th.size != fdnn_theta_len(d):
+        raise ValueError(f"theta has {th.size} entries, expected {fdnn_theta_len(d)}")
+    y = np.empty_like(s)
+    met = np.zeros(5)
+    rc = lib().orc_fdnn_distort(C.byref(d), S, _p(s), _p(H), _p(W_all), _p(alpha_all), _p(pa_coef), _p(th),
+                                _p(y), _p(met))
+    if rc:
+        raise ValueError("bad dims")
+    return y, met
 
 
 # -- symbol errors at the users (Sec. V-B) -------------------------------------

@@ -379,6 +379,121 @@ int orc_distort(const orc_dims *d, int S, const cplx *s, const cplx *H, const cp
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. III-C: the FD-NN comparison DPD (see oracle.h for the parameter and    */
+/* input order).  Step by step: U IDFTs, the network at every time sample,     */
+/* U DFTs.                                                                     */
+/* ------------------------------------------------------------------------ */
+void orc_fdnn(const orc_dims *d, const cplx *s_sym, const double *theta, cplx *s_dpd)
+{
+    const int U = d->K, N = d->N, Nd = d->N_d, L1 = d->nn_L4 + 1, D = d->nn_D, NL = d->nn_layers;
+    const int nin = 2 * U * L1;
+    cplx *t = malloc(sizeof(cplx) * (size_t)U * N);     /* time-domain user streams */
+    cplx *o = malloc(sizeof(cplx) * (size_t)U * N);     /* predistorted streams     */
+    cplx *fd = calloc((size_t)N, sizeof(cplx));
+    for (int u = 0; u < U; ++u) {
+        for (int k = 0; k < N; ++k) fd[k] = 0;
+        for (int i = 0; i < Nd; ++i) fd[bin_of(d, i)] = s_sym[u * Nd + i];
+        orc_dft(N, fd, t + (long)u * N, 1);
+    }
+    const double *W0 = theta, *b0 = W0 + (long)D * nin;
+    const double *hid = b0 + D;                          /* (W_k, b_k), k = 1..NL-1 */
+    const double *Wo = hid + (long)(NL - 1) * (D * D + D), *bo = Wo + (long)2 * U * D;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; ++n) {
+        double *in = malloc(sizeof(double) * (size_t)nin);
+        double *h = malloc(sizeof(double) * (size_t)D), *h2 = malloc(sizeof(double) * (size_t)D);
+        for (int u = 0; u < U; ++u)
+            for (int l = 0; l < L1; ++l) {
+                const cplx v = t[(long)u * N + wrapi(n - l, N)];
+                in[u * L1 + l] = creal(v);
+                in[U * L1 + u * L1 + l] = cimag(v);
+            }
+        for (int a = 0; a < D; ++a) {
+            double acc = b0[a];
+            for (int j = 0; j < nin; ++j) acc += W0[(long)a * nin + j] * in[j];
+            h[a] = acc > 0 ? acc : 0;
+        }
+        for (int k = 1; k < NL; ++k) {
+            const double *Wk = hid + (long)(k - 1) * (D * D + D), *bk = Wk + (long)D * D;
+            for (int a = 0; a < D; ++a) {
+                double acc = bk[a];
+                for (int j = 0; j < D; ++j) acc += Wk[a * D + j] * h[j];
+                h2[a] = acc > 0 ? acc : 0;
+            }
+            memcpy(h, h2, sizeof(double) * (size_t)D);
+        }
+        for (int u = 0; u < U; ++u) {
+            double re = bo[u], im = bo[U + u];
+            for (int a = 0; a < D; ++a) {
+                re += Wo[(long)u * D + a] * h[a];
+                im += Wo[(long)(U + u) * D + a] * h[a];
+            }
+            o[(long)u * N + n] = (d->residual ? t[(long)u * N + n] : 0) + re + I * im;
+        }
+        free(in); free(h); free(h2);
+    }
+    for (int u = 0; u < U; ++u) orc_dft(N, o + (long)u * N, s_dpd + (long)u * N, 0);
+    free(t); free(o); free(fd);
+}
+
+int orc_fdnn_distort(const orc_dims *d, int S, const cplx *s, const cplx *H, const cplx *W_all,
+                     const double *alpha_all, const cplx *pa, const double *theta, cplx *y, double *metrics)
+{
+    if (d->M < 1 || d->K < 1 || d->N < 2 || d->N_d < 1 || d->N_d > d->N || d->S_per_real < 1) return -1;
+    if (d->nn_L4 < 0 || d->nn_D < 1 || d->nn_layers < 1 || d->n_orders < 1 || d->L < 0) return -1;
+    const int M = d->M, K = d->K, N = d->N, Nd = d->N_d, P = d->n_orders, L1 = d->L + 1;
+    const long symN = (long)K * Nd;
+    double met[5] = {0, 0, 0, 0, 0};
+    cplx *sd = malloc(sizeof(cplx) * (size_t)K * N);
+    cplx *X = malloc(sizeof(cplx) * (size_t)M * N);
+    double *gp = malloc(sizeof(double) * (size_t)M), *dp = malloc(sizeof(double) * (size_t)M);
+    for (int t = 0; t < S; ++t) {
+        const int r = t / d->S_per_real;
+        const cplx *Wr = W_all + (long)r * N * M * K, *Hr = H + (long)r * Nd * K * M;
+        const double *al = alpha_all + (long)r * N;
+        const cplx *s_sym = s + t * symN;
+        orc_fdnn(d, s_sym, theta, sd);
+#pragma omp parallel for schedule(static)
+        for (int m = 0; m < M; ++m) {
+            cplx *xh = malloc(sizeof(cplx) * (size_t)N), *x = malloc(sizeof(cplx) * (size_t)N);
+            cplx *xpa = malloc(sizeof(cplx) * (size_t)N);
+            for (int k = 0; k < N; ++k) {          /* every bin is precoded (Sec. III-C) */
+                cplx acc = 0;
+                for (int u = 0; u < K; ++u) acc += Wr[((long)k * M + m) * K + u] * sd[(long)u * N + k];
+                xh[k] = al[k] * acc;
+            }
+            orc_dft(N, xh, x, 1);
+            orc_pa_gmp(N, x, P, d->orders, d->L, d->Gx, pa + (long)m * P * L1 * (1 + 2 * (d->Gx > 0 ? d->Gx : 0)), xpa);
+            orc_dft(N, xpa, X + (long)m * N, 0);
+            double gsum = 0, dat = 0;
+            for (int k = 0; k < N; ++k) {
+                const cplx v = X[(long)m * N + k];
+                if (((k - d->first_bin) % N + N) % N < Nd) dat += creal(v * conj(v));
+                else gsum += creal(v * conj(v));
+            }
+            gp[m] = gsum;
+            dp[m] = dat;
+            free(xh); free(x); free(xpa);
+        }
+        for (int m = 0; m < M; ++m) { met[3] += gp[m]; met[4] += dp[m]; }
+        for (int u = 0; u < K; ++u)
+            for (int i = 0; i < Nd; ++i) {
+                const int k = bin_of(d, i);
+                cplx acc = 0;
+                for (int m = 0; m < M; ++m) acc += Hr[((long)i * K + u) * M + m] * X[(long)m * N + k];
+                const cplx yb = acc / al[k], e = yb - s_sym[u * Nd + i];
+                if (y) y[t * symN + u * Nd + i] = yb;
+                met[1] += creal(e * conj(e));
+                met[2] += creal(s_sym[u * Nd + i] * conj(s_sym[u * Nd + i]));
+            }
+    }
+    free(sd); free(X); free(gp); free(dp);
+    met[0] = met[1] / ((double)S * symN);
+    if (metrics) memcpy(metrics, met, sizeof met);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint of the whole chain for L = mean |y/alpha - s|^2 (Sec. V-A training */
 /* criterion).  Gradients of a real L w.r.t. a complex z are carried as       */
 /* g(z) = dL/dRe z + j dL/dIm z; a complex-linear map A has adjoint A^H, and  */

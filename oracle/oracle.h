@@ -33,6 +33,9 @@ typedef struct {
     double P_T;
     int Gx;   /* PA cross-term length (Eq. 9): 0 = memory polynomial */
     int per_user;  /* 1: every user u has its own FD-CNN parameters theta_u (Sec. IV-A) */
+    /* FD-NN of Sec. III-C (the comparison workload): memory length L_4, D neurons per hidden
+     * layer, K^NN hidden layers; its residual form follows `residual` above               */
+    int nn_L4, nn_D, nn_layers;
 } orc_dims;
 
 int  orc_num_threads(void);
@@ -58,6 +61,24 @@ int  orc_update(const orc_dims *d, int S, const double complex *s, const double 
                 const double complex *W, const double *alpha, const double complex *pa,
                 double *theta, double lr, int iters, int adam, double *adam_m, double *adam_v,
                 int *adam_t, double *metrics);
+/* FD-NN of Sec. III-C for one OFDM symbol: each user's symbols (data bins, guard bins
+ * zero) go to the time domain by the unitary IDFT; at every sample n a fully connected
+ * network with K^NN ReLU hidden layers of D neurons maps the real and imaginary parts of
+ * s_u[n], s_u[n-1], ..., s_u[n-L_4] of all users (taps circular in n) to 2U outputs, the
+ * predistorted time-domain sample of every user (added to s_u[n] when residual = 1);
+ * the unitary DFT takes each user back to all N bins.
+ *   s_sym [K][N_d] in, s_dpd [K][N] out (every bin, natural order)
+ *   theta: W_0 [D][2U(L_4+1)], b_0 [D], (W_k [D][D], b_k [D]) for k = 1..K^NN-1,
+ *          W_o [2U][D], b_o [2U]; input j < U(L_4+1) is Re s_u[n-l] at j = u(L_4+1) + l,
+ *          the imaginary parts follow; output u is the real part, U + u the imaginary. */
+void orc_fdnn(const orc_dims *d, const double complex *s_sym, const double *theta, double complex *s_dpd);
+/* The FD-NN chain over S symbols: FD-NN, ZF precoding of EVERY subcarrier (guard bins
+ * too, with W_all [R][N][M][K], alpha_all [R][N] indexed by FFT bin), IDFT, PA, DFT,
+ * combining at the data bins with H [R][N_d][K][M], equalised by alpha_all at the data
+ * bins; metrics as orc_distort.                                                      */
+int  orc_fdnn_distort(const orc_dims *d, int S, const double complex *s, const double complex *H,
+                      const double complex *W_all, const double *alpha_all, const double complex *pa,
+                      const double *theta, double complex *y, double *metrics);
 /* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ctr[4], key[2] -> out[4]. */
 void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);
 /* Symbol errors at the users (Sec. V-B; noise of Eq. 4-5): z = y + w / alpha with

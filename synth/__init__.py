@@ -57,6 +57,9 @@ class Config:
     K_C: int = 3
     K_S: int = 1
     N_conv: int = 2
+    nn_L4: int = 3              # FD-NN (Sec. III-C): memory length, neurons, hidden layers
+    nn_D: int = 15
+    nn_layers: int = 1
     iters: int = 1
     seed: int = 0
 
@@ -181,6 +184,24 @@ def channel_estimate(cfg: "Config", eta: float, S: Optional[int] = None, symbol_
     return out
 
 
+def channel_all_bins(cfg: "Config", S: Optional[int] = None, symbol_offset: int = 0) -> np.ndarray:
+    """The per-subcarrier channel of EVERY one of the N bins (natural bin order), [R][N][K][M]
+    complex64, of the same realisations make_workload draws (its H is this array at the
+    data bins): the precoder of the FD-NN workload covers the guard bins too."""
+    S = cfg.S if S is None else S
+    if symbol_offset % cfg.S_per_real:
+        raise ValueError("symbol_offset must start a realisation")
+    r0 = symbol_offset // cfg.S_per_real
+    R = (S + cfg.S_per_real - 1) // cfg.S_per_real
+    out = np.empty((R, cfg.N, cfg.K, cfg.M), dtype=np.complex64)
+    bins = np.arange(cfg.N)
+    for r in range(0, R, 8):
+        n = min(8, R - r)
+        taps = channel_taps(cfg.seed, n, cfg.T, cfg.K, cfg.M, cfg.rho, first_real=r0 + r)
+        out[r:r + n] = channel_fd(taps, cfg.N, bins)
+    return out
+
+
 def channel_fd(taps: np.ndarray, N: int, bins: np.ndarray) -> np.ndarray:
     """Per-subcarrier channel of the data bins: H_k = sum_t H_t exp(-j 2 pi k t / N).
     taps [R][T][K][M] -> [R][N_d][K][M]."""
@@ -284,6 +305,31 @@ def _theta_one(cfg: Config, st: "Stream", fc_scale: float) -> np.ndarray:
     fw = fc_scale * (2 * st.uniform(sz["fc_w"]) - 1) / math.sqrt(fan_fc)
     fb = fc_scale * 0.01 * (2 * st.uniform(sz["fc_b"]) - 1)
     return np.concatenate([cw, cb, fw, fb]).astype(np.float32)
+
+
+def fdnn_theta_len(cfg: Config) -> int:
+    U, L1, D = cfg.K, cfg.nn_L4 + 1, cfg.nn_D
+    return D * 2 * U * L1 + D + (cfg.nn_layers - 1) * (D * D + D) + 2 * U * D + 2 * U
+
+
+def fdnn_theta_init(cfg: Config, seed: int, out_scale: float = 0.0) -> np.ndarray:
+    """FD-NN parameters (Sec. III-C), flat FP32: W_0 [D][2U(L_4+1)], b_0 [D], the further
+    hidden layers (W_k [D][D], b_k [D]), W_o [2U][D], b_o [2U].  Hidden layers ~
+    U(+-1/sqrt(fan_in)); the output layer times out_scale (0 with the residual form gives
+    the identity predistorter)."""
+    st = Stream(seed, "fdnn")
+    U, L1, D = cfg.K, cfg.nn_L4 + 1, cfg.nn_D
+    parts = []
+    fan = 2 * U * L1
+    for k in range(cfg.nn_layers):
+        n_in = fan if k == 0 else D
+        b = 1.0 / math.sqrt(n_in)
+        parts.append(b * (2 * st.uniform(D * n_in) - 1))
+        parts.append(b * (2 * st.uniform(D) - 1))
+    b = 1.0 / math.sqrt(D)
+    parts.append(out_scale * b * (2 * st.uniform(2 * U * D) - 1))
+    parts.append(out_scale * b * (2 * st.uniform(2 * U) - 1))
+    return np.concatenate(parts).astype(np.float32)
 
 
 # ----------------------------------------------------------------------------
