@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-fast-variant", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-fdnn", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     return ap.parse_args()
 
 
@@ -118,6 +121,9 @@ def stage_work(cfg, S: int, prec: str, fp64_factor: bool = True, kept_xt: bool =
         "fc_bwd_d": (fc_bound, 2.0 * cols * F * 2 * Nd),
         "conv_bwd": ("hbm", cols * (Nd * c8 * L_U + F * 4)),
         "step": ("hbm", 3 * theta_len * 4),
+        # Z x per (symbol, subcarrier) from the factor's Y (one of two launches: precode side,
+        # adjoint side): Y's lower triangles in, x in, result out
+        "zmul": ("hbm", R * Nd * (K * (K + 1) // 2) * 8 + 2 * S * K * Nd * c8),
     }
 
 
@@ -157,7 +163,7 @@ def source_files(stage: str, prec: str):
              "fftpa_adj": ("fftpa.cu", "fftpa.cuh", "fftpa_n11.cu"),
              "precode": bins, "combine": bins, "adj_combine": bins, "adj_precode": bins,
              "fc_fwd": fc, "fc_bwd_w": fc, "fc_bwd_d": fc, "fc_bwd_b": ("fdcnn.cu",),
-             "conv_fwd": ("fdcnn.cu",), "conv_bwd": ("fdcnn.cu",), "step": ("update.cu",)}
+             "conv_fwd": ("fdcnn.cu",), "conv_bwd": ("fdcnn.cu",), "step": ("update.cu",), "zmul": ("zf.cu",)}
     return files.get(stage, ("api.cu",))
 
 
@@ -231,6 +237,157 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# training run of the 128 x 16 system (Sec. V-A: theta learned by gradient descent through
+# the PA model): per-user FD-CNN parameters from the identity predistorter, 256 symbols
+# per step, each step's mini-batch with its own symbols and channel realisations (drawn
+# from a pool of `pool` distinct batches), the ZF build of that batch's channel inside
+# the step; EVM / ACPR before and after on a training batch and on a held-out batch
+# ---------------------------------------------------------------------------
+TRAIN_STEPS = 500
+TRAIN_POOL = 16   # distinct mini-batches (symbols and channel realisations) the run cycles through
+
+
+def train_run(fd, torch, prec, optimizer, lr, steps, pool, stream, per_user=1, eval_every=50):
+    import numpy as np
+
+    import synth
+    cfg = synth.CONFIGS["m128_k16_n2048_train"].with_(per_user=per_user)
+    S = cfg.S
+    stride = -(-S // cfg.S_per_real) * cfg.S_per_real       # batches start on realisation boundaries
+    P_T = synth.transmit_power(cfg)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    plan = fd.Plan.from_config(cfg, P_T, max_symbols=S, precision=prec, stream=stream)
+    theta0 = dev(synth.theta_init(cfg, cfg.seed, 0.0))      # the identity predistorter
+    pa = dev(synth.pa_coefficients(cfg.seed, cfg.M, cfg.pa_nominal, cfg.pa_spread, cfg.pa_spread_orders)
+             .astype(np.complex64))
+    data = [tuple(dev(a) for a in synth.batch(cfg, S, b * stride)) for b in range(pool + 1)]   # last: held out
+    R = data[0][1].shape[0]
+    W = torch.empty((R, cfg.N_d, cfg.M, cfg.K), dtype=torch.complex64, device="cuda") \
+        if prec == fd.FDDPD_FP32 else None
+    al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
+    met = torch.zeros(5, dtype=torch.float64, device="cuda")
+
+    def quality(theta, b):
+        s_b, H_b = data[b]
+        plan.precode(H_b, W, al)
+        plan.distort(s_b, H_b, W, al, pa, theta, None, met)
+        m = met.cpu().numpy()
+        return {"evm_db": 10 * math.log10(m[1] / m[2]), "acpr_db": 10 * math.log10(m[3] / m[4])}
+
+    before = {"train": quality(theta0, 0), "held_out": quality(theta0, pool)}
+    theta = theta0.clone()
+    plan.reset_optimizer()
+    hist = torch.zeros((steps // eval_every + 1, 5), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        s_b, H_b = data[i % pool]
+        plan.precode(H_b, W, al)
+        plan.update(s_b, H_b, W, al, pa, theta, lr, 1, optimizer, met)
+        if i % eval_every == 0:
+            hist[i // eval_every].copy_(met)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h = hist.cpu().numpy()
+    after = {"train": quality(theta, 0), "held_out": quality(theta, pool)}
+    return plan, cfg, data, W, al, pa, theta0, {
+        "precision": {fd.FDDPD_FP32: "fp32", fd.FDDPD_BF16: "bf16", fd.FDDPD_FP16: "fp16"}[prec],
+        "per_user": per_user, "optimizer": "adam" if optimizer == fd.FDDPD_ADAM else "gd", "lr": lr,
+        "steps": steps, "symbols_per_step": S, "distinct_batches": pool, "ms_per_step": ms,
+        "steps_per_s": 1e3 / ms, "before": before, "after": after,
+        "evm_db_of_step": {str(j * eval_every): 10 * math.log10(h[j, 1] / h[j, 2])
+                           for j in range(len(h)) if j * eval_every < steps}}
+
+
+def fdnn_run(fd, torch, stream, S=560, reps=10):
+    """The FD-NN comparison workload (Sec. III-C) on the 128 x 16, N = 2048 system: its
+    forward chain (FP32 plan; every bin precoded) against the FD-CNN forward chain of an
+    FP32 plan on the same symbols, both timed with CUDA events; and the running cost per
+    UE and symbol of both DPDs from the paper's FLOP formulas (FD-NN: its network, U
+    IDFT/DFT pairs and the guard-bin precoding; FD-CNN: convolution and dense layer)."""
+    import numpy as np
+
+    import synth
+    cfg = synth.CONFIGS["m128_k16_n2048"].with_(S=S)
+    w = synth.make_workload(cfg, fc_scale=0.05)
+    H_all = synth.channel_all_bins(cfg)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s, Hd, Ha, pa = dev(w.s), dev(w.H), dev(H_all), dev(w.pa)
+    R = w.H.shape[0]
+    out = {"workload": f"m128_k16_n2048, {S} symbols, FP32 plans", "fdnn": {"L4": cfg.nn_L4, "D": cfg.nn_D,
+                                                                          "layers": cfg.nn_layers}}
+    met = torch.zeros(5, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    pn = fd.Plan.fdnn_from_config(cfg, w.P_T, max_symbols=S, stream=stream)
+    th = dev(synth.fdnn_theta_init(cfg, cfg.seed, out_scale=0.1))
+    Wa = torch.empty((R, cfg.N, cfg.M, cfg.K), dtype=torch.complex64, device="cuda")
+    ala = torch.empty((R, cfg.N), dtype=torch.float32, device="cuda")
+    pn.precode(Ha, Wa, ala)
+    pn.profile(True)
+    pn.profile_read()
+    ms_nn = timed(lambda: pn.distort(s, Hd, Wa, ala, pa, th, None, met))
+    prof = pn.profile_read()
+    m = met.cpu().numpy()
+    out["fdnn_forward"] = {"value": S / (ms_nn / 1e3), "unit": UNIT, "ms": ms_nn,
+                           "evm_db": 10 * math.log10(m[1] / m[2]), "acpr_db": 10 * math.log10(m[3] / m[4]),
+                           "stages_ms": {k: v[0] / (reps + 1) for k, v in prof.items() if v[1] > 0}}
+    pn.close()
+    del Wa, ala, Ha
+    pc = fd.Plan.from_config(cfg, w.P_T, max_symbols=S, precision=fd.FDDPD_FP32, stream=stream)
+    W = torch.empty((R, cfg.N_d, cfg.M, cfg.K), dtype=torch.complex64, device="cuda")
+    al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
+    pc.precode(Hd, W, al)
+    thc = dev(w.theta)
+    ms_cnn = timed(lambda: pc.distort(s, Hd, W, al, pa, thc, None, met))
+    out["fdcnn_forward_fp32"] = {"value": S / (ms_cnn / 1e3), "unit": UNIT, "ms": ms_cnn}
+    pc.close()
+    # running cost per UE per OFDM symbol (the paper's counts, Sec. III-C and IV-B)
+    U, N, B, Nd, L, D, Knn = cfg.K, cfg.N, cfg.M, cfg.N_d, cfg.nn_L4, cfg.nn_D, cfg.nn_layers
+    nn_flops = (N * (4 * U * (L + 1) * D + 2 * (Knn - 1) * D * D + 4 * D * U) + 10 * U * N * math.log2(N)
+                + 8 * (N - Nd) * U * B) / U
+    cells = math.ceil(math.sqrt(Nd)) ** 2
+    cnn_flops = 2 * cfg.N_conv * cfg.L_U * (2 * cfg.K_C ** 2 - 1) * cells + 8 * Nd * cfg.L_U * cells
+    out["flops_per_ue_symbol"] = {"fdnn": nn_flops, "fdcnn": cnn_flops}
+    return out
+
+
+def torch_optim_run(fd, torch, plan, data, W, al, pa, theta0, steps=20, lr=1e-3):
+    """The same plan trained through the autograd wrapper (fddpd_loss) by torch.optim.Adam,
+    against fddpd_update's own Adam over the same steps on the first batch."""
+    s_b, H_b = data[0]
+    plan.precode(H_b, W, al)
+    th = torch.nn.Parameter(theta0.clone())
+    opt = torch.optim.Adam([th], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad()
+        loss = fd.fddpd_loss(th, plan, s_b, H_b, W, al, pa)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    ref = theta0.clone()
+    plan.reset_optimizer()
+    plan.update(s_b, H_b, W, al, pa, ref, lr, steps, fd.FDDPD_ADAM)
+    torch.cuda.synchronize()
+    d = (th.detach() - ref).double().norm() / (ref - theta0).double().norm()
+    return {"steps": steps, "lr": lr, "loss_first": losses[0], "loss_last": losses[-1],
+            "rel_diff_vs_library_adam": float(d)}
 
 
 # ---------------------------------------------------------------------------
@@ -343,9 +500,13 @@ def run_ours(args):
     al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
     met = torch.zeros(5, dtype=torch.float64, device="cuda")
 
+    # W is not formed on the training path: fddpd_precode keeps the precoder as its factors
+    # and the chain applies alpha H^H (Z s) (16-bit plans; FP32 plans form W)
+    Wt = W if prec == fd.FDDPD_FP32 else None
+
     def step():
-        plan.precode(H, W, al)
-        plan.update(s, H, W, al, pa, theta, LR, 1, fd.FDDPD_GD, met)
+        plan.precode(H, Wt, al)
+        plan.update(s, H, Wt, al, pa, theta, LR, 1, fd.FDDPD_GD, met)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -379,7 +540,7 @@ def run_ours(args):
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
-        plan.distort(s, H, W, al, pa, theta, None, met)
+        plan.distort(s, H, Wt, al, pa, theta, None, met)
     f1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = f0.elapsed_time(f1) / args.steps
@@ -396,7 +557,7 @@ def run_ours(args):
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     q0.record(stream)
     for it in range(args.steps):
-        plan.distort(s, H, W, al, pa, theta, y_ser, None)
+        plan.distort(s, H, Wt, al, pa, theta, y_ser, None)
         plan.ser(y_ser, s, al, cfg.Q, N0, 1000 + it, ser_counts)
     q1.record(stream)
     torch.cuda.synchronize()
@@ -421,7 +582,9 @@ def run_ours(args):
             stages_out[k].update({"bound": work[k][0], "achieved": a, "unit": u, "frac": a / pk})
     # step-level roofline: the largest resource lower bound of the whole step over its time
     lb = step_lower_bounds(work, mp, alu)
-    zf_res = plan.zf_residual(H, W, 1)   # the final FP64 check of H_k W_k = I, all subcarriers
+    plan.precode(H, W, al)               # W itself, for the final FP64 check of H_k W_k = I
+    zf_res = plan.zf_residual(H, W, 1)   # (all subcarriers) and the oracle comparison
+    plan.precode(H, Wt, al)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -430,7 +593,8 @@ def run_ours(args):
            "config": {"workload": WORKLOAD,
                       "symbols_per_step": S, "realisations_per_step": R, "precision": prec_name,
                       "arithmetic": ARITHMETIC if prec_name == "bf16" else "default options of the plan",
-                      "step": "ZF + FD-CNN + precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
+                      "step": "ZF (Gram + factor; the precoder applied through its factors, W not formed) + FD-CNN + "
+                              "precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
                       "l2": "inputs larger than L2 (H 2.8 GB), no flush",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": {"kernel": stage, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
@@ -456,8 +620,8 @@ def run_ours(args):
         metf = torch.zeros(5, dtype=torch.float64, device="cuda")
 
         def stepf():
-            plan.precode(H, W, al)
-            plan.update(s, H, W, al, pa, thf, LR, 1, fd.FDDPD_GD, metf)
+            plan.precode(H, Wt, al)
+            plan.update(s, H, Wt, al, pa, thf, LR, 1, fd.FDDPD_GD, metf)
 
         for _ in range(max(3, args.warmup)):
             stepf()
@@ -473,7 +637,7 @@ def run_ours(args):
         proff = plan.profile_read()
         plan.profile(False)
         msf = max_over_ranks(v0.elapsed_time(v1) / args.steps, dist, "cuda")
-        plan.distort(s, H, W, al, pa, theta0, None, metf)
+        plan.distort(s, H, Wt, al, pa, theta0, None, metf)
         mf = metf.cpu().numpy()
         out["fast_variant"] = {"arithmetic": FAST_ARITHMETIC, "value": job_rate(world, S, msf / 1e3), "unit": UNIT,
                                "ms_per_step": msf, "evm_db": 10 * math.log10(mf[1] / mf[2]),
@@ -531,7 +695,27 @@ def run_ours(args):
                             "evm_db": 10 * math.log10(m32[1] / m32[2]), "acpr_db": 10 * math.log10(m32[3] / m32[4])}
         del plan32
 
+    if rank == 0 and not args.no_fdnn:
+        out["fdnn_comparison"] = fdnn_run(fd, torch, stream)
+
+    # the training run of the 128 x 16 system (rank 0; informational, outside the timed step)
+    if rank == 0 and not args.no_train:
+        runs = []
+        # per-user parameters (the configuration's own), mixed precision, the paper's Adam and
+        # plain GD; the shared network for comparison; FP32 with torch.optim beside it
+        for prec_, pu_, opt_, lr_ in ((fd.FDDPD_BF16, 1, fd.FDDPD_ADAM, 1e-3), (fd.FDDPD_BF16, 1, fd.FDDPD_GD, 30.0),
+                                      (fd.FDDPD_BF16, 0, fd.FDDPD_ADAM, 1e-3), (fd.FDDPD_FP32, 1, fd.FDDPD_ADAM, 1e-3)):
+            tp, tcfg, tdata, tW, tal, tpa, tth0, res = train_run(fd, torch, prec_, opt_, lr_, args.train_steps,
+                                                                 TRAIN_POOL, stream, per_user=pu_)
+            if prec_ == fd.FDDPD_FP32:
+                res["torch_optim"] = torch_optim_run(fd, torch, tp, tdata, tW, tal, tpa, tth0)
+            runs.append(res)
+            tp.close()
+            del tdata
+        out["training"] = runs
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        plan.precode(H, W, al)
         out["cpu_baseline"] = cpu_baseline(cfg, w, args.cpu_sample, plan, s, H, W, al, pa, theta0)
     if rank == 0:
         print(json.dumps(out))

@@ -94,9 +94,37 @@ typedef struct {
     int N_conv;       /* number of kernels, 1..64                                        */
     int residual;     /* 1: s_tilde = s + FC(.); 0: s_tilde = FC(.) as printed           */
     int per_user;     /* 0: one theta for all users; 1: user u has its own theta_u (the  */
-                      /* K sets stacked by user; FP32 plans with L_U = 1, else           */
-                      /* FDDPD_ERR_UNSUPPORTED)                                          */
+                      /* K sets stacked by user; every precision and L_U)                */
 } fddpd_dpd_desc;
+
+/* The FD-NN of Sec. III-C, the frequency-domain NN DPD the paper compares the FD-CNN with:
+ * every user's symbols go to the time domain (unitary IDFT of the data bins, guard bins
+ * zero); at every sample n a fully connected network maps the real and imaginary parts of
+ * s_u[n], s_u[n-1], ..., s_u[n-L4] of all K users (taps circular in n) through `layers`
+ * ReLU layers of D neurons to 2K outputs, the predistorted samples (added to s_u[n] when
+ * residual = 1, the form in which zero output weights are the identity); the unitary DFT
+ * takes each user back to all N bins, so the precoder must cover the guard bins too.
+ * theta: W_0 [D][2K(L4+1)] (input j < K(L4+1) is Re s_u[n-l] at j = u(L4+1) + l, the
+ * imaginary parts follow), b_0 [D], then (W_k [D][D], b_k [D]) per further layer, W_o
+ * [2K][D] (row u the real part of user u, K + u the imaginary part), b_o [2K].       */
+typedef struct {
+    int L4;           /* memory length of the tapped delay lines, 0..15                  */
+    int D;            /* neurons per hidden layer, 1..32                                 */
+    int layers;       /* hidden layers K^NN, 1..4                                        */
+    int residual;     /* 1: output added to s_u[n]; 0: the network output alone          */
+} fddpd_fdnn_desc;
+
+/* Create an FD-NN plan (FP32 only; at most 12288 parameters): the running mode of the
+ * comparison workload.  On such a plan
+ *   fddpd_precode(plan, R, H_all [R][N][K][M], W_all [R][N][M][K], alpha_all [R][N]) builds
+ *       the ZF precoder of Eq. (6) on every one of the N bins (FFT bin order);
+ *   fddpd_distort(plan, S, s [S][K][N_d], H [R][N_d][K][M] (the data bins, for combining),
+ *       W_all, alpha_all, pa, theta, y, metrics) runs FD-NN, precoding of every bin, IDFT,
+ *       PA, DFT and the combining of the data bins (metrics as for the FD-CNN chain);
+ *   backward / update / update_host / autotune return FDDPD_ERR_UNSUPPORTED.
+ * Errors: ARG, UNSUPPORTED (precision, parameter count), NOMEM, CUDA.              */
+int fddpd_fdnn_plan_create(fddpd_plan **out, const fddpd_dims *dims, const fddpd_pa_desc *pa,
+                           const fddpd_fdnn_desc *nn, void *stream);
 
 /* Create a plan on `stream` (a cudaStream_t; NULL = legacy default stream).  Validates
  * the sizes, selects the kernels and allocates the workspace for max_symbols symbols.
@@ -171,7 +199,13 @@ int fddpd_invalidate_operands(fddpd_plan *plan);
  * backward / update calls with these same H and W pointers (calls with other pointers
  * re-pack from the FP32 arrays; after H or W is rewritten in place by other means than
  * this call, call fddpd_invalidate_operands).  R <= ceil(max_symbols /
- * S_per_real).  Errors: ARG, LAYOUT, SINGULAR (reported after the kernel completes:
+ * S_per_real).
+ * W = NULL (16-bit plans): no W is formed.  The plan keeps the precoder as its factors --
+ * the 16-bit copies of H and H^H and Y = L^{-1} of the Cholesky factor G = L L^H -- and
+ * distort / backward / update calls given these same H and alpha with W = NULL apply
+ * alpha W s = alpha H^H (Z s), Z = Y^H Y = G^{-1} (Eq. 6 by associativity), until the
+ * next fddpd_precode or fddpd_invalidate_operands.  FP32 plans: UNSUPPORTED.
+ * Errors: ARG, LAYOUT, UNSUPPORTED, SINGULAR (reported after the kernel completes:
  * this call synchronises the stream once to read the status word).              */
 int fddpd_precode(fddpd_plan *plan, int R, const fddpd_c32 *H, fddpd_c32 *W, float *alpha);
 
@@ -185,7 +219,8 @@ int fddpd_zf_residual(fddpd_plan *plan, int R, const fddpd_c32 *H, const fddpd_c
 
 /* Forward chain over S symbols (running mode of the FD-DPD, Sec. III-A and IV).
  *   s       [S][K][N_d]       in : unit-power QAM symbols of the data bins
- *   H, W, alpha               in : as produced for realisations 0..ceil(S/S_per_real)-1
+ *   H, W, alpha               in : as produced for realisations 0..ceil(S/S_per_real)-1 (W may
+ *                                    be NULL after fddpd_precode(H, NULL, alpha) on this plan)
  *   pa_coef [M][n_orders][L+1] in: per-antenna PA coefficients c^b_{p,l} (with cross
  *           terms, G > 0: [M][n_orders (L+1) (1 + 2G)] as fddpd_pa_desc describes)
  *   theta                     in : FD-CNN parameters (layout above)
@@ -293,7 +328,8 @@ enum fddpd_stage {
     FDDPD_STAGE_ZF_GRAM = 0, FDDPD_STAGE_ZF_FACTOR, FDDPD_STAGE_ZF_APPLY, FDDPD_STAGE_CONV_FWD, FDDPD_STAGE_FC_FWD, FDDPD_STAGE_PRECODE,
     FDDPD_STAGE_FFTPA_FWD, FDDPD_STAGE_COMBINE, FDDPD_STAGE_ADJ_COMBINE, FDDPD_STAGE_FFTPA_ADJ,
     FDDPD_STAGE_ADJ_PRECODE, FDDPD_STAGE_FC_BWD_W, FDDPD_STAGE_FC_BWD_B, FDDPD_STAGE_FC_BWD_D,
-    FDDPD_STAGE_CONV_BWD, FDDPD_STAGE_STEP, FDDPD_STAGE_PACK, FDDPD_N_STAGES
+    FDDPD_STAGE_CONV_BWD, FDDPD_STAGE_STEP, FDDPD_STAGE_PACK, FDDPD_STAGE_ZMUL, FDDPD_STAGE_FDNN_ROWS,
+    FDDPD_STAGE_FDNN_MLP, FDDPD_N_STAGES
 };
 
 /* While enabled, every stage's kernels are bracketed by CUDA events on the plan's

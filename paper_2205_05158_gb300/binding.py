@@ -31,10 +31,11 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
             "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune",
             "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak",
-            "fddpd_get_optimizer_state", "fddpd_set_optimizer_state"]
+            "fddpd_get_optimizer_state", "fddpd_set_optimizer_state", "fddpd_fdnn_plan_create"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
-          "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"]
+          "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack", "zmul", "fdnn_rows",
+          "fdnn_mlp"]
 
 
 class Dims(C.Structure):
@@ -49,6 +50,10 @@ class PaDesc(C.Structure):
 class DpdDesc(C.Structure):
     _fields_ = [("G", C.c_int), ("L_U", C.c_int), ("K_C", C.c_int), ("K_S", C.c_int), ("N_conv", C.c_int),
                 ("residual", C.c_int), ("per_user", C.c_int)]
+
+
+class FdnnDesc(C.Structure):
+    _fields_ = [("L4", C.c_int), ("D", C.c_int), ("layers", C.c_int), ("residual", C.c_int)]
 
 
 class FddpdError(RuntimeError):
@@ -77,6 +82,8 @@ def load(build_if_missing: bool = True):
     L = C.CDLL(path)
     P, I = C.c_void_p, C.c_int
     L.fddpd_plan_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Dims), C.POINTER(PaDesc), C.POINTER(DpdDesc), P]
+    L.fddpd_fdnn_plan_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Dims), C.POINTER(PaDesc),
+                                         C.POINTER(FdnnDesc), P]
     L.fddpd_plan_destroy.argtypes = [P]
     L.fddpd_last_error.argtypes = [P]
     L.fddpd_last_error.restype = C.c_char_p
@@ -113,7 +120,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_alu_peak.argtypes = [I, C.POINTER(C.c_double), P]
     L.fddpd_get_optimizer_state.argtypes = [P, P, P, C.POINTER(C.c_longlong)]
     L.fddpd_set_optimizer_state.argtypes = [P, P, P, C.c_longlong]
-    for f in ("fddpd_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
+    for f in ("fddpd_plan_create", "fddpd_fdnn_plan_create", "fddpd_plan_destroy", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
               "fddpd_backward", "fddpd_update", "fddpd_reset_optimizer", "fddpd_update_host",
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
               "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power",
@@ -152,7 +159,7 @@ class Plan:
     def __init__(self, M: int, K: int, N: int, N_d: int, S_per_real: int, max_symbols: int, P_T: float,
                  orders: Sequence[int], L: int, G: int, L_U: int = 1, K_C: int = 3, K_S: int = 1, N_conv: int = 2,
                  residual: int = 1, precision: int = FDDPD_FP32, first_bin: int = -1, stream=None,
-                 pa_G: int = 0, per_user: int = 0):
+                 pa_G: int = 0, per_user: int = 0, fdnn: Optional[Sequence[int]] = None):
         self._lib = load()
         d = Dims(M, K, N, N_d, first_bin, S_per_real, max_symbols, precision, float(P_T))
         pa = PaDesc()
@@ -161,9 +168,14 @@ class Plan:
             pa.orders[i] = int(p)
         pa.L = L
         pa.G = pa_G
-        dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual, per_user)
         h = C.c_void_p()
-        rc = self._lib.fddpd_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(dpd), _stream_ptr(stream))
+        if fdnn is not None:   # the FD-NN comparison plan: fdnn = (L4, D, layers)
+            nn = FdnnDesc(int(fdnn[0]), int(fdnn[1]), int(fdnn[2]), residual)
+            rc = self._lib.fddpd_fdnn_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(nn),
+                                                  _stream_ptr(stream))
+        else:
+            dpd = DpdDesc(G, L_U, K_C, K_S, N_conv, residual, per_user)
+            rc = self._lib.fddpd_plan_create(C.byref(h), C.byref(d), C.byref(pa), C.byref(dpd), _stream_ptr(stream))
         if rc:
             raise FddpdError(rc, self._lib.fddpd_last_error(None).decode())
         self._h = h
@@ -177,6 +189,16 @@ class Plan:
         return cls(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.S_per_real, max_symbols or cfg.S, P_T, cfg.orders, cfg.L,
                    cfg.grid, cfg.L_U, cfg.K_C, cfg.K_S, cfg.N_conv, residual, precision, cfg.first_bin, stream,
                    getattr(cfg, "pa_G", 0), getattr(cfg, "per_user", 0))
+
+    @classmethod
+    def fdnn_from_config(cls, cfg, P_T: float, max_symbols: Optional[int] = None, residual: int = 1,
+                         stream=None) -> "Plan":
+        """The FD-NN comparison plan (Sec. III-C, fddpd_fdnn_plan_create; FP32): precode takes
+        the channel of all N bins, distort the data-bin H for combining and W / alpha of
+        every bin."""
+        return cls(cfg.M, cfg.K, cfg.N, cfg.N_d, cfg.S_per_real, max_symbols or cfg.S, P_T, cfg.orders, cfg.L,
+                   cfg.grid, residual=residual, precision=FDDPD_FP32, first_bin=cfg.first_bin, stream=stream,
+                   pa_G=getattr(cfg, "pa_G", 0), fdnn=(cfg.nn_L4, cfg.nn_D, cfg.nn_layers))
 
     def _check(self, rc: int):
         if rc:

@@ -18,7 +18,7 @@ LIB = os.path.join(OUT, "libfddpd.so")
 SOURCES = ["api.cu", "zf.cu", "fdcnn.cu", "bingemm.cu", "bingemm_f32.cu", "bingemm_bf16.cu", "bingemm_f16.cu",
            "fftpa.cu", *[f"fftpa_n{n}.cu" for n in range(6, 13)],
            *[f"fftpa16_n{n}.cu" for n in range(6, 13)], "update.cu", "tc_gemm.cu",
-           "pack16.cu", "noalloc.cu", "tcbin.cu", "tczf.cu", "ser.cu", "check.cu"]
+           "pack16.cu", "noalloc.cu", "tcbin.cu", "tczf.cu", "ser.cu", "check.cu", "fdnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -30,7 +30,6 @@ struct fddpd_plan {
     c32 *st, *gy, *gst, *xh, *Xpa, *tw;
     void *zf_scratch;
     float *act, *gpre, *partials, *grad, *adam_m, *adam_v;
-    c32 *pu_s, *pu_st;  // per-user parameters: one user's symbols and FD-CNN output [S][N_d]
     double *met;
     int *status;        // [0] singular subcarriers of the last precode, [1] sticky device timeouts
     int *status_host;
@@ -48,6 +47,12 @@ struct fddpd_plan {
     size_t gxh_off;                // BF16 planes, recomputed x(t): g_xhat's offset in the X^PA buffer
     const void *pk_H, *pk_W;       // the FP32 arrays the copies were made from
     int pk_R;
+    bool wfree;                    // W16 holds H^H and the ZF scratch Y = L^{-1} of pk_H (fddpd_precode, W = NULL)
+    // FD-NN comparison plans (fddpd_fdnn_plan_create)
+    bool nn;
+    fdk::FdnnDesc nnd;
+    c32 *nn_t, *nn_o;              // user streams in time [S K][N]; network output, then its DFT
+    float *nn_al;                  // alpha of the data bins [R_max][N_d]
     long adam_t;
     // stage tracing
     int prof;
@@ -68,7 +73,7 @@ struct fddpd_plan {
 
 static const char *kStageNames[FDDPD_N_STAGES] = {
     "zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
-    "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack"};
+    "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack", "zmul", "fdnn_rows", "fdnn_mlp"};
 
 static int stage_begin(fddpd_plan *p, int stage) {
     if (!p->prof || p->nrec >= kMaxRec) return -1;
@@ -138,8 +143,6 @@ static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dp
     if (dpd->N_conv < 1 || dpd->N_conv > 64) return set_err(nullptr, FDDPD_ERR_ARG, "N_conv=%d outside 1..64", dpd->N_conv);
     if (dpd->residual != 0 && dpd->residual != 1) return set_err(nullptr, FDDPD_ERR_ARG, "residual must be 0 or 1");
     if (dpd->per_user != 0 && dpd->per_user != 1) return set_err(nullptr, FDDPD_ERR_ARG, "per_user must be 0 or 1");
-    if (dpd->per_user && (d->precision != FDDPD_FP32 || dpd->L_U != 1))
-        return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "per-user parameters need an FP32 plan and L_U = 1");
     return FDDPD_OK;
 }
 
@@ -222,7 +225,6 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_h16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
         o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
     }
-    const size_t o_pu = dpd->per_user ? take(2 * sizeof(c32) * (size_t)S * g.N_d) : 0;
     p->bytes = off;
     cudaError_t e = cudaMalloc(&p->base, off);
     if (e != cudaSuccess) {
@@ -237,10 +239,6 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
     p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
     p->zf_scratch = b + o_zf;
-    if (dpd->per_user) {
-        p->pu_s = (c32 *)(b + o_pu);
-        p->pu_st = p->pu_s + (size_t)S * g.N_d;
-    }
     if (p->p16) {
         p->act16 = (__nv_bfloat16 *)(b + o_a16); p->actT16 = (__nv_bfloat16 *)(b + o_aT);
         p->gd16 = (__nv_bfloat16 *)(b + o_g16); p->gdT16 = (__nv_bfloat16 *)(b + o_gT);
@@ -256,6 +254,79 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 2 * sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_m, 0, sizeof(float) * g.theta_len, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_v, 0, sizeof(float) * g.theta_len, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        set_err(nullptr, FDDPD_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e));
+        fddpd_plan_destroy(p);
+        return FDDPD_ERR_CUDA;
+    }
+    *out = p;
+    return FDDPD_OK;
+}
+
+// Every subcarrier as a data bin in FFT bin order: the geometry of the FD-NN chain's
+// precoder, which covers the guard bins too.
+static Geo all_bins(const Geo &g) {
+    Geo a = g;
+    a.N_d = g.N;
+    a.first_bin = 0;
+    return a;
+}
+
+extern "C" int fddpd_fdnn_plan_create(fddpd_plan **out, const fddpd_dims *d, const fddpd_pa_desc *pa,
+                                      const fddpd_fdnn_desc *nn, void *stream) {
+    if (!out) return set_err(nullptr, FDDPD_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!d || !nn) return set_err(nullptr, FDDPD_ERR_ARG, "null descriptor");
+    fddpd_dpd_desc dummy{};
+    dummy.G = 1;
+    while (dummy.G * dummy.G < d->N_d) ++dummy.G;
+    dummy.L_U = 1; dummy.K_C = 1; dummy.K_S = 1; dummy.N_conv = 1; dummy.residual = 1;
+    int rc = validate(d, pa, &dummy);
+    if (rc) return rc;
+    if (d->precision != FDDPD_FP32) return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "FD-NN plans are FP32");
+    if (nn->L4 < 0 || nn->L4 > 15 || nn->D < 1 || nn->D > 32 || nn->layers < 1 || nn->layers > 4 ||
+        (nn->residual != 0 && nn->residual != 1))
+        return set_err(nullptr, FDDPD_ERR_ARG, "FD-NN: L4 0..15, D 1..32, layers 1..4, residual 0 or 1");
+    fddpd_plan *p = new (std::nothrow) fddpd_plan;
+    if (!p) return set_err(nullptr, FDDPD_ERR_NOMEM, "host allocation failed");
+    memset(p, 0, sizeof *p);
+    p->d = *d; p->pa = *pa; p->dpd = dummy;
+    p->g = make_geo(d, pa, &dummy);
+    p->nn = true;
+    p->nnd = fdk::FdnnDesc{nn->L4, nn->D, nn->layers, nn->residual};
+    p->g.theta_len = fdk::fdnn_theta_len(p->g, p->nnd);
+    if (p->g.theta_len > 12288) {
+        delete p;
+        return set_err(nullptr, FDDPD_ERR_UNSUPPORTED, "FD-NN with more than 12288 parameters");
+    }
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->fp64_factor = true;
+    const Geo &g = p->g;
+    const long S = d->max_symbols;
+    p->R_max = (int)((S + g.S_per_real - 1) / g.S_per_real);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_t = take(sizeof(c32) * S * g.K * g.N), o_o = take(sizeof(c32) * S * g.K * g.N),
+                 o_xh = take(sizeof(c32) * S * g.M * g.N), o_X = take(sizeof(c32) * S * g.M * g.N_d),
+                 o_al = take(sizeof(float) * (size_t)p->R_max * g.N_d), o_tw = take(sizeof(c32) * g.N),
+                 o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int)),
+                 o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N));
+    p->bytes = off;
+    cudaError_t e = cudaMalloc(&p->base, off);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return set_err(nullptr, FDDPD_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
+    }
+    char *b = static_cast<char *>(p->base);
+    p->nn_t = (c32 *)(b + o_t); p->nn_o = (c32 *)(b + o_o); p->xh = (c32 *)(b + o_xh); p->Xpa = (c32 *)(b + o_X);
+    p->nn_al = (float *)(b + o_al); p->tw = (c32 *)(b + o_tw); p->met = (double *)(b + o_met);
+    p->status = (int *)(b + o_stat); p->zf_scratch = b + o_zf;
+    e = cudaMallocHost(&p->status_host, 2 * sizeof(int));
+    if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
+    p->launches = 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 2 * sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         set_err(nullptr, FDDPD_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e));
@@ -337,6 +408,7 @@ extern "C" int fddpd_invalidate_operands(fddpd_plan *p) {
     p->pk_H = nullptr;
     p->pk_W = nullptr;
     p->pk_R = 0;
+    p->wfree = false;
     return FDDPD_OK;
 }
 
@@ -376,19 +448,40 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
     if (!p) return FDDPD_ERR_ARG;
     if (R < 0 || R > p->R_max) return set_err(p, FDDPD_ERR_ARG, "R=%d outside 0..%d", R, p->R_max);
     if (R == 0) return FDDPD_OK;
-    if (!H || !W || !alpha) return set_err(p, FDDPD_ERR_ARG, "null pointer");
-    if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    if (!H || !alpha) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (p->nn) {   // the FD-NN chain precodes every bin: ZF of all N subcarriers
+        if (!W) return set_err(p, FDDPD_ERR_ARG, "FD-NN plans need W");
+        if (!aligned(H, 8) || !aligned(W, 8) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+        const Geo ga = all_bins(p->g);
+        FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+        for (int ph = 0; ph < 3; ++ph)
+            FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
+                     fdk::zf_phase(ph, ga, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha,
+                                   p->status, p->zf_scratch, nullptr, nullptr, fdk::OUT_F32, false, true,
+                                   p->status + 1, p->stream));
+        FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+        FD_CK(p, cudaStreamSynchronize(p->stream));
+        if (p->status_host[0]) return set_err(p, FDDPD_ERR_SINGULAR, "a Gram matrix H_k H_k^H is not positive definite");
+        return FDDPD_OK;
+    }
+    if (!W && !p->p16) return set_err(p, FDDPD_ERR_UNSUPPORTED, "W = NULL (precoder kept as its factors) needs a 16-bit plan");
+    if (!aligned(H, 8) || (W && !aligned(W, 8)) || !aligned(alpha, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     cudaStream_t st = p->stream;
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
-    for (int ph = 0; ph < 3; ++ph)
+    // W = NULL: the Gram kernel writes the 16-bit H^H beside H's copy and the factor's Y
+    // stays in the scratch; the chain then applies W s = H^H (Z s) and no W is formed
+    const int nph = W ? 3 : 2;
+    for (int ph = 0; ph < nph; ++ph)
         FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
                  fdk::zf_phase(ph, p->g, R, reinterpret_cast<const c32 *>(H), reinterpret_cast<c32 *>(W), alpha,
-                               p->status, p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 ? p->W16 : nullptr,
-                               p->kind16, p->tc_bin, p->fp64_factor, p->status + 1, st));
+                               p->status, p->zf_scratch, p->p16 ? p->H16 : nullptr, p->p16 && W ? p->W16 : nullptr,
+                               p->kind16, p->tc_bin, p->fp64_factor, p->status + 1, st, true,
+                               W ? nullptr : p->W16));
     if (p->p16) {
         p->pk_H = H;
         p->pk_W = W;
         p->pk_R = R;
+        p->wfree = !W;
     }
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FD_CK(p, cudaStreamSynchronize(st));
@@ -399,8 +492,14 @@ extern "C" int fddpd_precode(fddpd_plan *p, int R, const fddpd_c32 *H, fddpd_c32
 static int check_chain(fddpd_plan *p, int S, const void *s, const void *H, const void *W, const void *alpha,
                        const void *pa, const void *theta) {
     if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
-    if (!s || !H || !W || !alpha || !pa || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
-    if (!aligned(s, 8) || !aligned(H, 8) || !aligned(W, 8) || !aligned(pa, 8) || !aligned(alpha, 4) || !aligned(theta, 4))
+    if (!s || !H || !alpha || !pa || !theta) return set_err(p, FDDPD_ERR_ARG, "null pointer");
+    if (!W) {   // the precoder kept as its factors by fddpd_precode(H, NULL, alpha)
+        const int R = (S + p->g.S_per_real - 1) / p->g.S_per_real;
+        if (!p->wfree || p->pk_H != H || p->pk_R < R)
+            return set_err(p, FDDPD_ERR_ARG, "W is null but no factor of this H is kept (fddpd_precode with W = NULL first)");
+    }
+    if (!aligned(s, 8) || !aligned(H, 8) || (W && !aligned(W, 8)) || !aligned(pa, 8) || !aligned(alpha, 4) ||
+        !aligned(theta, 4))
         return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     return FDDPD_OK;
 }
@@ -419,6 +518,10 @@ static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps
     }
     const Geo &g = p->g;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
+    if (!W) {   // checked by check_chain: the copies of H and H^H of the kept factor
+        o = BinOps{p->H16, p->W16, p->kind16};
+        return FDDPD_OK;
+    }
     if (p->pk_H != H || p->pk_W != W || p->pk_R < R) {
         const long n = (long)R * g.N_d * g.K * g.M;
         FD_STAGE(p, FDDPD_STAGE_PACK, 2,
@@ -428,6 +531,7 @@ static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps
         p->pk_H = H;
         p->pk_W = W;
         p->pk_R = R;
+        p->wfree = false;
     }
     o = BinOps{p->H16, p->W16, p->kind16};
     return FDDPD_OK;
@@ -483,14 +587,6 @@ static int pass_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, const
     return FDDPD_OK;
 }
 
-// The geometry of one user's FD-CNN (per-user parameters): the same network, K = 1.
-static Geo one_user(const Geo &g) {
-    Geo g1 = g;
-    g1.K = 1;
-    g1.theta_len = g.theta_len / g.K;
-    return g1;
-}
-
 static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
                        const c32 *pa, const float *theta, c32 *y, c32 *gy, const Pass *ps = nullptr) {
     const Geo &g = p->g;
@@ -502,32 +598,43 @@ static int run_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c
     int rc0 = pass_operands(p, S, H, W, ps, ops);
     if (rc0) return rc0;
     if (first) FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
-    if (p->p16) {
+    if (p->dpd.per_user) {
+        // user u's own network theta_u over its column block (FD-CNN column t is chain column
+        // t K + u): the shared network's kernels once per user, s and s_tilde addressed in place
+        const long len1 = g.theta_len / g.K;
+        for (int u = 0; u < g.K; ++u) {
+            const float *th = theta + u * len1;
+            if (p->p16) {
+                __nv_bfloat16 *a16 = p->act16 + (long)u * S * p->ldF;
+                FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, th, a16, p->ldF, st, u));
+                FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, th, p->fcw16, p->ldF, p->fbi, st));
+                const fdk::GemmArgs ga{a16, p->fcw16, S, 2 * g.N_d, g.F, p->ldF, p->ldF, 1, 1};
+                FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
+                         fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
+                                            p->fbi, g.N_d, g.residual, p->status + 1, st, g.K, u));
+            } else {
+                float *act = p->act + (long)u * S * g.F;
+                FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, th, act, st, u));
+                FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, S, act, th, s, p->st, st, u));
+            }
+        }
+    } else if (p->p16) {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward_bf16(g, S, s, theta, p->act16, p->ldF, st));
         if (first) FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw(g, theta, p->fcw16, p->ldF, p->fbi, st));
         const fdk::GemmArgs ga{p->act16, p->fcw16, (int)cols, 2 * g.N_d, g.F, p->ldF, p->ldF, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1,
                  fdk::tc_fc_forward(ga, reinterpret_cast<float *>(p->st), reinterpret_cast<const float *>(s),
                                     p->fbi, g.N_d, g.residual, p->status + 1, st));
-    } else if (p->dpd.per_user) {
-        // user u's own network theta_u on its own symbols (L_U = 1): the one-user kernels
-        // on user u's column of s, gathered and scattered by strided copies
-        const Geo g1 = one_user(g);
-        const long len1 = g.theta_len / g.K;
-        const size_t row = sizeof(c32) * g.N_d, pitch = row * g.K;
-        for (int u = 0; u < g.K; ++u) {
-            const float *th = theta + u * len1;
-            float *act = p->act + (long)u * S * g.F;
-            FD_CK(p, cudaMemcpy2DAsync(p->pu_s, row, s + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
-            FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g1, S, p->pu_s, th, act, st));
-            FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g1, S, act, th, p->pu_s, p->pu_st, st));
-            FD_CK(p, cudaMemcpy2DAsync(p->st + (long)u * g.N_d, pitch, p->pu_st, row, row, S, cudaMemcpyDeviceToDevice, st));
-        }
     } else {
         FD_STAGE(p, FDDPD_STAGE_CONV_FWD, 1, fdk::conv_forward(g, S, s, theta, p->act, st));
         FD_STAGE(p, FDDPD_STAGE_FC_FWD, 1, fdk::fc_forward_f32(g, (int)cols, p->act, theta, s, p->st, st));
     }
-    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
+    if (W) {
+        FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->st, p->xh, 1.0f));
+    } else {   // x_hat = alpha H^H (Z s_tilde): Z s_tilde into gst (free until the adjoint)
+        FD_STAGE(p, FDDPD_STAGE_ZMUL, 1, fdk::zf_zmul(g, S, p->zf_scratch, p->st, p->gst, st));
+        FD_STAGE(p, FDDPD_STAGE_PRECODE, 1, expand_op(p, fdk::PRECODE, S, ops, alpha, p->gst, p->xh, 1.0f));
+    }
     // a backward follows when gy is wanted: keep the time-domain PA input for its adjoint
     // when the plan is set to (FDDPD_OPT_KEEP_PA_INPUT); by default the adjoint recomputes it
     void *xt = keeps_xt(p) && gy ? p->xt16 : nullptr;
@@ -562,9 +669,53 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     void *gxh = !a16 ? (void *)p->Xpa : kept ? (void *)p->xh : (void *)((char *)p->Xpa + p->gxh_off);
     FD_STAGE(p, FDDPD_STAGE_FFTPA_ADJ, 1,
              fdk::fftpa_adjoint(g, S * g.M, p->xh, pa, p->tw, p->Xpa, gxh, act_kind(p), kept ? p->xt16 : nullptr, st));
-    FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
-             reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
+    if (W) {
+        FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
+                 reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
+    } else {   // g_s_tilde = Z (alpha H g_xhat): the reduction into gy (read by the adjoint of combine, now free)
+        FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
+                 reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gy, nullptr, nullptr, nullptr, 0.0, gsc));
+        FD_STAGE(p, FDDPD_STAGE_ZMUL, 1, fdk::zf_zmul(g, S, p->zf_scratch, p->gy, p->gst, st));
+    }
     const float *gd = reinterpret_cast<const float *>(p->gst);
+    if (p->dpd.per_user) {
+        // user u's pass over its column block with theta_u and its slice of grad (gd, s in
+        // the chain's column order; the dense layer's 16-bit operands one block at a time)
+        const long len1 = g.theta_len / g.K, W2 = 2L * g.N_d, ldCu = (S + 7) / 8 * 8;
+        for (int u = 0; u < g.K; ++u) {
+            const float *th = theta + u * len1;
+            float *gr = grad + u * len1;
+            if (first) FD_CK(p, cudaMemsetAsync(gr + g.off_fb, 0, sizeof(float) * W2, st));
+            if (p->p16) {
+                __nv_bfloat16 *a16 = p->act16 + (long)u * S * p->ldF, *g16 = p->gd16 + (long)u * S * p->ld2N;
+                float *gpre = p->gpre + (long)u * S * p->ldF;
+                FD_STAGE(p, FDDPD_STAGE_PACK, 2,
+                         fdk::bf16_and_transpose(gd + u * W2, S, W2, g.K * W2, g16, p->ld2N, p->gdT16, ldCu, st) ==
+                                 cudaSuccess
+                             ? fdk::transpose_bf16(a16, S, g.F, p->ldF, p->actT16, ldCu, st)
+                             : cudaGetLastError());
+                if (first) FD_CK(p, cudaMemsetAsync(gr + g.off_fw, 0, sizeof(float) * W2 * g.F, st));
+                const fdk::GemmArgs gw{p->gdT16, p->actT16, (int)W2, g.F, S, ldCu, ldCu, 1, 2};
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1,
+                         fdk::tc_fc_backward_weight(gw, gr + g.off_fw, g.N_d, g.F, p->status + 1, st));
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, S, gd, gr, st, u));
+                FD_STAGE(p, FDDPD_STAGE_PACK, 1, fdk::pack_fcw_t(g, th, p->fcwT16, p->ld2N, st));
+                const fdk::GemmArgs gdx{g16, p->fcwT16, S, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1,
+                         fdk::tc_fc_backward_data(gdx, gpre, p->ldF, a16, p->ldF, p->status + 1, st));
+                FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, gpre, p->ldF, p->partials, st, u));
+            } else {
+                const float *act = p->act + (long)u * S * g.F;
+                float *gpre = p->gpre + (long)u * S * g.F;
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, S, gd, act, gr, !first, st, u));
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, S, gd, gr, st, u));
+                FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g, S, gd, th, act, gpre, st, u));
+                FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g, S, s, gpre, g.F, p->partials, st, u));
+            }
+            FD_CK(p, fdk::conv_reduce(g, S, p->partials, gr, !first, st));
+        }
+        return FDDPD_OK;
+    }
     if (first) FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
     if (p->p16) {
         const long W2 = 2L * g.N_d;
@@ -583,28 +734,6 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
         const fdk::GemmArgs gdx{p->gd16, p->fcwT16, cols, g.F, (int)W2, p->ld2N, p->ld2N, 1, 1};
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::tc_fc_backward_data(gdx, p->gpre, p->ldF, p->act16, p->ldF, p->status + 1, st));
-    } else if (p->dpd.per_user) {
-        // per user: user u's slices of the activations and of theta / grad (the bias
-        // gradients were cleared above for user 0 only)
-        const Geo g1 = one_user(g);
-        const long len1 = g.theta_len / g.K;
-        const size_t row = sizeof(c32) * g.N_d, pitch = row * g.K;
-        for (int u = 0; u < g.K; ++u) {
-            const float *th = theta + u * len1;
-            float *gr = grad + u * len1;
-            const float *act = p->act + (long)u * S * g.F;
-            float *gpre = p->gpre + (long)u * S * g.F;
-            const float *gdu = reinterpret_cast<const float *>(p->pu_st);
-            if (first && u > 0) FD_CK(p, cudaMemsetAsync(gr + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
-            FD_CK(p, cudaMemcpy2DAsync(p->pu_st, row, p->gst + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
-            FD_CK(p, cudaMemcpy2DAsync(p->pu_s, row, s + (long)u * g.N_d, pitch, row, S, cudaMemcpyDeviceToDevice, st));
-            FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g1, S, gdu, act, gr, !first, st));
-            FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g1, S, gdu, gr, st));
-            FD_STAGE(p, FDDPD_STAGE_FC_BWD_D, 1, fdk::fc_backward_data_f32(g1, S, gdu, th, act, gpre, st));
-            FD_STAGE(p, FDDPD_STAGE_CONV_BWD, 2, fdk::conv_backward(g1, S, p->pu_s, gpre, g.F, p->partials, st));
-            FD_CK(p, fdk::conv_reduce(g1, S, p->partials, gr, !first, st));
-        }
-        return FDDPD_OK;
     } else {
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_W, 1, fdk::fc_backward_weight_f32(g, cols, gd, p->act, grad, !first, st));
         FD_STAGE(p, FDDPD_STAGE_FC_BWD_B, 1, fdk::colsum_fcb(g, cols, gd, grad, st));
@@ -615,10 +744,49 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     return FDDPD_OK;
 }
 
+// The FD-NN chain (Sec. III-C): per-user IDFT, the time-domain network, per-user DFT onto
+// every bin, precoding of every bin (W, alpha over all N), IDFT / PA / DFT, combining at
+// the data bins (H of the data bins, alpha gathered at them).
+static int run_fdnn_forward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const c32 *W, const float *alpha,
+                            const c32 *pa, const float *theta, c32 *y) {
+    const Geo &g = p->g;
+    cudaStream_t st = p->stream;
+    const long rows = (long)S * g.K;
+    const double inv_count = 1.0 / ((double)rows * g.N_d);
+    Geo gi = g;
+    gi.in_all = 1;
+    FD_CK(p, cudaMemsetAsync(p->met, 0, sizeof(double) * 8, st));
+    FD_STAGE(p, FDDPD_STAGE_FDNN_ROWS, 1, fdk::fdnn_user_rows(g, rows, true, s, p->nn_t, p->tw, st));
+    FD_STAGE(p, FDDPD_STAGE_FDNN_MLP, 1, fdk::fdnn_mlp(g, p->nnd, S, theta, p->nn_t, p->nn_o, st));
+    FD_STAGE(p, FDDPD_STAGE_FDNN_ROWS, 1, fdk::fdnn_user_rows(g, rows, false, p->nn_o, p->nn_o, p->tw, st));
+    FD_STAGE(p, FDDPD_STAGE_PRECODE, 1,
+             fdk::bin_expand(all_bins(g), fdk::PRECODE, S, W, fdk::OUT_F32, alpha, p->nn_o, p->xh, st));
+    FD_STAGE(p, FDDPD_STAGE_FFTPA_FWD, 1,
+             fdk::fftpa_forward(gi, S * g.M, p->xh, pa, p->tw, p->Xpa, fdk::OUT_F32, p->met, nullptr, st));
+    FD_CK(p, fdk::fdnn_alpha_data(g, (S + g.S_per_real - 1) / g.S_per_real, alpha, p->nn_al, st));
+    FD_STAGE(p, FDDPD_STAGE_COMBINE, 1,
+             fdk::bin_reduce(g, fdk::COMBINE, S, H, fdk::OUT_F32, p->nn_al, p->Xpa, y, s, nullptr, p->met, inv_count,
+                             st));
+    FD_CK(p, fdk::finalize_metrics(p->met, inv_count, st));
+    p->launches += 2;
+    return FDDPD_OK;
+}
+
 extern "C" int fddpd_distort(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
                              const float *alpha, const fddpd_c32 *pa_coef, const float *theta, fddpd_c32 *y,
                              double *metrics) {
     if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) {
+        if (!W) return set_err(p, FDDPD_ERR_ARG, "FD-NN plans need W");
+        int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
+        if (rc) return rc;
+        if ((y && !aligned(y, 8)) || (metrics && !aligned(metrics, 8))) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned output");
+        rc = run_fdnn_forward(p, S, (const c32 *)s, (const c32 *)H, (const c32 *)W, alpha, (const c32 *)pa_coef, theta,
+                              (c32 *)y);
+        if (rc) return rc;
+        if (metrics) FD_CK(p, cudaMemcpyAsync(metrics, p->met, sizeof(double) * 5, cudaMemcpyDeviceToDevice, p->stream));
+        return FDDPD_OK;
+    }
     int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
     if (rc) return rc;
     if ((y && !aligned(y, 8)) || (metrics && !aligned(metrics, 8))) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned output");
@@ -633,6 +801,7 @@ extern "C" int fddpd_backward(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
                               const float *alpha, const fddpd_c32 *pa_coef, const float *theta, float *grad,
                               double *metrics) {
     if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans run the forward chain only");
     int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
     if (rc) return rc;
     if (!grad) return set_err(p, FDDPD_ERR_ARG, "grad is null");
@@ -659,6 +828,7 @@ extern "C" int fddpd_update(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
                             const float *alpha, const fddpd_c32 *pa_coef, float *theta, float lr, int iters,
                             int optimizer, double *metrics) {
     if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans run the forward chain only");
     int rc = check_chain(p, S, s, H, W, alpha, pa_coef, theta);
     if (rc) return rc;
     if (iters < 0) return set_err(p, FDDPD_ERR_ARG, "iters < 0");
@@ -783,6 +953,9 @@ static int update_host_impl(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
     }
     FD_CK(p, cudaMemsetAsync(p->status, 0, sizeof(int), st));
     const size_t h16_real = h_real / 2;
+    // one iteration in a 16-bit plan: each chunk's precoder stays as its factors (H^H and the
+    // chunk's Y, used right after by its own pass), so no W is formed at all
+    const bool wfree = p->p16 && iters == 1;
     for (int c = 0; c < nch; ++c) {
         const long r0 = rb[c], r1 = rb[c + 1];
         const long t0 = r0 * g.S_per_real, t1 = r1 * g.S_per_real < S ? r1 * g.S_per_real : S;
@@ -790,23 +963,26 @@ static int update_host_impl(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
         c32 *Wc = (c32 *)((char *)p->hW + r0 * h_real);
         float *alc = p->hal + r0 * g.N_d;
         FD_CK(p, cudaStreamWaitEvent(st, p->cev[1 + c], 0));
-        for (int ph = 0; ph < 3; ++ph)
+        void *W16c = p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr;
+        for (int ph = 0; ph < (wfree ? 2 : 3); ++ph)
             FD_STAGE(p, FDDPD_STAGE_ZF_GRAM + ph, 1,
                      fdk::zf_phase(ph, g, (int)(r1 - r0), Hc, Wc, alc, p->status, p->zf_scratch,
-                                   p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr,
-                                   p->p16 ? (char *)p->W16 + r0 * h16_real : nullptr, p->kind16, p->tc_bin,
-                                   p->fp64_factor, p->status + 1, st, !p->p16));   // 16-bit plans read only W's copy
+                                   p->p16 ? (char *)p->H16 + r0 * h16_real : nullptr, wfree ? nullptr : W16c,
+                                   p->kind16, p->tc_bin, p->fp64_factor, p->status + 1, st,
+                                   !p->p16,                        // 16-bit plans read only W's copy
+                                   wfree ? W16c : nullptr));
         if (iters > 0) {
             const Pass ps{inv_count, c == 0, c == nch - 1, (int)r0};
-            int rc1 = run_backward(p, (int)(t1 - t0), (const c32 *)((const char *)p->hs + t0 * s_sym), Hc, Wc, alc,
-                                   p->hpa, p->htheta, p->grad, &ps);
+            int rc1 = run_backward(p, (int)(t1 - t0), (const c32 *)((const char *)p->hs + t0 * s_sym), Hc,
+                                   wfree ? nullptr : Wc, alc, p->hpa, p->htheta, p->grad, &ps);
             if (rc1) return rc1;
         }
     }
-    if (p->p16) {
-        p->pk_H = p->hH;
-        p->pk_W = p->hW;
-        p->pk_R = (int)R;
+    if (p->p16) {   // the scratch holds only the last chunk's factor: no kept factor after this call
+        p->pk_H = wfree ? nullptr : p->hH;
+        p->pk_W = wfree ? nullptr : p->hW;
+        p->pk_R = wfree ? 0 : (int)R;
+        p->wfree = false;
     }
     // a singular Gram matrix fails the call before the step, leaving theta as it was
     FD_CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -831,6 +1007,7 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
                                  const fddpd_c32 *pa_coef, float *theta, float lr, int iters, int optimizer,
                                  double *metrics) {
     if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans run the forward chain only");
     const int rc = update_host_impl(p, S, s, H, pa_coef, theta, lr, iters, optimizer, metrics);
     // a call that fails part-way may have copies of the caller's host arrays in flight:
     // they end before the call returns, so the caller may reuse or free the arrays (a
@@ -866,6 +1043,7 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
                               const float *alpha, const fddpd_c32 *pa_coef, const float *theta, int reps,
                               float *ms) {
     if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans have one implementation");
     if (reps < 1) return set_err(p, FDDPD_ERR_ARG, "reps < 1");
     float t[2] = {-1.0f, -1.0f};
     const bool was = p->tc_bin;

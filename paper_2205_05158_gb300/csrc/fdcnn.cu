@@ -16,6 +16,16 @@
 
 namespace fdk {
 
+// FD-CNN column -> (symbol, user) of the chain's [S][K] order.  A shared network runs over
+// every column c = t K + u; per-user parameters run one pass per user u over that user's
+// own column block, FD-CNN column t being chain column t K + u.
+struct ColMap {
+    int K, u;   // u < 0: all columns of the chain
+    FD_HD long chain(long c) const { return u < 0 ? c : c * K + u; }
+    FD_HD long sym(long c) const { return u < 0 ? c / K : c; }
+    FD_HD int user(long c) const { return u < 0 ? (int)(c % K) : u; }
+};
+
 // ---------------------------------------------------------------------------
 // conv + ReLU forward and the conv parameter gradient.  The input grids sit in
 // shared memory zero padded to Gp = (Go - 1) K_S + K_C per side (data at offset pad),
@@ -40,7 +50,7 @@ FD_D void load_padded(const Geo &g, const c32 *s, long t, int u, float *Xp) {
 }
 
 template <int KC, typename TOut>
-__global__ void __launch_bounds__(256) conv_fwd_kernel(Geo g, int cols_per_cta, long cols,
+__global__ void __launch_bounds__(256) conv_fwd_kernel(Geo g, ColMap cm, int cols_per_cta, long cols,
                                                        const c32 *__restrict__ s, const float *__restrict__ theta,
                                                        TOut *__restrict__ act, long ld) {
     extern __shared__ float Xp[];
@@ -49,7 +59,7 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(Geo g, int cols_per_cta, 
     const long c0 = (long)blockIdx.x * cols_per_cta;
     for (long col = c0; col < min(cols, c0 + cols_per_cta); ++col) {
         __syncthreads();
-        load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
+        load_padded(g, s, cm.sym(col), cm.user(col), Xp);
         __syncthreads();
         for (int f = threadIdx.x; f < g.F; f += blockDim.x) {
             const int o = f / GoGo, rem = f % GoGo, i = rem / g.Go, j = rem % g.Go;
@@ -122,7 +132,7 @@ FD_D ConvPos conv_positions(const Geo &g) {
 }
 
 template <typename TOut>
-__global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, const c32 *__restrict__ s,
+__global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, ColMap cm, long cols, const c32 *__restrict__ s,
                                                             const float *__restrict__ theta, TOut *__restrict__ act,
                                                             long ld) {
     const int G = g.G, GG = G * G;
@@ -137,9 +147,9 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, co
     }
     const ConvPos cp = conv_positions(g);
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
-        const c32 *row = s + col * g.N_d;   // L_U = 1: the column's own user
+        const c32 *row = s + cm.chain(col) * g.N_d;   // L_U = 1: the column's own user
         TOut *out = act + col * ld;
-        if (col + gridDim.x < cols) prefetch_row_l1(row + gridDim.x * g.N_d, g.N_d);
+        if (col + gridDim.x < cols) prefetch_row_l1(s + cm.chain(col + gridDim.x) * g.N_d, g.N_d);
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, long cols, co
 
 // parameter gradient: every thread accumulates the 36 weight and 2 bias partial sums of
 // its positions over the CTA's columns; one block reduction per CTA
-__global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, const c32 *__restrict__ s,
+__global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, ColMap cm, long cols, const c32 *__restrict__ s,
                                                             const float *__restrict__ gpre, long ldg,
                                                             float *__restrict__ partials) {
     constexpr int NW = 2 * 2 * 9 + 2;
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, co
     };
     load_g(blockIdx.x);
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
-        const c32 *row = s + col * g.N_d;
+        const c32 *row = s + cm.chain(col) * g.N_d;
         float gc[2][CF_PPT];
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, long cols, co
             gc[1][k] = gn[1][k];
         }
         load_g(col + gridDim.x);
-        if (col + gridDim.x < cols) prefetch_row_l1(row + gridDim.x * g.N_d, g.N_d);
+        if (col + gridDim.x < cols) prefetch_row_l1(s + cm.chain(col + gridDim.x) * g.N_d, g.N_d);
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -259,36 +269,38 @@ static int conv_cols_per_cta(long cols) { return cols >= 152 * 64 ? 8 : 1; }
 
 template <typename TOut>
 static cudaError_t conv_fwd_launch(const Geo &g, int S, const c32 *s, const float *theta, TOut *act, long ld,
-                                   cudaStream_t st) {
-    const long cols = (long)S * g.K;
+                                   cudaStream_t st, int user) {
+    const ColMap cm{g.K, user};
+    const long cols = user < 0 ? (long)S * g.K : S;
     if (!cols) return cudaSuccess;
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * (size_t)g.Cin * Gp * Gp;
     if (conv_fast(g) && g.L_U == 1) {
-        conv_fwd_fast_kernel<TOut><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cols, s, theta, act, ld);
+        conv_fwd_fast_kernel<TOut><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cm, cols, s, theta, act, ld);
         return cudaGetLastError();
     }
     const int cpc = conv_cols_per_cta(cols);
     const unsigned blocks = (unsigned)((cols + cpc - 1) / cpc);
-    if (g.K_C == 3) conv_fwd_kernel<3, TOut><<<blocks, 256, sm, st>>>(g, cpc, cols, s, theta, act, ld);
-    else conv_fwd_kernel<0, TOut><<<blocks, 256, sm, st>>>(g, cpc, cols, s, theta, act, ld);
+    if (g.K_C == 3) conv_fwd_kernel<3, TOut><<<blocks, 256, sm, st>>>(g, cm, cpc, cols, s, theta, act, ld);
+    else conv_fwd_kernel<0, TOut><<<blocks, 256, sm, st>>>(g, cm, cpc, cols, s, theta, act, ld);
     return cudaGetLastError();
 }
 
-cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st) {
-    return conv_fwd_launch(g, S, s, theta, act, g.F, st);
+cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st,
+                         int user) {
+    return conv_fwd_launch(g, S, s, theta, act, g.F, st, user);
 }
 
 cudaError_t conv_forward_bf16(const Geo &g, int S, const c32 *s, const float *theta, __nv_bfloat16 *act, long ld,
-                              cudaStream_t st) {
-    return conv_fwd_launch(g, S, s, theta, act, ld, st);
+                              cudaStream_t st, int user) {
+    return conv_fwd_launch(g, S, s, theta, act, ld, st, user);
 }
 
 // Parameter gradient: thread owns output positions (o-independent) and, for a batch of
 // columns, accumulates every (o, c, a, b) product and the bias sums in registers; one
 // block reduction per CTA writes the CTA's partial sums.
 template <int KC, int NCONV, int CIN>
-__global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, long cols,
+__global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, ColMap cm, int cols_per_cta, long cols,
                                                        const c32 *__restrict__ s, const float *__restrict__ gpre,
                                                        long ldg, float *__restrict__ partials) {
     extern __shared__ float smf[];
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, 
     const long c0 = (long)blockIdx.x * cols_per_cta;
     for (long col = c0; col < min(cols, c0 + cols_per_cta); ++col) {
         __syncthreads();
-        load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
+        load_padded(g, s, cm.sym(col), cm.user(col), Xp);
         for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * ldg + f];
         __syncthreads();
         for (int p = threadIdx.x; p < GoGo; p += blockDim.x) {
@@ -343,14 +355,14 @@ __global__ void __launch_bounds__(256) conv_bwd_kernel(Geo g, int cols_per_cta, 
 
 // generic fallback (any kernel size / channel count): one warp per parameter, lanes
 // over positions, one column per CTA
-__global__ void conv_bwd_generic_kernel(Geo g, const c32 *__restrict__ s, const float *__restrict__ gpre, long ldg,
-                                        float *__restrict__ partials) {
+__global__ void conv_bwd_generic_kernel(Geo g, ColMap cm, const c32 *__restrict__ s, const float *__restrict__ gpre,
+                                        long ldg, float *__restrict__ partials) {
     extern __shared__ float smf[];
     const int Gp = padded_side(g), GpGp = Gp * Gp, GoGo = g.Go * g.Go, KC = g.K_C;
     float *Xp = smf;
     float *gp = Xp + g.Cin * GpGp;
     const long col = blockIdx.x;
-    load_padded(g, s, col / g.K, (int)(col % g.K), Xp);
+    load_padded(g, s, cm.sym(col), cm.user(col), Xp);
     for (int f = threadIdx.x; f < g.F; f += blockDim.x) gp[f] = gpre[col * ldg + f];
     __syncthreads();
     const int nw = g.n_convw + g.N_conv;
@@ -380,14 +392,15 @@ static long conv_partial_rows(const Geo &g, long cols) {
 }
 
 cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, long ldg, float *partials,
-                          cudaStream_t st) {
-    const long cols = (long)S * g.K;
+                          cudaStream_t st, int user) {
+    const ColMap cm{g.K, user};
+    const long cols = user < 0 ? (long)S * g.K : S;
     if (!cols) return cudaSuccess;
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * ((size_t)g.Cin * Gp * Gp + g.F);
     cudaError_t e;
     if (conv_fast(g) && g.L_U == 1) {
-        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cols, s, gpre, ldg, partials);
+        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cm, cols, s, gpre, ldg, partials);
         return cudaGetLastError();
     }
     if (conv_bwd_fast(g)) {
@@ -395,11 +408,11 @@ cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, 
         const unsigned blocks = (unsigned)conv_partial_rows(g, cols);
         e = cudaFuncSetAttribute(conv_bwd_kernel<3, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        conv_bwd_kernel<3, 2, 2><<<blocks, 256, sm, st>>>(g, cpc, cols, s, gpre, ldg, partials);
+        conv_bwd_kernel<3, 2, 2><<<blocks, 256, sm, st>>>(g, cm, cpc, cols, s, gpre, ldg, partials);
     } else {
         e = cudaFuncSetAttribute(conv_bwd_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        conv_bwd_generic_kernel<<<(unsigned)cols, 256, sm, st>>>(g, s, gpre, ldg, partials);
+        conv_bwd_generic_kernel<<<(unsigned)cols, 256, sm, st>>>(g, cm, s, gpre, ldg, partials);
     }
     return cudaGetLastError();
 }
@@ -422,22 +435,23 @@ cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *gr
 }
 
 // fc_b gradient: column sums of gd [cols][2 N_d] (interleaved rows) -> grad[off_fb + pi(n')]
-__global__ void colsum_fcb_kernel(Geo g, int cols, int chunk, const float *__restrict__ gd, float *__restrict__ gfb) {
+__global__ void colsum_fcb_kernel(Geo g, ColMap cm, int cols, int chunk, const float *__restrict__ gd,
+                                  float *__restrict__ gfb) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int W2 = 2 * g.N_d;
     if (n >= W2) return;
     const long c0 = (long)blockIdx.y * chunk, c1 = min((long)cols, c0 + chunk);
     float acc = 0.f;
-    for (long c = c0; c < c1; ++c) acc += gd[c * W2 + n];
+    for (long c = c0; c < c1; ++c) acc += gd[cm.chain(c) * W2 + n];
     const int row = (n & 1) * g.N_d + (n >> 1);
     atomicAdd(gfb + row, acc);
 }
 
-cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st) {
+cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st, int user) {
     const int W2 = 2 * g.N_d, chunk = 256;
     dim3 grid((W2 + 255) / 256, (cols + chunk - 1) / chunk);
     if (!cols) return cudaSuccess;
-    colsum_fcb_kernel<<<grid, 256, 0, st>>>(g, cols, chunk, gd, grad + g.off_fb);
+    colsum_fcb_kernel<<<grid, 256, 0, st>>>(g, ColMap{g.K, user}, cols, chunk, gd, grad + g.off_fb);
     return cudaGetLastError();
 }
 
@@ -450,10 +464,11 @@ struct FcFwd {   // A = act [cols][F]; B(n', f) = fc_w[pi(n')][f]; C -> s_tilde 
     const float *s;
     float *st;
     int F, Nd, residual;
+    ColMap cm;      // s and s_tilde in the chain's column order
     FD_D float a(long m, long k) const { return act[m * F + k]; }
     FD_D float b(long n, long k) const { return fw[(long)((n & 1) * Nd + (n >> 1)) * F + k]; }
     FD_D void store(long m, long n, float v) const {
-        const long idx = m * 2 * Nd + n;
+        const long idx = cm.chain(m) * 2 * Nd + n;
         st[idx] = v + fb[(n & 1) * Nd + (n >> 1)] + (residual ? s[idx] : 0.f);
     }
 };
@@ -461,7 +476,8 @@ struct FcBwdData {   // A = gd [cols][2N_d]; B(f, n') = fc_w[pi(n')][f]; C -> gp
     const float *gd, *fw, *act;
     float *gpre;
     int F, Nd;
-    FD_D float a(long m, long k) const { return gd[m * 2 * Nd + k]; }
+    ColMap cm;         // gd in the chain's column order
+    FD_D float a(long m, long k) const { return gd[cm.chain(m) * 2 * Nd + k]; }
     FD_D float b(long n, long k) const { return fw[(long)((k & 1) * Nd + (k >> 1)) * F + n]; }
     FD_D void store(long m, long n, float v) const {
         const long idx = m * F + n;
@@ -472,7 +488,8 @@ struct FcBwdWeight {   // A(n', c) = gd[c][n']; B(f, c) = act[c][f]; C -> grad f
     const float *gd, *act;
     float *gfw;
     int F, Nd, accumulate;
-    FD_D float a(long m, long k) const { return gd[k * 2 * Nd + m]; }
+    ColMap cm;           // gd in the chain's column order
+    FD_D float a(long m, long k) const { return gd[cm.chain(k) * 2 * Nd + m]; }
     FD_D float b(long n, long k) const { return act[k * F + n]; }
     FD_D void store(long m, long n, float v) const {
         float *dst = gfw + (long)((m & 1) * Nd + (m >> 1)) * F + n;
@@ -530,21 +547,21 @@ static cudaError_t run_sgemm(const Op &op, long Mdim, long Ndim, long Kdim, cuda
 }
 
 cudaError_t fc_forward_f32(const Geo &g, int cols, const float *act, const float *theta, const c32 *s, c32 *st,
-                           cudaStream_t stm) {
+                           cudaStream_t stm, int user) {
     FcFwd op{act, theta + g.off_fw, theta + g.off_fb, reinterpret_cast<const float *>(s),
-             reinterpret_cast<float *>(st), g.F, g.N_d, g.residual};
+             reinterpret_cast<float *>(st), g.F, g.N_d, g.residual, ColMap{g.K, user}};
     return run_sgemm<FcFwd, true, true>(op, cols, 2L * g.N_d, g.F, stm);
 }
 
 cudaError_t fc_backward_data_f32(const Geo &g, int cols, const float *gd, const float *theta, const float *act,
-                                 float *gpre, cudaStream_t stm) {
-    FcBwdData op{gd, theta + g.off_fw, act, gpre, g.F, g.N_d};
+                                 float *gpre, cudaStream_t stm, int user) {
+    FcBwdData op{gd, theta + g.off_fw, act, gpre, g.F, g.N_d, ColMap{g.K, user}};
     return run_sgemm<FcBwdData, true, false>(op, cols, g.F, 2L * g.N_d, stm);
 }
 
 cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, const float *act, float *grad,
-                                   bool accumulate, cudaStream_t stm) {
-    FcBwdWeight op{gd, act, grad + g.off_fw, g.F, g.N_d, accumulate ? 1 : 0};
+                                   bool accumulate, cudaStream_t stm, int user) {
+    FcBwdWeight op{gd, act, grad + g.off_fw, g.F, g.N_d, accumulate ? 1 : 0, ColMap{g.K, user}};
     return run_sgemm<FcBwdWeight, false, false>(op, 2L * g.N_d, g.F, cols, stm);
 }
 

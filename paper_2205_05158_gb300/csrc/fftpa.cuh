@@ -419,7 +419,9 @@ FD_HD size_t fftpa_smem_base_(const Geo &g) {
     const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * pa_coef_count(g));
     return (b + 15) & ~size_t(15);
 }
-inline size_t fwd_stage_bytes(const Geo &g) { return sizeof(c32) * (size_t)((g.N_d + 1) & ~1); }   // x_hat row
+// x_hat row: the N_d data bins, or every bin (in_all: the precoded rows of the FD-NN chain)
+FD_HD int fwd_in_len(const Geo &g) { return g.in_all ? g.N : g.N_d; }
+inline size_t fwd_stage_bytes(const Geo &g) { return sizeof(c32) * (size_t)((fwd_in_len(g) + 1) & ~1); }
 inline size_t adj_stage_bytes(const Geo &g) { return 4 * (size_t)(g.N + ((g.N_d + 3) & ~3)); }    // x(t), gX rows
 inline size_t fftpa_smem_bytes_(const Geo &g) {
     return fftpa_smem_base_(g) + (size_t)rows_per_cta(g.N) * fwd_stage_bytes(g);
@@ -459,7 +461,8 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
     // x_hat rows of the next row group, in flight while this one is transformed
-    c32 *stage = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((g.N_d + 1) & ~1);
+    const int in_nd = fwd_in_len(g);
+    c32 *stage = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((in_nd + 1) & ~1);
     __shared__ double red[32];
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     bool any_even = false;
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     auto prefetch = [&](long gg) {
         const long r = gg * RPC + grp;
         if (gg < ngroups && r < rows)
-            for (int i = t; i < g.N_d; i += F::T) cp_async_n<8>(stage + i, xh + r * g.N_d + i);
+            for (int i = t; i < in_nd; i += F::T) cp_async_n<8>(stage + i, xh + r * in_nd + i);
         cp_async_commit_all();
     };
     prefetch(blockIdx.x);
@@ -487,7 +490,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
         c32 x[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
+            const int i = g.in_all ? t + q * F::T : data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
             x[q] = (active && i >= 0) ? stage[i] : make_float2(0.f, 0.f);
         }
         __syncthreads();   // the staged rows are read
@@ -657,6 +660,48 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
                 if (i >= 0) orow[i] = Operand<TOut>::from(gv[q]);
             }
         }
+    }
+}
+
+// Plain unitary transforms of user rows (the FD-NN comparison workload of Sec. III-C):
+// INV: [rows][N_d] data bins (guard bins zero) -> [rows][N] time samples (the IDFT of
+// the users' symbols); !INV: [rows][N] time samples -> [rows][N] every bin (the DFT of
+// the predistorted streams).  Rows of RPC per CTA as in the PA row kernels; in place
+// allowed (a row is read whole before it is written).
+template <int LOG2N, bool INV>
+__global__ void __launch_bounds__(256, 2) user_rows_kernel(Geo g, long rows, const c32 *in, c32 *out,
+                                                           const c32 *__restrict__ twp_g) {
+    using F = Fft<LOG2N>;
+    constexpr int RPC = rows_per_cta_t<LOG2N>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / F::T, t = threadIdx.x % F::T;
+    c32 *twp = reinterpret_cast<c32 *>(smem_raw);
+    c32 *bufA = twp + F::N + grp * 2 * F::PADN;
+    c32 *bufB = bufA + F::PADN;
+    for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
+    __syncthreads();
+    const float rs = rsqrtf((float)F::N);
+    const long ngroups = (rows + RPC - 1) / RPC;
+    for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
+        const long row = grp0 * RPC + grp;
+        const bool active = row < rows;
+        c32 x[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int n = t + q * F::T;
+            if (INV) {
+                const int i = data_index(n, g.first_bin, F::N, g.N_d);
+                x[q] = (active && i >= 0) ? in[row * g.N_d + i] : make_float2(0.f, 0.f);
+            } else {
+                x[q] = active ? in[row * F::N + n] : make_float2(0.f, 0.f);
+            }
+        }
+        transform<LOG2N, INV>(x, bufA, bufB, twp, t, rs);
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) out[row * F::N + t + q * F::T] = x[q];
+        }
+        __syncthreads();   // the last pass has read its buffer
     }
 }
 

@@ -15,6 +15,7 @@ struct Geo {
     int M, K, N, N_d, first_bin, S_per_real, log2N;
     int n_orders, orders[8], L;
     int pa_G;                // PA cross-term length of Eq. 9 (0: memory polynomial)
+    int in_all;              // the forward row kernel reads x_hat rows of all N bins (FD-NN chain)
     int G, Go, L_U, Cin, K_C, K_S, pad, N_conv, F, residual;
     int n_convw;             // N_conv * Cin * K_C * K_C
     long off_cb, off_fw, off_fb, theta_len;
@@ -54,11 +55,16 @@ cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, in
 // tc: W on the tensor cores when kind is 16-bit and M <= 128, K <= 16 (err: timeout word)
 // keep_w32 = false: with the tensor-core apply, only the 16-bit copy of W is written
 // fp64: Cholesky and triangular inverse in FP64 (else FP32; FP32 kinds always FP64)
+// HH16 (16-bit kinds, may be null): the Gram phase also writes H^H in W's layout [bin][m][u]
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, bool tc, bool fp64, int *err, cudaStream_t st,
-                     bool keep_w32 = true);
-// W = H^H Z (Z = G^{-1}, lower triangle in the factor's scratch layout) with BF16 hi / lo
-// operand splits on the tensor cores; W16 of the given 16-bit kind beside it
+                     bool keep_w32 = true, void *HH16 = nullptr);
+// out = Z X per (symbol, subcarrier) of S symbols, Z = G^{-1} = Y^H Y from the factor's Y
+// in `scratch` (the realisations of those symbols, from the first); X, out [S][K][N_d]
+cudaError_t zf_zmul(const Geo &g, int S, const void *scratch, const c32 *X, c32 *out, cudaStream_t st);
+// W = H^H Z, Z = G^{-1} = Y^H Y formed in FP32 from the factor's Y = L^{-1} (lower triangle
+// in its scratch layout), with BF16 hi / lo operand splits on the tensor cores; W16 of the
+// given 16-bit kind beside it
 cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,
                         int kind, int *err, cudaStream_t st);
 bool tc_bin_supported(const Geo &g);
@@ -67,22 +73,27 @@ bool tc_bin_supported(const Geo &g);
 cudaError_t ser_count(const Geo &g, int S, const c32 *y, const c32 *s, const float *alpha, int Q, float N0,
                       unsigned long long seed, unsigned long long *counts, cudaStream_t st);
 
-// FD-CNN
-cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st);
-// gact: gradient at the pre-activations, [S K][ldg] FP32
+// FD-CNN.  `user` < 0: the shared network over all S K columns (chain order, column
+// t K + u); user u >= 0: user u's own pass over its S columns, FD-CNN column t reading
+// and writing chain column t K + u of s, s_tilde and their gradients (the activations
+// act / gact are that pass's own [S][.] block; theta / grad point at user u's set)
+cudaError_t conv_forward(const Geo &g, int S, const c32 *s, const float *theta, float *act, cudaStream_t st,
+                         int user = -1);
+// gact: gradient at the pre-activations, [cols][ldg] FP32
 cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gact, long ldg, float *partials,
-                          cudaStream_t st);
-// grad[conv_w, conv_b] = (accumulate ? grad + : ) the sum of the partial rows
+                          cudaStream_t st, int user = -1);
+// grad[conv_w, conv_b] = (accumulate ? grad + : ) the sum of the partial rows (cols: the
+// columns of the conv_backward call)
 cudaError_t conv_reduce(const Geo &g, int cols, const float *partials, float *grad, bool accumulate, cudaStream_t st);
-cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st);
+cudaError_t colsum_fcb(const Geo &g, int cols, const float *gd, float *grad, cudaStream_t st, int user = -1);
 
 // FP32 GEMM with the FD-CNN dense-layer layouts (rows of fc_w interleaved Re/Im)
 cudaError_t fc_forward_f32(const Geo &g, int cols, const float *act, const float *theta, const c32 *s, c32 *st,
-                           cudaStream_t stm);
+                           cudaStream_t stm, int user = -1);
 cudaError_t fc_backward_data_f32(const Geo &g, int cols, const float *gd, const float *theta, const float *act,
-                                 float *gpre, cudaStream_t stm);
+                                 float *gpre, cudaStream_t stm, int user = -1);
 cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, const float *act, float *grad,
-                                   bool accumulate, cudaStream_t stm);
+                                   bool accumulate, cudaStream_t stm, int user = -1);
 
 // per-subcarrier complex contractions (FP32 operands)
 enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3 };
@@ -118,6 +129,19 @@ cudaError_t zf_residual(const Geo &g, long nbins, long every, const c32 *H, cons
                         cudaStream_t st);
 // FMA-loop peak of the FP32 (kind 0 scalar, 1 packed pairs) or FP64 (kind 2) pipe, TFLOP/s
 cudaError_t alu_peak(int kind, double *tflops, cudaStream_t st);
+
+// FD-NN comparison workload (Sec. III-C), FP32: per-user IDFT of the data bins into
+// t [S K][N]; the time-domain network at every sample into o [S K][N]; the per-user DFT
+// of o in place (every bin); alpha of the data bins from the all-bins alpha
+struct FdnnDesc {
+    int L4, D, layers, residual;
+};
+cudaError_t fdnn_user_rows(const Geo &g, long rows, bool inverse, const c32 *in, c32 *out, const c32 *tw,
+                           cudaStream_t st);
+cudaError_t fdnn_mlp(const Geo &g, const FdnnDesc &nn, int S, const float *theta, const c32 *t, c32 *o,
+                     cudaStream_t st);
+cudaError_t fdnn_alpha_data(const Geo &g, int R, const float *alpha_all, float *alpha, cudaStream_t st);
+long fdnn_theta_len(const Geo &g, const FdnnDesc &nn);
 
 // parameter updates and bookkeeping
 cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);

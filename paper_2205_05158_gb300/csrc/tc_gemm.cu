@@ -291,14 +291,16 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
     float *st;
     const float *s, *fbi;   // fbi: the bias in output order
     int Nd, residual, vec;  // vec: st and s rows 32-byte aligned, fbi 16-byte aligned
+    int row_mul, row_add;   // output row m is chain column m row_mul + row_add
+    FD_D long col(int m) const { return (long)m * row_mul + row_add; }
     FD_D void operator()(int m, int n, float v) const {
-        const long idx = (long)m * 2 * Nd + n;
+        const long idx = col(m) * 2 * Nd + n;
         st[idx] = v + fbi[n] + (residual ? s[idx] : 0.f);
     }
     FD_D void prefetch(int m, int n, Pre &p) const {
         if (!vec) return;
         if (residual) {
-            const float4 *s4 = reinterpret_cast<const float4 *>(s + (long)m * 2 * Nd + n);
+            const float4 *s4 = reinterpret_cast<const float4 *>(s + col(m) * 2 * Nd + n);
 #pragma unroll
             for (int h = 0; h < 4; ++h) p.r[h] = s4[h];
         }
@@ -309,7 +311,7 @@ struct EpiFcFwd {          // s_tilde (interleaved floats) = acc + fc_b[pi(n)] +
             for (int j = 0; j < 16; ++j) (*this)(m, n + j, v[j]);
             return;
         }
-        const long idx = (long)m * 2 * Nd + n;
+        const long idx = col(m) * 2 * Nd + n;
         float o[16];
         const float4 *b4 = reinterpret_cast<const float4 *>(fbi + n);   // the same for every row
 #pragma unroll
@@ -398,10 +400,10 @@ cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaS
 static bool al(const void *p, int b) { return !(reinterpret_cast<uintptr_t>(p) & (uintptr_t)(b - 1)); }
 
 cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fbi, int Nd, int residual,
-                          int *err, cudaStream_t st) {
+                          int *err, cudaStream_t st, int row_mul, int row_add) {
     // rows of 2 N_d floats: whole sectors when that is a multiple of 8 and both bases align
     const int vec = (2 * Nd) % 8 == 0 && al(st_out, 32) && (!residual || al(s, 16)) && al(fbi, 16);
-    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fbi, Nd, residual, vec}, err, st);
+    return tc::launch<256>(g, tc::EpiFcFwd{st_out, s, fbi, Nd, residual, vec, row_mul, row_add}, err, st);
 }
 
 cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,

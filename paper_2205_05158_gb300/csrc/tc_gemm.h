@@ -18,8 +18,9 @@ struct GemmArgs {
 
 cudaError_t tc_gemm_store(const GemmArgs &g, float *C, long ldc, int *err, cudaStream_t st);
 // fbi: fc_b in the output's interleaved order [2 N_d] (as pack_fcw writes it)
+// output row m is chain column m row_mul + row_add of s and s_tilde (per-user passes: K, u)
 cudaError_t tc_fc_forward(const GemmArgs &g, float *st_out, const float *s, const float *fbi, int Nd, int residual,
-                          int *err, cudaStream_t st);
+                          int *err, cudaStream_t st, int row_mul = 1, int row_add = 0);
 // gpre [rows][ld_g] FP32 (ld_g a multiple of 8 for whole-sector stores)
 cudaError_t tc_fc_backward_data(const GemmArgs &g, float *gpre, long ld_g, const __nv_bfloat16 *act, long ld_act,
                                 int *err, cudaStream_t st);
@@ -27,7 +28,7 @@ cudaError_t tc_fc_backward_weight(const GemmArgs &g, float *gfw, int Nd, int F, 
 
 // 16-bit operand preparation (pack16.cu)
 cudaError_t conv_forward_bf16(const struct Geo &g, int S, const float2 *s, const float *theta, __nv_bfloat16 *act,
-                              long ld, cudaStream_t st);
+                              long ld, cudaStream_t st, int user = -1);
 // fc_w rows in interleaved order: out[n'][f] = bf16(fc_w[pi(n')][f]), ld_out; and the
 // bias in the same order, fbi[n'] = fc_b[pi(n')] (FP32)
 cudaError_t pack_fcw(const struct Geo &g, const float *theta, __nv_bfloat16 *out, long ld_out, float *fbi,

@@ -1,6 +1,7 @@
 // Zero-forcing precoder matrix W_i = H_i^H Z_i, Z_i = (H_i H_i^H)^{-1} (Eq. 6), on the
 // 5th-generation tensor cores, for 16-bit plans (K <= 16, M <= 128).  The factor kernel
-// leaves Z (lower triangle, FP32) in its scratch layout [bin / 32][entry][bin % 32].
+// leaves Y = L^{-1} (lower triangle, FP32) in its scratch layout [bin / 32][entry][bin % 32],
+// and Z = Y^H Y is formed here in FP32 while the operands are staged.
 //
 // W[m][u] = sum_i conj(H[i][m]) Z[i][u] is an expand-shaped contraction: A = H^T with
 // antenna rows m and k = (i, c) interleaved (re, im) pairs, B = the conjugate real form
@@ -44,13 +45,13 @@ FD_D void split(c32 v, uint32_t &hi, uint32_t &lo) {
 
 // One CTA of 512 threads per SM walks its items with two raw stages.
 // While item j is converted, multiplied and written out, cp.async brings item j + 1's
-// H block (4 subcarriers are contiguous in H), its Z lower triangles (4 subcarriers are
+// H block (4 subcarriers are contiguous in H), its Y lower triangles (4 subcarriers are
 // contiguous per entry in the scratch layout) and its alpha into the other stage, so the
 // loads are never on the item's critical path.  16 warps: warp w reads TMEM lane quarter
 // w % 4 (antennas) of subcarrier w / 4.
 constexpr int PT = 512;
 constexpr int RAW_H = NBI * 16 * 128 * 8;            // H of 4 subcarriers, [b][u][m]
-constexpr int RAW_Z = NBI * 136 * 8;                  // Z entries [e][b]
+constexpr int RAW_Z = NBI * 136 * 8;                  // Y entries [e][b]
 constexpr int STAGE = RAW_H + RAW_Z + 16;             // + alpha of the 4 subcarriers
 constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 2 * STAGE + 1024;
 
@@ -136,12 +137,18 @@ __global__ void __launch_bounds__(PT, 1)
             *reinterpret_cast<uint4 *>(aHi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4 *>(aLo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        // B: element (i, u, subcarrier b) = Z[i][u] from the lower triangle; rows 2u and
-        // 2u + 1 of pair tile b >> 1 at k = 32 (b & 1) + 2i
+        // B: element (i, u, subcarrier b) = Z[i][u] = sum_{k >= max(i, u)} conj(Y[k][i]) Y[k][u]
+        // (FP32, from the factor's lower-triangular Y = L^{-1}); rows 2u and 2u + 1 of pair
+        // tile b >> 1 at k = 32 (b & 1) + 2i
         for (int e = tid; e < 16 * 16 * NBI; e += PT) {
             const int b = e & 3, u = (e >> 2) & 15, i = e >> 6;
             c32 z = make_float2(0.f, 0.f);
-            if (b < nb && i < K && u < K) z = i >= u ? rZ[(tri(i) + u) * 4 + b] : cconj(rZ[(tri(u) + i) * 4 + b]);
+            if (b < nb && i < K && u < K)
+                for (int k = i > u ? i : u; k < K; ++k) {
+                    const c32 yi = rZ[(tri(k) + i) * 4 + b], yu = rZ[(tri(k) + u) * 4 + b];
+                    z.x = fmaf(yi.x, yu.x, fmaf(yi.y, yu.y, z.x));
+                    z.y = fmaf(yi.x, yu.y, fmaf(-yi.y, yu.x, z.y));
+                }
             uint32_t h0, l0, h1, l1;
             split(z, h0, l0);                                  // (Zr, Zi)
             split(make_float2(z.y, -z.x), h1, l1);             // (Zi, -Zr)

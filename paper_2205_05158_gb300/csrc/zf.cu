@@ -69,7 +69,7 @@ FD_D void cp_async8z(void *dst, const void *src, bool valid) {
 template <typename T16, int NT>   // NT: tasks per lane (2 when K > 28)
 __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
                                                                 c32 *__restrict__ Gs, T16 *__restrict__ H16,
-                                                                int buf_bytes) {
+                                                                T16 *__restrict__ HH16, int buf_bytes) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int K = g.K, M = g.M, T = tri(K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel
         }
         if (H16 && m0 + lane < M)
             for (int u = 0; u < K; ++u) H16[(b * K + u) * M + m0 + lane] = Operand<T16>::from(sH[u * GR_LD + lane]);
+        if (HH16 && m0 + lane < M)   // H^H in W's layout [b][m][u]
+            for (int u = 0; u < K; ++u)
+                HH16[(b * M + m0 + lane) * K + u] = Operand<T16>::from(cconj(sH[u * GR_LD + lane]));
 #pragma unroll
         for (int q = 0; q < NT; ++q) {
             if (q >= ntask) break;
@@ -181,7 +184,8 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel
 // same 11 steps.  The three groups' partial sums meet by warp shuffles.
 template <typename T16>
 __global__ void __launch_bounds__(32 * ZF_WARPS, 3)
-    zf_gram16_kernel(Geo g, long nbins, const c32 *__restrict__ H, c32 *__restrict__ Gs, T16 *__restrict__ H16) {
+    zf_gram16_kernel(Geo g, long nbins, const c32 *__restrict__ H, c32 *__restrict__ Gs, T16 *__restrict__ H16,
+                     T16 *__restrict__ HH16) {
     constexpr int K = 16, T = 136, LD = GR_LD, BUF = K * LD;
     extern __shared__ __align__(16) unsigned char sm[];
     const int M = g.M;
@@ -227,6 +231,19 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, 3)
                 T16 *dst = H16 + b * K * M + ch * GR_CHUNK + lane;
 #pragma unroll
                 for (int u = 0; u < K; ++u) dst[(long)u * M] = Operand<T16>::from(sH[u * LD + lane]);
+            }
+            if (HH16) {   // H^H in W's layout: antenna row m = 32 ch + lane, 16 users (64 bytes)
+                uint4 *dst = reinterpret_cast<uint4 *>(HH16 + (b * M + ch * GR_CHUNK + lane) * K);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const T16 v = Operand<T16>::from(cconj(sH[(4 * q + j) * LD + lane]));
+                        w[j] = *reinterpret_cast<const uint32_t *>(&v);
+                    }
+                    dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
@@ -282,115 +299,150 @@ template <> struct Fac<float> {
     }
 };
 
-template <typename Real>
-__global__ void __launch_bounds__(32) zf_factor_kernel(Geo g, long nbins, const c32 *__restrict__ Gs,
-                                                       c32 *__restrict__ Ys, float *__restrict__ alpha, int *status,
-                                                       int emit_z) {
+// LPB lanes per bin: the bin's Cholesky rows (and the partial sums of its pivots) and
+// its triangular-inverse rows are dealt round-robin to the LPB lanes, which sit BPW =
+// 32 / LPB lanes apart in one warp (so a shared-memory phase of 8 lanes reads 8 bins,
+// conflict free).  FP64 runs 4 lanes per bin in 4-warp CTAs, so that every SM
+// sub-partition holds warps of the slow FP64 pipe's work; FP32 one lane per bin.
+template <typename Real, int LPB>
+__global__ void __launch_bounds__(128) zf_factor_kernel(Geo g, long nbins, const c32 *__restrict__ Gs,
+                                                        c32 *__restrict__ Ys, float *__restrict__ alpha, int *status) {
     using F = Fac<Real>;
     using C = typename F::C;
+    constexpr int BPW = 32 / LPB, RMAX = LPB > 1 ? (32 + LPB - 1) / LPB : 1;   // bins per warp, rows per lane
     extern __shared__ __align__(16) unsigned char sm[];
     const int K = g.K, T = tri(K);
-    const int lane = threadIdx.x, NB = blockDim.x;          // NB bins per CTA, one per thread
-    C *A = reinterpret_cast<C *>(sm);                       // [T][NB]: lower triangle, becomes L, then Y
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int part = lane / BPW, lb = warp * BPW + lane % BPW;
+    const int NB = (int)(blockDim.x >> 5) * BPW;             // bins per CTA
+    C *A = reinterpret_cast<C *>(sm);                        // [T][NB]: lower triangle, becomes L, then Y
     Real *inv = reinterpret_cast<Real *>(A + (size_t)T * NB);   // [K][NB]
-    const long b = (long)blockIdx.x * NB + lane;
+    const long b = (long)blockIdx.x * NB + lb;
     const bool live = b < nbins;
     const long bb = live ? b : 0;
-    for (int e = 0; e < T; ++e) {
+    for (int e = part; e < T; e += LPB) {
         const c32 v = Gs[soa(bb, e, T)];
-        A[e * NB + lane] = C{(Real)v.x, (Real)v.y};
+        A[e * NB + lb] = C{(Real)v.x, (Real)v.y};
     }
+    __syncwarp();
     bool bad = false;
     // Cholesky, left-looking: column j from the columns left of it
     for (int j = 0; j < K; ++j) {
         const int dj = tri(j) + j;
-        Real d = A[dj * NB + lane].x;
-        const Real g0 = d;
-        for (int k = 0; k < j; ++k) {
-            const C l = A[(tri(j) + k) * NB + lane];
-            d = fma(-l.x, l.x, d);
-            d = fma(-l.y, l.y, d);
+        Real q = 0;
+        for (int k = part; k < j; k += LPB) {
+            const C l = A[(tri(j) + k) * NB + lb];
+            q = fma(l.x, l.x, q);
+            q = fma(l.y, l.y, q);
         }
+        for (int o = BPW; o < 32; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        const Real g0 = A[dj * NB + lb].x;
+        const Real d = g0 - q;
         const bool ok = d > F::kPivot * g0;
         bad |= !ok;
         const Real r = ok ? F::rsqrt(d) : Real(1);
-        A[dj * NB + lane] = C{ok ? d * r : Real(1), Real(0)};
-        inv[j * NB + lane] = r;
-        for (int i = j + 1; i < K; ++i) {
-            C s = A[(tri(i) + j) * NB + lane];
+        for (int i = j + 1 + part; i < K; i += LPB) {
+            C s = A[(tri(i) + j) * NB + lb];
             for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
-                const C a = A[(tri(i) + k) * NB + lane], c = A[(tri(j) + k) * NB + lane];
+                const C a = A[(tri(i) + k) * NB + lb], c = A[(tri(j) + k) * NB + lb];
                 s.x = fma(-a.x, c.x, s.x);
                 s.x = fma(-a.y, c.y, s.x);
                 s.y = fma(-a.y, c.x, s.y);
                 s.y = fma(a.x, c.y, s.y);
             }
-            A[(tri(i) + j) * NB + lane] = C{s.x * r, s.y * r};
+            A[(tri(i) + j) * NB + lb] = C{s.x * r, s.y * r};
         }
+        if (part == 0) {
+            A[dj * NB + lb] = C{ok ? d * r : Real(1), Real(0)};
+            inv[j * NB + lb] = r;
+        }
+        __syncwarp();
     }
     // in-place inverse: for j = K-1..0, Y[j][j] = 1/L[j][j], and for i = K-1..j+1
-    // Y[i][j] = -(1/L[j][j]) sum_{k=j+1}^{i} Y[i][k] L[k][j]  (L[k][j], k <= i, not yet overwritten)
+    // Y[i][j] = -(1/L[j][j]) sum_{k=j+1}^{i} Y[i][k] L[k][j]; a column's new values are
+    // held until every lane has read its L entries
     Real tr = 0;
-    for (int j = K - 1; j >= 0; --j) {
-        const Real r = inv[j * NB + lane];
+    for (int j = K - 1; j >= 0 && LPB == 1; --j) {   // one lane per bin: rows in descending order, in place
+        const Real r = inv[j * NB + lb];
         for (int i = K - 1; i > j; --i) {
             C s = C{Real(0), Real(0)};
             for (int k = j + 1; k <= i; ++k) {
-                const C y = A[(tri(i) + k) * NB + lane], l = A[(tri(k) + j) * NB + lane];
+                const C y = A[(tri(i) + k) * NB + lb], l = A[(tri(k) + j) * NB + lb];
                 s.x = fma(y.x, l.x, s.x);
                 s.x = fma(-y.y, l.y, s.x);
                 s.y = fma(y.x, l.y, s.y);
                 s.y = fma(y.y, l.x, s.y);
             }
             const C v = C{-s.x * r, -s.y * r};
-            A[(tri(i) + j) * NB + lane] = v;
+            A[(tri(i) + j) * NB + lb] = v;
             tr = fma(v.x, v.x, tr);
             tr = fma(v.y, v.y, tr);
         }
-        A[(tri(j) + j) * NB + lane] = C{r, Real(0)};
+        A[(tri(j) + j) * NB + lb] = C{r, Real(0)};
         tr = fma(r, r, tr);
     }
-    if (live) {
-        if (emit_z) {
-            // Z = Y^H Y = G^{-1}, lower triangle: Z[i][u] = sum_{k >= i} conj(Y[k][i]) Y[k][u]
-            for (int i = 0; i < K; ++i)
-                for (int u = 0; u <= i; ++u) {
-                    C z = C{Real(0), Real(0)};
-                    for (int k = i; k < K; ++k) {
-                        const C yi = A[(tri(k) + i) * NB + lane], yu = A[(tri(k) + u) * NB + lane];
-                        z.x = fma(yi.x, yu.x, z.x);
-                        z.x = fma(yi.y, yu.y, z.x);
-                        z.y = fma(yi.x, yu.y, z.y);
-                        z.y = fma(-yi.y, yu.x, z.y);
-                    }
-                    Ys[soa(b, tri(i) + u, T)] = make_float2((float)z.x, (float)z.y);
+    for (int j = K - 1; j >= 0 && LPB > 1; --j) {
+        const Real r = inv[j * NB + lb];
+        C out[RMAX];
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int i = K - 1 - part - t * LPB;
+            if (i > j) {
+                C s = C{Real(0), Real(0)};
+                for (int k = j + 1; k <= i; ++k) {
+                    const C y = A[(tri(i) + k) * NB + lb], l = A[(tri(k) + j) * NB + lb];
+                    s.x = fma(y.x, l.x, s.x);
+                    s.x = fma(-y.y, l.y, s.x);
+                    s.y = fma(y.x, l.y, s.y);
+                    s.y = fma(y.y, l.x, s.y);
                 }
-        } else {
-            for (int e = 0; e < T; ++e) {
-                const C v = A[e * NB + lane];
-                Ys[soa(b, e, T)] = make_float2((float)v.x, (float)v.y);
+                out[t] = C{-s.x * r, -s.y * r};
             }
         }
-        alpha[b] = bad ? 0.0f : (float)sqrt(g.P_T / (double)tr);
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int i = K - 1 - part - t * LPB;
+            if (i > j) {
+                A[(tri(i) + j) * NB + lb] = out[t];
+                tr = fma(out[t].x, out[t].x, tr);
+                tr = fma(out[t].y, out[t].y, tr);
+            }
+        }
+        if (part == 0) {
+            A[(tri(j) + j) * NB + lb] = C{r, Real(0)};
+            tr = fma(r, r, tr);
+        }
+        __syncwarp();
     }
-    if (live && bad) atomicOr(status, 1);
+    for (int o = BPW; o < 32; o <<= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (live) {
+        for (int e = part; e < T; e += LPB) {
+            const C v = A[e * NB + lb];
+            Ys[soa(b, e, T)] = make_float2((float)v.x, (float)v.y);
+        }
+        if (part == 0) alpha[b] = bad ? 0.0f : (float)sqrt(g.P_T / (double)tr);
+    }
+    if (live && bad && part == 0) atomicOr(status, 1);
 }
 
 template <typename Real>
 static cudaError_t launch_factor(const Geo &g, long nbins, const c32 *Gs, c32 *Ys, float *alpha, int *status,
-                                 int emit_z, cudaStream_t st) {
+                                 cudaStream_t st) {
     using C = typename Fac<Real>::C;
+    constexpr int LPB = sizeof(Real) == 8 ? 4 : 1;
     const int T = tri(g.K);
-    int NB = 32;
-    size_t smem = (sizeof(C) * T + sizeof(Real) * g.K) * NB;
-    if (smem > 200 * 1024) {
-        NB = 16;
-        smem = (sizeof(C) * T + sizeof(Real) * g.K) * NB;
-    }
-    cudaError_t e = cudaFuncSetAttribute(zf_factor_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int threads = sizeof(Real) == 8 ? 128 : 32;
+    auto bytes = [&](int thr) { return (sizeof(C) * T + sizeof(Real) * g.K) * (size_t)(thr / LPB); };
+    while (bytes(threads) > 200 * 1024 && threads > 32) threads /= 2;
+    if (bytes(threads) > 200 * 1024) return cudaErrorInvalidConfiguration;
+    const int NB = threads / LPB;
+    const size_t smem = bytes(threads);
+    cudaError_t e = cudaFuncSetAttribute(zf_factor_kernel<Real, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    zf_factor_kernel<Real><<<(unsigned)((nbins + NB - 1) / NB), NB, smem, st>>>(g, nbins, Gs, Ys, alpha, status,
-                                                                                emit_z);
+    zf_factor_kernel<Real, LPB><<<(unsigned)((nbins + NB - 1) / NB), threads, smem, st>>>(g, nbins, Gs, Ys, alpha,
+                                                                                        status);
     return cudaGetLastError();
 }
 
@@ -491,7 +543,7 @@ static cudaError_t launch_apply(const Geo &g, long nbins, const c32 *H, const c3
 template <typename T16>
 static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                               T16 *H16, T16 *W16, int phase, bool fp64_factor, bool tc_apply, int *err,
-                              cudaStream_t st) {
+                              cudaStream_t st, T16 *HH16) {
     const long nbins = (long)R * g.N_d;
     if (nbins == 0) return cudaSuccess;
     const int T = tri(g.K);
@@ -504,27 +556,27 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
         const size_t smem = (size_t)ZF_WARPS * 2 * per_buf;
         long blocks = 0;
         cudaError_t e;
-        if (g.K == 16 && g.M % GR_CHUNK == 0) {
+        if (g.K == 16 && g.M % GR_CHUNK == 0 && !(reinterpret_cast<uintptr_t>(HH16) & 15)) {
             const size_t smem16 = (size_t)ZF_WARPS * 2 * 16 * GR_LD * sizeof(c32);
             e = persistent_launch_dims(zf_gram16_kernel<T16>, 32 * ZF_WARPS, smem16, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
-            zf_gram16_kernel<T16><<<(unsigned)blocks, 32 * ZF_WARPS, smem16, st>>>(g, nbins, H, Gs, H16);
+            zf_gram16_kernel<T16><<<(unsigned)blocks, 32 * ZF_WARPS, smem16, st>>>(g, nbins, H, Gs, H16, HH16);
         } else if (g.K <= 28) {
             e = persistent_launch_dims(zf_gram_kernel<T16, 1>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
-            zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_buf);
+            zf_gram_kernel<T16, 1><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, HH16, per_buf);
         } else {
             e = persistent_launch_dims(zf_gram_kernel<T16, 2>, 32 * ZF_WARPS, smem, nbins, ZF_WARPS, blocks);
             if (e != cudaSuccess) return e;
-            zf_gram_kernel<T16, 2><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, per_buf);
+            zf_gram_kernel<T16, 2><<<(unsigned)blocks, 32 * ZF_WARPS, smem, st>>>(g, nbins, H, Gs, H16, HH16, per_buf);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     // factor
     if (phase < 0 || phase == 1) {
-        cudaError_t e = fp64_factor ? launch_factor<double>(g, nbins, Gs, Ys, alpha, status, tc_apply, st)
-                                    : launch_factor<float>(g, nbins, Gs, Ys, alpha, status, tc_apply, st);
+        cudaError_t e = fp64_factor ? launch_factor<double>(g, nbins, Gs, Ys, alpha, status, st)
+                                    : launch_factor<float>(g, nbins, Gs, Ys, alpha, status, st);
         if (e != cudaSuccess) return e;
     }
     // apply
@@ -539,21 +591,100 @@ static cudaError_t zf_build_t(const Geo &g, int R, const c32 *H, c32 *W, float *
 }
 
 cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
-                     void *H16, void *W16, int kind, bool tc, bool fp64, int *err, cudaStream_t st, bool keep_w32) {
+                     void *H16, void *W16, int kind, bool tc, bool fp64, int *err, cudaStream_t st, bool keep_w32,
+                     void *HH16) {
     // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128;
     // it may leave the FP32 W out when only the copy is wanted
     const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_bin_supported(g);
     if (tc_apply && !keep_w32) W = nullptr;
     if (kind == OUT_F16)
         return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, fp64, tc_apply, err,
-                          st);
+                          st, (cf16 *)HH16);
     return zf_build_t(g, R, H, W, alpha, status, scratch, (cbf16 *)H16, (cbf16 *)W16, phase, fp64 || kind == OUT_F32,
-                      tc_apply, err, st);
+                      tc_apply, err, st, (cbf16 *)HH16);
+}
+
+// ---------------------------------------------------------------------------
+// out = Z X per (symbol, subcarrier), Z = G^{-1} = Y^H Y from the factor's lower-triangular
+// Y = L^{-1} (FP32 scratch, [bin / 32][entry][bin % 32]): the precoder applied through its
+// factors, W s = H^H (Z s) (Eq. 6 by associativity), and the adjoint side Z (H g).  A CTA
+// takes one 32-bin block of Y into shared memory and then every (bin, symbol of its
+// realisation) pair of the block, one per thread: w = Y x, u = Y^H w.  X, out [S][K][N_d].
+template <int KM>
+__global__ void __launch_bounds__(256) zmul_kernel(Geo g, int S, long nbins, const c32 *__restrict__ Ys,
+                                                   const c32 *__restrict__ X, c32 *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    c32 *sY = reinterpret_cast<c32 *>(sm);   // [T][32]
+    const int K = g.K, T = tri(K), Nd = g.N_d, Sr = g.S_per_real;
+    const long nblk = (nbins + 31) / 32;
+    for (long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        __syncthreads();
+        const c32 *src = Ys + blk * (long)T * 32;
+        for (int e = threadIdx.x; e < T * 32; e += blockDim.x) sY[e] = src[e];
+        __syncthreads();
+        for (int task = threadIdx.x; task < 32 * Sr; task += blockDim.x) {
+            const int lb = task & 31, t = task >> 5;
+            const long b = blk * 32 + lb;
+            if (b >= nbins) continue;
+            const long r = b / Nd;
+            const int i = (int)(b - r * Nd);
+            const long s = r * Sr + t;
+            if (s >= S) continue;
+            const c32 *xs = X + s * K * Nd + i;
+            c32 w[KM];
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                c32 acc = make_float2(0.f, 0.f);
+                if (k < K) {
+#pragma unroll
+                    for (int j = 0; j <= k; ++j) acc = cfma(sY[(tri(k) + j) * 32 + lb], xs[(long)j * Nd], acc);
+                }
+                w[k] = acc;
+            }
+            c32 *os = out + s * K * Nd + i;
+#pragma unroll
+            for (int j = 0; j < KM; ++j) {
+                if (j < K) {
+                    c32 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = j; k < KM; ++k)
+                        if (k < K) acc = cfma(cconj(sY[(tri(k) + j) * 32 + lb]), w[k], acc);
+                    os[(long)j * Nd] = acc;
+                }
+            }
+        }
+    }
+}
+
+template <int KM>
+static cudaError_t launch_zmul(const Geo &g, int S, long nbins, const c32 *Ys, const c32 *X, c32 *out,
+                               cudaStream_t st) {
+    const size_t smem = sizeof(c32) * tri(g.K) * 32;
+    cudaError_t e = cudaFuncSetAttribute(zmul_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    long blocks = (long)resident_ctas(zmul_kernel<KM>, 256, smem) * sm_count();
+    const long nblk = (nbins + 31) / 32;
+    if (blocks > nblk) blocks = nblk;
+    if (blocks < 1) blocks = 1;
+    zmul_kernel<KM><<<(unsigned)blocks, 256, smem, st>>>(g, S, nbins, Ys, X, out);
+    return cudaGetLastError();
+}
+
+cudaError_t zf_zmul(const Geo &g, int S, const void *scratch, const c32 *X, c32 *out, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const long R = (S + g.S_per_real - 1) / g.S_per_real, nbins = R * g.N_d;
+    const long nb32 = (nbins + 31) / 32 * 32;
+    const c32 *Ys = reinterpret_cast<const c32 *>(reinterpret_cast<const char *>(scratch) +
+                                                  al16(sizeof(c32) * (size_t)nb32 * tri(g.K)));
+    if (g.K <= 4) return launch_zmul<4>(g, S, nbins, Ys, X, out, st);
+    if (g.K <= 8) return launch_zmul<8>(g, S, nbins, Ys, X, out, st);
+    if (g.K <= 16) return launch_zmul<16>(g, S, nbins, Ys, X, out, st);
+    return launch_zmul<32>(g, S, nbins, Ys, X, out, st);
 }
 
 cudaError_t zf_build(const Geo &g, int R, const c32 *H, c32 *W, float *alpha, int *status, void *scratch,
                      void *H16, void *W16, int kind, cudaStream_t st) {
-    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, false, true, nullptr, st);
+    return zf_phase(-1, g, R, H, W, alpha, status, scratch, H16, W16, kind, false, true, nullptr, st, true, nullptr);
 }
 
 }  // namespace fdk

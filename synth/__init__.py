@@ -302,8 +302,11 @@ def _theta_one(cfg: Config, st: "Stream", fc_scale: float) -> np.ndarray:
     cw = b * (2 * st.uniform(sz["conv_w"]) - 1)
     cb = b * (2 * st.uniform(sz["conv_b"]) - 1)
     fan_fc = sz["fc_w"] // (2 * cfg.N_d)
-    fw = fc_scale * (2 * st.uniform(sz["fc_w"]) - 1) / math.sqrt(fan_fc)
-    fb = fc_scale * 0.01 * (2 * st.uniform(sz["fc_b"]) - 1)
+    if fc_scale == 0.0:   # the identity predistorter: the dense layer is zero (no draws needed)
+        fw, fb = np.zeros(sz["fc_w"]), np.zeros(sz["fc_b"])
+    else:
+        fw = fc_scale * (2 * st.uniform(sz["fc_w"]) - 1) / math.sqrt(fan_fc)
+        fb = fc_scale * 0.01 * (2 * st.uniform(sz["fc_b"]) - 1)
     return np.concatenate([cw, cb, fw, fb]).astype(np.float32)
 
 
@@ -343,6 +346,19 @@ class Workload:
     pa: np.ndarray         # complex64 [M][P][L+1]
     theta: np.ndarray      # float32 flat
     P_T: float
+
+
+def batch(cfg: Config, S: int, symbol_offset: int):
+    """Symbols [S][K][N_d] and data-bin channel [R][N_d][K][M] (complex64) of the S symbols
+    from `symbol_offset` on (a realisation boundary): the mini-batches of a training run,
+    each with its own symbols and channel realisations."""
+    if symbol_offset % cfg.S_per_real:
+        raise ValueError("symbol_offset must start a realisation")
+    r0 = symbol_offset // cfg.S_per_real
+    R = (S + cfg.S_per_real - 1) // cfg.S_per_real
+    s = qam_symbols(cfg.seed, cfg.Q, (S, cfg.K, cfg.N_d), offset=symbol_offset * cfg.K * cfg.N_d).astype(np.complex64)
+    taps = channel_taps(cfg.seed, R, cfg.T, cfg.K, cfg.M, cfg.rho, first_real=r0)
+    return s, channel_fd(taps, cfg.N, data_bins(cfg.N, cfg.N_d)).astype(np.complex64)
 
 
 def make_workload(cfg: Config, S: Optional[int] = None, fc_scale: float = 0.0,

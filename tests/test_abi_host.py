@@ -78,8 +78,7 @@ def _create(lib, **over):
     (dict(G_pa=3), binding.FDDPD_ERR_ARG), (dict(G_pa=-1), binding.FDDPD_ERR_ARG),
     (dict(orders=[0], G_pa=1), binding.FDDPD_ERR_ARG),
     # per-user FD-CNN parameters: 0 or 1, FP32 plans with one input user each
-    (dict(per_user=2), binding.FDDPD_ERR_ARG), (dict(per_user=1, precision=1), binding.FDDPD_ERR_UNSUPPORTED),
-    (dict(per_user=1, L_U=2), binding.FDDPD_ERR_UNSUPPORTED),
+    (dict(per_user=2), binding.FDDPD_ERR_ARG),
 ])
 def test_plan_rejects_bad_descriptors(lib, over, code):
     rc, h = _create(lib, **over)

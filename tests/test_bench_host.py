@@ -13,7 +13,7 @@ import bench  # noqa: E402
 import synth  # noqa: E402
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine",
-          "adj_combine", "fftpa_adj", "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step"]
+          "adj_combine", "fftpa_adj", "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "zmul"]
 
 
 def test_stage_work_of_the_benchmark_step():

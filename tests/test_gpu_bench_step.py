@@ -164,3 +164,75 @@ def test_options_validated():
         with pytest.raises(fd.FddpdError) as e:
             plan.set_option(opt, 2)
         assert e.value.code == fd.FDDPD_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+def test_precoder_kept_as_factors(prec):
+    """fddpd_precode(H, NULL, alpha): no W is formed; the chain applies alpha H^H (Z s) with
+    Z = Y^H Y from the FP64 factor (Eq. 6 by associativity).  Forward, gradient and one
+    GD step against the oracle at the 16-bit tolerances, and against the W path."""
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    cfg, w, go, meto = _reference()
+    plan = fd.Plan.from_config(cfg, w.P_T, max_symbols=S, precision=prec)
+    s, H, pa, theta = dev(w.s), dev(w.H), dev(w.pa), dev(w.theta)
+    R = w.H.shape[0]
+    W = T.empty((R, cfg.N_d, cfg.M, cfg.K), dtype=T.complex64, device="cuda")
+    al = T.empty((R, cfg.N_d), dtype=T.float32, device="cuda")
+    al2 = T.empty_like(al)
+    plan.precode(H, W, al)
+    y_w = T.empty_like(s)
+    plan.distort(s, H, W, al, pa, theta, y_w)
+    plan.precode(H, None, al2)
+    assert T.equal(al, al2)
+    y = T.empty_like(s)
+    met = T.zeros(5, dtype=T.float64, device="cuda")
+    plan.distort(s, H, None, al2, pa, theta, y, met)
+    g = T.empty(plan.theta_len, dtype=T.float32, device="cuda")
+    plan.backward(s, H, None, al2, pa, theta, g)
+    plan.sync()
+    yn, yw = y.cpu().numpy(), y_w.cpu().numpy()
+    assert np.sum(np.abs(yn - yw) ** 2) / np.sum(np.abs(yw) ** 2) <= 1e-4
+    m = met.cpu().numpy()
+    assert abs(oracle.evm_db(m) - oracle.evm_db(meto)) <= 0.1
+    assert abs(oracle.acpr_db(m) - oracle.acpr_db(meto)) <= 0.2
+    g = g.cpu().numpy().astype(np.float64)
+    assert rel_l2(g, go) <= 2e-2, rel_l2(g, go)
+    for blk, sl in _blocks(cfg).items():
+        assert rel_l2(g[sl], go[sl]) <= 2e-2, (blk, rel_l2(g[sl], go[sl]))
+    th0 = theta.clone()
+    plan.update(s, H, None, al2, pa, theta, LR, 1, fd.FDDPD_GD)
+    plan.sync()
+    step = (theta - th0).cpu().numpy().astype(np.float64)
+    assert rel_l2(step, -LR * go) <= 2e-2
+
+
+def test_precoder_kept_as_factors_errors():
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    cfg = synth.CONFIGS["m16_k2_n64"]
+    w = synth.make_workload(cfg)
+    H, s, pa, th = dev(w.H), dev(w.s), dev(w.pa), dev(w.theta)
+    al = T.empty((1, cfg.N_d), dtype=T.float32, device="cuda")
+    W = T.empty((1, cfg.N_d, cfg.M, cfg.K), dtype=T.complex64, device="cuda")
+    p32 = fd.Plan.from_config(cfg, w.P_T, precision=fd.FDDPD_FP32)
+    with pytest.raises(fd.FddpdError) as e:
+        p32.precode(H, None, al)
+    assert e.value.code == fd.FDDPD_ERR_UNSUPPORTED
+    p16 = fd.Plan.from_config(cfg, w.P_T, precision=fd.FDDPD_BF16)
+    with pytest.raises(fd.FddpdError) as e:        # no factor kept yet
+        p16.distort(s, H, None, al, pa, th)
+    assert e.value.code == fd.FDDPD_ERR_ARG
+    p16.precode(H, W, al)                           # the W path keeps no factor
+    with pytest.raises(fd.FddpdError) as e:
+        p16.distort(s, H, None, al, pa, th)
+    assert e.value.code == fd.FDDPD_ERR_ARG
+    p16.precode(H, None, al)
+    p16.distort(s, H, None, al, pa, th)             # accepted
+    with pytest.raises(fd.FddpdError) as e:        # another H
+        p16.distort(s, H.clone(), None, al, pa, th)
+    assert e.value.code == fd.FDDPD_ERR_ARG
+    p16.invalidate_operands()
+    with pytest.raises(fd.FddpdError) as e:
+        p16.distort(s, H, None, al, pa, th)
+    assert e.value.code == fd.FDDPD_ERR_ARG

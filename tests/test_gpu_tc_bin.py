@@ -100,3 +100,26 @@ def test_tc_zf_apply(name, cfg, prec):
     assert np.abs(W1n - W0n).max() <= 1e-4 * np.abs(Wo).max()
     HW = np.einsum("rbkm,rbmu->rbku", c.w.H.astype(np.complex128), W1n)
     assert np.abs(HW - np.eye(cfg.K)).max() <= 1e-3
+
+
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "cuda_cores"])
+@pytest.mark.parametrize("name,cfg", CFGS[:3], ids=[n for n, _ in CFGS[:3]])
+def test_precoder_kept_as_factors_ragged(name, cfg, tc):
+    """fddpd_precode(H, NULL, alpha) on ragged shapes (K = 3, 13, 16; the generic and the
+    K = 16 Gram kernels write H^H): forward and gradient against the oracle."""
+    c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=1)
+    _opt(c, tc)
+    c.plan.precode(c.H, None, c.alpha)
+    T = __import__("torch")
+    y = T.empty_like(c.s)
+    met = T.zeros(5, dtype=T.float64, device="cuda")
+    c.plan.distort(c.s, c.H, None, c.alpha, c.pa, c.theta, y, met)
+    g = T.empty(c.plan.theta_len, dtype=T.float32, device="cuda")
+    c.plan.backward(c.s, c.H, None, c.alpha, c.pa, c.theta, g)
+    c.plan.sync()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    go, _ = oracle.backward(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert nmse(y.cpu().numpy(), yo) <= 1e-4
+    assert abs(oracle.evm_db(met.cpu().numpy()) - oracle.evm_db(meto)) <= 0.1
+    assert rel_l2(g.cpu().numpy(), go) <= 2e-2

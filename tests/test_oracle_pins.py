@@ -497,11 +497,12 @@ def test_gmp_adjoint_central_differences():
 
 
 # --- per-user FD-CNN parameters theta_u (Sec. IV-A) ------------------------------
-def test_per_user_equal_parameters_reduce_to_shared():
+@pytest.mark.parametrize("L_U", [1, 2])
+def test_per_user_equal_parameters_reduce_to_shared(L_U):
     """K copies of one theta: the same forward chain as the shared network, and the
     per-user gradient slices add up to the shared gradient (the shared gradient is the
     sum of every user's contribution)."""
-    cfg = _small_cfg(L_U=1)
+    cfg = _small_cfg(L_U=L_U)
     w, d, W, al = _setup(cfg, fc_scale=0.5)
     th = w.theta.astype(np.float64)
     dp = oracle.dims_from_config(cfg.with_(per_user=1), w.P_T)
@@ -515,11 +516,12 @@ def test_per_user_equal_parameters_reduce_to_shared():
     assert np.abs(gp.reshape(cfg.K, -1).sum(axis=0) - g).max() <= 1e-12 * np.abs(g).max()
 
 
-def test_per_user_outputs_follow_their_own_parameters():
+@pytest.mark.parametrize("L_U", [1, 2])
+def test_per_user_outputs_follow_their_own_parameters(L_U):
     """A linear PA and perfect CSI pass s_tilde through unchanged (y = s_tilde), so with
     per-user parameters user u receives exactly the FD-CNN of theta_u applied to its own
-    symbols (L_U = 1), whatever the other users' parameters are."""
-    cfg = _small_cfg(L_U=1, per_user=1)
+    input users (u, ..., u + L_U - 1), whatever the other users' parameters are."""
+    cfg = _small_cfg(L_U=L_U, per_user=1)
     w, d, W, al = _setup(cfg, fc_scale=0.5, pa=synth.linear_pa(cfg))
     thK = w.theta.astype(np.float64).reshape(cfg.K, -1)
     assert not np.allclose(thK[0], thK[1])
