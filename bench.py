@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-fast-variant", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-fdnn", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     return ap.parse_args()
 
@@ -365,6 +366,97 @@ def fdnn_run(fd, torch, stream, S=560, reps=10):
     cnn_flops = 2 * cfg.N_conv * cfg.L_U * (2 * cfg.K_C ** 2 - 1) * cells + 8 * Nd * cfg.L_U * cells
     out["flops_per_ue_symbol"] = {"fdnn": nn_flops, "fdcnn": cnn_flops}
     return out
+
+
+def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
+    """The batched uneven workload: n independent instances (M 32..256, K 4..32 with
+    K <= M / 4, N 512..4096 with about 58 % of the bins occupied, 64-QAM, i.i.d. Rayleigh
+    taps, orders {1,3} or {1,3,5}), BF16 plans with the precoder kept as its factors, each
+    autotuned (choices stored per shape), the forward chain of every instance recorded on
+    `lanes` concurrent lanes of one CUDA graph and replayed as one launch; against the same
+    calls one by one on one stream.  The symbols and channel taps of this timing run are
+    drawn on the device from a seeded torch generator (shapes and PA sets from synth)."""
+    import numpy as np
+
+    import synth
+    cfgs = synth.uneven_instances(n, S=S)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    free0 = torch.cuda.mem_get_info()[0]
+    insts = []
+    for cfg in cfgs:
+        if torch.cuda.mem_get_info()[0] < 0.12 * free0:   # keep well inside the device memory
+            break
+        R = -(-S // cfg.S_per_real)
+        side = int(round(math.sqrt(cfg.Q)))
+        lv = torch.tensor(synth.qam_levels(cfg.Q), dtype=torch.float32, device="cuda")
+        idx = torch.randint(0, side, (2, S, cfg.K, cfg.N_d), device="cuda", generator=gen)
+        s = torch.complex(lv[idx[0]], lv[idx[1]]).contiguous()
+        taps = torch.randn((R, cfg.T, cfg.K, cfg.M, 2), device="cuda", generator=gen) * math.sqrt(0.5 / cfg.T)
+        taps = torch.complex(taps[..., 0], taps[..., 1]).to(torch.complex128)
+        bins = torch.tensor(synth.data_bins(cfg.N, cfg.N_d), device="cuda", dtype=torch.float64)
+        ph = torch.exp(-2j * math.pi * bins[:, None] * torch.arange(cfg.T, device="cuda", dtype=torch.float64)[None] / cfg.N)
+        H = torch.einsum("bt,rtkm->rbkm", ph, taps).to(torch.complex64).contiguous()
+        pa = torch.from_numpy(synth.pa_coefficients(cfg.seed, cfg.M, cfg.pa_nominal, 0.1).astype(np.complex64)).cuda()
+        theta = torch.from_numpy(synth.theta_init(cfg, cfg.seed, 0.0)).cuda()
+        try:
+            plan = fd.Plan.from_config(cfg, synth.transmit_power(cfg), max_symbols=S, precision=fd.FDDPD_BF16,
+                                       stream=stream)
+        except fd.FddpdError:
+            break
+        al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
+        plan.precode(H, None, al)
+        insts.append((cfg, plan, s, H, al, pa, theta))
+    fd.autotune_forget()
+    t0 = time.perf_counter()
+    for cfg, plan, s, H, al, pa, theta in insts:
+        plan.autotune(s, H, None, al, pa, theta, reps=2)
+    tune_s = time.perf_counter() - t0
+    ys = [torch.empty_like(x[2]) for x in insts]
+
+    def one_by_one():
+        for (cfg, plan, s, H, al, pa, theta), y in zip(insts, ys):
+            plan.distort(s, H, None, al, pa, theta, y)
+
+    one_by_one()
+    torch.cuda.synchronize()
+    ref = [y.clone() for y in ys]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        one_by_one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(b) / reps
+    main = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    with fd.Graph.record_lanes(main, lanes) as (g, lane_streams):
+        for i, (cfg, plan, s, H, al, pa, theta) in enumerate(insts):
+            plan.set_stream(lane_streams[i % lanes])
+            plan.distort(s, H, None, al, pa, theta, ys[i])
+    rec_s = time.perf_counter() - t0
+    g.launch()
+    main.synchronize()
+    a.record(main)
+    for _ in range(reps):
+        g.launch()
+    b.record(main)
+    main.synchronize()
+    ms_graph = a.elapsed_time(b) / reps
+    same = all(torch.equal(y, r) for y, r in zip(ys, ref))
+    shapes = {(c.M, c.K, c.N) for c, *_ in insts}
+    tc = sum(p.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS) for _, p, *_ in insts)
+    one_cta = sum(p.get_option(fd.FDDPD_OPT_ROW_CTAS) == 1 for _, p, *_ in insts)
+    nsym = len(insts) * S
+    for _, p, *_ in insts:
+        p.close()
+    del g
+    return {"instances": len(insts), "requested": n, "symbols_per_instance": S, "distinct_shapes": len(shapes),
+            "lanes": lanes, "graph": {"value": nsym / (ms_graph / 1e3), "unit": UNIT, "ms": ms_graph},
+            "one_by_one": {"value": nsym / (ms_seq / 1e3), "unit": UNIT, "ms": ms_seq},
+            "graph_equals_one_by_one": same, "autotune_s": tune_s, "record_s": rec_s,
+            "autotuned": {"tensor_core_contractions": tc, "row_kernels_one_cta_per_sm": one_cta},
+            "precision": "bf16", "data": "device-drawn seeded symbols and channel taps"}
 
 
 def torch_optim_run(fd, torch, plan, data, W, al, pa, theta0, steps=20, lr=1e-3):
@@ -695,11 +787,24 @@ def run_ours(args):
                             "evm_db": 10 * math.log10(m32[1] / m32[2]), "acpr_db": 10 * math.log10(m32[3] / m32[4])}
         del plan32
 
+    # the informational sections below report their own failure instead of losing the line
+    def section(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as exc:   # noqa: BLE001
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     if rank == 0 and not args.no_fdnn:
-        out["fdnn_comparison"] = fdnn_run(fd, torch, stream)
+        section("fdnn_comparison", lambda: fdnn_run(fd, torch, stream))
+
+    # the batched uneven workload: 512 instances in one graph launch (rank 0, informational)
+    if rank == 0 and not args.no_batched:
+        section("batched_uneven", lambda: batched_run(fd, torch, stream))
 
     # the training run of the 128 x 16 system (rank 0; informational, outside the timed step)
-    if rank == 0 and not args.no_train:
+    def training():
         runs = []
         # per-user parameters (the configuration's own), mixed precision, the paper's Adam and
         # plain GD; the shared network for comparison; FP32 with torch.optim beside it
@@ -712,7 +817,10 @@ def run_ours(args):
             runs.append(res)
             tp.close()
             del tdata
-        out["training"] = runs
+        return runs
+
+    if rank == 0 and not args.no_train:
+        section("training", training)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         plan.precode(H, W, al)

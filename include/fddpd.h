@@ -171,10 +171,15 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *   FDDPD_OPT_FACTOR_FP64  1 (default): the Cholesky factor and triangular inverse of
  *       every Gram matrix run in FP64; 0: in FP32 in 16-bit plans (whose W is rounded to
  *       16 bits afterwards; faster).  FP32 plans always factor in FP64.
- * Returns FDDPD_ERR_ARG for an unknown option or value. */
+ *   FDDPD_OPT_ROW_CTAS  0 (default): the IFFT / PA / FFT row kernels' persistent grids
+ *       hold as many CTAs per SM as fit; 1..8: at most that many (fewer leave room for
+ *       the kernels of other plans recorded on other lanes of one graph).
+ * Returns FDDPD_ERR_ARG for an unknown option or value.  fddpd_get_option reads one
+ * back (*value; ARG for an unknown option).                                          */
 enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2, FDDPD_OPT_KEEP_PA_INPUT = 3,
-       FDDPD_OPT_FACTOR_FP64 = 4 };
+       FDDPD_OPT_FACTOR_FP64 = 4, FDDPD_OPT_ROW_CTAS = 5 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
+int fddpd_get_option(const fddpd_plan *plan, int option, int *value);
 
 /* Transmit power P_T of Eq. (6) for the plan's next fddpd_precode / fddpd_update_host
  * calls (the ZF normalisation alpha_k = sqrt(P_T / tr((H_k H_k^H)^{-1})); W does not
@@ -242,7 +247,9 @@ int fddpd_backward(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 
 /* `iters` training iterations over the S symbols (Sec. V-A): each runs forward, the
  * adjoint and one step theta -= lr * grad (FDDPD_GD), or one Adam step with
  * beta1 = 0.9, beta2 = 0.999, eps = 1e-8 (FDDPD_ADAM; the moments live in the plan
- * and persist across calls until fddpd_reset_optimizer).  theta is updated in place.
+ * and persist across calls until fddpd_reset_optimizer; the plan's first Adam step
+ * allocates them -- NOMEM if that fails -- so make one before recording Adam steps into
+ * a graph).  theta is updated in place.
  * metrics: those of the last iteration's forward pass (before its step).          */
 int fddpd_update(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H,
                  const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
@@ -297,16 +304,26 @@ int fddpd_update_host(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c
 int fddpd_ser(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
               float N0, unsigned long long seed, unsigned long long *counts);
 
-/* Per-shape implementation choice (for batches of uneven plans): times `reps` forward
- * passes (fddpd_distort) of each implementation of the per-subcarrier contractions the
- * plan's shape admits -- tcgen05 (16-bit plans with M <= 128, K <= 16) and CUDA cores --
- * with CUDA events on the plan's stream, and keeps the faster set
- * (FDDPD_OPT_TENSOR_CONTRACTIONS).  Arguments as fddpd_distort; ms[2] (host, may be NULL)
- * receives the mean times (tensor-core first; -1 where not admitted).  Synchronises,
- * so it cannot be recorded into a graph (call it before fddpd_graph_begin).  On an error
- * the previous choice is kept.  Errors as fddpd_distort, ARG for reps < 1.          */
+/* fddpd_ser, and per symbol: wrong [S][K][N_d] (device bytes) receives 1 for an error, 0
+ * for a correct decision and 2 where the subcarrier is singular (not compared), so that
+ * decisions can be compared symbol by symbol.  Errors as fddpd_ser, ARG for a null wrong. */
+int fddpd_ser_decisions(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
+                        float N0, unsigned long long seed, unsigned long long *counts, unsigned char *wrong);
+
+/* Per-shape launch choice (for batches of uneven plans): times `reps` forward passes
+ * (fddpd_distort) of every candidate -- the per-subcarrier contraction implementations
+ * the plan's shape admits (tcgen05 in 16-bit plans with M <= 128, K <= 16; CUDA cores)
+ * times the row kernels' grid (FDDPD_OPT_ROW_CTAS 0 or 1) -- with CUDA events on the
+ * plan's stream, and keeps the fastest.  The choice is stored per shape (M, K, N, N_d,
+ * S_per_real, precision, PA shape, FD-CNN shape, S) in the process: a later plan of a
+ * stored shape takes it without timing (fddpd_autotune_forget clears the store).  ms[2]
+ * (host, may be NULL) receives the best time of each contraction implementation
+ * (tensor-core first; -1 where not admitted).  Synchronises, so it cannot be recorded
+ * into a graph (call it before fddpd_graph_begin).  On an error the previous choice is
+ * kept.  No counterpart in the paper.  Errors as fddpd_distort, ARG for reps < 1.    */
 int fddpd_autotune(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
                    const float *alpha, const fddpd_c32 *pa_coef, const float *theta, int reps, float *ms);
+int fddpd_autotune_forget(void);
 
 /* Batched launch of many plans (uneven M, K, N) as one CUDA graph.  Between
  * fddpd_graph_begin and fddpd_graph_end every fddpd_distort / fddpd_backward /
@@ -316,9 +333,17 @@ int fddpd_autotune(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 
  * recording time (the data behind them may change between launches).  fddpd_precode,
  * fddpd_update_host, fddpd_autotune and fddpd_sync synchronise and cannot be recorded
  * (they fail with FDDPD_ERR_CUDA).
+ * fddpd_graph_begin_lanes records on `stream` and `lanes` side streams forked from it
+ * (created by the call, returned in lane_streams[lanes]); plans bound to the lanes
+ * (fddpd_set_stream) run concurrently inside the one launch, and fddpd_graph_end joins
+ * the lanes back.  The lane streams live until fddpd_graph_destroy; rebind the plans
+ * to other streams before calling them outside the graph.  One recording per host
+ * thread at a time.
  * Errors: ARG, CUDA (a call that cannot be recorded ends the recording).            */
+#define FDDPD_GRAPH_MAX_LANES 32
 typedef struct fddpd_graph fddpd_graph;
 int fddpd_graph_begin(void *stream);
+int fddpd_graph_begin_lanes(void *stream, int lanes, void **lane_streams);
 int fddpd_graph_end(void *stream, fddpd_graph **out);
 int fddpd_graph_launch(fddpd_graph *graph, void *stream);
 int fddpd_graph_destroy(fddpd_graph *graph);
@@ -351,6 +376,16 @@ long long fddpd_launch_count(const fddpd_plan *plan);
  * last report: FDDPD_ERR_TIMEOUT when a bounded wait inside a tensor-core kernel gave
  * up (its results are then invalid).  Clears the record.                           */
 int fddpd_sync(fddpd_plan *plan);
+
+/* Failure paths on purpose, without a GPU fault (no counterpart in the paper).
+ * fddpd_selftest_wait runs, on the plan's stream, one bounded wait on an mbarrier that
+ * nothing arrives at (no copy or MMA in flight); after limit_us (1..1000000) it gives up
+ * and records the timeout as the tensor-core kernels do, so the next fddpd_sync returns
+ * FDDPD_ERR_TIMEOUT (and clears it).  fddpd_debug_fail_allocs(n): the library's next n
+ * device allocations fail as if the GPU were out of memory (plan creation, staging,
+ * Adam moments, kept PA input): the callers get FDDPD_ERR_NOMEM.                      */
+int fddpd_selftest_wait(fddpd_plan *plan, int limit_us);
+int fddpd_debug_fail_allocs(int n);
 
 /* The library's tensor-core GEMM on its own (used to validate it):
  *   C[m][n] (+)= sum_k A[m][k] B[n][k],  A [M][lda], B [N][ldb] 16-bit (ab_type 1 = BF16,

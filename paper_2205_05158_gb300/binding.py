@@ -23,6 +23,7 @@ FDDPD_OPT_TENSOR_CONTRACTIONS = 1
 FDDPD_OPT_HOST_CHUNKS = 2
 FDDPD_OPT_KEEP_PA_INPUT = 3
 FDDPD_OPT_FACTOR_FP64 = 4
+FDDPD_OPT_ROW_CTAS = 5
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",
@@ -31,7 +32,9 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_sync", "fddpd_tc_gemm", "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_ser",
             "fddpd_graph_begin", "fddpd_graph_end", "fddpd_graph_launch", "fddpd_graph_destroy", "fddpd_autotune",
             "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak",
-            "fddpd_get_optimizer_state", "fddpd_set_optimizer_state", "fddpd_fdnn_plan_create"]
+            "fddpd_get_optimizer_state", "fddpd_set_optimizer_state", "fddpd_fdnn_plan_create", "fddpd_get_option",
+            "fddpd_autotune_forget", "fddpd_graph_begin_lanes", "fddpd_ser_decisions", "fddpd_selftest_wait",
+            "fddpd_debug_fail_allocs"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack", "zmul", "fdnn_rows",
@@ -113,6 +116,12 @@ def load(build_if_missing: bool = True):
     L.fddpd_ser.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P]
     L.fddpd_autotune.argtypes = [P, I, P, P, P, P, P, P, I, P]
     L.fddpd_graph_begin.argtypes = [P]
+    L.fddpd_graph_begin_lanes.argtypes = [P, I, C.POINTER(C.c_void_p)]
+    L.fddpd_get_option.argtypes = [P, I, C.POINTER(C.c_int)]
+    L.fddpd_autotune_forget.argtypes = []
+    L.fddpd_ser_decisions.argtypes = [P, I, P, P, P, I, C.c_float, C.c_ulonglong, P, P]
+    L.fddpd_selftest_wait.argtypes = [P, I]
+    L.fddpd_debug_fail_allocs.argtypes = [I]
     L.fddpd_graph_end.argtypes = [P, C.POINTER(C.c_void_p)]
     L.fddpd_graph_launch.argtypes = [P, P]
     L.fddpd_graph_destroy.argtypes = [P]
@@ -125,7 +134,8 @@ def load(build_if_missing: bool = True):
               "fddpd_profile_enable", "fddpd_profile_read", "fddpd_sync", "fddpd_tc_gemm",
               "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power",
               "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak", "fddpd_get_optimizer_state",
-              "fddpd_set_optimizer_state"):
+              "fddpd_set_optimizer_state", "fddpd_get_option", "fddpd_autotune_forget", "fddpd_graph_begin_lanes",
+              "fddpd_ser_decisions", "fddpd_selftest_wait", "fddpd_debug_fail_allocs"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -293,6 +303,11 @@ class Plan:
         contractions of a 16-bit plan on CUDA cores instead of the tensor cores."""
         self._check(self._lib.fddpd_set_option(self._h, int(option), int(value)))
 
+    def get_option(self, option: int) -> int:
+        v = C.c_int(0)
+        self._check(self._lib.fddpd_get_option(self._h, int(option), C.byref(v)))
+        return v.value
+
     def invalidate_operands(self):
         """fddpd_invalidate_operands: the next call re-packs H and W (16-bit plans) --
         needed after H or W was rewritten in place other than by ``precode``."""
@@ -367,6 +382,21 @@ class Plan:
         self._check(self._lib.fddpd_ser(self._h, S, _ptr(y, torch.complex64), _ptr(s, torch.complex64),
                                         _ptr(alpha, torch.float32), int(Q), float(N0),
                                         int(seed) & (2 ** 64 - 1), _ptr(counts, torch.int64)))
+
+    def ser_decisions(self, y, s, alpha, Q: int, N0: float, seed: int, counts, wrong, S: Optional[int] = None):
+        """fddpd_ser_decisions: as ``ser``, and wrong (a device uint8 tensor shaped like y)
+        receives 1 / 0 per symbol (2 on singular subcarriers)."""
+        import torch
+        S = y.shape[0] if S is None else S
+        self._check(self._lib.fddpd_ser_decisions(self._h, S, _ptr(y, torch.complex64), _ptr(s, torch.complex64),
+                                                  _ptr(alpha, torch.float32), int(Q), float(N0),
+                                                  int(seed) & (2 ** 64 - 1), _ptr(counts, torch.int64),
+                                                  _ptr(wrong, torch.uint8)))
+
+    def selftest_wait(self, limit_us: int):
+        """fddpd_selftest_wait: a bounded wait that must run out (the next sync raises
+        FDDPD_ERR_TIMEOUT)."""
+        self._check(self._lib.fddpd_selftest_wait(self._h, int(limit_us)))
 
     def update_host(self, s, H, pa, theta, lr: float, iters: int = 1, optimizer: int = FDDPD_GD, metrics=None,
                     S: Optional[int] = None):
@@ -474,6 +504,14 @@ class Graph:
     def record(cls, stream):
         return _Recording(cls(stream))
 
+    @classmethod
+    def record_lanes(cls, stream, lanes: int):
+        """Record on `stream` and `lanes` side streams forked from it
+        (fddpd_graph_begin_lanes): ``with Graph.record_lanes(s, 8) as (g, lane_streams):``
+        bind plans to the lane streams (Plan.set_stream) and call them; the lanes run
+        concurrently inside the one launch."""
+        return _LaneRecording(cls(stream), lanes)
+
     def launch(self):
         rc = self._lib.fddpd_graph_launch(self._h, self._stream)
         if rc:
@@ -483,6 +521,35 @@ class Graph:
         if getattr(self, "_h", None) and self._h.value:
             self._lib.fddpd_graph_destroy(self._h)
             self._h = C.c_void_p()
+
+
+class _LaneRecording:
+    def __init__(self, g: Graph, lanes: int):
+        self.g = g
+        self.lanes = lanes
+
+    def __enter__(self):
+        arr = (C.c_void_p * self.lanes)()
+        rc = self.g._lib.fddpd_graph_begin_lanes(self.g._stream, self.lanes, arr)
+        if rc:
+            raise FddpdError(rc, self.g._lib.fddpd_last_error(None).decode())
+        return self.g, [int(arr[i]) for i in range(self.lanes)]
+
+    def __exit__(self, exc_type, exc, tb):
+        rc = self.g._lib.fddpd_graph_end(self.g._stream, C.byref(self.g._h))
+        if rc and exc_type is None:
+            raise FddpdError(rc, self.g._lib.fddpd_last_error(None).decode())
+        return False
+
+
+def debug_fail_allocs(n: int):
+    """fddpd_debug_fail_allocs: the library's next n device allocations fail (NOMEM)."""
+    load().fddpd_debug_fail_allocs(int(n))
+
+
+def autotune_forget():
+    """fddpd_autotune_forget: clear the per-shape choices of fddpd_autotune."""
+    load().fddpd_autotune_forget()
 
 
 class _Recording:

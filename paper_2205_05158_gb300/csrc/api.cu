@@ -1,13 +1,17 @@
 // C-ABI of the fddpd library: plan life cycle, argument checks, workspace layout and
 // the order in which the stage kernels run on the plan's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <climits>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "fddpd.h"
 #include "kernels.h"
@@ -113,6 +117,21 @@ static int set_err(fddpd_plan *p, int code, const char *fmt, ...) {
     } while (0)
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Device allocations of the library; fddpd_debug_fail_allocs(n) makes the next n of them
+// fail (host-side fault injection: the failure paths run without exhausting the GPU).
+static std::atomic<int> g_fail_allocs{0};
+static cudaError_t dev_alloc(void **ptr, size_t bytes) {
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+extern "C" int fddpd_debug_fail_allocs(int n) {
+    if (n < 0) return FDDPD_ERR_ARG;
+    g_fail_allocs.store(n);
+    return FDDPD_OK;
+}
 static bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
 static int validate(const fddpd_dims *d, const fddpd_pa_desc *pa, const fddpd_dpd_desc *dpd) {
@@ -197,8 +216,8 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
                  o_tw = take(sizeof(c32) * g.N),
                  o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * ((g.F + 7) / 8 * 8)),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
-                 o_grad = take(sizeof(float) * g.theta_len), o_m = take(sizeof(float) * g.theta_len),
-                 o_v = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int));
+                 o_grad = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8),
+                 o_stat = take(2 * sizeof(int));
     const size_t o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N_d));
     p->p16 = d->precision != FDDPD_FP32;
     p->tc_bin = true;
@@ -226,7 +245,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         o_wq16 = take(4 * (size_t)p->R_max * g.N_d * g.K * g.M);
     }
     p->bytes = off;
-    cudaError_t e = cudaMalloc(&p->base, off);
+    cudaError_t e = dev_alloc(&p->base, off);
     if (e != cudaSuccess) {
         delete p;
         cudaGetLastError();
@@ -236,7 +255,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->st = (c32 *)(b + o_st); p->gy = (c32 *)(b + o_gy); p->gst = (c32 *)(b + o_gst);
     p->xh = (c32 *)(b + o_xh); p->Xpa = (c32 *)(b + o_X); p->tw = (c32 *)(b + o_tw);
     p->act = (float *)(b + o_act); p->gpre = (float *)(b + o_gpre); p->partials = (float *)(b + o_part);
-    p->grad = (float *)(b + o_grad); p->adam_m = (float *)(b + o_m); p->adam_v = (float *)(b + o_v);
+    p->grad = (float *)(b + o_grad);   // the Adam moments are allocated by the first Adam step
     p->met = (double *)(b + o_met); p->status = (int *)(b + o_stat);
     p->zf_scratch = b + o_zf;
     if (p->p16) {
@@ -252,8 +271,6 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     if (e == cudaSuccess) e = fdk::pass_twiddles(g.log2N, p->tw, p->stream);
     p->launches = 1;
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, 2 * sizeof(int), p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_m, 0, sizeof(float) * g.theta_len, p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->adam_v, 0, sizeof(float) * g.theta_len, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         set_err(nullptr, FDDPD_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e));
@@ -261,6 +278,22 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
         return FDDPD_ERR_CUDA;
     }
     *out = p;
+    return FDDPD_OK;
+}
+
+// The Adam moments [theta_len] each, zeroed, allocated the first time they are needed (a
+// plan that only runs forward passes, or GD, never holds them).
+static int ensure_adam(fddpd_plan *p) {
+    if (p->adam_m) return FDDPD_OK;
+    const size_t n = sizeof(float) * (size_t)p->g.theta_len;
+    void *m = nullptr;
+    if (dev_alloc(&m, 2 * n) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(p, FDDPD_ERR_NOMEM, "Adam moments (%zu bytes)", 2 * n);
+    }
+    FD_CK(p, cudaMemsetAsync(m, 0, 2 * n, p->stream));
+    p->adam_m = static_cast<float *>(m);
+    p->adam_v = p->adam_m + p->g.theta_len;
     return FDDPD_OK;
 }
 
@@ -313,7 +346,7 @@ extern "C" int fddpd_fdnn_plan_create(fddpd_plan **out, const fddpd_dims *d, con
                  o_met = take(sizeof(double) * 8), o_stat = take(2 * sizeof(int)),
                  o_zf = take(fdk::zf_scratch_bytes(g, (long)p->R_max * g.N));
     p->bytes = off;
-    cudaError_t e = cudaMalloc(&p->base, off);
+    cudaError_t e = dev_alloc(&p->base, off);
     if (e != cudaSuccess) {
         delete p;
         cudaGetLastError();
@@ -341,6 +374,7 @@ extern "C" int fddpd_plan_destroy(fddpd_plan *p) {
     if (!p) return FDDPD_OK;
     if (p->base) cudaFree(p->base);
     if (p->xt16) cudaFree(p->xt16);
+    if (p->adam_m) cudaFree(p->adam_m);
     if (p->stage_base) cudaFree(p->stage_base);
     if (p->cstream) {
         cudaStreamDestroy(p->cstream);
@@ -379,7 +413,7 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
         // BF16 plans only: the BF16 copy of x(t), [max_symbols][M][N], allocated once
         if (value && p->d.precision == FDDPD_BF16 && !p->xt16) {
             const size_t n = 4 * (size_t)p->d.max_symbols * p->g.M * p->g.N;
-            if (cudaMalloc(&p->xt16, n) != cudaSuccess) {
+            if (dev_alloc(&p->xt16, n) != cudaSuccess) {
                 cudaGetLastError();
                 p->xt16 = nullptr;
                 return set_err(p, FDDPD_ERR_NOMEM, "kept PA input (%zu bytes)", n);
@@ -392,7 +426,23 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
         p->fp64_factor = value != 0 || !p->p16;   // FP32 plans always factor in FP64
         return FDDPD_OK;
     }
+    if (option == FDDPD_OPT_ROW_CTAS && value >= 0 && value <= 8) {
+        p->g.row_ctas = value;
+        return FDDPD_OK;
+    }
     return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
+}
+
+extern "C" int fddpd_get_option(const fddpd_plan *p, int option, int *value) {
+    if (!p || !value) return FDDPD_ERR_ARG;
+    switch (option) {
+        case FDDPD_OPT_TENSOR_CONTRACTIONS: *value = p->tc_bin ? 1 : 0; return FDDPD_OK;
+        case FDDPD_OPT_HOST_CHUNKS: *value = p->host_chunks; return FDDPD_OK;
+        case FDDPD_OPT_KEEP_PA_INPUT: *value = p->keep_xt ? 1 : 0; return FDDPD_OK;
+        case FDDPD_OPT_FACTOR_FP64: *value = p->fp64_factor ? 1 : 0; return FDDPD_OK;
+        case FDDPD_OPT_ROW_CTAS: *value = p->g.row_ctas; return FDDPD_OK;
+        default: return FDDPD_ERR_ARG;
+    }
 }
 
 extern "C" int fddpd_set_power(fddpd_plan *p, double P_T) {
@@ -415,8 +465,7 @@ extern "C" int fddpd_invalidate_operands(fddpd_plan *p) {
 extern "C" int fddpd_reset_optimizer(fddpd_plan *p) {
     if (!p) return FDDPD_ERR_ARG;
     p->adam_t = 0;
-    FD_CK(p, cudaMemsetAsync(p->adam_m, 0, sizeof(float) * p->g.theta_len, p->stream));
-    FD_CK(p, cudaMemsetAsync(p->adam_v, 0, sizeof(float) * p->g.theta_len, p->stream));
+    if (p->adam_m) FD_CK(p, cudaMemsetAsync(p->adam_m, 0, 2 * sizeof(float) * p->g.theta_len, p->stream));
     return FDDPD_OK;
 }
 
@@ -424,6 +473,8 @@ extern "C" int fddpd_get_optimizer_state(fddpd_plan *p, float *m, float *v, long
     if (!p) return FDDPD_ERR_ARG;
     if (!m || !v || !t) return set_err(p, FDDPD_ERR_ARG, "null pointer");
     if (!aligned(m, 4) || !aligned(v, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    const int rc = ensure_adam(p);
+    if (rc) return rc;
     const size_t n = sizeof(float) * (size_t)p->g.theta_len;
     FD_CK(p, cudaMemcpyAsync(m, p->adam_m, n, cudaMemcpyDefault, p->stream));
     FD_CK(p, cudaMemcpyAsync(v, p->adam_v, n, cudaMemcpyDefault, p->stream));
@@ -436,6 +487,8 @@ extern "C" int fddpd_set_optimizer_state(fddpd_plan *p, const float *m, const fl
     if (!p) return FDDPD_ERR_ARG;
     if (!m || !v || t < 0) return set_err(p, FDDPD_ERR_ARG, "null pointer or negative step count");
     if (!aligned(m, 4) || !aligned(v, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
+    const int rc = ensure_adam(p);
+    if (rc) return rc;
     const size_t n = sizeof(float) * (size_t)p->g.theta_len;
     FD_CK(p, cudaMemcpyAsync(p->adam_m, m, n, cudaMemcpyDefault, p->stream));
     FD_CK(p, cudaMemcpyAsync(p->adam_v, v, n, cudaMemcpyDefault, p->stream));
@@ -816,6 +869,8 @@ static int opt_step(fddpd_plan *p, float *theta, float lr, int optimizer) {
     if (optimizer == FDDPD_GD) {
         FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, p->grad, lr, p->stream));
     } else {
+        const int rc = ensure_adam(p);
+        if (rc) return rc;
         const long t = ++p->adam_t;
         const float c1 = (float)(1.0 - pow(0.9, (double)t)), c2 = (float)(1.0 - pow(0.999, (double)t));
         FD_STAGE(p, FDDPD_STAGE_STEP, 1,
@@ -899,7 +954,7 @@ static int update_host_impl(fddpd_plan *p, int S, const fddpd_c32 *s, const fddp
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     if (!p->stage_base) {
         const size_t tot = up(n_s) + 2 * up(n_H) + up(n_al) + up(n_pa) + up(n_th) + up(8 * sizeof(double));
-        if (cudaMalloc(&p->stage_base, tot) != cudaSuccess) {
+        if (dev_alloc(&p->stage_base, tot) != cudaSuccess) {
             cudaGetLastError();
             p->stage_base = nullptr;
             return set_err(p, FDDPD_ERR_NOMEM, "staging buffers (%zu bytes)", tot);
@@ -1024,8 +1079,8 @@ extern "C" int fddpd_update_host(fddpd_plan *p, int S, const fddpd_c32 *s, const
     return rc;
 }
 
-extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
-                         float N0, unsigned long long seed, unsigned long long *counts) {
+static int ser_impl(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q, float N0,
+                    unsigned long long seed, unsigned long long *counts, unsigned char *wrong) {
     if (!p) return FDDPD_ERR_ARG;
     if (S < 1 || S > p->d.max_symbols) return set_err(p, FDDPD_ERR_ARG, "S=%d outside 1..%d", S, p->d.max_symbols);
     if (!y || !s || !alpha || !counts) return set_err(p, FDDPD_ERR_ARG, "null pointer");
@@ -1034,10 +1089,49 @@ extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c
     if (!aligned(y, 8) || !aligned(s, 8) || !aligned(alpha, 4) || !aligned(counts, 8))
         return set_err(p, FDDPD_ERR_LAYOUT, "misaligned pointer");
     FD_CK(p, fdk::ser_count(p->g, S, reinterpret_cast<const c32 *>(y), reinterpret_cast<const c32 *>(s), alpha, Q, N0,
-                            seed, counts, p->stream));
+                            seed, counts, p->stream, wrong));
     p->launches += 1;
     return FDDPD_OK;
 }
+
+extern "C" int fddpd_ser(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha, int Q,
+                         float N0, unsigned long long seed, unsigned long long *counts) {
+    return ser_impl(p, S, y, s, alpha, Q, N0, seed, counts, nullptr);
+}
+
+extern "C" int fddpd_ser_decisions(fddpd_plan *p, int S, const fddpd_c32 *y, const fddpd_c32 *s, const float *alpha,
+                                   int Q, float N0, unsigned long long seed, unsigned long long *counts,
+                                   unsigned char *wrong) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (!wrong) return set_err(p, FDDPD_ERR_ARG, "wrong is null");
+    return ser_impl(p, S, y, s, alpha, Q, N0, seed, counts, wrong);
+}
+
+extern "C" int fddpd_selftest_wait(fddpd_plan *p, int limit_us) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (limit_us < 1 || limit_us > 1000000) return set_err(p, FDDPD_ERR_ARG, "limit_us outside 1..1000000");
+    FD_CK(p, fdk::wait_probe(1000ull * (unsigned long long)limit_us, p->status + 1, p->stream));
+    p->launches += 1;
+    return FDDPD_OK;
+}
+
+// Choices of fddpd_autotune per shape: a plan of a shape met before takes the stored
+// choice without timing (many instances of a few shapes in one batched launch).
+struct TuneKey {
+    int M, K, N, N_d, S_per_real, precision, n_orders, L, pa_G, per_user, L_U, G, S;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(M, K, N, N_d, S_per_real, precision, n_orders, L, pa_G, per_user, L_U, G, S) <
+               std::tie(o.M, o.K, o.N, o.N_d, o.S_per_real, o.precision, o.n_orders, o.L, o.pa_G, o.per_user, o.L_U,
+                        o.G, o.S);
+    }
+};
+struct TuneChoice {
+    bool tc;
+    int row_ctas;
+    float ms[2];
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune_cache;
 
 extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,
                               const float *alpha, const fddpd_c32 *pa_coef, const float *theta, int reps,
@@ -1045,8 +1139,26 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
     if (!p) return FDDPD_ERR_ARG;
     if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans have one implementation");
     if (reps < 1) return set_err(p, FDDPD_ERR_ARG, "reps < 1");
-    float t[2] = {-1.0f, -1.0f};
-    const bool was = p->tc_bin;
+    const TuneKey key{p->g.M, p->g.K, p->g.N, p->g.N_d, p->g.S_per_real, p->d.precision, p->g.n_orders, p->g.L,
+                      p->g.pa_G, p->dpd.per_user, p->dpd.L_U, p->dpd.G, S};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->tc_bin = it->second.tc;
+            p->g.row_ctas = it->second.row_ctas;
+            if (ms) {
+                ms[0] = it->second.ms[0];
+                ms[1] = it->second.ms[1];
+            }
+            return FDDPD_OK;
+        }
+    }
+    // candidates: the contraction implementations the shape admits (tcgen05 in 16-bit plans
+    // with M <= 128, K <= 16; CUDA cores) x the row kernels' CTAs per SM (as many as fit; one)
+    float t[2][2] = {{-1.0f, -1.0f}, {-1.0f, -1.0f}};
+    const bool was_tc = p->tc_bin;
+    const int was_rc = p->g.row_ctas;
     const bool tc_ok = p->p16 && fdk::tc_bin_supported(p->g);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     FD_CK(p, cudaEventCreate(&e0));
@@ -1057,33 +1169,56 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
     int rc = FDDPD_OK;
     for (int v = 0; v < 2 && rc == FDDPD_OK; ++v) {
         if (v == 0 && !tc_ok) continue;
-        p->tc_bin = v == 0;
-        rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);   // warm-up (and re-pack)
-        if (rc) break;
-        if (cudaEventRecord(e0, p->stream) != cudaSuccess) { rc = set_err(p, FDDPD_ERR_CUDA, "event record"); break; }
-        for (int r = 0; r < reps && rc == FDDPD_OK; ++r)
-            rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);
-        if (rc) break;
-        float el = 0.0f;
-        if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
-            rc = set_err(p, FDDPD_ERR_CUDA, "event timing");
-            break;
+        for (int c = 0; c < 2 && rc == FDDPD_OK; ++c) {
+            p->tc_bin = v == 0;
+            p->g.row_ctas = c == 0 ? 0 : 1;
+            rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);   // warm-up (and re-pack)
+            if (rc) break;
+            if (cudaEventRecord(e0, p->stream) != cudaSuccess) { rc = set_err(p, FDDPD_ERR_CUDA, "event record"); break; }
+            for (int r = 0; r < reps && rc == FDDPD_OK; ++r)
+                rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);
+            if (rc) break;
+            float el = 0.0f;
+            if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
+                rc = set_err(p, FDDPD_ERR_CUDA, "event timing");
+                break;
+            }
+            t[v][c] = el / reps;
         }
-        t[v] = el / reps;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {
-        p->tc_bin = was;
+        p->tc_bin = was_tc;
+        p->g.row_ctas = was_rc;
         return rc;
     }
-    p->tc_bin = tc_ok && t[0] <= t[1];
+    int bv = -1, bc = 0;
+    for (int v = 0; v < 2; ++v)
+        for (int c = 0; c < 2; ++c)
+            if (t[v][c] >= 0 && (bv < 0 || t[v][c] < t[bv][bc])) { bv = v; bc = c; }
+    p->tc_bin = bv == 0;
+    p->g.row_ctas = bc == 0 ? 0 : 1;
+    TuneChoice ch{p->tc_bin, p->g.row_ctas, {-1.0f, -1.0f}};
+    for (int v = 0; v < 2; ++v)
+        for (int c = 0; c < 2; ++c)
+            if (t[v][c] >= 0 && (ch.ms[v] < 0 || t[v][c] < ch.ms[v])) ch.ms[v] = t[v][c];
     if (ms) {
-        ms[0] = t[0];
-        ms[1] = t[1];
+        ms[0] = ch.ms[0];
+        ms[1] = ch.ms[1];
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = ch;
     }
     return fddpd_sync(p);
+}
+
+extern "C" int fddpd_autotune_forget(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
+    return FDDPD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1091,7 +1226,60 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
 struct fddpd_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    int lanes;
+    cudaStream_t lane[FDDPD_GRAPH_MAX_LANES];
 };
+
+// Lanes of a recording in progress on this host thread: side streams forked from the
+// recording stream at fddpd_graph_begin_lanes and joined back at fddpd_graph_end.
+struct LaneSet {
+    cudaStream_t main;
+    int n;
+    cudaStream_t lane[FDDPD_GRAPH_MAX_LANES];
+    cudaEvent_t fork, join[FDDPD_GRAPH_MAX_LANES];
+};
+static thread_local LaneSet g_lanes{};
+
+static void release_lanes(LaneSet &ls, bool streams) {
+    if (ls.fork) cudaEventDestroy(ls.fork);
+    for (int i = 0; i < ls.n; ++i) {
+        if (ls.join[i]) cudaEventDestroy(ls.join[i]);
+        if (streams && ls.lane[i]) cudaStreamDestroy(ls.lane[i]);
+    }
+    ls = LaneSet{};
+}
+
+extern "C" int fddpd_graph_begin_lanes(void *stream, int lanes, void **lane_streams) {
+    if (!stream || !lane_streams || lanes < 1 || lanes > FDDPD_GRAPH_MAX_LANES)
+        return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_begin_lanes: a stream, 1..%d lanes", FDDPD_GRAPH_MAX_LANES);
+    if (g_lanes.n) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_begin_lanes: a recording is in progress");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaneSet ls{};
+    ls.main = st;
+    cudaError_t e = cudaEventCreateWithFlags(&ls.fork, cudaEventDisableTiming);
+    for (int i = 0; i < lanes && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&ls.lane[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ls.join[i], cudaEventDisableTiming);
+        ls.n = i + 1;
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    bool capturing = e == cudaSuccess;
+    if (e == cudaSuccess) e = cudaEventRecord(ls.fork, st);
+    for (int i = 0; i < lanes && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ls.lane[i], ls.fork, 0);
+    if (e != cudaSuccess) {
+        if (capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        release_lanes(ls, true);
+        return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_begin_lanes: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < lanes; ++i) lane_streams[i] = ls.lane[i];
+    g_lanes = ls;
+    return FDDPD_OK;
+}
 
 extern "C" int fddpd_graph_begin(void *stream) {
     if (!stream) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_begin: the default stream cannot record");
@@ -1103,24 +1291,42 @@ extern "C" int fddpd_graph_begin(void *stream) {
 extern "C" int fddpd_graph_end(void *stream, fddpd_graph **out) {
     if (!stream || !out) return set_err(nullptr, FDDPD_ERR_ARG, "fddpd_graph_end: null argument");
     *out = nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaneSet ls{};
+    if (g_lanes.n && g_lanes.main == st) {   // join the lanes back into the recording stream
+        ls = g_lanes;
+        g_lanes = LaneSet{};
+        for (int i = 0; i < ls.n; ++i) {
+            cudaEventRecord(ls.join[i], ls.lane[i]);
+            cudaStreamWaitEvent(st, ls.join[i], 0);
+        }
+    }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
+        release_lanes(ls, true);
         return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_end: %s", cudaGetErrorString(e));
     }
     cudaGraphExec_t x = nullptr;
     e = cudaGraphInstantiate(&x, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
+        release_lanes(ls, true);
         return set_err(nullptr, FDDPD_ERR_CUDA, "fddpd_graph_end: instantiate: %s", cudaGetErrorString(e));
     }
-    fddpd_graph *r = new (std::nothrow) fddpd_graph{g, x};
+    fddpd_graph *r = new (std::nothrow) fddpd_graph{};
     if (!r) {
         cudaGraphExecDestroy(x);
         cudaGraphDestroy(g);
+        release_lanes(ls, true);
         return set_err(nullptr, FDDPD_ERR_NOMEM, "fddpd_graph_end: host allocation failed");
     }
+    r->graph = g;
+    r->exec = x;
+    r->lanes = ls.n;   // the lane streams live as long as the graph (plans may still name them)
+    for (int i = 0; i < ls.n; ++i) r->lane[i] = ls.lane[i];
+    release_lanes(ls, false);
     *out = r;
     return FDDPD_OK;
 }
@@ -1136,6 +1342,7 @@ extern "C" int fddpd_graph_destroy(fddpd_graph *graph) {
     if (!graph) return FDDPD_OK;
     cudaGraphExecDestroy(graph->exec);
     cudaGraphDestroy(graph->graph);
+    for (int i = 0; i < graph->lanes; ++i) cudaStreamDestroy(graph->lane[i]);
     delete graph;
     return FDDPD_OK;
 }

@@ -1,4 +1,4 @@
-// Two measurements that sit beside the chain.
+// Measurements and checks that sit beside the chain.
 //
 //   zf_residual : the FP64 check of the zero-forcing identity of Eq. (6), H_k W_k = I_K,
 //                 on the precoders a plan produced: max over the checked subcarriers of
@@ -10,11 +10,13 @@
 //                 FMA loop (16 independent dependency chains per thread, a grid of
 //                 resident CTAs on every SM), timed with CUDA events.  It is the
 //                 denominator of the ALU rooflines; the paper has no counterpart.
+//   wait_probe  : the bounded-wait failure path of the tensor-core kernels, made to run out.
 #include <cstdint>
 
 #include "fddpd.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace fdk {
 
@@ -97,6 +99,24 @@ cudaError_t zf_residual(const Geo &g, long nbins, long every, const c32 *H, cons
     long blocks = (long)(sms > 0 ? sms : 1) * 8;
     if (blocks > nchk) blocks = nchk;
     zf_residual_kernel<<<(unsigned)blocks, RES_THREADS, 0, st>>>(g.M, g.K, nbins, every, H, W, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The bounded-wait failure path of the tensor-core kernels, run on purpose: one thread
+// waits on an mbarrier that nothing arrives at (no copy or MMA is in flight), gives up
+// after limit_ns, sets the error word as a real timeout does, and the kernel returns.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc::mbar_wait_for(&bar, 0, err, limit_ns);
+    }
+}
+
+cudaError_t wait_probe(unsigned long long limit_ns, int *err, cudaStream_t st) {
+    wait_probe_kernel<<<1, 32, 0, st>>>(limit_ns, err);
     return cudaGetLastError();
 }
 

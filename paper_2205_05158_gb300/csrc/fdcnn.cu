@@ -131,7 +131,7 @@ FD_D ConvPos conv_positions(const Geo &g) {
     return cp;
 }
 
-template <typename TOut>
+template <typename TOut, bool PU>   // PU: a per-user pass (column map t -> t K + u)
 __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, ColMap cm, long cols, const c32 *__restrict__ s,
                                                             const float *__restrict__ theta, TOut *__restrict__ act,
                                                             long ld) {
@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, ColMap cm, lo
     }
     const ConvPos cp = conv_positions(g);
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
-        const c32 *row = s + cm.chain(col) * g.N_d;   // L_U = 1: the column's own user
+        const c32 *row = s + (PU ? cm.chain(col) : col) * g.N_d;   // L_U = 1: the column's own user
         TOut *out = act + col * ld;
-        if (col + gridDim.x < cols) prefetch_row_l1(s + cm.chain(col + gridDim.x) * g.N_d, g.N_d);
+        if (col + gridDim.x < cols) prefetch_row_l1(s + (PU ? cm.chain(col + gridDim.x) : col + gridDim.x) * g.N_d, g.N_d);
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(256) conv_fwd_fast_kernel(Geo g, ColMap cm, lo
 
 // parameter gradient: every thread accumulates the 36 weight and 2 bias partial sums of
 // its positions over the CTA's columns; one block reduction per CTA
+template <bool PU>
 __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, ColMap cm, long cols, const c32 *__restrict__ s,
                                                             const float *__restrict__ gpre, long ldg,
                                                             float *__restrict__ partials) {
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, ColMap cm, lo
     };
     load_g(blockIdx.x);
     for (long col = blockIdx.x; col < cols; col += gridDim.x) {
-        const c32 *row = s + cm.chain(col) * g.N_d;
+        const c32 *row = s + (PU ? cm.chain(col) : col) * g.N_d;
         float gc[2][CF_PPT];
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256) conv_bwd_fast_kernel(Geo g, ColMap cm, lo
             gc[1][k] = gn[1][k];
         }
         load_g(col + gridDim.x);
-        if (col + gridDim.x < cols) prefetch_row_l1(s + cm.chain(col + gridDim.x) * g.N_d, g.N_d);
+        if (col + gridDim.x < cols) prefetch_row_l1(s + (PU ? cm.chain(col + gridDim.x) : col + gridDim.x) * g.N_d, g.N_d);
 #pragma unroll
         for (int k = 0; k < CF_PPT; ++k) {
             const int p = threadIdx.x + 256 * k;
@@ -276,7 +277,12 @@ static cudaError_t conv_fwd_launch(const Geo &g, int S, const c32 *s, const floa
     const int Gp = padded_side(g);
     const size_t sm = sizeof(float) * (size_t)g.Cin * Gp * Gp;
     if (conv_fast(g) && g.L_U == 1) {
-        conv_fwd_fast_kernel<TOut><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cm, cols, s, theta, act, ld);
+        if (user < 0)
+            conv_fwd_fast_kernel<TOut, false><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cm, cols, s, theta,
+                                                                                                 act, ld);
+        else
+            conv_fwd_fast_kernel<TOut, true><<<(unsigned)conv_fast_blocks(cols), 256, 0, st>>>(g, cm, cols, s, theta,
+                                                                                                act, ld);
         return cudaGetLastError();
     }
     const int cpc = conv_cols_per_cta(cols);
@@ -400,7 +406,12 @@ cudaError_t conv_backward(const Geo &g, int S, const c32 *s, const float *gpre, 
     const size_t sm = sizeof(float) * ((size_t)g.Cin * Gp * Gp + g.F);
     cudaError_t e;
     if (conv_fast(g) && g.L_U == 1) {
-        conv_bwd_fast_kernel<<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cm, cols, s, gpre, ldg, partials);
+        if (user < 0)
+            conv_bwd_fast_kernel<false><<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cm, cols, s, gpre, ldg,
+                                                                                             partials);
+        else
+            conv_bwd_fast_kernel<true><<<(unsigned)conv_partial_rows(g, cols), 256, 0, st>>>(g, cm, cols, s, gpre, ldg,
+                                                                                            partials);
         return cudaGetLastError();
     }
     if (conv_bwd_fast(g)) {

@@ -706,10 +706,11 @@ __global__ void __launch_bounds__(256, 2) user_rows_kernel(Geo g, long rows, con
 }
 
 template <class Kern>
-inline cudaError_t persistent_blocks(Kern k, int N, long rows, int threads, size_t sm, long &blocks) {
+inline cudaError_t persistent_blocks(Kern k, int N, long rows, int threads, size_t sm, long &blocks, int cap = 0) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int per_sm = resident_ctas(k, threads, sm);
+    int per_sm = resident_ctas(k, threads, sm);
+    if (cap > 0 && cap < per_sm) per_sm = cap;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -726,7 +727,8 @@ inline cudaError_t fwd_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     const int threads = 256;
     const size_t sm = fftpa_smem_bytes_(g);
     long blocks = 0;
-    cudaError_t e = persistent_blocks(fftpa_forward_kernel<LOG2N, P_, L_, TOut>, g.N, rows, threads, sm, blocks);
+    cudaError_t e =
+        persistent_blocks(fftpa_forward_kernel<LOG2N, P_, L_, TOut>, g.N, rows, threads, sm, blocks, g.row_ctas);
     if (e != cudaSuccess) return e;
     fftpa_forward_kernel<LOG2N, P_, L_, TOut><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, X, metrics,
                                                                                      xt);
@@ -740,7 +742,8 @@ inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, 
     const size_t sm = fftpa_smem_base_(g) + (std::is_same<TA, cbf16>::value && xt
                                                  ? (size_t)rows_per_cta(g.N) * adj_stage_bytes(g) : 0);
     long blocks = 0;
-    cudaError_t e = persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA>, g.N, rows, threads, sm, blocks);
+    cudaError_t e =
+        persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA>, g.N, rows, threads, sm, blocks, g.row_ctas);
     if (e != cudaSuccess) return e;
     fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA><<<(unsigned)blocks, threads, sm, st>>>(g, rows, xh, pa, twp, gX, gxh,
                                                                                        xt);

@@ -16,6 +16,7 @@ struct Geo {
     int n_orders, orders[8], L;
     int pa_G;                // PA cross-term length of Eq. 9 (0: memory polynomial)
     int in_all;              // the forward row kernel reads x_hat rows of all N bins (FD-NN chain)
+    int row_ctas;            // CTAs per SM of the row kernels' persistent grids (0: as many as fit)
     int G, Go, L_U, Cin, K_C, K_S, pad, N_conv, F, residual;
     int n_convw;             // N_conv * Cin * K_C * K_C
     long off_cb, off_fw, off_fb, theta_len;
@@ -70,8 +71,12 @@ cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, c
 bool tc_bin_supported(const Geo &g);
 
 // symbol errors at the users: counts[0] += errors, counts[1] += symbols compared
+// wrong (may be null): per (symbol, user, subcarrier) 1 = error, 0 = correct, 2 = not compared
 cudaError_t ser_count(const Geo &g, int S, const c32 *y, const c32 *s, const float *alpha, int Q, float N0,
-                      unsigned long long seed, unsigned long long *counts, cudaStream_t st);
+                      unsigned long long seed, unsigned long long *counts, cudaStream_t st,
+                      unsigned char *wrong = nullptr);
+// a wait on an mbarrier nothing arrives at, bounded by limit_ns: sets err bit 2 when it gives up
+cudaError_t wait_probe(unsigned long long limit_ns, int *err, cudaStream_t st);
 
 // FD-CNN.  `user` < 0: the shared network over all S K columns (chain order, column
 // t K + u); user u >= 0: user u's own pass over its S columns, FD-CNN column t reading

@@ -40,14 +40,18 @@ template <typename IDX>
 __global__ void __launch_bounds__(256) ser_kernel(Geo g, IDX n, const c32 *__restrict__ y,
                                                   const c32 *__restrict__ s, const float *__restrict__ alpha,
                                                   int side, float inv_step, float sigma, uint2 key,
-                                                  unsigned long long *__restrict__ counts) {
+                                                  unsigned long long *__restrict__ counts,
+                                                  unsigned char *__restrict__ wrong_out) {
     const IDX per_sym = (IDX)g.K * (IDX)g.N_d, nd = (IDX)g.N_d, spr = (IDX)g.S_per_real;
     unsigned errors = 0, compared = 0;
     for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < n; e += (IDX)gridDim.x * blockDim.x) {
         const IDX t = e / per_sym;
         const IDX i = e % nd;
         const float al = alpha[(long)(t / spr) * g.N_d + (long)i];
-        if (!(al > 0.f)) continue;   // a singular subcarrier carries no symbol
+        if (!(al > 0.f)) {   // a singular subcarrier carries no symbol
+            if (wrong_out) wrong_out[e] = 2;
+            continue;
+        }
         c32 z = y[e];
         if (sigma > 0.f) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)((unsigned long long)e >> 32), 0u, 0u), key);
@@ -64,6 +68,7 @@ __global__ void __launch_bounds__(256) ser_kernel(Geo g, IDX n, const c32 *__res
                            pam_index(z.y, inv_step, side) != pam_index(sv.y, inv_step, side);
         errors += wrong ? 1u : 0u;
         ++compared;
+        if (wrong_out) wrong_out[e] = wrong ? 1 : 0;
     }
     __shared__ unsigned red[2][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(256) ser_kernel(Geo g, IDX n, const c32 *__res
 }
 
 cudaError_t ser_count(const Geo &g, int S, const c32 *y, const c32 *s, const float *alpha, int Q, float N0,
-                      unsigned long long seed, unsigned long long *counts, cudaStream_t st) {
+                      unsigned long long seed, unsigned long long *counts, cudaStream_t st, unsigned char *wrong) {
     const long n = (long)S * g.K * g.N_d;
     if (n == 0) return cudaSuccess;
     int side = 1;
@@ -105,10 +110,10 @@ cudaError_t ser_count(const Geo &g, int S, const c32 *y, const c32 *s, const flo
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     if (n + 256L * blocks < 0xFFFFFFFFL)   // no flat index (nor its grid-stride successor) wraps
         ser_kernel<uint32_t><<<(unsigned)blocks, 256, 0, st>>>(g, (uint32_t)n, y, s, alpha, side, inv_step, sqrtf(N0),
-                                                              key, counts);
+                                                              key, counts, wrong);
     else
         ser_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, st>>>(g, (unsigned long long)n, y, s, alpha, side,
-                                                                        inv_step, sqrtf(N0), key, counts);
+                                                                        inv_step, sqrtf(N0), key, counts, wrong);
     return cudaGetLastError();
 }
 

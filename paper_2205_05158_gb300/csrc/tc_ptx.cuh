@@ -44,20 +44,21 @@ FD_D bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false (and *err set) on timeout.  The
-// clock is read once per 256 polls, not after every one.
-FD_D bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+// Bounded wait for the phase with the given parity; false (and *err set) once limit_ns
+// have passed.  The clock is read once per 256 polls, not after every one.
+FD_D bool mbar_wait_for(uint64_t *bar, uint32_t parity, int *err, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
         for (int i = 0; i < 256; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicOr(err, 2);
             return false;
         }
     }
 }
+FD_D bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) { return mbar_wait_for(bar, parity, err, kWaitNs); }
 
 FD_D void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(

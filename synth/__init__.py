@@ -230,6 +230,33 @@ def pa_coefficients(seed: int, M: int, nominal: Dict[int, List[complex]], spread
     return base[None] * (1.0 + delta)
 
 
+PA_NOMINAL_MP13 = {p: PA_NOMINAL_MP135[p] for p in (1, 3)}
+
+
+def uneven_instances(n: int, S: int = 50, seed: int = 0, S_per_real: int = 14) -> List[Config]:
+    """Independent downlink instances of uneven size (the batched workload): instance i
+    draws M from {32, 64, 128, 256}, K from {4, 8, 16, 32} (redrawn until K <= M / 4), N
+    from {512, 1024, 2048, 4096} with N_d = round(600 N / 1024) data bins (about 58 %),
+    64-QAM, an i.i.d. Rayleigh channel, and a memory-polynomial PA of orders {1, 3} or
+    {1, 3, 5} (taps 0..3), each with its own seed; S symbols each."""
+    st = Stream(seed, "uneven")
+    out = []
+    for i in range(n):
+        u = st.u32(8)
+        M = (32, 64, 128, 256)[int(u[0]) % 4]
+        K = (4, 8, 16, 32)[int(u[1]) % 4]
+        j = 2
+        while K > M // 4:
+            K = (4, 8, 16, 32)[int(u[j % 8]) % 4] if j < 8 else 4
+            j += 1
+        N = (512, 1024, 2048, 4096)[int(u[7]) % 4]
+        N_d = int(round(N * 600 / 1024))
+        pa = PA_NOMINAL_MP13 if int(u[6]) % 2 == 0 else PA_NOMINAL_MP135
+        out.append(Config(f"uneven{i}", M=M, K=K, N=N, N_d=N_d, Q=64, S=S, S_per_real=S_per_real, pa_nominal=pa,
+                          seed=1000 + i))
+    return out
+
+
 # The ideal linear-clipping PA of Sec. V-B (Fig. 3): order 0 with one coefficient, the
 # clipping amplitude A (y = x for |x| <= A, A x / |x| above).
 PA_LINEAR_CLIP = {0: [1.0]}

@@ -113,3 +113,75 @@ def test_autotune_fp32_plan_has_one_choice():
     c.gpu_zf()
     t_tc, t_cc = c.plan.autotune(c.s, c.H, c.W, c.alpha, c.pa, c.theta, reps=1)
     assert t_tc == -1.0 and t_cc > 0
+
+
+def _uneven_case(cfg):
+    c = Case(cfg, S=cfg.S, fc_scale=0.2, precision=1)
+    c.plan.precode(c.H, None, c.alpha)          # the precoder kept as its factors
+    return c
+
+
+def test_graph_lanes_uneven_instances_with_autotune():
+    """Sixteen instances of the uneven batched workload (M 32..256, K 4..32, N 512..4096,
+    orders {1,3} or {1,3,5}), each autotuned (choices stored per shape), recorded on four
+    concurrent lanes of one graph and replayed twice: the same outputs as one by one; the
+    two smallest instances within the 16-bit tolerances of the oracle."""
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    fd.autotune_forget()
+    cfgs = synth.uneven_instances(16, S=6, S_per_real=3)
+    cases = [_uneven_case(cfg) for cfg in cfgs]
+    for c in cases:
+        c.plan.autotune(c.s, c.H, None, c.alpha, c.pa, c.theta, reps=1)
+    ref = []
+    for c in cases:
+        y = T.empty_like(c.s)
+        m = T.zeros(5, dtype=T.float64, device="cuda")
+        c.plan.distort(c.s, c.H, None, c.alpha, c.pa, c.theta, y, m)
+        ref.append((y, m))
+    T.cuda.synchronize()
+    main = T.cuda.Stream()
+    ys = [T.empty_like(c.s) for c in cases]
+    ms = [T.zeros(5, dtype=T.float64, device="cuda") for c in cases]
+    with fd.Graph.record_lanes(main, 4) as (g, lanes):
+        for i, (c, y, m) in enumerate(zip(cases, ys, ms)):
+            c.plan.set_stream(lanes[i % 4])
+            c.plan.distort(c.s, c.H, None, c.alpha, c.pa, c.theta, y, m)
+    for _ in range(2):
+        g.launch()
+    main.synchronize()
+    for c in cases:
+        c.plan.set_stream(None)
+    for (y0, m0), y, m in zip(ref, ys, ms):
+        assert T.equal(y, y0)
+        assert np.allclose(m.cpu().numpy(), m0.cpu().numpy(), rtol=1e-12, atol=0)
+    small = sorted(range(len(cfgs)), key=lambda i: cfgs[i].M * cfgs[i].N)[:2]
+    for i in small:
+        c = cases[i]
+        Wo, alo = c.oracle_zf()
+        yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+        assert nmse(ref[i][0].cpu().numpy(), yo) <= 1e-4
+        assert abs(oracle.evm_db(ref[i][1].cpu().numpy()) - oracle.evm_db(meto)) <= 0.1
+
+
+def test_autotune_choice_stored_per_shape_and_row_ctas_exact():
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    fd.autotune_forget()
+    cfg = synth.uneven_instances(1, S=6, S_per_real=3)[0].with_(M=64, K=8, N=1024, N_d=600)
+    a, b = _uneven_case(cfg), _uneven_case(cfg.with_(seed=7))
+    ta = a.plan.autotune(a.s, a.H, None, a.alpha, a.pa, a.theta, reps=1)
+    tb = b.plan.autotune(b.s, b.H, None, b.alpha, b.pa, b.theta, reps=1)
+    assert ta == tb                                   # the stored choice, not a new timing
+    for o in (fd.FDDPD_OPT_TENSOR_CONTRACTIONS, fd.FDDPD_OPT_ROW_CTAS):
+        assert a.plan.get_option(o) == b.plan.get_option(o)
+    outs = []
+    for rc in (0, 1, 2):                              # the grid shape changes no arithmetic
+        a.plan.set_option(fd.FDDPD_OPT_ROW_CTAS, rc)
+        y = T.empty_like(a.s)
+        a.plan.distort(a.s, a.H, None, a.alpha, a.pa, a.theta, y)
+        outs.append(y)
+    T.cuda.synchronize()
+    assert T.equal(outs[0], outs[1]) and T.equal(outs[0], outs[2])
+    with pytest.raises(fd.FddpdError):
+        a.plan.set_option(fd.FDDPD_OPT_ROW_CTAS, 9)

@@ -195,3 +195,33 @@ def test_ser_sweep_over_drive(prec):
         with pytest.raises(fd.FddpdError) as ei:
             c.plan.set_power(bad)
         assert ei.value.code == fd.FDDPD_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16"])
+def test_ser_decisions_symbol_by_symbol(prec):
+    """fddpd_ser_decisions against the oracle's per-symbol wrong[]: equal at every symbol
+    whose noisy value is not within 1e-4 level steps of a decision boundary, and the
+    per-symbol flags add up to the counts."""
+    T = torch()
+    cfg = synth.CONFIGS["m16_k2_n64"]
+    c = Case(cfg, S=60, fc_scale=0.3, precision=prec)
+    c.gpu_zf()
+    y = T.empty_like(c.s)
+    c.plan.distort(c.s, c.H, c.W, c.alpha, c.pa, c.theta, y)
+    al = c.alpha.cpu().numpy()
+    N0 = float(np.mean(al ** 2)) * 10 ** (-12.0 / 10)
+    counts = T.zeros(2, dtype=T.int64, device="cuda")
+    wrong = T.full(tuple(c.s.shape), 255, dtype=T.uint8, device="cuda")
+    c.plan.ser_decisions(y, c.s, c.alpha, cfg.Q, N0, 77, counts, wrong)
+    T.cuda.synchronize()
+    wg = wrong.cpu().numpy()
+    e_o, n_o, z, wo = oracle.ser(c.d, y.cpu().numpy(), c.w.s, al, cfg.Q, N0, 77)
+    side = int(round(math.sqrt(cfg.Q)))
+    inv_step = math.sqrt(2.0 * (cfg.Q - 1) / 3.0) / 2.0
+    near = np.zeros(z.shape, dtype=bool)
+    for comp in (z.real, z.imag):
+        x = comp * inv_step + 0.5 * (side - 1)
+        near |= (x > 0) & (x < side - 1) & (np.abs(x - np.floor(x) - 0.5) < 1e-4)
+    assert set(np.unique(wg)) <= {0, 1}
+    assert np.array_equal(wg[~near], wo[~near].astype(np.uint8))
+    assert int(wg.sum()) == int(counts.cpu().numpy()[0]) and e_o > 0
