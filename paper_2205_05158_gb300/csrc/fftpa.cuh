@@ -562,37 +562,43 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
     c32 *coef = twp + F::N + RPC * 2 * F::PADN;
-    // with a kept x(t) and BF16 gX: both rows of the next row group, in flight while this
-    // one is transformed ([N] then [N_d rounded to 4] 4-byte words per row)
+    // the next row group's inputs, in flight while this one is transformed: with a kept x(t)
+    // and BF16 gX both rows ([N] then [N_d rounded to 4] 4-byte words per row); with x(t)
+    // recomputed the x_hat row ([N_d rounded to 2] complex values; gX is read directly)
     constexpr bool STAGE = std::is_same<TIn, cbf16>::value;
     const int ndp = (g.N_d + 3) & ~3;
     uint32_t *sx = reinterpret_cast<uint32_t *>(smem_raw + fftpa_smem_base_(g)) + grp * (F::N + ndp);
     uint32_t *sg = sx + F::N;
+    c32 *sxh = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((g.N_d + 1) & ~1);
+    const bool stage_xh = !xt;
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     const float rs = rsqrtf((float)F::N);
     const long ngroups = (rows + RPC - 1) / RPC;
     auto prefetch = [&](long gg) {
         const long r = gg * RPC + grp;
         if (gg < ngroups && r < rows) {
-            const uint4 *srcx = reinterpret_cast<const uint4 *>(xt + r * F::N);
-            for (int c = t; c < F::N / 4; c += F::T) cp_async_n<16>(sx + 4 * c, srcx + c);
-            const uint32_t *srcg = reinterpret_cast<const uint32_t *>(gX + r * g.N_d);
-            for (int i = t; i < g.N_d; i += F::T) cp_async_n<4>(sg + i, srcg + i);
+            if (stage_xh) {
+                for (int i = t; i < g.N_d; i += F::T) cp_async_n<8>(sxh + i, xh + r * g.N_d + i);
+            } else {
+                const uint4 *srcx = reinterpret_cast<const uint4 *>(xt + r * F::N);
+                for (int c = t; c < F::N / 4; c += F::T) cp_async_n<16>(sx + 4 * c, srcx + c);
+                const uint32_t *srcg = reinterpret_cast<const uint32_t *>(gX + r * g.N_d);
+                for (int i = t; i < g.N_d; i += F::T) cp_async_n<4>(sg + i, srcg + i);
+            }
         }
         cp_async_commit_all();
     };
-    if (STAGE && xt) prefetch(blockIdx.x);
+    if ((STAGE && xt) || stage_xh) prefetch(blockIdx.x);
 
     for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
         const int m = (int)(rowc % g.M);
-        if (STAGE && xt) cp_async_wait_none();
+        if ((STAGE && xt) || stage_xh) cp_async_wait_none();
         __syncthreads();
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
-        const c32 *xrow = xh + rowc * g.N_d;
         const TIn *grow = gX + rowc * g.N_d;
         c32 x[16], gv[16];
         if (STAGE && xt) {   // the forward kept the time-domain PA input; both rows staged
@@ -614,13 +620,15 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
                 x[q] = active ? Operand<cbf16>::load(xrow_t + t + q * F::T) : make_float2(0.f, 0.f);
                 gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
             }
-        } else {
+        } else {   // x(t) recomputed from the staged x_hat row
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int i = data_index(t + q * F::T, g.first_bin, F::N, g.N_d);
-                x[q] = (active && i >= 0) ? xrow[i] : make_float2(0.f, 0.f);
+                x[q] = (active && i >= 0) ? sxh[i] : make_float2(0.f, 0.f);
                 gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
             }
+            __syncthreads();   // the staged rows are read
+            prefetch(grp0 + gridDim.x);
             transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
             __syncthreads();
         }
@@ -739,8 +747,9 @@ template <int LOG2N, int P_, int L_, typename TA>
 inline cudaError_t adj_t(const Geo &g, long rows, const c32 *xh, const c32 *pa, const c32 *twp, const TA *gX,
                          TA *gxh, const cbf16 *xt, cudaStream_t st) {
     const int threads = 256;
-    const size_t sm = fftpa_smem_base_(g) + (std::is_same<TA, cbf16>::value && xt
-                                                 ? (size_t)rows_per_cta(g.N) * adj_stage_bytes(g) : 0);
+    const size_t sm = fftpa_smem_base_(g) + (size_t)rows_per_cta(g.N) *
+                                                (std::is_same<TA, cbf16>::value && xt ? adj_stage_bytes(g)
+                                                                                      : fwd_stage_bytes(g));
     long blocks = 0;
     cudaError_t e =
         persistent_blocks(fftpa_adjoint_kernel<LOG2N, P_, L_, TA, TA>, g.N, rows, threads, sm, blocks, g.row_ctas);

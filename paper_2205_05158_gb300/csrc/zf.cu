@@ -341,16 +341,42 @@ __global__ void __launch_bounds__(128) zf_factor_kernel(Geo g, long nbins, const
         const bool ok = d > F::kPivot * g0;
         bad |= !ok;
         const Real r = ok ? F::rsqrt(d) : Real(1);
-        for (int i = j + 1 + part; i < K; i += LPB) {
-            C s = A[(tri(i) + j) * NB + lb];
-            for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
-                const C a = A[(tri(i) + k) * NB + lb], c = A[(tri(j) + k) * NB + lb];
-                s.x = fma(-a.x, c.x, s.x);
-                s.x = fma(-a.y, c.y, s.x);
-                s.y = fma(-a.y, c.x, s.y);
-                s.y = fma(a.x, c.y, s.y);
+        // rows i > j: each row's sum over k < j on one lane (rows dealt to the lanes), or --
+        // where that leaves lanes idle, for few long rows -- every row's sum split over
+        // the lanes by k and combined by shuffles; the choice depends on j alone
+        const int nr = K - 1 - j;
+        const bool ksplit = LPB > 1 && nr * ((j + LPB - 1) / LPB) < ((nr + LPB - 1) / LPB) * j;
+        if (ksplit) {
+            for (int i = j + 1; i < K; ++i) {
+                C s = C{Real(0), Real(0)};
+                for (int k = part; k < j; k += LPB) {   // s += L[i][k] conj(L[j][k])
+                    const C a = A[(tri(i) + k) * NB + lb], c = A[(tri(j) + k) * NB + lb];
+                    s.x = fma(a.x, c.x, s.x);
+                    s.x = fma(a.y, c.y, s.x);
+                    s.y = fma(a.y, c.x, s.y);
+                    s.y = fma(-a.x, c.y, s.y);
+                }
+                for (int o = BPW; o < 32; o <<= 1) {
+                    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+                }
+                if (part == (i & (LPB - 1))) {
+                    const C a = A[(tri(i) + j) * NB + lb];
+                    A[(tri(i) + j) * NB + lb] = C{(a.x - s.x) * r, (a.y - s.y) * r};
+                }
             }
-            A[(tri(i) + j) * NB + lb] = C{s.x * r, s.y * r};
+        } else {
+            for (int i = j + 1 + part; i < K; i += LPB) {
+                C s = A[(tri(i) + j) * NB + lb];
+                for (int k = 0; k < j; ++k) {     // s -= L[i][k] conj(L[j][k])
+                    const C a = A[(tri(i) + k) * NB + lb], c = A[(tri(j) + k) * NB + lb];
+                    s.x = fma(-a.x, c.x, s.x);
+                    s.x = fma(-a.y, c.y, s.x);
+                    s.y = fma(-a.y, c.x, s.y);
+                    s.y = fma(a.x, c.y, s.y);
+                }
+                A[(tri(i) + j) * NB + lb] = C{s.x * r, s.y * r};
+            }
         }
         if (part == 0) {
             A[dj * NB + lb] = C{ok ? d * r : Real(1), Real(0)};
@@ -384,9 +410,11 @@ __global__ void __launch_bounds__(128) zf_factor_kernel(Geo g, long nbins, const
     for (int j = K - 1; j >= 0 && LPB > 1; --j) {
         const Real r = inv[j * NB + lb];
         C out[RMAX];
+        // rows dealt in snake order (K-1 .. K-LPB to lanes 0..LPB-1, the next LPB rows back
+        // from lane LPB-1), which evens out the rows' unequal lengths i - j
 #pragma unroll
         for (int t = 0; t < RMAX; ++t) {
-            const int i = K - 1 - part - t * LPB;
+            const int i = K - 1 - t * LPB - ((t & 1) ? LPB - 1 - part : part);
             if (i > j) {
                 C s = C{Real(0), Real(0)};
                 for (int k = j + 1; k <= i; ++k) {
@@ -402,7 +430,7 @@ __global__ void __launch_bounds__(128) zf_factor_kernel(Geo g, long nbins, const
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < RMAX; ++t) {
-            const int i = K - 1 - part - t * LPB;
+            const int i = K - 1 - t * LPB - ((t & 1) ? LPB - 1 - part : part);
             if (i > j) {
                 A[(tri(i) + j) * NB + lb] = out[t];
                 tr = fma(out[t].x, out[t].x, tr);
