@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-fdnn", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-regime", action="store_true", help="skip the symbols-per-realisation sweep")
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     return ap.parse_args()
 
@@ -366,6 +367,73 @@ def fdnn_run(fd, torch, stream, S=560, reps=10):
     cnn_flops = 2 * cfg.N_conv * cfg.L_U * (2 * cfg.K_C ** 2 - 1) * cells + 8 * Nd * cfg.L_U * cells
     out["flops_per_ue_symbol"] = {"fdnn": nn_flops, "fdcnn": cnn_flops}
     return out
+
+
+def regime_run(fd, torch, stream, S=1792, reps=5):
+    """The per-subcarrier contractions as the symbols per channel realisation grow (14, 64,
+    256; S = 1792 symbols in each case, the 128 x 16 x 2048 system, BF16 plan, precoder
+    kept as its factors, forward chain): per contraction stage its milliseconds, its
+    algorithmic bytes and flops (a complex multiply-add = 8 flops) as fractions of the
+    measured HBM and sustained BF16 peaks.  Symbols and i.i.d. Rayleigh channel taps are
+    drawn on the device from a seeded torch generator."""
+    import numpy as np
+
+    import synth
+    base = synth.CONFIGS["m128_k16_n2048"]
+    mp, _ = peaks()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    rows = []
+    for Sr in (14, 64, 256):
+        cfg = base.with_(S=S, S_per_real=Sr)
+        R = -(-S // Sr)
+        side = int(round(math.sqrt(cfg.Q)))
+        lv = torch.tensor(synth.qam_levels(cfg.Q), dtype=torch.float32, device="cuda")
+        idx = torch.randint(0, side, (2, S, cfg.K, cfg.N_d), device="cuda", generator=gen)
+        s = torch.complex(lv[idx[0]], lv[idx[1]]).contiguous()
+        del idx
+        taps = torch.randn((R, cfg.T, cfg.K, cfg.M, 2), device="cuda", generator=gen) * math.sqrt(0.5 / cfg.T)
+        taps = torch.complex(taps[..., 0], taps[..., 1]).to(torch.complex128)
+        bins = torch.tensor(synth.data_bins(cfg.N, cfg.N_d), device="cuda", dtype=torch.float64)
+        ph = torch.exp(-2j * math.pi * bins[:, None] * torch.arange(cfg.T, device="cuda", dtype=torch.float64)[None] / cfg.N)
+        H = torch.einsum("bt,rtkm->rbkm", ph, taps).to(torch.complex64).contiguous()
+        del taps, ph
+        pa = torch.from_numpy(synth.pa_coefficients(cfg.seed, cfg.M, cfg.pa_nominal, 0.1).astype(np.complex64)).cuda()
+        theta = torch.from_numpy(synth.theta_init(cfg, cfg.seed, 0.0)).cuda()
+        plan = fd.Plan.from_config(cfg, synth.transmit_power(cfg), max_symbols=S, precision=fd.FDDPD_BF16,
+                                   stream=stream)
+        al = torch.empty((R, cfg.N_d), dtype=torch.float32, device="cuda")
+        met = torch.zeros(5, dtype=torch.float64, device="cuda")
+        plan.precode(H, None, al)
+        plan.distort(s, H, None, al, pa, theta, None, met)
+        torch.cuda.synchronize()
+        plan.profile(True)
+        plan.profile_read()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            plan.distort(s, H, None, al, pa, theta, None, met)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        prof = plan.profile_read()
+        plan.profile(False)
+        plan.close()
+        work = stage_work(cfg, S, "bf16")
+        flops = 8.0 * cfg.M * cfg.K * cfg.N_d * S
+        entry = {"S_per_real": Sr, "realisations": R, "forward_ms": ms, "symbols_per_s": S / (ms / 1e3)}
+        for st in ("precode", "combine", "zmul"):
+            if st in prof and prof[st][1] > 0:
+                t = prof[st][0] / prof[st][1] / 1e3
+                e = {"ms": t * 1e3, "hbm_bytes": work[st][1], "hbm_frac": work[st][1] / t / (mp["hbm_gbs"] * 1e9)}
+                if st != "zmul":
+                    e["tflops"] = flops / t / 1e12
+                    e["tensor_frac"] = flops / t / (mp["bf16_tflops_sustained"] * 1e12)
+                entry[st] = e
+        rows.append(entry)
+        del s, H, pa, theta, al
+        torch.cuda.empty_cache()
+    return {"symbols": S, "system": "M=128 K=16 N=2048 N_d=1200, BF16, forward chain", "rows": rows}
 
 
 def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
@@ -798,6 +866,10 @@ def run_ours(args):
 
     if rank == 0 and not args.no_fdnn:
         section("fdnn_comparison", lambda: fdnn_run(fd, torch, stream))
+
+    # the contractions as the symbols per realisation grow (rank 0, informational)
+    if rank == 0 and not args.no_regime:
+        section("regime_sweep", lambda: regime_run(fd, torch, stream))
 
     # the batched uneven workload: 512 instances in one graph launch (rank 0, informational)
     if rank == 0 and not args.no_batched:

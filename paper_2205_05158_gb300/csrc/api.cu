@@ -725,9 +725,11 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     if (W) {
         FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
                  reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gst, nullptr, nullptr, nullptr, 0.0, gsc));
-    } else {   // g_s_tilde = Z (alpha H g_xhat): the reduction into gy (read by the adjoint of combine, now free)
+    } else {   // g_s_tilde = Z (alpha H g_xhat): the reduction into gy (read by the adjoint of combine, now free);
+               // the tensor-core form reads H's own copy with direct row loads
+        const int mode = use_tc_bin(p) ? fdk::ADJ_PRECODE_F : fdk::ADJ_PRECODE;
         FD_STAGE(p, FDDPD_STAGE_ADJ_PRECODE, 1,
-                 reduce_op(p, fdk::ADJ_PRECODE, S, ops, alpha, gxh, p->gy, nullptr, nullptr, nullptr, 0.0, gsc));
+                 reduce_op(p, mode, S, ops, alpha, gxh, p->gy, nullptr, nullptr, nullptr, 0.0, gsc));
         FD_STAGE(p, FDDPD_STAGE_ZMUL, 1, fdk::zf_zmul(g, S, p->zf_scratch, p->gy, p->gst, st));
     }
     const float *gd = reinterpret_cast<const float *>(p->gst);

@@ -101,7 +101,9 @@ cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, cons
                                    bool accumulate, cudaStream_t stm, int user = -1);
 
 // per-subcarrier complex contractions (FP32 operands)
-enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3 };
+// ADJ_PRECODE_F: the adjoint of precoding through the ZF factors, alpha H g (the A operand
+// is H's own 16-bit copy, read as in COMBINE; Z is applied afterwards)
+enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3, ADJ_PRECODE_F = 4 };
 // A is FP32 (a_kind OUT_F32) or the 16-bit copy (OUT_BF16 / OUT_F16) of W or H
 cudaError_t bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                        c32 *out, cudaStream_t st);

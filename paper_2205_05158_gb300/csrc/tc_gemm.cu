@@ -11,8 +11,12 @@
 //   warp 1 lane 0 : issues tcgen05.mma (M = 128, N = BN, K = 16) into one of two TMEM
 //                   accumulators of BN columns (tile j uses buffer j & 1), commits each
 //                   stage back to its producer barrier and the tile to tfull;
-//   warps 2..5    : epilogue of tile j while tile j + 1 accumulates: tcgen05.ld of the
-//                   lanes of their quarter, a caller-supplied functor, then tempty.
+//   warps 2..9    : epilogue of tile j while tile j + 1 accumulates: two warps per TMEM
+//                   lane quarter (warp w reads lanes 32 (w % 4) .. + 31), each taking half
+//                   of the tile's columns -- tcgen05.ld, a caller-supplied functor, then
+//                   tempty.  Each lane owns one output row, so the operands the functor
+//                   reads are strided by rows; two warps per quarter halve each tile's
+//                   serial chain of prefetch latencies and double the loads in flight.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); a timeout sets the
 // error word, the waiting role stops, the MMA warp still drains its commits, and
 // TMEM is freed before the CTA exits.
@@ -27,7 +31,7 @@
 namespace fdk {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
+constexpr int BM = 128, BK = 64, STAGES = 4, EPI_WARPS = 8, THREADS = 64 + 32 * EPI_WARPS;
 
 template <int BN>
 struct Smem {
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 128);   // the four epilogue warps
+            mbar_init(&tempty[b], 32 * EPI_WARPS);   // every epilogue thread
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -156,7 +160,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
         // the accumulator (residual, activation) are fetched PRE chunks ahead, the first
         // ones while the tile's MMAs run
         constexpr int PRE = 4, NCH = BN / 16;
-        const int q = warp & 3;
+        constexpr int NH = NCH >= 2 ? 2 : 1, HCH = NCH / NH;   // column halves per tile, chunks per half
+        const int q = warp & 3, half = NH > 1 ? (warp - 2) / 4 : 0;
+        const bool idle = warp - 2 >= 4 * NH;                    // one warp per quarter when BN = 16
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             int m0, n0, kbeg, nkb;
@@ -164,19 +170,21 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
             const int buf = j & 1;
             const int row = m0 + 32 * q + lane;
             const bool rok = row < Mdim;
+            const int nh = n0 + 16 * HCH * half;   // first column of this warp's half
             typename Epi::Pre pre[PRE];
 #pragma unroll
             for (int c = 0; c < PRE; ++c)
-                if (rok && n0 + 16 * c + 16 <= Ndim) epi.prefetch(row, n0 + 16 * c, pre[c]);
+                if (!idle && c < HCH && rok && nh + 16 * c + 16 <= Ndim) epi.prefetch(row, nh + 16 * c, pre[c]);
             if (!mbar_wait(&tfull[buf], (uint32_t)(j >> 1) & 1, err)) break;
             fence_after();
-            const bool ok = nkb > 0 && !abort_flag;
-            const uint32_t trow = tmem + (uint32_t)(buf * L::TMEM_COLS) + ((uint32_t)(32 * q) << 16);
+            const bool ok = nkb > 0 && !abort_flag && !idle;
+            const uint32_t trow =
+                tmem + (uint32_t)(buf * L::TMEM_COLS + 16 * HCH * half) + ((uint32_t)(32 * q) << 16);
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
+            for (int c = 0; c < HCH; ++c) {
                 float v[16];
                 tmem_ld16(trow + (uint32_t)(16 * c), v);
-                const int n = n0 + 16 * c;
+                const int n = nh + 16 * c;
                 if (ok && rok && n < Ndim) {
                     if (n + 16 <= Ndim) {
                         epi.chunk(row, n, v, pre[c % PRE]);   // 16 contiguous columns of the row
@@ -186,7 +194,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_kernel(const __grid_constant_
                             if (n + jj < Ndim) epi(row, n + jj, v[jj]);
                     }
                 }
-                if (c + PRE < NCH && rok && n + 16 * PRE + 16 <= Ndim) epi.prefetch(row, n + 16 * PRE, pre[c % PRE]);
+                if (!idle && c + PRE < HCH && rok && n + 16 * PRE + 16 <= Ndim)
+                    epi.prefetch(row, n + 16 * PRE, pre[c % PRE]);
             }
             fence_before();
             mbar_arrive(&tempty[buf]);

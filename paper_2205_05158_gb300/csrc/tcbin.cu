@@ -5,6 +5,8 @@
 //                                ADJ_COMBINE  g_x = H_i^H g_y / alpha_i
 //   reduce (antennas -> users)   COMBINE      y = H_i x / alpha_i and the loss terms (Eq. 5)
 //                                ADJ_PRECODE  g_s = alpha_i W_i^H g_x
+//                                ADJ_PRECODE_F  alpha_i H_i g_x (W^H = Z H with the ZF factor's
+//                                             Z applied afterwards: COMBINE's form, times alpha)
 // i runs over data subcarriers; every realisation's symbols share its H_i and W_i.
 //
 // Complex products as real MMAs.  An A row holds complex entries a_j as interleaved
@@ -989,6 +991,10 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
                 auto k = reduce_pipe_kernel<false, false, true>;
                 if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, vec_ok, err);
+            } else if (mode == ADJ_PRECODE_F) {
+                auto k = reduce_pipe_kernel<false, false, false>;
+                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, vec_ok, err);
             } else {
                 auto k = reduce_pipe_kernel<true, true, false>;
                 if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
@@ -1001,6 +1007,11 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
         auto k = full ? reduce_kernel<T16, false, false, true, TX, true> : reduce_kernel<T16, false, false, true, TX, false>;
         if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, b_scale, vec_ok,
+                                            err);
+    } else if (mode == ADJ_PRECODE_F) {
+        auto k = full ? reduce_kernel<T16, false, false, false, TX, true> : reduce_kernel<T16, false, false, false, TX, false>;
+        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, b_scale, vec_ok,
                                             err);
     } else {
         auto k = full ? reduce_kernel<T16, true, true, false, TX, true> : reduce_kernel<T16, true, true, false, TX, false>;
@@ -1032,7 +1043,8 @@ cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_ki
 cudaError_t tc_bin_reduce(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const void *B,
                           int act_kind, c32 *out, const c32 *s_ref, c32 *gy, double *metrics, double inv_count,
                           float b_scale, int *err, cudaStream_t st) {
-    if (!tc_bin_supported(g) || (mode != COMBINE && mode != ADJ_PRECODE)) return cudaErrorInvalidValue;
+    if (!tc_bin_supported(g) || (mode != COMBINE && mode != ADJ_PRECODE && mode != ADJ_PRECODE_F))
+        return cudaErrorInvalidValue;
     if (act_kind == OUT_BF16) {
         if (a_kind != OUT_BF16 || b_scale != 1.0f) return cudaErrorInvalidValue;
         return tcb::reduce_t<cbf16>(g, mode, S, A, alpha, static_cast<const cbf16 *>(B), out, s_ref, gy, metrics,

@@ -65,6 +65,11 @@ FD_D void cp_async8z(void *dst, const void *src, bool valid) {
                  "l"(src), "r"(valid ? 8 : 0)
                  : "memory");
 }
+FD_D void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
 
 template <typename T16, int NT>   // NT: tasks per lane (2 when K > 28)
 __global__ void __launch_bounds__(32 * ZF_WARPS, NT == 1 ? 3 : 1) zf_gram_kernel(Geo g, long nbins, const c32 *__restrict__ H,
@@ -227,22 +232,31 @@ __global__ void __launch_bounds__(32 * ZF_WARPS, 3)
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             __syncwarp();
-            if (H16) {
-                T16 *dst = H16 + b * K * M + ch * GR_CHUNK + lane;
+            if (H16 || HH16) {   // one shared read of antenna 32 ch + lane's users for both copies,
+                                 // eight users at a time
 #pragma unroll
-                for (int u = 0; u < K; ++u) dst[(long)u * M] = Operand<T16>::from(sH[u * LD + lane]);
-            }
-            if (HH16) {   // H^H in W's layout: antenna row m = 32 ch + lane, 16 users (64 bytes)
-                uint4 *dst = reinterpret_cast<uint4 *>(HH16 + (b * M + ch * GR_CHUNK + lane) * K);
+                for (int h = 0; h < 2; ++h) {
+                    c32 hv[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t w[4];
+                    for (int u = 0; u < 8; ++u) hv[u] = sH[(8 * h + u) * LD + lane];
+                    if (H16) {
+                        T16 *dst = H16 + b * K * M + ch * GR_CHUNK + lane;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const T16 v = Operand<T16>::from(cconj(sH[(4 * q + j) * LD + lane]));
-                        w[j] = *reinterpret_cast<const uint32_t *>(&v);
+                        for (int u = 0; u < 8; ++u) dst[(long)(8 * h + u) * M] = Operand<T16>::from(hv[u]);
                     }
-                    dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    if (HH16) {   // H^H in W's layout: antenna row m = 32 ch + lane, 16 users (64 bytes)
+                        uint4 *dst = reinterpret_cast<uint4 *>(HH16 + (b * M + ch * GR_CHUNK + lane) * K);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const T16 v = Operand<T16>::from(cconj(hv[4 * q + j]));
+                                w[j] = *reinterpret_cast<const uint32_t *>(&v);
+                            }
+                            dst[2 * h + q] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -635,50 +649,87 @@ cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float
 // ---------------------------------------------------------------------------
 // out = Z X per (symbol, subcarrier), Z = G^{-1} = Y^H Y from the factor's lower-triangular
 // Y = L^{-1} (FP32 scratch, [bin / 32][entry][bin % 32]): the precoder applied through its
-// factors, W s = H^H (Z s) (Eq. 6 by associativity), and the adjoint side Z (H g).  A CTA
-// takes one 32-bin block of Y into shared memory and then every (bin, symbol of its
-// realisation) pair of the block, one per thread: w = Y x, u = Y^H w.  X, out [S][K][N_d].
+// factors, W s = H^H (Z s) (Eq. 6 by associativity), and the adjoint side Z (H g).
+// X, out [S][K][N_d].
+//
+// A CTA takes a 32-bin block: Y's block (contiguous, 16-byte cp.async) and the block's
+// symbol vectors -- up to sc symbols of each bin's realisation at a time, one 8-byte
+// cp.async per (symbol, user, bin), so blocks that straddle two realisations need no
+// special case -- are staged in shared memory, then one thread per (bin, symbol) forms
+// u = Y^H (Y x) row by row: row k of Y goes into registers once, gives
+// w_k = sum_{j <= k} Y_kj x_j and is reused for u_j += conj(Y_kj) w_k, j <= k.  Lanes run
+// along the bins, so every shared load of a warp is 32 consecutive entries and every
+// store 32 consecutive subcarriers.  Up to K = 16 two CTAs share an SM: one stages while
+// the other computes.
+constexpr int ZM_SC = 14;   // symbols staged per pass at most (the benchmark's 14 per realisation)
+
 template <int KM>
-__global__ void __launch_bounds__(256) zmul_kernel(Geo g, int S, long nbins, const c32 *__restrict__ Ys,
-                                                   const c32 *__restrict__ X, c32 *__restrict__ out) {
+__global__ void __launch_bounds__(256, KM > 16 ? 1 : 2)
+    zmul_kernel(Geo g, int S, long nbins, int sc_max, const c32 *__restrict__ Ys, const c32 *__restrict__ X,
+                c32 *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char sm[];
-    c32 *sY = reinterpret_cast<c32 *>(sm);   // [T][32]
     const int K = g.K, T = tri(K), Nd = g.N_d, Sr = g.S_per_real;
+    c32 *sY = reinterpret_cast<c32 *>(sm);   // [T][32]
+    c32 *sX = sY + T * 32;                   // [sc_max][K][32]
     const long nblk = (nbins + 31) / 32;
+    // blockDim is whole warps, so a thread's staged entries and tasks all belong to bin
+    // (block, lane): its realisation and subcarrier are found once per block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        __syncthreads();
+        __syncthreads();   // the previous block's shared reads are done
         const c32 *src = Ys + blk * (long)T * 32;
-        for (int e = threadIdx.x; e < T * 32; e += blockDim.x) sY[e] = src[e];
-        __syncthreads();
-        for (int task = threadIdx.x; task < 32 * Sr; task += blockDim.x) {
-            const int lb = task & 31, t = task >> 5;
-            const long b = blk * 32 + lb;
-            if (b >= nbins) continue;
-            const long r = b / Nd;
-            const int i = (int)(b - r * Nd);
-            const long s = r * Sr + t;
-            if (s >= S) continue;
-            const c32 *xs = X + s * K * Nd + i;
-            c32 w[KM];
-#pragma unroll
-            for (int k = 0; k < KM; ++k) {
-                c32 acc = make_float2(0.f, 0.f);
-                if (k < K) {
-#pragma unroll
-                    for (int j = 0; j <= k; ++j) acc = cfma(sY[(tri(k) + j) * 32 + lb], xs[(long)j * Nd], acc);
+        for (int c = threadIdx.x; c < T * 16; c += blockDim.x) cp_async16(sY + 2 * c, src + 2 * c, true);
+        const long b = blk * 32 + lane;
+        const bool bok = b < nbins;
+        const long r = bok ? b / Nd : 0;
+        const int i = (int)(b - r * Nd);
+        const long s0 = r * Sr;   // the realisation's first symbol
+        for (int t0 = 0; t0 < Sr; t0 += sc_max) {
+            const int sc = min(sc_max, Sr - t0);
+            if (t0) __syncthreads();   // the previous symbols' shared reads are done
+            // entry (t, u, lane) of the staged block: warp wid takes rows tu = wid, wid + nw, ...
+            int t = wid / K, u = wid - (wid / K) * K;
+            for (int tu = wid; tu < sc * K; tu += nw) {
+                const long s = s0 + t0 + t;
+                const bool ok = bok && s < S;
+                cp_async8z(sX + tu * 32 + lane, ok ? X + (s * K + u) * Nd + i : X, ok);
+                u += nw;
+                while (u >= K) {
+                    u -= K;
+                    ++t;
                 }
-                w[k] = acc;
             }
-            c32 *os = out + s * K * Nd + i;
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            for (int tt = wid; tt < sc; tt += nw) {   // task (lane's bin, symbol t0 + tt)
+                const long s = s0 + t0 + tt;
+                if (!bok || s >= S) continue;
+                const c32 *xs = sX + tt * K * 32 + lane;
+                c32 x[KM], uacc[KM];
 #pragma unroll
-            for (int j = 0; j < KM; ++j) {
-                if (j < K) {
-                    c32 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int k = j; k < KM; ++k)
-                        if (k < K) acc = cfma(cconj(sY[(tri(k) + j) * 32 + lb]), w[k], acc);
-                    os[(long)j * Nd] = acc;
+                for (int j = 0; j < KM; ++j) {
+                    x[j] = j < K ? xs[j * 32] : make_float2(0.f, 0.f);
+                    uacc[j] = make_float2(0.f, 0.f);
                 }
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (k < K) {
+                        c32 y[KM];
+                        c32 w = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int j = 0; j <= k; ++j) {
+                            y[j] = sY[(tri(k) + j) * 32 + lane];
+                            w = cfma(y[j], x[j], w);
+                        }
+#pragma unroll
+                        for (int j = 0; j <= k; ++j) uacc[j] = cfma(cconj(y[j]), w, uacc[j]);
+                    }
+                }
+                c32 *os = out + s * K * Nd + i;
+#pragma unroll
+                for (int j = 0; j < KM; ++j)
+                    if (j < K) os[(long)j * Nd] = uacc[j];
             }
         }
     }
@@ -687,14 +738,22 @@ __global__ void __launch_bounds__(256) zmul_kernel(Geo g, int S, long nbins, con
 template <int KM>
 static cudaError_t launch_zmul(const Geo &g, int S, long nbins, const c32 *Ys, const c32 *X, c32 *out,
                                cudaStream_t st) {
-    const size_t smem = sizeof(c32) * tri(g.K) * 32;
+    // symbols per pass: as many as fit beside Y in half (K <= 16) or all of the SM's shared memory
+    const long budget = KM > 16 ? 200 * 1024 : 100 * 1024, ybytes = (long)sizeof(c32) * tri(g.K) * 32;
+    int sc = (int)((budget - ybytes) / ((long)sizeof(c32) * g.K * 32));
+    sc = sc < 1 ? 1 : sc > ZM_SC ? ZM_SC : sc;
+    if (sc > g.S_per_real) sc = g.S_per_real;
+    const size_t smem = (size_t)ybytes + sizeof(c32) * (size_t)sc * g.K * 32;
     cudaError_t e = cudaFuncSetAttribute(zmul_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    long blocks = (long)resident_ctas(zmul_kernel<KM>, 256, smem) * sm_count();
+    // one thread per (bin, staged symbol) in as few rounds of at most 256 threads as fit,
+    // whole warps (14 symbols: 224 threads, two rounds)
+    const int rounds = (32 * sc + 255) / 256, threads = 32 * ((sc + rounds - 1) / rounds);
+    long blocks = (long)resident_ctas(zmul_kernel<KM>, threads, smem) * sm_count();
     const long nblk = (nbins + 31) / 32;
     if (blocks > nblk) blocks = nblk;
     if (blocks < 1) blocks = 1;
-    zmul_kernel<KM><<<(unsigned)blocks, 256, smem, st>>>(g, S, nbins, Ys, X, out);
+    zmul_kernel<KM><<<(unsigned)blocks, threads, smem, st>>>(g, S, nbins, sc, Ys, X, out);
     return cudaGetLastError();
 }
 

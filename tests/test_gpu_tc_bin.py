@@ -102,11 +102,17 @@ def test_tc_zf_apply(name, cfg, prec):
     assert np.abs(HW - np.eye(cfg.K)).max() <= 1e-3
 
 
+# K = 24 (the K > 16 form of Z x, CUDA-core contractions) with 17 symbols per realisation
+# (two staged passes of symbols); 150 data bins put realisation boundaries inside 32-bin blocks
+FACTOR_CFGS = CFGS[:3] + [("k24", small_cfg(M=64, K=24, S=40, S_per_real=17))]
+
+
 @pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "cuda_cores"])
-@pytest.mark.parametrize("name,cfg", CFGS[:3], ids=[n for n, _ in CFGS[:3]])
+@pytest.mark.parametrize("name,cfg", FACTOR_CFGS, ids=[n for n, _ in FACTOR_CFGS])
 def test_precoder_kept_as_factors_ragged(name, cfg, tc):
-    """fddpd_precode(H, NULL, alpha) on ragged shapes (K = 3, 13, 16; the generic and the
-    K = 16 Gram kernels write H^H): forward and gradient against the oracle."""
+    """fddpd_precode(H, NULL, alpha) on ragged shapes (K = 3, 13, 16, 24; the generic and
+    the K = 16 Gram kernels write H^H; Z x with 3, 20 and 17 symbols per realisation):
+    forward and gradient against the oracle."""
     c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=1)
     _opt(c, tc)
     c.plan.precode(c.H, None, c.alpha)
