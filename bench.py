@@ -97,10 +97,11 @@ def stage_work(cfg, S: int, prec: str, fp64_factor: bool = True, kept_xt: bool =
     fc_bound = "alu" if prec == "fp32" else "tensor"
     theta_len = cfg.N_conv * 2 * L_U * cfg.K_C ** 2 + cfg.N_conv + 2 * Nd * F + 2 * Nd
     return {
-        # Gram: read H (+ write its 16-bit copy); factor: K^3/3 complex MACs per subcarrier
-        # (Cholesky + triangular inverse, 4 FMA = 8 flop each), FP64 in FP32 plans and FP32
-        # in 16-bit plans; apply: read H, write W
-        "zf_gram": ("hbm", R * Nd * K * M * (c8 + (0 if prec == "fp32" else 4))),
+        # Gram: read H (+ write its 16-bit copy and, with the precoder kept as its factors,
+        # the 16-bit H^H); factor: K^3/3 complex MACs per subcarrier (Cholesky + triangular
+        # inverse, 4 FMA = 8 flop each), FP64 unless a 16-bit plan selects FP32; apply: read
+        # H, write W
+        "zf_gram": ("hbm", R * Nd * K * M * (c8 + (0 if prec == "fp32" else 8))),
         "zf_factor": ("fp64" if (prec == "fp32" or fp64_factor) else "alu", R * Nd * 8.0 * (K ** 3 / 3.0)),
         "zf_apply": ("hbm", R * Nd * K * M * (2 * c8 + (0 if prec == "fp32" else 4)) + R * Nd * 4),
         "conv_fwd": ("hbm", cols * Nd * c8 * L_U + cols * F * 4),

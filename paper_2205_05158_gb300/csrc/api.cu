@@ -207,6 +207,9 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
 
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    // rows of the dense layer's 16-bit operands (and of its FP32 pre-activation gradient)
+    // start on 128-byte boundaries, so every 64-element TMA box row is whole 32-byte sectors
+    auto r64 = [](long v) { return (v + 63) / 64 * 64; };
     const size_t o_st = take(sizeof(c32) * cols * g.N_d), o_gy = take(sizeof(c32) * cols * g.N_d),
                  o_gst = take(sizeof(c32) * cols * g.N_d), o_xh = take(std::max(sizeof(c32) * S * g.M * g.N_d, fdk::blk_plane_bytes(g, S))),
                  // X^PA buffer: the FP32 plane, or (BF16 planes) the blocked X^PA, or the BF16 rows
@@ -214,7 +217,7 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
                  gxh_off = (4 * (size_t)S * g.M * g.N_d + 255) & ~size_t(255),
                  o_X = take(std::max(sizeof(c32) * S * g.M * g.N_d, gxh_off + fdk::blk_plane_bytes(g, S))),
                  o_tw = take(sizeof(c32) * g.N),
-                 o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * ((g.F + 7) / 8 * 8)),
+                 o_act = take(sizeof(float) * cols * g.F), o_gpre = take(sizeof(float) * cols * r64(g.F)),
                  o_part = take(sizeof(float) * cols * (g.n_convw + g.N_conv)),
                  o_grad = take(sizeof(float) * g.theta_len), o_met = take(sizeof(double) * 8),
                  o_stat = take(2 * sizeof(int));
@@ -225,10 +228,9 @@ extern "C" int fddpd_plan_create(fddpd_plan **out, const fddpd_dims *d, const fd
     p->fp64_factor = true;
     p->gxh_off = gxh_off;
     p->host_chunks = 7;
-    auto r8 = [](long v) { return (v + 7) / 8 * 8; };
-    p->ldF = r8(g.F);
-    p->ld2N = r8(2L * g.N_d);
-    p->ldC = r8(cols);
+    p->ldF = r64(g.F);
+    p->ld2N = r64(2L * g.N_d);
+    p->ldC = r64(cols);
     size_t o_a16 = 0, o_aT = 0, o_g16 = 0, o_gT = 0, o_w16 = 0, o_wT = 0, o_fbi = 0;
     if (p->p16) {
         o_a16 = take(2 * (size_t)cols * p->ldF);
@@ -736,7 +738,7 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     if (p->dpd.per_user) {
         // user u's pass over its column block with theta_u and its slice of grad (gd, s in
         // the chain's column order; the dense layer's 16-bit operands one block at a time)
-        const long len1 = g.theta_len / g.K, W2 = 2L * g.N_d, ldCu = (S + 7) / 8 * 8;
+        const long len1 = g.theta_len / g.K, W2 = 2L * g.N_d, ldCu = (S + 63) / 64 * 64;
         for (int u = 0; u < g.K; ++u) {
             const float *th = theta + u * len1;
             float *gr = grad + u * len1;

@@ -284,7 +284,9 @@ struct RowPa {
         }
     }
     // gx_n = sum_l A_l(x_n) g_{n+l} + B_l(x_n) conj(g_{n+l}); gs holds g in natural order
-    // xs: x in natural order (read by the cross terms of the general path only)
+    // and gx the thread's own samples of g on entry (tap 0 of the compiled shapes), the
+    // gradient on return; xs: x in natural order (read by the cross terms of the general
+    // path only)
     static FD_D void adjoint(const Geo &g, int N, int T, int t, const c32 (&x)[16], const c32 *gs, const c32 *cp,
                              c32 (&gx)[16], const c32 *xs) {
         if constexpr (P_ > 0) {
@@ -304,11 +306,11 @@ struct RowPa {
             const int stepq = T + (T >> 4);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                c32 G[P_];
+                c32 G[P_];   // tap l = 0 is this thread's own sample, gx[q] on entry
 #pragma unroll
-                for (int k = 0; k < P_; ++k) G[k] = make_float2(0.f, 0.f);
+                for (int k = 0; k < P_; ++k) G[k] = cmul(cc[k][0], gx[q]);
 #pragma unroll
-                for (int l = 0; l < L1; ++l) {
+                for (int l = 1; l < L1; ++l) {
                     const c32 gl = ((T & 15) == 0 && q < 15) ? gs[pidx(t + l) + q * stepq]
                                                              : gs[pidx((t + q * T + l) & (N - 1))];
 #pragma unroll
@@ -431,16 +433,18 @@ inline size_t fftpa_smem_bytes_(const Geo &g) {
 // row's values are staged as BF16 in its (now free) buffer, and the CTA then writes 16-byte
 // pieces (4 subcarriers of one row), rows of the group fastest, so that the pieces of the
 // group's adjacent antennas land side by side.  Padding subcarriers past N_d are zero.
+// rbase[rr]: row rr's first element in the plane (BlkPlane::row), or -1 past the last row;
+// written once per group by one thread of the row, so the pieces need no division.
 template <int RPC>
-FD_D void store_blk_rows(const Geo &g, long row0, long rows, const uint32_t *stage, int stride, cbf16 *out) {
-    const BlkPlane bp(g);
+FD_D void store_blk_rows(const Geo &g, const long *rbase, const uint32_t *stage, int stride, cbf16 *out) {
+    const long per_group = BlkPlane(g).per_group;   // sub(4 j) = j per_group
     const int ng4 = (g.N_d + 3) >> 2;
     for (int idx = threadIdx.x; idx < RPC * ng4; idx += blockDim.x) {
         const int rr = idx % RPC, j = idx / RPC;
-        const long row = row0 + rr;
-        if (row >= rows) continue;
+        const long b = rbase[rr];
+        if (b < 0) continue;
         const uint4 v = *reinterpret_cast<const uint4 *>(stage + rr * stride + 4 * j);
-        *reinterpret_cast<uint4 *>(out + bp.row(g, row / g.M, (int)(row % g.M)) + bp.sub(4 * j)) = v;
+        *reinterpret_cast<uint4 *>(out + b + (long)j * per_group) = v;
     }
 }
 
@@ -464,6 +468,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     const int in_nd = fwd_in_len(g);
     c32 *stage = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((in_nd + 1) & ~1);
     __shared__ double red[32];
+    __shared__ long rbase[RPC];   // blocked-plane start of each row of the group (BF16 X)
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     bool any_even = false;
     for (int p = 0; p < P; ++p) any_even |= !(g.orders[p] & 1);
@@ -482,9 +487,11 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
-        const int m = (int)(rowc % g.M);
+        const long sym = rowc / g.M;
+        const int m = (int)(rowc - sym * g.M);
         cp_async_wait_none();
         __syncthreads();   // this group's rows are staged; the previous row is done with coef and buffers
+        if (std::is_same<TOut, cbf16>::value && t == 0) rbase[grp] = active ? BlkPlane(g).row(g, sym, m) : -1;
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
         c32 x[16];
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
         if constexpr (BLK) {
             for (int i = g.N_d + t; i < 4 * ((g.N_d + 3) >> 2); i += F::T) so[i] = 0u;
             __syncthreads();
-            store_blk_rows<RPC>(g, grp0 * RPC, rows, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
+            store_blk_rows<RPC>(g, rbase, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
                                 reinterpret_cast<cbf16 *>(Xout));
         }
     }
@@ -571,6 +578,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     uint32_t *sg = sx + F::N;
     c32 *sxh = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((g.N_d + 1) & ~1);
     const bool stage_xh = !xt;
+    __shared__ long rbase[RPC];   // blocked-plane start of each row of the group (BF16 g_xhat)
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     const float rs = rsqrtf((float)F::N);
     const long ngroups = (rows + RPC - 1) / RPC;
@@ -594,9 +602,11 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
-        const int m = (int)(rowc % g.M);
+        const long sym = rowc / g.M;
+        const int m = (int)(rowc - sym * g.M);
         if ((STAGE && xt) || stage_xh) cp_async_wait_none();
         __syncthreads();
+        if (std::is_same<TOut, cbf16>::value && t == 0) rbase[grp] = active ? BlkPlane(g).row(g, sym, m) : -1;
         c32 *cp = coef + grp * PL;
         for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
         const TIn *grow = gX + rowc * g.N_d;
@@ -658,7 +668,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
             }
             for (int i = g.N_d + t; i < 4 * ((g.N_d + 3) >> 2); i += F::T) so[i] = 0u;
             __syncthreads();
-            store_blk_rows<RPC>(g, grp0 * RPC, rows, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
+            store_blk_rows<RPC>(g, rbase, reinterpret_cast<uint32_t *>(twp + F::N), 4 * F::PADN,
                                 reinterpret_cast<cbf16 *>(gxh));
         } else if (active) {
             TOut *orow = gxh + row * g.N_d;
