@@ -414,11 +414,12 @@ FD_HD int rows_per_cta(int N) { return N >= 4096 ? 1 : 4096 / N; }
 // (Eq. 9) the lagging [P][L+1][G] and the leading [P][L+1][G]
 FD_HD int pa_coef_count(const Geo &g) { return g.n_orders * (g.L + 1) * (1 + 2 * g.pa_G); }
 
-// smem: per-pass twiddles, 2 buffers per row, coefficients per row, then the staging of
-// the next row group's inputs (stage_bytes per row)
+// smem: per-pass twiddles, 2 buffers per row, two sets of coefficients per row (this row
+// group's and the next one's, in flight), then the staging of the next row group's inputs
+// (stage_bytes per row)
 FD_HD size_t fftpa_smem_base_(const Geo &g) {
     const int N = g.N, padN = N + (N >> 4), r = rows_per_cta(N);
-    const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + (size_t)r * pa_coef_count(g));
+    const size_t b = sizeof(c32) * ((size_t)N + 2 * (size_t)r * padN + 2 * (size_t)r * pa_coef_count(g));
     return (b + 15) & ~size_t(15);
 }
 // x_hat row: the N_d data bins, or every bin (in_all: the precoded rows of the FD-NN chain)
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
-    c32 *coef = twp + F::N + RPC * 2 * F::PADN;
+    c32 *coef = twp + F::N + RPC * 2 * F::PADN;   // [2][RPC][PL]: this group's and the next one's
     // x_hat rows of the next row group, in flight while this one is transformed
     const int in_nd = fwd_in_len(g);
     c32 *stage = reinterpret_cast<c32 *>(smem_raw + fftpa_smem_base_(g)) + grp * ((in_nd + 1) & ~1);
@@ -475,25 +476,37 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
     const float rs = rsqrtf((float)F::N);
     float gpow = 0.f, dpow = 0.f;
     const long ngroups = (rows + RPC - 1) / RPC;
-    auto prefetch = [&](long gg) {
+    // group gg's x_hat rows and PA coefficients (antenna r mod M; antenna 0 past the last
+    // row) into coefficient set pb
+    auto prefetch = [&](long gg, int pb) {
         const long r = gg * RPC + grp;
-        if (gg < ngroups && r < rows)
-            for (int i = t; i < in_nd; i += F::T) cp_async_n<8>(stage + i, xh + r * in_nd + i);
+        if (gg < ngroups && r < rows) {
+            if (!(in_nd & 1)) {   // rows start on 16 bytes: two subcarriers a copy
+                for (int i = t; i < (in_nd >> 1); i += F::T) cp_async_n<16>(stage + 2 * i, xh + r * in_nd + 2 * i);
+            } else {
+                for (int i = t; i < in_nd; i += F::T) cp_async_n<8>(stage + i, xh + r * in_nd + i);
+            }
+        }
+        if (gg < ngroups) {
+            const c32 *src = pa + (long)((unsigned)(r < rows ? r : 0) % (unsigned)g.M) * PL;
+            c32 *dst = coef + (pb * RPC + grp) * PL;
+            for (int i = t; i < PL; i += F::T) cp_async_n<8>(dst + i, src + i);
+        }
         cp_async_commit_all();
     };
-    prefetch(blockIdx.x);
+    prefetch(blockIdx.x, 0);
 
-    for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
+    int pb = 0;   // coefficient set of this group
+    for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x, pb ^= 1) {
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
-        const long sym = rowc / g.M;
+        const long sym = (long)((unsigned)rowc / (unsigned)g.M);   // rows < 2^31 (an int on the host)
         const int m = (int)(rowc - sym * g.M);
         cp_async_wait_none();
-        __syncthreads();   // this group's rows are staged; the previous row is done with coef and buffers
+        __syncthreads();   // this group's rows and coefficients are staged; the previous group is done with the buffers
         if (std::is_same<TOut, cbf16>::value && t == 0) rbase[grp] = active ? BlkPlane(g).row(g, sym, m) : -1;
-        c32 *cp = coef + grp * PL;
-        for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
+        const c32 *cp = coef + (pb * RPC + grp) * PL;
         c32 x[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_forward_kernel(Geo g, long rows,
             x[q] = (active && i >= 0) ? stage[i] : make_float2(0.f, 0.f);
         }
         __syncthreads();   // the staged rows are read
-        prefetch(grp0 + gridDim.x);
+        prefetch(grp0 + gridDim.x, pb ^ 1);
         transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
         if (xt && active) {   // the time-domain PA input, kept (BF16) for the adjoint
             cbf16 *xrow_t = xt + row * F::N;
@@ -568,7 +581,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     c32 *twp = reinterpret_cast<c32 *>(smem_raw);
     c32 *bufA = twp + F::N + grp * 2 * F::PADN;
     c32 *bufB = bufA + F::PADN;
-    c32 *coef = twp + F::N + RPC * 2 * F::PADN;
+    c32 *coef = twp + F::N + RPC * 2 * F::PADN;   // [2][RPC][PL]: this group's and the next one's
     // the next row group's inputs, in flight while this one is transformed: with a kept x(t)
     // and BF16 gX both rows ([N] then [N_d rounded to 4] 4-byte words per row); with x(t)
     // recomputed the x_hat row ([N_d rounded to 2] complex values; gX is read directly)
@@ -582,33 +595,40 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
     for (int i = threadIdx.x; i < F::TW; i += blockDim.x) twp[i] = twp_g[i];
     const float rs = rsqrtf((float)F::N);
     const long ngroups = (rows + RPC - 1) / RPC;
-    auto prefetch = [&](long gg) {
+    // group gg's staged rows (where this form stages them) and PA coefficients (antenna
+    // r mod M; antenna 0 past the last row) into coefficient set pb
+    auto prefetch = [&](long gg, int pb) {
         const long r = gg * RPC + grp;
-        if (gg < ngroups && r < rows) {
-            if (stage_xh) {
-                for (int i = t; i < g.N_d; i += F::T) cp_async_n<8>(sxh + i, xh + r * g.N_d + i);
-            } else {
-                const uint4 *srcx = reinterpret_cast<const uint4 *>(xt + r * F::N);
-                for (int c = t; c < F::N / 4; c += F::T) cp_async_n<16>(sx + 4 * c, srcx + c);
-                const uint32_t *srcg = reinterpret_cast<const uint32_t *>(gX + r * g.N_d);
-                for (int i = t; i < g.N_d; i += F::T) cp_async_n<4>(sg + i, srcg + i);
-            }
+        if (gg < ngroups && r < rows && stage_xh && !(g.N_d & 1)) {   // 16-byte rows: two subcarriers a copy
+            for (int i = t; i < (g.N_d >> 1); i += F::T) cp_async_n<16>(sxh + 2 * i, xh + r * g.N_d + 2 * i);
+        } else if (gg < ngroups && r < rows && stage_xh) {
+            for (int i = t; i < g.N_d; i += F::T) cp_async_n<8>(sxh + i, xh + r * g.N_d + i);
+        } else if (gg < ngroups && r < rows && STAGE && xt) {
+            const uint4 *srcx = reinterpret_cast<const uint4 *>(xt + r * F::N);
+            for (int c = t; c < F::N / 4; c += F::T) cp_async_n<16>(sx + 4 * c, srcx + c);
+            const uint32_t *srcg = reinterpret_cast<const uint32_t *>(gX + r * g.N_d);
+            for (int i = t; i < g.N_d; i += F::T) cp_async_n<4>(sg + i, srcg + i);
+        }
+        if (gg < ngroups) {
+            const c32 *src = pa + (long)((unsigned)(r < rows ? r : 0) % (unsigned)g.M) * PL;
+            c32 *dst = coef + (pb * RPC + grp) * PL;
+            for (int i = t; i < PL; i += F::T) cp_async_n<8>(dst + i, src + i);
         }
         cp_async_commit_all();
     };
-    if ((STAGE && xt) || stage_xh) prefetch(blockIdx.x);
+    prefetch(blockIdx.x, 0);
 
-    for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x) {
+    int pb = 0;   // coefficient set of this group
+    for (long grp0 = blockIdx.x; grp0 < ngroups; grp0 += gridDim.x, pb ^= 1) {
         const long row = grp0 * RPC + grp;
         const bool active = row < rows;
         const long rowc = active ? row : 0;
-        const long sym = rowc / g.M;
+        const long sym = (long)((unsigned)rowc / (unsigned)g.M);   // rows < 2^31 (an int on the host)
         const int m = (int)(rowc - sym * g.M);
-        if ((STAGE && xt) || stage_xh) cp_async_wait_none();
-        __syncthreads();
+        cp_async_wait_none();
+        __syncthreads();   // this group's staged rows and coefficients are in; the previous group is done
         if (std::is_same<TOut, cbf16>::value && t == 0) rbase[grp] = active ? BlkPlane(g).row(g, sym, m) : -1;
-        c32 *cp = coef + grp * PL;
-        for (int i = t; i < PL; i += F::T) cp[i] = pa[(long)m * PL + i];
+        const c32 *cp = coef + (pb * RPC + grp) * PL;
         const TIn *grow = gX + rowc * g.N_d;
         c32 x[16], gv[16];
         if (STAGE && xt) {   // the forward kept the time-domain PA input; both rows staged
@@ -621,7 +641,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
                                            : make_float2(0.f, 0.f);
             }
             __syncthreads();   // the staged rows are read
-            prefetch(grp0 + gridDim.x);
+            prefetch(grp0 + gridDim.x, pb ^ 1);
         } else if (xt) {
             const cbf16 *xrow_t = xt + rowc * F::N;
 #pragma unroll
@@ -630,6 +650,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
                 x[q] = active ? Operand<cbf16>::load(xrow_t + t + q * F::T) : make_float2(0.f, 0.f);
                 gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
             }
+            prefetch(grp0 + gridDim.x, pb ^ 1);   // the next group's coefficients
         } else {   // x(t) recomputed from the staged x_hat row
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -638,7 +659,7 @@ __global__ void __launch_bounds__(256, 2) fftpa_adjoint_kernel(Geo g, long rows,
                 gv[q] = (active && i >= 0) ? Operand<TIn>::load(grow + i) : make_float2(0.f, 0.f);
             }
             __syncthreads();   // the staged rows are read
-            prefetch(grp0 + gridDim.x);
+            prefetch(grp0 + gridDim.x, pb ^ 1);
             transform<LOG2N, true>(x, bufA, bufB, twp, t, rs);
             __syncthreads();
         }
