@@ -663,12 +663,14 @@ cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float
 // the other computes.
 constexpr int ZM_SC = 14;   // symbols staged per pass at most (the benchmark's 14 per realisation)
 
-template <int KM>
+// KM: the unrolled bound on K; EX: K == KM, compiled in (the run-time K otherwise costs
+// every unrolled product a predicate: 12 % of the kernel's time at K = 16)
+template <int KM, bool EX>
 __global__ void __launch_bounds__(256, KM > 16 ? 1 : 2)
     zmul_kernel(Geo g, int S, long nbins, int sc_max, const c32 *__restrict__ Ys, const c32 *__restrict__ X,
                 c32 *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char sm[];
-    const int K = g.K, T = tri(K), Nd = g.N_d, Sr = g.S_per_real;
+    const int K = EX ? KM : g.K, T = tri(K), Nd = g.N_d, Sr = g.S_per_real;
     c32 *sY = reinterpret_cast<c32 *>(sm);   // [T][32]
     c32 *sX = sY + T * 32;                   // [sc_max][K][32]
     const long nblk = (nbins + 31) / 32;
@@ -744,16 +746,21 @@ static cudaError_t launch_zmul(const Geo &g, int S, long nbins, const c32 *Ys, c
     sc = sc < 1 ? 1 : sc > ZM_SC ? ZM_SC : sc;
     if (sc > g.S_per_real) sc = g.S_per_real;
     const size_t smem = (size_t)ybytes + sizeof(c32) * (size_t)sc * g.K * 32;
-    cudaError_t e = cudaFuncSetAttribute(zmul_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool ex = g.K == KM;
+    cudaError_t e = cudaFuncSetAttribute(zmul_kernel<KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(zmul_kernel<KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // one thread per (bin, staged symbol) in as few rounds of at most 256 threads as fit,
     // whole warps (14 symbols: 224 threads, two rounds)
     const int rounds = (32 * sc + 255) / 256, threads = 32 * ((sc + rounds - 1) / rounds);
-    long blocks = (long)resident_ctas(zmul_kernel<KM>, threads, smem) * sm_count();
+    long blocks = (long)resident_ctas(zmul_kernel<KM, false>, threads, smem) * sm_count();
     const long nblk = (nbins + 31) / 32;
     if (blocks > nblk) blocks = nblk;
     if (blocks < 1) blocks = 1;
-    zmul_kernel<KM><<<(unsigned)blocks, threads, smem, st>>>(g, S, nbins, sc, Ys, X, out);
+    if (ex)
+        zmul_kernel<KM, true><<<(unsigned)blocks, threads, smem, st>>>(g, S, nbins, sc, Ys, X, out);
+    else
+        zmul_kernel<KM, false><<<(unsigned)blocks, threads, smem, st>>>(g, S, nbins, sc, Ys, X, out);
     return cudaGetLastError();
 }
 
