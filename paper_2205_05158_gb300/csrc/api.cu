@@ -771,6 +771,8 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
             }
             FD_CK(p, fdk::conv_reduce(g, S, p->partials, gr, !first, st));
         }
+        // the shared network's tail below (convolution gradient and its reduction) is done
+        // per user inside the loop above: a change to that tail belongs in both places
         return FDDPD_OK;
     }
     if (first) FD_CK(p, cudaMemsetAsync(grad + g.off_fb, 0, sizeof(float) * 2 * g.N_d, st));
