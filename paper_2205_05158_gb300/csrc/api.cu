@@ -564,7 +564,9 @@ static int check_chain(fddpd_plan *p, int S, const void *s, const void *H, const
 struct BinOps {
     const void *H, *W;
     int kind;
-    const void *W_or_H(int mode) const { return (mode == fdk::PRECODE || mode == fdk::ADJ_PRECODE) ? W : H; }
+    const void *W_or_H(int mode) const {
+        return (mode == fdk::PRECODE || mode == fdk::ADJ_PRECODE || mode == fdk::ADJ_COMBINE_F) ? W : H;
+    }
 };
 static int bin_operands(fddpd_plan *p, int S, const c32 *H, const c32 *W, BinOps &o) {
     if (!p->p16) {
@@ -716,7 +718,10 @@ static int run_backward(fddpd_plan *p, int S, const c32 *s, const c32 *H, const 
     rc = pass_operands(p, S, H, W, ps, ops);
     if (rc) return rc;
     const float gsc = grad_scale(p, ps ? ps->inv_count : 1.0 / ((double)cols * g.N_d));
-    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, fdk::ADJ_COMBINE, S, ops, alpha, p->gy, p->Xpa, gsc));
+    // with the precoder kept as its factors the 16-bit W slot holds H^H: the tensor-core form
+    // reads it with direct row loads
+    const int acm = (!W && use_tc_bin(p)) ? fdk::ADJ_COMBINE_F : fdk::ADJ_COMBINE;
+    FD_STAGE(p, FDDPD_STAGE_ADJ_COMBINE, 1, expand_op(p, acm, S, ops, alpha, p->gy, p->Xpa, gsc));
     // BF16 planes: g_xhat goes to a blocked plane -- in x_hat's buffer when the adjoint
     // reads the kept x(t), else behind the rows of g_X (x_hat is read to recompute x(t));
     // FP32 planes: in place over g_X

@@ -101,9 +101,11 @@ cudaError_t fc_backward_weight_f32(const Geo &g, int cols, const float *gd, cons
                                    bool accumulate, cudaStream_t stm, int user = -1);
 
 // per-subcarrier complex contractions (FP32 operands)
-// ADJ_PRECODE_F: the adjoint of precoding through the ZF factors, alpha H g (the A operand
-// is H's own 16-bit copy, read as in COMBINE; Z is applied afterwards)
-enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3, ADJ_PRECODE_F = 4 };
+// With the precoder kept as its ZF factors (the 16-bit copies are H and H^H):
+// ADJ_PRECODE_F: the adjoint of precoding, alpha H g (the A operand is H's own copy, read
+// as in COMBINE; Z is applied afterwards); ADJ_COMBINE_F: the adjoint of combining,
+// H^H g / alpha (the A operand is the H^H copy, read as in PRECODE)
+enum BinMode { PRECODE = 0, ADJ_COMBINE = 1, COMBINE = 2, ADJ_PRECODE = 3, ADJ_PRECODE_F = 4, ADJ_COMBINE_F = 5 };
 // A is FP32 (a_kind OUT_F32) or the 16-bit copy (OUT_BF16 / OUT_F16) of W or H
 cudaError_t bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                        c32 *out, cudaStream_t st);

@@ -3,6 +3,8 @@
 // tensor memory).  Same operations as the CUDA-core kernels of bingemm.cuh:
 //   expand (users -> antennas)   PRECODE      x = alpha_i W_i s~           (Eq. 1)
 //                                ADJ_COMBINE  g_x = H_i^H g_y / alpha_i
+//                                ADJ_COMBINE_F  the same from the H^H copy (precoder kept
+//                                             as its factors): PRECODE's form over 1 / alpha
 //   reduce (antennas -> users)   COMBINE      y = H_i x / alpha_i and the loss terms (Eq. 5)
 //                                ADJ_PRECODE  g_s = alpha_i W_i^H g_x
 //                                ADJ_PRECODE_F  alpha_i H_i g_x (W^H = Z H with the ZF factor's
@@ -948,10 +950,10 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
     cudaError_t e;
     if constexpr (std::is_same<T16, cbf16>::value) {
         if (g.M == 128 && g.K == 16 && g.S_per_real <= TS && b_scale == 1.0f) {
-            if (mode == PRECODE) {
+            if (mode == PRECODE || mode == ADJ_COMBINE_F) {
                 auto k = expand_pipe_kernel<false, false, TO>;
                 if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
-                k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 0, vec_ok, err);
+                k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, mode == ADJ_COMBINE_F, vec_ok, err);
             } else {
                 auto k = expand_pipe_kernel<true, true, TO>;
                 if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
@@ -960,10 +962,10 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
             return cudaGetLastError();
         }
     }
-    if (mode == PRECODE) {
+    if (mode == PRECODE || mode == ADJ_COMBINE_F) {
         auto k = expand_kernel<T16, false, false, TO>;
         if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
-        k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 0, b_scale, vec_ok, err);
+        k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, mode == ADJ_COMBINE_F, b_scale, vec_ok, err);
     } else {
         auto k = expand_kernel<T16, true, true, TO>;
         if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
@@ -1028,7 +1030,8 @@ bool tc_bin_supported(const Geo &g) { return g.M >= 1 && g.M <= 128 && g.K >= 1 
 
 cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                           void *out, int act_kind, float b_scale, int *err, cudaStream_t st) {
-    if (!tc_bin_supported(g) || (mode != PRECODE && mode != ADJ_COMBINE)) return cudaErrorInvalidValue;
+    if (!tc_bin_supported(g) || (mode != PRECODE && mode != ADJ_COMBINE && mode != ADJ_COMBINE_F))
+        return cudaErrorInvalidValue;
     if (act_kind == OUT_BF16) {
         if (a_kind != OUT_BF16 || b_scale != 1.0f) return cudaErrorInvalidValue;
         return tcb::expand_t<cbf16>(g, mode, S, A, alpha, B, static_cast<cbf16 *>(out), b_scale, err, st);
