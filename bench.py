@@ -624,6 +624,18 @@ def job_rate(world: int, symbols: int, seconds: float) -> float:
     return world * symbols / seconds
 
 
+def data_parallel_step(backward, all_reduce, apply, world: int):
+    """One data-parallel training step, the one exchange the path has on more than one
+    GPU: this rank's gradient over its own symbols (backward() returns it), summed over
+    the ranks in place by all_reduce, then the same step -- the sum scaled by 1 / world,
+    the gradient of the mean loss over every rank's symbols -- applied on every rank."""
+    g = backward()
+    if world > 1:
+        all_reduce(g)
+    apply(g, 1.0 / world)
+    return g
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -665,9 +677,22 @@ def run_ours(args):
     # and the chain applies alpha H^H (Z s) (16-bit plans; FP32 plans form W)
     Wt = W if prec == fd.FDDPD_FP32 else None
 
+    # one training step of a plan: on one GPU fddpd_update (forward, adjoint, GD step); on
+    # several, data-parallel: fddpd_backward on this rank's symbols, the gradients summed
+    # over the ranks (NCCL all-reduce on the plan's stream), the same averaged step on
+    # every rank (fddpd_apply_gradient)
+    def train_step(p, th, mt, Wx, alx, gbuf):
+        p.precode(H, Wx, alx)
+        if world == 1:
+            p.update(s, H, Wx, alx, pa, th, LR, 1, fd.FDDPD_GD, mt)
+            return
+        data_parallel_step(lambda: (p.backward(s, H, Wx, alx, pa, th, gbuf, mt), gbuf)[1], dist.all_reduce,
+                           lambda g, sc: p.apply_gradient(th, g, LR, fd.FDDPD_GD, sc), world)
+
+    gbuf = torch.empty(plan.theta_len, dtype=torch.float32, device="cuda") if world > 1 else None
+
     def step():
-        plan.precode(H, Wt, al)
-        plan.update(s, H, Wt, al, pa, theta, LR, 1, fd.FDDPD_GD, met)
+        train_step(plan, theta, met, Wt, al, gbuf)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -757,7 +782,9 @@ def run_ours(args):
                       "step": "ZF (Gram + factor; the precoder applied through its factors, W not formed) + FD-CNN + "
                               "precode + IFFT/PA/FFT + combine + loss + adjoint + GD update",
                       "l2": "inputs larger than L2 (H 2.8 GB), no flush",
-                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                      "parallelism": (f"data-parallel x{world}: each rank its own symbols and channels, "
+                                      "gradients summed by an NCCL all-reduce, the same step on every rank")
+                                     if world > 1 else "single GPU"},
            "roofline": {"kernel": stage, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                         "work_per_launch": amount},
@@ -781,8 +808,7 @@ def run_ours(args):
         metf = torch.zeros(5, dtype=torch.float64, device="cuda")
 
         def stepf():
-            plan.precode(H, Wt, al)
-            plan.update(s, H, Wt, al, pa, thf, LR, 1, fd.FDDPD_GD, metf)
+            train_step(plan, thf, metf, Wt, al, gbuf)
 
         for _ in range(max(3, args.warmup)):
             stepf()
@@ -814,13 +840,31 @@ def run_ours(args):
         hpa = torch.from_numpy(w.pa).pin_memory().numpy()
         hth = torch.from_numpy(w.theta.copy()).pin_memory().numpy()
         hmet = torch.zeros(5, dtype=torch.float64).pin_memory().numpy()
+        if world > 1:   # the data-parallel step from host buffers: copies in, step, theta and metrics out
+            ts, tH, tpa, tth = (torch.from_numpy(a) for a in (hs, hH, hpa, hth))
+            ds, dH, dpa, dth = (torch.empty_like(a, device="cuda") for a in (ts, tH, tpa, tth))
+            dmet = torch.zeros(5, dtype=torch.float64, device="cuda")
+
+            def host_step():
+                for dst, src in ((ds, ts), (dH, tH), (dpa, tpa), (dth, tth)):
+                    dst.copy_(src, non_blocking=True)
+                plan.precode(dH, Wt, al)
+                data_parallel_step(lambda: (plan.backward(ds, dH, Wt, al, dpa, dth, gbuf, dmet), gbuf)[1],
+                                   dist.all_reduce, lambda g, sc: plan.apply_gradient(dth, g, LR, fd.FDDPD_GD, sc),
+                                   world)
+                tth.copy_(dth, non_blocking=True)
+                torch.from_numpy(hmet).copy_(dmet, non_blocking=True)
+                torch.cuda.synchronize()
+        else:
+            def host_step():
+                plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
         for _ in range(max(1, args.warmup)):
-            plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
+            host_step()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            plan.update_host(hs, hH, hpa, hth, LR, 1, fd.FDDPD_GD, hmet)
+            host_step()
         sec = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         out["e2e"] = {"value": job_rate(world, S, sec), "unit": UNIT,
                       "h2d_bytes_per_step": int(hs.nbytes + hH.nbytes + hpa.nbytes + hth.nbytes),
@@ -836,8 +880,7 @@ def run_ours(args):
         al32 = torch.empty_like(al)
 
         def step32():
-            plan32.precode(H, W32, al32)
-            plan32.update(s, H, W32, al32, pa, th32, LR, 1, fd.FDDPD_GD, met32)
+            train_step(plan32, th32, met32, W32, al32, gbuf)
 
         for _ in range(2):
             step32()

@@ -255,6 +255,18 @@ int fddpd_update(fddpd_plan *plan, int S, const fddpd_c32 *s, const fddpd_c32 *H
                  const fddpd_c32 *W, const float *alpha, const fddpd_c32 *pa_coef,
                  float *theta, float lr, int iters, int optimizer, double *metrics);
 
+/* One optimizer step from a gradient the caller supplies (the step of fddpd_update, Sec.
+ * V-A), for training loops that combine gradients themselves -- data-parallel training
+ * runs fddpd_backward on each GPU's own symbols, sums the gradients across the GPUs (an
+ * all-reduce) and applies the same step on every GPU with scale = 1 / GPUs:
+ *   theta -= lr * scale * grad (FDDPD_GD), or one Adam step on g = scale * grad with the
+ *   plan's moments and step counter (FDDPD_ADAM, as fddpd_update; the plan's first Adam
+ *   step allocates the moments -- NOMEM if that fails).
+ * theta [theta_len] in/out and grad [theta_len] in: device FP32, 4-byte aligned, caller
+ * owned; stream-ordered on the plan's stream.  Errors: ARG (null pointer, scale or lr
+ * not finite, unknown optimizer), LAYOUT, UNSUPPORTED (FD-NN plans), NOMEM, CUDA.   */
+int fddpd_apply_gradient(fddpd_plan *plan, float *theta, const float *grad, float scale, float lr, int optimizer);
+
 /* Zero the Adam moments and step counter. */
 int fddpd_reset_optimizer(fddpd_plan *plan);
 

@@ -34,7 +34,7 @@ EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddp
             "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak",
             "fddpd_get_optimizer_state", "fddpd_set_optimizer_state", "fddpd_fdnn_plan_create", "fddpd_get_option",
             "fddpd_autotune_forget", "fddpd_graph_begin_lanes", "fddpd_ser_decisions", "fddpd_selftest_wait",
-            "fddpd_debug_fail_allocs"]
+            "fddpd_debug_fail_allocs", "fddpd_apply_gradient"]
 
 STAGES = ["zf_gram", "zf_factor", "zf_apply", "conv_fwd", "fc_fwd", "precode", "fftpa_fwd", "combine", "adj_combine", "fftpa_adj",
           "adj_precode", "fc_bwd_w", "fc_bwd_b", "fc_bwd_d", "conv_bwd", "step", "pack", "zmul", "fdnn_rows",
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.fddpd_backward.argtypes = [P, I, P, P, P, P, P, P, P, P]
     L.fddpd_update.argtypes = [P, I, P, P, P, P, P, P, C.c_float, I, I, P]
     L.fddpd_reset_optimizer.argtypes = [P]
+    L.fddpd_apply_gradient.argtypes = [P, P, P, C.c_float, C.c_float, I]
     L.fddpd_update_host.argtypes = [P, I, P, P, P, P, C.c_float, I, I, P]
     L.fddpd_profile_enable.argtypes = [P, I]
     L.fddpd_profile_read.argtypes = [P, P, P]
@@ -135,7 +136,7 @@ def load(build_if_missing: bool = True):
               "fddpd_precode_noalloc", "fddpd_set_option", "fddpd_set_power",
               "fddpd_invalidate_operands", "fddpd_zf_residual", "fddpd_alu_peak", "fddpd_get_optimizer_state",
               "fddpd_set_optimizer_state", "fddpd_get_option", "fddpd_autotune_forget", "fddpd_graph_begin_lanes",
-              "fddpd_ser_decisions", "fddpd_selftest_wait", "fddpd_debug_fail_allocs"):
+              "fddpd_ser_decisions", "fddpd_selftest_wait", "fddpd_debug_fail_allocs", "fddpd_apply_gradient"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -259,6 +260,13 @@ class Plan:
                                            _ptr(W, torch.complex64), _ptr(alpha, torch.float32),
                                            _ptr(pa, torch.complex64), _ptr(theta, torch.float32), float(lr),
                                            int(iters), int(optimizer), _ptr(metrics, torch.float64)))
+
+    def apply_gradient(self, theta, grad, lr: float, optimizer: int = FDDPD_GD, scale: float = 1.0):
+        """fddpd_apply_gradient: one GD / Adam step of theta from `grad` (scaled by `scale`),
+        e.g. a gradient summed over data-parallel ranks with scale = 1 / ranks."""
+        import torch
+        self._check(self._lib.fddpd_apply_gradient(self._h, _ptr(theta, torch.float32), _ptr(grad, torch.float32),
+                                                   float(scale), float(lr), int(optimizer)))
 
     def reset_optimizer(self):
         self._check(self._lib.fddpd_reset_optimizer(self._h))

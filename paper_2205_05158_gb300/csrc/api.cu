@@ -876,18 +876,31 @@ extern "C" int fddpd_backward(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
     return FDDPD_OK;
 }
 
-static int opt_step(fddpd_plan *p, float *theta, float lr, int optimizer) {
+static int opt_step(fddpd_plan *p, float *theta, float lr, int optimizer, const float *grad = nullptr,
+                    float gscale = 1.0f) {
+    if (!grad) grad = p->grad;
     if (optimizer == FDDPD_GD) {
-        FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, p->grad, lr, p->stream));
+        FD_STAGE(p, FDDPD_STAGE_STEP, 1, fdk::sgd_step(p->g.theta_len, theta, grad, lr, p->stream, gscale));
     } else {
         const int rc = ensure_adam(p);
         if (rc) return rc;
         const long t = ++p->adam_t;
         const float c1 = (float)(1.0 - pow(0.9, (double)t)), c2 = (float)(1.0 - pow(0.999, (double)t));
         FD_STAGE(p, FDDPD_STAGE_STEP, 1,
-                 fdk::adam_step(p->g.theta_len, theta, p->grad, p->adam_m, p->adam_v, lr, c1, c2, p->stream));
+                 fdk::adam_step(p->g.theta_len, theta, grad, p->adam_m, p->adam_v, lr, c1, c2, p->stream, gscale));
     }
     return FDDPD_OK;
+}
+
+extern "C" int fddpd_apply_gradient(fddpd_plan *p, float *theta, const float *grad, float scale, float lr,
+                                    int optimizer) {
+    if (!p) return FDDPD_ERR_ARG;
+    if (p->nn) return set_err(p, FDDPD_ERR_UNSUPPORTED, "FD-NN plans run the forward chain only");
+    if (!theta || !grad) return set_err(p, FDDPD_ERR_ARG, "null theta or grad");
+    if (!aligned(theta, 4) || !aligned(grad, 4)) return set_err(p, FDDPD_ERR_LAYOUT, "misaligned theta or grad");
+    if (!std::isfinite(scale) || !std::isfinite(lr)) return set_err(p, FDDPD_ERR_ARG, "scale and lr must be finite");
+    if (optimizer != FDDPD_GD && optimizer != FDDPD_ADAM) return set_err(p, FDDPD_ERR_ARG, "optimizer=%d", optimizer);
+    return opt_step(p, theta, lr, optimizer, grad, scale);
 }
 
 extern "C" int fddpd_update(fddpd_plan *p, int S, const fddpd_c32 *s, const fddpd_c32 *H, const fddpd_c32 *W,

@@ -153,9 +153,10 @@ cudaError_t fdnn_alpha_data(const Geo &g, int R, const float *alpha_all, float *
 long fdnn_theta_len(const Geo &g, const FdnnDesc &nn);
 
 // parameter updates and bookkeeping
-cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st);
+// gscale multiplies the gradient (1: the library's own steps)
+cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st, float gscale = 1.0f);
 cudaError_t adam_step(long n, float *theta, const float *grad, float *m, float *v, float lr, float c1, float c2,
-                      cudaStream_t st);
+                      cudaStream_t st, float gscale = 1.0f);
 cudaError_t finalize_metrics(double *metrics, double inv_count, cudaStream_t st);
 cudaError_t twiddles(int N, c32 *tw, cudaStream_t st);
 cudaError_t pass_twiddles(int log2N, c32 *tw, cudaStream_t st);

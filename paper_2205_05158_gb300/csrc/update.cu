@@ -5,18 +5,20 @@
 
 namespace fdk {
 
-__global__ void sgd_kernel(long n, float *__restrict__ theta, const float *__restrict__ grad, float lr) {
+// The gradient enters scaled by gscale (1 for the library's own steps; 1 / ranks for a
+// gradient summed over data-parallel ranks).
+__global__ void sgd_kernel(long n, float *__restrict__ theta, const float *__restrict__ grad, float lr, float gscale) {
     for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x)
-        theta[j] = fmaf(-lr, grad[j], theta[j]);
+        theta[j] = fmaf(-lr, gscale * grad[j], theta[j]);
 }
 
 // Kingma & Ba: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 // theta -= lr (m / c1) / (sqrt(v / c2) + eps), c1 = 1 - b1^t, c2 = 1 - b2^t.
 __global__ void adam_kernel(long n, float *__restrict__ theta, const float *__restrict__ grad, float *__restrict__ m,
-                            float *__restrict__ v, float lr, float c1, float c2) {
+                            float *__restrict__ v, float lr, float c1, float c2, float gscale) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
-        const float gj = grad[j];
+        const float gj = gscale * grad[j];
         const float mj = fmaf(b1, m[j], (1.f - b1) * gj);
         const float vj = fmaf(b2, v[j], (1.f - b2) * gj * gj);
         m[j] = mj;
@@ -30,14 +32,14 @@ static unsigned grid_for(long n) {
     return (unsigned)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
 }
 
-cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st) {
-    sgd_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, grad, lr);
+cudaError_t sgd_step(long n, float *theta, const float *grad, float lr, cudaStream_t st, float gscale) {
+    sgd_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, grad, lr, gscale);
     return cudaGetLastError();
 }
 
 cudaError_t adam_step(long n, float *theta, const float *grad, float *m, float *v, float lr, float c1, float c2,
-                      cudaStream_t st) {
-    adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, grad, m, v, lr, c1, c2);
+                      cudaStream_t st, float gscale) {
+    adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, grad, m, v, lr, c1, c2, gscale);
     return cudaGetLastError();
 }
 

@@ -357,9 +357,15 @@ __global__ void __launch_bounds__(128) zf_factor_kernel(Geo g, long nbins, const
         const Real r = ok ? F::rsqrt(d) : Real(1);
         // rows i > j: each row's sum over k < j on one lane (rows dealt to the lanes), or --
         // where that leaves lanes idle, for few long rows -- every row's sum split over
-        // the lanes by k and combined by shuffles; the choice depends on j alone
+        // the lanes by k and combined by shuffles.  The choice depends on j alone and
+        // counts the FP64 instructions a lane issues for the column either way: dealt
+        // rows, ceil(nr / LPB) rows of j multiply-adds (4 each) and a scaling (2); split
+        // sums, nr rows of ceil(j / LPB) multiply-adds, the shuffle reduction's adds
+        // (2 per halving step) and the subtract-and-scale (4)
         const int nr = K - 1 - j;
-        const bool ksplit = LPB > 1 && nr * ((j + LPB - 1) / LPB) < ((nr + LPB - 1) / LPB) * j;
+        const int lg = LPB >= 4 ? 2 : LPB == 2 ? 1 : 0;
+        const bool ksplit = LPB > 1 && nr * (4 * ((j + LPB - 1) / LPB) + 2 * lg + 4) <
+                                           ((nr + LPB - 1) / LPB) * (4 * j + 2);
         if (ksplit) {
             for (int i = j + 1; i < K; ++i) {
                 C s = C{Real(0), Real(0)};

@@ -97,7 +97,7 @@ def test_null_plan_calls(lib):
 PLAN_CALLS = ["fddpd_set_stream", "fddpd_precode", "fddpd_distort", "fddpd_backward", "fddpd_update",
               "fddpd_reset_optimizer", "fddpd_update_host", "fddpd_profile_enable", "fddpd_profile_read",
               "fddpd_sync", "fddpd_set_option", "fddpd_set_power", "fddpd_invalidate_operands", "fddpd_ser",
-              "fddpd_autotune"]
+              "fddpd_autotune", "fddpd_apply_gradient"]
 
 
 @pytest.mark.parametrize("name", PLAN_CALLS)

@@ -190,6 +190,33 @@ def test_adam_update_matches_oracle():
     assert rel_l2((th_g - th0)[mask], (th_o - th0)[mask]) <= 1e-3
 
 
+@pytest.mark.parametrize("opt", ["gd", "adam"])
+def test_apply_gradient_equals_update(opt):
+    """fddpd_apply_gradient (the step of a data-parallel loop: backward, an all-reduce,
+    then this) on the plan's own gradient gives fddpd_update's step bit for bit, for GD
+    and over two Adam steps; a gradient passed doubled with scale 1/2 gives the same
+    step (the scaling is exact)."""
+    import paper_2205_05158_gb300 as fd
+    T = torch()
+    o = fd.FDDPD_GD if opt == "gd" else fd.FDDPD_ADAM
+    lr = 1e-2 if opt == "gd" else 1e-3
+    a = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
+    b = Case(synth.CONFIGS["m16_k2_n64"], fc_scale=0.3)
+    for c in (a, b):
+        c.use_oracle_zf_on_gpu()
+    g = T.empty(b.plan.theta_len, dtype=T.float32, device="cuda")
+    for it in range(2):
+        a.plan.update(a.s, a.H, a.W, a.alpha, a.pa, a.theta, lr, 1, o)
+        b.plan.backward(b.s, b.H, b.W, b.alpha, b.pa, b.theta, g)
+        g2 = g * 2.0
+        b.plan.apply_gradient(b.theta, g2, lr, o, scale=0.5)
+    T.cuda.synchronize()
+    assert T.equal(a.theta, b.theta)
+    assert not T.equal(a.theta, a.theta.new_tensor(a.w.theta))   # the steps moved theta
+    with pytest.raises(fd.FddpdError):
+        b.plan.apply_gradient(b.theta, g, float("nan"), o)
+
+
 # --- argument errors reported by the device-facing entry points ------------------------
 def test_call_argument_errors():
     import paper_2205_05158_gb300 as fd

@@ -1,7 +1,9 @@
-"""The N > 1 path of the benchmark on two CPU ranks (gloo): independent replicas, each
-drawing its own symbols and channels, timed by the maximum over ranks and counted as the
+"""The N > 1 path of the benchmark on two CPU ranks (gloo): each rank draws its own
+symbols and channels, the timing is the maximum over ranks and the value counts the
 whole job's symbols; the oracle's SER counts of two ranks add up to those of one process
-over both ranks' symbols.  No GPU, no collective on the data path."""
+over both ranks' symbols; a data-parallel training step (gradients summed over the
+ranks, the same averaged step on every rank) equals one process's step over the union
+of the ranks' symbols.  No GPU."""
 import os
 import socket
 import sys
@@ -85,3 +87,80 @@ def test_single_process_helpers(monkeypatch):
     assert bench.rank_config(0, 2000).S == 2000 and bench.rank_config(3, 2000).seed == 3
     with pytest.raises(ZeroDivisionError):
         bench.job_rate(1, 10, 0.0)
+
+
+def _dp_rank_main(rank, world, port, q):
+    """One rank of a data-parallel GD step on CPU: the oracle's gradient over this
+    rank's shard of symbols (whole realisations), bench.data_parallel_step with a gloo
+    all-reduce, the step applied to this rank's copy of theta."""
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    import oracle
+    import synth
+    dist.init_process_group("gloo", rank=rank, world_size=world, init_method=f"tcp://127.0.0.1:{port}")
+    cfg = synth.CONFIGS["m16_k2_n64"].with_(S=4, S_per_real=2)
+    w = synth.make_workload(cfg, fc_scale=0.3)
+    d = oracle.dims_from_config(cfg, w.P_T)
+    W, al = oracle.precode(d, w.H)
+    sh = slice(2 * rank, 2 * rank + 2)   # this rank's symbols: realisation `rank`
+    theta = torch.from_numpy(w.theta.astype(np.float64))
+    lr = 0.5
+
+    def backward():
+        g, _ = oracle.backward(d, w.s[sh], w.H[rank:rank + 1], W[rank:rank + 1], al[rank:rank + 1], w.pa, w.theta)
+        return torch.from_numpy(g)
+
+    def apply(g, scale):
+        theta.sub_(lr * scale * g)
+
+    g = bench.data_parallel_step(backward, dist.all_reduce, apply, world)
+    q.put((rank, theta.numpy().copy(), g.numpy().copy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_data_parallel_step_on_gloo():
+    """Data-parallel training on two ranks equals one process training on both ranks'
+    symbols: the summed per-shard gradients, scaled by 1 / ranks, are the gradient of the
+    mean loss over the union (equal shards), and both ranks hold the same theta after
+    the step.  The per-rank gradients come from the FP64 oracle."""
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dp_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, th0, g0), (_, th1, g1) = res
+    cfg = synth.CONFIGS["m16_k2_n64"].with_(S=4, S_per_real=2)
+    w = synth.make_workload(cfg, fc_scale=0.3)
+    d = oracle.dims_from_config(cfg, w.P_T)
+    W, al = oracle.precode(d, w.H)
+    g_all, _ = oracle.backward(d, w.s, w.H, W, al, w.pa, w.theta)
+    assert np.array_equal(th0, th1)                       # the same step on every rank
+    assert np.array_equal(g0, g1)                         # the all-reduced sum
+    assert np.linalg.norm(g_all) > 0
+    assert np.allclose(g0 / 2, g_all, rtol=1e-10, atol=1e-12 * np.abs(g_all).max())
+    ref = w.theta.astype(np.float64) - 0.5 * g_all
+    assert np.allclose(th0, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_data_parallel_step_single_rank():
+    """With one rank the step applies this rank's own gradient unscaled and exchanges nothing."""
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+    g = bench.data_parallel_step(lambda: np.array([2.0, -4.0]), lambda x: calls.append("reduce"),
+                                 lambda x, sc: calls.append(("apply", sc)), 1)
+    assert calls == [("apply", 1.0)] and g.tolist() == [2.0, -4.0]
