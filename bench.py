@@ -516,6 +516,8 @@ def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
     shapes = {(c.M, c.K, c.N) for c, *_ in insts}
     tc = sum(p.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS) for _, p, *_ in insts)
     one_cta = sum(p.get_option(fd.FDDPD_OPT_ROW_CTAS) == 1 for _, p, *_ in insts)
+    one_bin_cta = sum(p.get_option(fd.FDDPD_OPT_CONTRACTION_CTAS) == 1 and p.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS)
+                      for _, p, *_ in insts)
     nsym = len(insts) * S
     for _, p, *_ in insts:
         p.close()
@@ -524,7 +526,8 @@ def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
             "lanes": lanes, "graph": {"value": nsym / (ms_graph / 1e3), "unit": UNIT, "ms": ms_graph},
             "one_by_one": {"value": nsym / (ms_seq / 1e3), "unit": UNIT, "ms": ms_seq},
             "graph_equals_one_by_one": same, "autotune_s": tune_s, "record_s": rec_s,
-            "autotuned": {"tensor_core_contractions": tc, "row_kernels_one_cta_per_sm": one_cta},
+            "autotuned": {"tensor_core_contractions": tc, "row_kernels_one_cta_per_sm": one_cta,
+                          "contractions_one_cta_per_sm": one_bin_cta},
             "precision": "bf16", "data": "device-drawn seeded symbols and channel taps"}
 
 

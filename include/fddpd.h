@@ -174,10 +174,13 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *   FDDPD_OPT_ROW_CTAS  0 (default): the IFFT / PA / FFT row kernels' persistent grids
  *       hold as many CTAs per SM as fit; 1..8: at most that many (fewer leave room for
  *       the kernels of other plans recorded on other lanes of one graph).
+ *   FDDPD_OPT_CONTRACTION_CTAS  0 or 2 (default): the tensor-core per-subcarrier
+ *       contractions' persistent grids hold two CTAs per SM; 1: one (fddpd_get_option
+ *       reads 2 or 1).  The arithmetic does not depend on it.
  * Returns FDDPD_ERR_ARG for an unknown option or value.  fddpd_get_option reads one
  * back (*value; ARG for an unknown option).                                          */
 enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2, FDDPD_OPT_KEEP_PA_INPUT = 3,
-       FDDPD_OPT_FACTOR_FP64 = 4, FDDPD_OPT_ROW_CTAS = 5 };
+       FDDPD_OPT_FACTOR_FP64 = 4, FDDPD_OPT_ROW_CTAS = 5, FDDPD_OPT_CONTRACTION_CTAS = 6 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
 int fddpd_get_option(const fddpd_plan *plan, int option, int *value);
 
@@ -324,8 +327,9 @@ int fddpd_ser_decisions(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd
 
 /* Per-shape launch choice (for batches of uneven plans): times `reps` forward passes
  * (fddpd_distort) of every candidate -- the per-subcarrier contraction implementations
- * the plan's shape admits (tcgen05 in 16-bit plans with M <= 128, K <= 16; CUDA cores)
- * times the row kernels' grid (FDDPD_OPT_ROW_CTAS 0 or 1) -- with CUDA events on the
+ * the plan's shape admits (tcgen05 in 16-bit plans with M <= 128, K <= 16, with their
+ * grid at two or one CTAs per SM, FDDPD_OPT_CONTRACTION_CTAS; CUDA cores) times the row
+ * kernels' grid (FDDPD_OPT_ROW_CTAS 0 or 1) -- with CUDA events on the
  * plan's stream, and keeps the fastest.  The choice is stored per shape (M, K, N, N_d,
  * S_per_real, precision, PA shape, FD-CNN shape, S) in the process: a later plan of a
  * stored shape takes it without timing (fddpd_autotune_forget clears the store).  ms[2]

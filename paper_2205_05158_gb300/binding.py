@@ -24,6 +24,7 @@ FDDPD_OPT_HOST_CHUNKS = 2
 FDDPD_OPT_KEEP_PA_INPUT = 3
 FDDPD_OPT_FACTOR_FP64 = 4
 FDDPD_OPT_ROW_CTAS = 5
+FDDPD_OPT_CONTRACTION_CTAS = 6
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",

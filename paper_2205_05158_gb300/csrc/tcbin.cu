@@ -922,13 +922,14 @@ static int sm_count() {
 // Two CTAs per SM only fit with the largest shared-memory carveout; the occupancy query
 // assumes the function's preferred carveout, so it is set first.
 // Two CTAs per SM (both kernels are sized for it: shared memory below half the SM's, at
-// most 128 registers a thread, at most 256 TMEM columns each) with the largest carveout.
-template <class Kern> static cudaError_t grid_for(Kern k, int smem, long items, unsigned &blocks) {
+// most 128 registers a thread, at most 256 TMEM columns each) with the largest carveout,
+// or one (Geo::bin_ctas = 1: room for other plans' kernels running beside these).
+template <class Kern> static cudaError_t grid_for(const Geo &g, Kern k, int smem, long items, unsigned &blocks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    long b = 2L * sm_count();
+    long b = (g.bin_ctas == 1 ? 1L : 2L) * sm_count();
     if (b > items) b = items;
     blocks = (unsigned)(b > 0 ? b : 1);
     return cudaSuccess;
@@ -952,11 +953,11 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
         if (g.M == 128 && g.K == 16 && g.S_per_real <= TS && b_scale == 1.0f) {
             if (mode == PRECODE || mode == ADJ_COMBINE_F) {
                 auto k = expand_pipe_kernel<false, false, TO>;
-                if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+                if ((e = grid_for(g, k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, mode == ADJ_COMBINE_F, vec_ok, err);
             } else {
                 auto k = expand_pipe_kernel<true, true, TO>;
-                if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+                if ((e = grid_for(g, k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 1, vec_ok, err);
             }
             return cudaGetLastError();
@@ -964,11 +965,11 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
     }
     if (mode == PRECODE || mode == ADJ_COMBINE_F) {
         auto k = expand_kernel<T16, false, false, TO>;
-        if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+        if ((e = grid_for(g, k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, mode == ADJ_COMBINE_F, b_scale, vec_ok, err);
     } else {
         auto k = expand_kernel<T16, true, true, TO>;
-        if ((e = grid_for(k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
+        if ((e = grid_for(g, k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, EX_SMEM, st>>>(g, S, a, alpha, B, out, 1, b_scale, vec_ok, err);
     }
     return cudaGetLastError();
@@ -991,15 +992,15 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
         if (full && g.S_per_real <= TS && b_scale == 1.0f) {
             if (mode == COMBINE) {
                 auto k = reduce_pipe_kernel<false, false, true>;
-                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, vec_ok, err);
             } else if (mode == ADJ_PRECODE_F) {
                 auto k = reduce_pipe_kernel<false, false, false>;
-                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, vec_ok, err);
             } else {
                 auto k = reduce_pipe_kernel<true, true, false>;
-                if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+                if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
                 k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, vec_ok, err);
             }
             return cudaGetLastError();
@@ -1007,17 +1008,17 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
     }
     if (mode == COMBINE) {
         auto k = full ? reduce_kernel<T16, false, false, true, TX, true> : reduce_kernel<T16, false, false, true, TX, false>;
-        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, s_ref, gy, metrics, inv_count, 1, b_scale, vec_ok,
                                             err);
     } else if (mode == ADJ_PRECODE_F) {
         auto k = full ? reduce_kernel<T16, false, false, false, TX, true> : reduce_kernel<T16, false, false, false, TX, false>;
-        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, b_scale, vec_ok,
                                             err);
     } else {
         auto k = full ? reduce_kernel<T16, true, true, false, TX, true> : reduce_kernel<T16, true, true, false, TX, false>;
-        if ((e = grid_for(k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
+        if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;
         k<<<blocks, THREADS, RD_SMEM, st>>>(g, S, a, alpha, B, out, nullptr, nullptr, nullptr, 0.0, 0, b_scale,
                                             vec_ok, err);
     }
