@@ -149,13 +149,14 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
 
 /* Plan options (no counterpart in the paper; they select among implementations of the
  * same arithmetic).
- *   FDDPD_OPT_TENSOR_CONTRACTIONS  1 (default): in 16-bit plans with M <= 128 and
- *       K <= 16, the four per-subcarrier contractions (precode, combine and their
+ *   FDDPD_OPT_TENSOR_CONTRACTIONS  1 (default): in 16-bit plans with M <= 256 and
+ *       K <= 32, the four per-subcarrier contractions (precode, combine and their
  *       adjoints) run as tcgen05 MMAs with 16-bit B operands (the activations rounded
- *       to the plan's 16-bit type), and the ZF matrix W = H^H (H H^H)^{-1} as tcgen05
- *       MMAs on BF16 high / low splits of H and (H H^H)^{-1} (relative error near
- *       2^-16); 0: CUDA-core contractions on the same 16-bit copies of H and W with
- *       FP32 activations, and W computed on CUDA cores in FP32 before its rounding.
+ *       to the plan's 16-bit type), and, with M <= 128 and K <= 16, the ZF matrix
+ *       W = H^H (H H^H)^{-1} as tcgen05 MMAs on BF16 high / low splits of H and
+ *       (H H^H)^{-1} (relative error near 2^-16); 0: CUDA-core contractions on the same
+ *       16-bit copies of H and W with FP32 activations, and W computed on CUDA cores in
+ *       FP32 before its rounding.
  *       Ignored by FP32 plans.
  *   FDDPD_OPT_HOST_CHUNKS  1..16 (default 7): the number of realisation chunks in which
  *       fddpd_update_host moves a batch and overlaps its copies with the step; 1 copies
@@ -327,7 +328,7 @@ int fddpd_ser_decisions(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd
 
 /* Per-shape launch choice (for batches of uneven plans): times `reps` forward passes
  * (fddpd_distort) of every candidate -- the per-subcarrier contraction implementations
- * the plan's shape admits (tcgen05 in 16-bit plans with M <= 128, K <= 16, with their
+ * the plan's shape admits (tcgen05 in 16-bit plans with M <= 256, K <= 32, with their
  * grid at two or one CTAs per SM, FDDPD_OPT_CONTRACTION_CTAS; CUDA cores) times the row
  * kernels' grid (FDDPD_OPT_ROW_CTAS 0 or 1) -- with CUDA events on the
  * plan's stream, and keeps the fastest.  The choice is stored per shape (M, K, N, N_d,

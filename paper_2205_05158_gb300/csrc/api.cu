@@ -1185,7 +1185,7 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
         }
     }
     // candidates: the contraction implementations the shape admits (tcgen05 in 16-bit plans
-    // with M <= 128, K <= 16, at two or one CTAs per SM; CUDA cores) x the row kernels'
+    // with M <= 256, K <= 32, at two or one CTAs per SM; CUDA cores) x the row kernels'
     // CTAs per SM (as many as fit; one)
     float t[2][2][2] = {{{-1.0f, -1.0f}, {-1.0f, -1.0f}}, {{-1.0f, -1.0f}, {-1.0f, -1.0f}}};
     const bool was_tc = p->tc_bin;

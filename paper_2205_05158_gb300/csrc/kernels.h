@@ -69,7 +69,10 @@ cudaError_t zf_zmul(const Geo &g, int S, const void *scratch, const c32 *X, c32 
 // given 16-bit kind beside it
 cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,
                         int kind, int *err, cudaStream_t st);
+// the tensor-core contractions: M <= 256 antennas, K <= 32 users
 bool tc_bin_supported(const Geo &g);
+// the tensor-core ZF apply (W = H^H Z): M <= 128, K <= 16
+bool tc_apply_supported(const Geo &g);
 
 // symbol errors at the users: counts[0] += errors, counts[1] += symbols compared
 // wrong (may be null): per (symbol, user, subcarrier) 1 = error, 0 = correct, 2 = not compared

@@ -24,7 +24,9 @@
 // expand: an item is 8 consecutive subcarriers of one realisation.  A_i = [m][(u, c)]
 //   (antenna rows, 16 user slots = 32 k), two subcarriers side by side in each 128-byte
 //   row of a swizzled tile; MMA i (M = 128, N = 32, K = 2 x 16) accumulates into TMEM
-//   columns 32 i .. 32 i + 31, and the epilogue reads antenna m from lane m.
+//   columns 32 i .. 32 i + 31, and the epilogue reads antenna m from lane m.  (Generic
+//   form: 4 subcarriers of 32 user slots each, one per tile row, with K > 16; the
+//   antennas in items of 128.)
 // reduce: an item is 4 subcarriers, computed transposed (y^T = x^T H^T): A holds the real
 //   form of all 4 subcarriers' activations (rows (b, t, c'), 128), B their 4 x 16 user
 //   rows of H (or W^H), so one MMA (M = 128, N = 64) per K step covers the item and the
@@ -150,6 +152,10 @@ FD_D void teardown(uint64_t *bar, uint32_t phase, bool alive, uint32_t tmem, uin
 // expand.  AT = false: A = W16 [bin][m][u] (rows m, PRECODE); AT = true: A = H16
 // [bin][u][m] read transposed (ADJ_COMBINE).  out[t][m][i] = scale_i D / b_scale, stored
 // as TO (c32, or cbf16 for the BF16 activation planes).
+// Up to 256 antennas and 32 users: an item covers 128 antennas (M > 128: two items per
+// subcarrier group, antennas 128 h ..); with K > 16 a subcarrier's 32 user slots fill a
+// whole 128-byte tile row (one subcarrier per tile, 4 per item, 4 MMA K steps) instead
+// of two subcarriers side by side.
 template <typename T16, bool CONJ, bool AT, typename TO>
 __global__ void __launch_bounds__(THREADS, 2)
     expand_kernel(Geo g, int S, const uint32_t *__restrict__ A, const float *__restrict__ alpha,
@@ -162,21 +168,26 @@ __global__ void __launch_bounds__(THREADS, 2)
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int M = g.M, K = g.K, Nd = g.N_d;
-    const int ngroups = (Nd + EXB - 1) / EXB;
+    const int spt = K > 16 ? 1 : 2;        // subcarriers per tile (per 128-byte row)
+    const int exb = 4 * spt;               // subcarriers per item
+    const int MH = (M + 127) >> 7;         // 128-antenna parts, one item each
+    const int ngroups = (Nd + exb - 1) / exb;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
-    const long nitems = (long)R * ngroups;
+    const long nitems = (long)R * ngroups * MH;
     const uint32_t tmem = setup(&bar, &tmem_slot, 256);
     const uint32_t idesc = instr_desc(Pk<T16>::type, 128, 32);
-    const int nks = K > 8 ? 2 : 1;
+    const int nks = K > 16 ? 4 : K > 8 ? 2 : 1;
     uint32_t phase = 0;
     bool alive = true;
 
     for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
-        const int r = (int)(item / ngroups), i0 = (int)(item % ngroups) * EXB;
+        const int m0 = 128 * (int)(item % MH);
+        const long grp = item / MH;
+        const int r = (int)(grp / ngroups), i0 = (int)(grp % ngroups) * exb;
         const long t0 = (long)r * g.S_per_real;
         const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
         const long bin0 = (long)r * Nd + i0;
-        const int nb = min(EXB, Nd - i0);
+        const int nb = min(exb, Nd - i0);
         // the subcarrier scales, loaded before they are needed
         float sc[EXB];
 #pragma unroll
@@ -185,23 +196,25 @@ __global__ void __launch_bounds__(THREADS, 2)
             sc[j] = (inv_alpha ? 1.0f / al : al) / b_scale;
         }
 
-        // A: chunk (tile p, row m, 16-byte chunk ch) = users 4 (ch & 3) .. + 3 of
-        // subcarrier 2p + (ch >> 2) at antenna m, copied with cp.async (zero outside)
+        // A: chunk (tile p, row m, 16-byte chunk ch) = users u0 .. u0 + 3 of subcarrier b at
+        // antenna m0 + m -- b = 2p + (ch >> 2), u0 = 4 (ch & 3) with two subcarriers a tile,
+        // b = p, u0 = 4 ch with one -- copied with cp.async (zero outside)
         if (!AT) {
-            if (K == 16) {
+            if (!(K & 3)) {   // whole 16-byte runs of 4 users
                 for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
-                    const int ch = c & 7, m = (c >> 3) & 127, b = 2 * (c >> 10) + (ch >> 2);
-                    const bool ok = b < nb && m < M;
-                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m) * 16 + 4 * (ch & 3) : A;
-                    cp_async16(sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8), src, ok);
+                    const int ch = c & 7, m = (c >> 3) & 127, p = c >> 10;
+                    const int b = spt == 2 ? 2 * p + (ch >> 2) : p, u0 = spt == 2 ? 4 * (ch & 3) : 4 * ch;
+                    const bool ok = b < nb && m0 + m < M && u0 < K;
+                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m0 + m) * K + u0 : A;
+                    cp_async16(sA + p * 16384 + sw128_offset(m, ch * 8), src, ok);
                 }
             } else {
                 for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
-                    const int ch = c & 7, m = (c >> 3) & 127, b = 2 * (c >> 10) + (ch >> 2);
-                    const int u0 = 4 * (ch & 3);
-                    uint8_t *dst = sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8);
-                    const bool ok = b < nb && m < M;
-                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m) * K : A;
+                    const int ch = c & 7, m = (c >> 3) & 127, p = c >> 10;
+                    const int b = spt == 2 ? 2 * p + (ch >> 2) : p, u0 = spt == 2 ? 4 * (ch & 3) : 4 * ch;
+                    uint8_t *dst = sA + p * 16384 + sw128_offset(m, ch * 8);
+                    const bool ok = b < nb && m0 + m < M;
+                    const uint32_t *src = ok ? A + ((bin0 + b) * M + m0 + m) * K : A;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) cp_async4(dst + 4 * j, ok && u0 + j < K ? src + u0 + j : A, ok && u0 + j < K);
                 }
@@ -209,37 +222,39 @@ __global__ void __launch_bounds__(THREADS, 2)
         } else {
             // transposed: the four users of a chunk are M entries apart; lanes run along m
             for (int c = tid; c < 4 * 128 * 8; c += THREADS) {
-                const int m = c & 127, ch = (c >> 7) & 7, b = 2 * (c >> 10) + (ch >> 2);
-                const int u0 = 4 * (ch & 3);
-                uint8_t *dst = sA + (c >> 10) * 16384 + sw128_offset(m, ch * 8);
-                const bool ok = b < nb && m < M;
+                const int m = c & 127, ch = (c >> 7) & 7, p = c >> 10;
+                const int b = spt == 2 ? 2 * p + (ch >> 2) : p, u0 = spt == 2 ? 4 * (ch & 3) : 4 * ch;
+                uint8_t *dst = sA + p * 16384 + sw128_offset(m, ch * 8);
+                const bool ok = b < nb && m0 + m < M;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const bool okj = ok && u0 + j < K;
-                    cp_async4(dst + 4 * j, okj ? A + ((bin0 + b) * K + u0 + j) * M + m : A, okj);
+                    cp_async4(dst + 4 * j, okj ? A + ((bin0 + b) * K + u0 + j) * M + m0 + m : A, okj);
                 }
             }
         }
 
         for (int s0 = 0; s0 < nsym && alive; s0 += TS) {
             const int ns = min(TS, nsym - s0);
-            // B: element (t, u, subcarrier b), b fastest; rows 2t and 2t + 1 of pair tile
-            // b >> 1, k = 32 (b & 1) + 2u
+            // B: element (t, u, subcarrier b), b fastest (16 user slots x 8 subcarriers, or
+            // 32 x 4); rows 2t and 2t + 1 of tile b / spt, k = 32 (b % spt) + 2u
             for (int e0 = tid; e0 < TS * 16 * EXB; e0 += 8 * THREADS) {
                 c32 v[8];
 #pragma unroll
                 for (int h = 0; h < 8; ++h) {
-                    const int e = e0 + h * THREADS, b = e & 7, u = (e >> 3) & 15, t = e >> 7;
+                    const int e = e0 + h * THREADS, t = e >> 7;
+                    const int b = spt == 2 ? e & 7 : e & 3, u = spt == 2 ? (e >> 3) & 15 : (e >> 2) & 31;
                     v[h] = (t < ns && u < K && b < nb) ? B[((t0 + s0 + t) * K + u) * Nd + i0 + b]
                                                        : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int h = 0; h < 8; ++h) {
-                    const int e = e0 + h * THREADS, b = e & 7, u = (e >> 3) & 15, t = e >> 7;
+                    const int e = e0 + h * THREADS, t = e >> 7;
+                    const int b = spt == 2 ? e & 7 : e & 3, u = spt == 2 ? (e >> 3) & 15 : (e >> 2) & 31;
                     uint32_t w0, w1;
                     real_rows<T16, CONJ>(v[h].x * b_scale, v[h].y * b_scale, w0, w1);
-                    uint8_t *tile = sB + (b >> 1) * 4096;
-                    const int k = 32 * (b & 1) + 2 * u;
+                    uint8_t *tile = sB + (spt == 2 ? b >> 1 : b) * 4096;
+                    const int k = (spt == 2 ? 32 * (b & 1) : 0) + 2 * u;
                     st32(tile + sw128_offset(2 * t, k), w0);
                     st32(tile + sw128_offset(2 * t + 1, k), w1);
                 }
@@ -251,15 +266,16 @@ __global__ void __launch_bounds__(THREADS, 2)
                 fence_after();
                 for (int b = 0; b < nb; ++b)
                     for (int ks = 0; ks < nks; ++ks) {
-                        const uint32_t off = (b & 1) * 64 + ks * 32;
-                        mma_f16(tmem + 32 * b, smem_desc(sA + (b >> 1) * 16384 + off),
-                                smem_desc(sB + (b >> 1) * 4096 + off), idesc, ks ? 1u : 0u);
+                        const int p = spt == 2 ? b >> 1 : b;
+                        const uint32_t off = (spt == 2 ? (b & 1) * 64 : 0) + ks * 32;
+                        mma_f16(tmem + 32 * b, smem_desc(sA + p * 16384 + off), smem_desc(sB + p * 4096 + off),
+                                idesc, ks ? 1u : 0u);
                     }
                 mma_commit(&bar);
             }
             alive = wait_mma(&bar, phase, err);
             if (alive) {
-                const int q = warp & 3, m = 32 * q + lane;
+                const int q = warp & 3, m = m0 + 32 * q + lane;
                 const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
                 if constexpr (std::is_same<TO, c32>::value) {
                     // warp w: antennas 32 (w & 3) .., subcarriers 4 (w >> 2) .. + 3: one
@@ -341,6 +357,9 @@ __global__ void __launch_bounds__(THREADS, 2)
 // reads TMEM lanes 32 b .. (its subcarrier's symbols) at columns 16 b .. 16 b + 15.
 // FULL: M = 128 antennas and K = 16 users as compile-time constants, so the index
 // arithmetic of the tile builds and the epilogue is shifts and masks.
+// Up to 256 antennas and 32 users: the antennas go in parts of 128 (A and B rebuilt per
+// part, the MMAs accumulating in TMEM), the users in halves of 16 (TMEM columns 64 h ..,
+// B rebuilt per half); then one epilogue pass per user half.
 template <typename T16, bool CONJ, bool AT, bool COMB, typename TX, bool FULL>
 __global__ void __launch_bounds__(THREADS, 2)
     reduce_kernel(Geo g, int S, const uint32_t *__restrict__ Wt, const float *__restrict__ alpha,
@@ -356,12 +375,14 @@ __global__ void __launch_bounds__(THREADS, 2)
     __shared__ double red[32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int M = FULL ? 128 : g.M, K = FULL ? 16 : g.K, Nd = g.N_d;
-    const int MP = FULL ? 128 : (M + 7) & ~7;   // antennas padded to one K step (8 complex)
-    const int MC = MP / 4, nks = MP / 8;
+    const int MH = FULL ? 1 : (M + 127) >> 7;   // 128-antenna parts
+    const int UH = FULL ? 1 : (K + 15) >> 4;    // 16-user halves
+    const bool one_b = MH == 1 && UH == 1;      // B loaded once per item
     const int ngroups = (Nd + RDB - 1) / RDB;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long nitems = (long)R * ngroups;
-    const uint32_t tmem = setup(&bar, &tmem_slot, 64);
+    const uint32_t tcols = UH > 1 ? 128 : 64;
+    const uint32_t tmem = setup(&bar, &tmem_slot, tcols);
     const uint32_t idesc = instr_desc(Pk<T16>::type, 128, 64);
     const float gscale = (float)(2.0 * inv_count);
     uint32_t phase = 0;
@@ -381,152 +402,171 @@ __global__ void __launch_bounds__(THREADS, 2)
             sc = (inv_alpha ? 1.0f / al : al) / b_scale;
         }
 
-        // B rows 16 b + u (u < K), k-block m / 32, copied with cp.async; antennas
-        // M .. MP - 1 are zero
-        if (!AT) {
-            const int n = RDB * K * MC;
-            for (int c = tid; c < n; c += THREADS) {
-                const int mc = c % MC, bu = c / MC, u = bu % K, b = bu / K;
-                uint8_t *dst = sB + (mc >> 3) * 8192 + sw128_offset(16 * b + u, (mc & 7) * 8);
-                const uint32_t *src = Wt + ((bin0 + (b < nb ? b : 0)) * K + u) * M + 4 * mc;
-                if (!(M & 3)) {
-                    const bool ok = b < nb && 4 * mc < M;
-                    cp_async16(dst, ok ? src : Wt, ok);
-                } else {
+        // B rows 16 b + u' (user u = 16 uh + u' < K) of antenna part mh, k-block (m - 128 mh)
+        // / 32, copied with cp.async; antennas past the part's last are zero
+        auto load_b = [&](int mh, int uh) {
+            const int Mp = min(128, M - 128 * mh), Kh = min(16, K - 16 * uh), MC = ((Mp + 7) & ~7) / 4;
+            const int ma = 128 * mh, ua = 16 * uh;
+            if (!AT) {
+                const int n = RDB * Kh * MC;
+                for (int c = tid; c < n; c += THREADS) {
+                    const int mc = c % MC, bu = c / MC, u = bu % Kh, b = bu / Kh;
+                    uint8_t *dst = sB + (mc >> 3) * 8192 + sw128_offset(16 * b + u, (mc & 7) * 8);
+                    const uint32_t *src = Wt + ((bin0 + (b < nb ? b : 0)) * K + ua + u) * M + ma + 4 * mc;
+                    if (!(M & 3)) {
+                        const bool ok = b < nb && 4 * mc < Mp;
+                        cp_async16(dst, ok ? src : Wt, ok);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const bool ok = b < nb && 4 * mc + j < Mp;
+                            cp_async4(dst + 4 * j, ok ? src + j : Wt, ok);
+                        }
+                    }
+                }
+            } else {
+                // transposed: a 16-byte run of W16 (4 users at antenna m) feeds 4 rows
+                const int MPp = (Mp + 7) & ~7, UQ = (Kh + 3) / 4, n = RDB * MPp * UQ;
+                for (int c = tid; c < n; c += THREADS) {
+                    const int uq = c % UQ, bm = c / UQ, m = bm % MPp, b = bm / MPp;
+                    const bool ok = b < nb && m < Mp;
+                    const uint32_t *src = ok ? Wt + ((bin0 + b) * M + ma + m) * K + ua + 4 * uq : Wt;
+                    uint8_t *dst = sB + (m >> 5) * 8192;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const bool ok = b < nb && 4 * mc + j < M;
-                        cp_async4(dst + 4 * j, ok ? src + j : Wt, ok);
+                        const int u = 4 * uq + j;
+                        if (u < Kh) cp_async4(dst + sw128_offset(16 * b + u, 2 * (m & 31)), ok ? src + j : Wt, ok);
                     }
                 }
             }
-        } else {
-            // transposed: a 16-byte run of W16 (4 users at antenna m) feeds 4 rows
-            const int UQ = (K + 3) / 4, n = RDB * MP * UQ;
-            for (int c = tid; c < n; c += THREADS) {
-                const int uq = c % UQ, bm = c / UQ, m = bm % MP, b = bm / MP;
-                const bool ok = b < nb && m < M;
-                const uint32_t *src = ok ? Wt + ((bin0 + b) * M + m) * K + 4 * uq : Wt;
-                uint8_t *dst = sB + (m >> 5) * 8192;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int u = 4 * uq + j;
-                    if (u < K) cp_async4(dst + sw128_offset(16 * b + u, 2 * (m & 31)), ok ? src + j : Wt, ok);
-                }
-            }
-        }
+        };
+        if (one_b) load_b(0, 0);
 
         for (int s0 = 0; s0 < nsym && alive; s0 += TS) {
             const int ns = min(TS, nsym - s0);
             const bool vec = vec_ok && nb == RDB;
-            // outputs (t, u, b), b fastest (4 subcarriers = 32 contiguous bytes): at most
-            // 16 x 16 x 4 = 4 per thread; the reference symbols are loaded ahead
-            const int nout = ns * K * RDB;
+            // outputs (t, u, b) of user half 0, b fastest (4 subcarriers = 32 contiguous
+            // bytes): at most 16 x 16 x 4 = 4 per thread; its reference symbols loaded ahead
             c32 sref[4];
+            auto load_sref = [&](int uh) {
+                const int Kh = min(16, K - 16 * uh), nout = ns * Kh * RDB;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int e = tid + k * THREADS;
-                const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
-                sref[k] = (COMB && e < nout && b < nb) ? s_ref[((t0 + s0 + t) * K + u) * Nd + i0 + b]
-                                                       : make_float2(0.f, 0.f);
-            }
-            // A: (t, m) pairs, m fastest, all 4 subcarriers (32 contiguous bytes of FP32,
-            // 16 of BF16) each; rows 32 b + 2t and 32 b + 2t + 1 of k-block m / 32
-            if constexpr (std::is_same<TX, c32>::value) {
-                for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
-                    c32 v[4][RDB];
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * THREADS;
+                    const int b = e & (RDB - 1), tu = e / RDB, u = 16 * uh + tu % Kh, t = tu / Kh;
+                    sref[k] = (COMB && e < nout && b < nb) ? s_ref[((t0 + s0 + t) * K + u) * Nd + i0 + b]
+                                                           : make_float2(0.f, 0.f);
+                }
+            };
+            load_sref(0);
+            for (int mh = 0; mh < MH && alive; ++mh) {
+                const int ma = 128 * mh, Mp = FULL ? 128 : min(128, M - ma);
+                const int MP = FULL ? 128 : (Mp + 7) & ~7;   // antennas padded to one K step (8 complex)
+                const int nks = MP / 8;
+                // A: (t, m) pairs of antennas ma + m, m fastest, all 4 subcarriers (32
+                // contiguous bytes of FP32, 16 of BF16) each; rows 32 b + 2t and 32 b + 2t + 1
+                // of k-block m / 32
+                if constexpr (std::is_same<TX, c32>::value) {
+                    for (int e0 = tid; e0 < TS * MP; e0 += 4 * THREADS) {
+                        c32 v[4][RDB];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
-                        const bool ok = e < TS * MP && t < ns && m < M;
-                        const c32 *src = X + ((t0 + s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * Nd + i0;
-                        if (ok && vec) {
-                            const float4 lo = reinterpret_cast<const float4 *>(src)[0];
-                            const float4 hi = reinterpret_cast<const float4 *>(src)[1];
-                            v[h][0] = make_float2(lo.x, lo.y);
-                            v[h][1] = make_float2(lo.z, lo.w);
-                            v[h][2] = make_float2(hi.x, hi.y);
-                            v[h][3] = make_float2(hi.z, hi.w);
+                        for (int h = 0; h < 4; ++h) {
+                            const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                            const bool ok = e < TS * MP && t < ns && m < Mp;
+                            const c32 *src = X + ((t0 + s0 + (ok ? t : 0)) * M + ma + (ok ? m : 0)) * Nd + i0;
+                            if (ok && vec) {
+                                const float4 lo = reinterpret_cast<const float4 *>(src)[0];
+                                const float4 hi = reinterpret_cast<const float4 *>(src)[1];
+                                v[h][0] = make_float2(lo.x, lo.y);
+                                v[h][1] = make_float2(lo.z, lo.w);
+                                v[h][2] = make_float2(hi.x, hi.y);
+                                v[h][3] = make_float2(hi.z, hi.w);
+                            } else {
+#pragma unroll
+                                for (int b = 0; b < RDB; ++b) v[h][b] = (ok && b < nb) ? src[b] : make_float2(0.f, 0.f);
+                            }
+                        }
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                            if (e >= TS * MP) break;
+                            uint8_t *tile = sA + (m >> 5) * 16384;
+                            const int k = 2 * (m & 31);
+#pragma unroll
+                            for (int b = 0; b < RDB; ++b) {
+                                uint32_t w0, w1;
+                                real_rows<T16, CONJ>(v[h][b].x * b_scale, v[h][b].y * b_scale, w0, w1);
+                                st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
+                                st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
+                            }
+                        }
+                    }
+                } else {
+                    // BF16 planes (BF16 plans, b_scale 1): every load of the unit in flight at once;
+                    // subcarriers past N_d in the last group are padding, read as zero
+                    constexpr int PER = TS * 128 / THREADS;
+                    const bool b1 = nb > 1, b2 = nb > 2, b3 = nb > 3;
+                    uint32_t w[PER][RDB];
+#pragma unroll
+                    for (int h = 0; h < PER; ++h) {
+                        const int e = tid + h * THREADS, m = e % MP, t = e / MP;
+                        const bool ok = e < TS * MP && t < ns && m < Mp;
+                        // the blocked plane: the item's 4 subcarriers at (slot, antenna) are 16 bytes
+                        const uint32_t *src = reinterpret_cast<const uint32_t *>(
+                            X + BlkPlane(g).item(r, i0 / RDB) + ((long)(s0 + (ok ? t : 0)) * M + ma + (ok ? m : 0)) * RDB);
+                        if (ok && vec_ok) {
+                            const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
+                            w[h][0] = q4.x;
+                            w[h][1] = b1 ? q4.y : 0u;
+                            w[h][2] = b2 ? q4.z : 0u;
+                            w[h][3] = b3 ? q4.w : 0u;
                         } else {
 #pragma unroll
-                            for (int b = 0; b < RDB; ++b) v[h][b] = (ok && b < nb) ? src[b] : make_float2(0.f, 0.f);
+                            for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < nb) ? src[b] : 0u;
                         }
                     }
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int e = e0 + h * THREADS, m = e % MP, t = e / MP;
+                    for (int h = 0; h < PER; ++h) {
+                        const int e = tid + h * THREADS, m = e % MP, t = e / MP;
                         if (e >= TS * MP) break;
                         uint8_t *tile = sA + (m >> 5) * 16384;
                         const int k = 2 * (m & 31);
 #pragma unroll
                         for (int b = 0; b < RDB; ++b) {
                             uint32_t w0, w1;
-                            real_rows<T16, CONJ>(v[h][b].x * b_scale, v[h][b].y * b_scale, w0, w1);
+                            real_rows_packed<CONJ>(w[h][b], w0, w1);
                             st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
                             st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
                         }
                     }
                 }
-            } else {
-                // BF16 planes (BF16 plans, b_scale 1): every load of the unit in flight at once;
-                // subcarriers past N_d in the last group are padding, read as zero
-                constexpr int PER = TS * 128 / THREADS;
-                const bool b1 = nb > 1, b2 = nb > 2, b3 = nb > 3;
-                uint32_t w[PER][RDB];
-#pragma unroll
-                for (int h = 0; h < PER; ++h) {
-                    const int e = tid + h * THREADS, m = e % MP, t = e / MP;
-                    const bool ok = e < TS * MP && t < ns && m < M;
-                    // the blocked plane: the item's 4 subcarriers at (slot, antenna) are 16 bytes
-                    const uint32_t *src = reinterpret_cast<const uint32_t *>(
-                        X + BlkPlane(g).item(r, i0 / RDB) + ((long)(s0 + (ok ? t : 0)) * M + (ok ? m : 0)) * RDB);
-                    if (ok && vec_ok) {
-                        const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
-                        w[h][0] = q4.x;
-                        w[h][1] = b1 ? q4.y : 0u;
-                        w[h][2] = b2 ? q4.z : 0u;
-                        w[h][3] = b3 ? q4.w : 0u;
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < RDB; ++b) w[h][b] = (ok && b < nb) ? src[b] : 0u;
+                for (int uh = 0; uh < UH && alive; ++uh) {
+                    if (!one_b) load_b(mh, uh);   // into the B tile the previous round's MMAs are done with
+                    cp_async_wait_all();
+                    fence_proxy_async();
+                    __syncthreads();
+                    if (tid == 0) {
+                        fence_after();
+                        for (int ks = 0; ks < nks; ++ks)
+                            mma_f16(tmem + 64 * uh, smem_desc(sA + (ks >> 2) * 16384 + (ks & 3) * 32),
+                                    smem_desc(sB + (ks >> 2) * 8192 + (ks & 3) * 32), idesc, (mh || ks) ? 1u : 0u);
+                        mma_commit(&bar);
                     }
-                }
-#pragma unroll
-                for (int h = 0; h < PER; ++h) {
-                    const int e = tid + h * THREADS, m = e % MP, t = e / MP;
-                    if (e >= TS * MP) break;
-                    uint8_t *tile = sA + (m >> 5) * 16384;
-                    const int k = 2 * (m & 31);
-#pragma unroll
-                    for (int b = 0; b < RDB; ++b) {
-                        uint32_t w0, w1;
-                        real_rows_packed<CONJ>(w[h][b], w0, w1);
-                        st32(tile + sw128_offset(32 * b + 2 * t, k), w0);
-                        st32(tile + sw128_offset(32 * b + 2 * t + 1, k), w1);
-                    }
+                    alive = wait_mma(&bar, phase, err);
                 }
             }
-            cp_async_wait_all();
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                fence_after();
-                for (int ks = 0; ks < nks; ++ks)
-                    mma_f16(tmem, smem_desc(sA + (ks >> 2) * 16384 + (ks & 3) * 32),
-                            smem_desc(sB + (ks >> 2) * 8192 + (ks & 3) * 32), idesc, ks ? 1u : 0u);
-                mma_commit(&bar);
-            }
-            alive = wait_mma(&bar, phase, err);
-            if (alive) {
+            for (int uh = 0; uh < UH && alive; ++uh) {
+                const int Kh = min(16, K - 16 * uh), nout = ns * Kh * RDB;
+                if (uh) load_sref(uh);
                 if (warp < RDB) {
-                    // lane = (t, c') of subcarrier b = warp; columns 16 b + u
+                    // lane = (t, c') of subcarrier b = warp; columns 64 uh + 16 b + u'
                     const int b = warp, t = lane >> 1, c = lane & 1;
                     float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 64 * uh + 16 * b, v);
                     if (b < nb && t < ns) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
-                            if (u < K) sY[t * RD_YT + (u * RDB + b) * 2 + c] = v[u] * sc;
+                            if (u < Kh) sY[t * RD_YT + (u * RDB + b) * 2 + c] = v[u] * sc;
                     }
                 }
                 __syncthreads();
@@ -534,10 +574,10 @@ __global__ void __launch_bounds__(THREADS, 2)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int e = tid + k * THREADS;
-                    const int b = e & (RDB - 1), tu = e / RDB, u = tu % K, t = tu / K;
+                    const int b = e & (RDB - 1), tu = e / RDB, u = tu % Kh, t = tu / Kh;
                     if (e >= nout || b >= nb) continue;
                     const c32 v = sYc[(t * RD_YT + (u * RDB + b) * 2) / 2];
-                    const long idx = ((t0 + s0 + t) * K + u) * Nd + i0 + b;
+                    const long idx = ((t0 + s0 + t) * K + 16 * uh + u) * Nd + i0 + b;
                     if (COMB) {
                         const c32 sr = sref[k];
                         const c32 d = csub(v, sr);
@@ -549,12 +589,13 @@ __global__ void __launch_bounds__(THREADS, 2)
                         out[idx] = v;
                     }
                 }
+                __syncthreads();   // sY is read before the next half writes it
             }
             fence_before();
             __syncthreads();
         }
     }
-    teardown(&bar, phase, alive, tmem, 64, err);
+    teardown(&bar, phase, alive, tmem, tcols, err);
     if (COMB && metrics) {
         const double es = block_sum((double)err_acc, red);
         const double ss = block_sum((double)sig_acc, red);
@@ -942,7 +983,8 @@ template <typename T16, typename TO>
 static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, TO *out,
                             float b_scale, int *err, cudaStream_t st) {
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
-    const long items = (long)R * ((g.N_d + EXB - 1) / EXB);
+    const int exb = g.K > 16 ? EXB / 2 : EXB;
+    const long items = (long)R * ((g.N_d + exb - 1) / exb) * ((g.M + 127) / 128);
     if (items == 0) return cudaSuccess;
     // one 32-byte sector = 4 FP32 or 8 BF16 subcarriers
     const int vec_ok = !(g.N_d & (std::is_same<TO, c32>::value ? 3 : 7)) && aligned32(out);
@@ -1027,7 +1069,8 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
 
 }  // namespace tcb
 
-bool tc_bin_supported(const Geo &g) { return g.M >= 1 && g.M <= 128 && g.K >= 1 && g.K <= 16; }
+bool tc_bin_supported(const Geo &g) { return g.M >= 1 && g.M <= 256 && g.K >= 1 && g.K <= 32; }
+bool tc_apply_supported(const Geo &g) { return g.M >= 1 && g.M <= 128 && g.K >= 1 && g.K <= 16; }
 
 cudaError_t tc_bin_expand(const Geo &g, int mode, int S, const void *A, int a_kind, const float *alpha, const c32 *B,
                           void *out, int act_kind, float b_scale, int *err, cudaStream_t st) {

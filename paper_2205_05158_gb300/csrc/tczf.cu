@@ -270,7 +270,7 @@ static cudaError_t launch(const Geo &g, long nbins, const c32 *H, const c32 *Zs,
 
 cudaError_t zf_apply_tc(const Geo &g, long nbins, const c32 *H, const c32 *Zs, const float *alpha, c32 *W, void *W16,
                         int kind, int *err, cudaStream_t st) {
-    if (!tc_bin_supported(g) || !W16) return cudaErrorInvalidValue;
+    if (!tc_apply_supported(g) || !W16) return cudaErrorInvalidValue;
     if (kind == OUT_F16) return tczf::launch(g, nbins, H, Zs, alpha, W, (cf16 *)W16, err, st);
     return tczf::launch(g, nbins, H, Zs, alpha, W, (cbf16 *)W16, err, st);
 }

@@ -643,7 +643,7 @@ cudaError_t zf_phase(int phase, const Geo &g, int R, const c32 *H, c32 *W, float
                      void *HH16) {
     // the tensor-core apply needs the 16-bit copy it writes beside W, and K <= 16, M <= 128;
     // it may leave the FP32 W out when only the copy is wanted
-    const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_bin_supported(g);
+    const bool tc_apply = tc && kind != OUT_F32 && W16 && tc_apply_supported(g);
     if (tc_apply && !keep_w32) W = nullptr;
     if (kind == OUT_F16)
         return zf_build_t(g, R, H, W, alpha, status, scratch, (cf16 *)H16, (cf16 *)W16, phase, fp64, tc_apply, err,

@@ -92,14 +92,13 @@ def test_graph_replays_training_steps():
 @pytest.mark.parametrize("shape_i", [1, 5], ids=["m64_k8", "m128_k32"])
 def test_autotune_picks_an_admitted_implementation(shape_i):
     """fddpd_autotune times the admitted contraction implementations and keeps the faster:
-    K = 32 admits only the CUDA-core one; the result stays within the 16-bit tolerances."""
+    16-bit plans of up to 256 antennas and 32 users admit both (K = 32: the tensor-core
+    form with two user halves); the result stays within the 16-bit tolerances."""
+    import paper_2205_05158_gb300 as fd
     c = _instance(shape_i, SHAPES[shape_i])
     t_tc, t_cc = c.plan.autotune(c.s, c.H, c.W, c.alpha, c.pa, c.theta, reps=2)
-    assert t_cc > 0
-    if SHAPES[shape_i][1] > 16:
-        assert t_tc == -1.0
-    else:
-        assert t_tc > 0
+    assert t_cc > 0 and t_tc > 0
+    assert c.plan.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS) == (1 if t_tc <= t_cc else 0)
     y, met = c.gpu_distort()
     Wo, alo = c.oracle_zf()
     yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)

@@ -21,6 +21,15 @@ CFGS = [
     ("full", small_cfg(M=128, K=16, S=33, S_per_real=14)),             # full tiles, ragged subcarrier groups
     ("m128_k16_n2048_140", synth.CONFIGS["m128_k16_n2048"].with_(S=140)),                   # several items per CTA
 ]
+# beyond 128 antennas and 16 users: antenna parts of 128 (expand items; reduce MMAs
+# accumulating in TMEM) and user halves of 16 (4 subcarriers a expand item, 32 user slots
+# a tile row; reduce TMEM column blocks)
+WIDE = [
+    ("m256_k32", small_cfg(M=256, K=32, N=512, N_d=300, S=10, S_per_real=5, G=18)),   # whole parts and halves
+    ("m200_k20", small_cfg(M=200, K=20, S=7, S_per_real=3)),                           # ragged part (72) and half (4)
+    ("m250_k21", small_cfg(M=250, K=21, S=5, S_per_real=5)),                           # M % 4 = 2, K % 4 = 1
+]
+CFGS = CFGS + WIDE
 
 
 def _opt(c, on):
@@ -47,7 +56,7 @@ def test_tc_forward(name, cfg, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
-@pytest.mark.parametrize("name,cfg", CFGS[:3], ids=[n for n, _ in CFGS[:3]])
+@pytest.mark.parametrize("name,cfg", CFGS[:3] + WIDE, ids=[n for n, _ in CFGS[:3] + WIDE])
 def test_tc_backward(name, cfg, prec):
     c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=prec)
     c.use_oracle_zf_on_gpu()
@@ -83,11 +92,13 @@ def test_option_rejects_unknown():
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
-@pytest.mark.parametrize("name,cfg", [CFGS[0], CFGS[1], ("m128_k16_n2048_28", synth.CONFIGS["m128_k16_n2048"].with_(S=28))],
-                         ids=["ragged", "pad", "m128_k16_n2048_28"])
+@pytest.mark.parametrize("name,cfg", [CFGS[0], CFGS[1], ("m128_k16_n2048_28", synth.CONFIGS["m128_k16_n2048"].with_(S=28)),
+                                      WIDE[0]],
+                         ids=["ragged", "pad", "m128_k16_n2048_28", "m256_k32"])
 def test_tc_zf_apply(name, cfg, prec):
     """W = H^H (H H^H)^{-1} (Eq. 6) from the tensor-core apply (BF16 hi / lo splits)
-    against the oracle and against the CUDA-core apply; alpha comes from the same factor."""
+    against the oracle and against the CUDA-core apply; alpha comes from the same factor.
+    Beyond 128 antennas or 16 users the apply stays on CUDA cores with the option on."""
     c = Case(cfg, S=cfg.S, precision=prec)
     _opt(c, True)
     W1, a1 = (x.clone() for x in c.gpu_zf())
@@ -102,9 +113,9 @@ def test_tc_zf_apply(name, cfg, prec):
     assert np.abs(HW - np.eye(cfg.K)).max() <= 1e-3
 
 
-# K = 24 (the K > 16 form of Z x, CUDA-core contractions) with 17 symbols per realisation
+# K = 24 (the K > 16 forms of Z x and of the tensor-core contractions) with 17 symbols per realisation
 # (two staged passes of symbols); 150 data bins put realisation boundaries inside 32-bin blocks
-FACTOR_CFGS = CFGS[:3] + [("k24", small_cfg(M=64, K=24, S=40, S_per_real=17))]
+FACTOR_CFGS = CFGS[:3] + [("k24", small_cfg(M=64, K=24, S=40, S_per_real=17)), WIDE[0], WIDE[2]]
 
 
 @pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "cuda_cores"])
