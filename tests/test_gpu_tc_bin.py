@@ -28,6 +28,8 @@ WIDE = [
     ("m256_k32", small_cfg(M=256, K=32, N=512, N_d=300, S=10, S_per_real=5, G=18)),   # whole parts and halves
     ("m200_k20", small_cfg(M=200, K=20, S=7, S_per_real=3)),                           # ragged part (72) and half (4)
     ("m250_k21", small_cfg(M=250, K=21, S=5, S_per_real=5)),                           # M % 4 = 2, K % 4 = 1
+    ("m256_k8", small_cfg(M=256, K=8, S=6, S_per_real=3)),                             # two parts, one user half
+    ("m136_k4", small_cfg(M=136, K=4, S=4, S_per_real=2)),                             # a second part of 8 antennas
 ]
 CFGS = CFGS + WIDE
 
