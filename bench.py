@@ -518,6 +518,8 @@ def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
     one_cta = sum(p.get_option(fd.FDDPD_OPT_ROW_CTAS) == 1 for _, p, *_ in insts)
     one_bin_cta = sum(p.get_option(fd.FDDPD_OPT_CONTRACTION_CTAS) == 1 and p.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS)
                       for _, p, *_ in insts)
+    half_items = sum(p.get_option(fd.FDDPD_OPT_CONTRACTION_ITEM) == 1 and p.get_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS)
+                     for _, p, *_ in insts)
     nsym = len(insts) * S
     for _, p, *_ in insts:
         p.close()
@@ -527,7 +529,7 @@ def batched_run(fd, torch, stream, n=512, S=50, lanes=8, reps=3):
             "one_by_one": {"value": nsym / (ms_seq / 1e3), "unit": UNIT, "ms": ms_seq},
             "graph_equals_one_by_one": same, "autotune_s": tune_s, "record_s": rec_s,
             "autotuned": {"tensor_core_contractions": tc, "row_kernels_one_cta_per_sm": one_cta,
-                          "contractions_one_cta_per_sm": one_bin_cta},
+                          "contractions_one_cta_per_sm": one_bin_cta, "contractions_half_items": half_items},
             "precision": "bf16", "data": "device-drawn seeded symbols and channel taps"}
 
 

@@ -178,10 +178,15 @@ int fddpd_set_stream(fddpd_plan *plan, void *stream);
  *   FDDPD_OPT_CONTRACTION_CTAS  0 or 2 (default): the tensor-core per-subcarrier
  *       contractions' persistent grids hold two CTAs per SM; 1: one (fddpd_get_option
  *       reads 2 or 1).  The arithmetic does not depend on it.
+ *   FDDPD_OPT_CONTRACTION_ITEM  0 (default): the tensor-core contractions' work items
+ *       span 8 subcarriers (expand; 4 with K > 16) and 4 (reduce); 1: half as many
+ *       (more, smaller items for small plans; the benchmark shape's pipelined kernels
+ *       then give way to the generic ones).  The arithmetic does not depend on it.
  * Returns FDDPD_ERR_ARG for an unknown option or value.  fddpd_get_option reads one
  * back (*value; ARG for an unknown option).                                          */
 enum { FDDPD_OPT_TENSOR_CONTRACTIONS = 1, FDDPD_OPT_HOST_CHUNKS = 2, FDDPD_OPT_KEEP_PA_INPUT = 3,
-       FDDPD_OPT_FACTOR_FP64 = 4, FDDPD_OPT_ROW_CTAS = 5, FDDPD_OPT_CONTRACTION_CTAS = 6 };
+       FDDPD_OPT_FACTOR_FP64 = 4, FDDPD_OPT_ROW_CTAS = 5, FDDPD_OPT_CONTRACTION_CTAS = 6,
+       FDDPD_OPT_CONTRACTION_ITEM = 7 };
 int fddpd_set_option(fddpd_plan *plan, int option, int value);
 int fddpd_get_option(const fddpd_plan *plan, int option, int *value);
 
@@ -329,7 +334,8 @@ int fddpd_ser_decisions(fddpd_plan *plan, int S, const fddpd_c32 *y, const fddpd
 /* Per-shape launch choice (for batches of uneven plans): times `reps` forward passes
  * (fddpd_distort) of every candidate -- the per-subcarrier contraction implementations
  * the plan's shape admits (tcgen05 in 16-bit plans with M <= 256, K <= 32, with their
- * grid at two or one CTAs per SM, FDDPD_OPT_CONTRACTION_CTAS; CUDA cores) times the row
+ * grid at two or one CTAs per SM, FDDPD_OPT_CONTRACTION_CTAS, and whole or half work
+ * items, FDDPD_OPT_CONTRACTION_ITEM; CUDA cores) times the row
  * kernels' grid (FDDPD_OPT_ROW_CTAS 0 or 1) -- with CUDA events on the
  * plan's stream, and keeps the fastest.  The choice is stored per shape (M, K, N, N_d,
  * S_per_real, precision, PA shape, FD-CNN shape, S) in the process: a later plan of a

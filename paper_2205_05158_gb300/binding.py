@@ -25,6 +25,7 @@ FDDPD_OPT_KEEP_PA_INPUT = 3
 FDDPD_OPT_FACTOR_FP64 = 4
 FDDPD_OPT_ROW_CTAS = 5
 FDDPD_OPT_CONTRACTION_CTAS = 6
+FDDPD_OPT_CONTRACTION_ITEM = 7
 
 EXPORTED = ["fddpd_plan_create", "fddpd_plan_destroy", "fddpd_last_error", "fddpd_theta_len",
             "fddpd_workspace_bytes", "fddpd_set_stream", "fddpd_precode", "fddpd_distort",

@@ -436,6 +436,10 @@ extern "C" int fddpd_set_option(fddpd_plan *p, int option, int value) {
         p->g.bin_ctas = value == 1 ? 1 : 0;
         return FDDPD_OK;
     }
+    if (option == FDDPD_OPT_CONTRACTION_ITEM && (value == 0 || value == 1)) {
+        p->g.bin_half = value;
+        return FDDPD_OK;
+    }
     return set_err(p, FDDPD_ERR_ARG, "fddpd_set_option: unknown option or value");
 }
 
@@ -448,6 +452,7 @@ extern "C" int fddpd_get_option(const fddpd_plan *p, int option, int *value) {
         case FDDPD_OPT_FACTOR_FP64: *value = p->fp64_factor ? 1 : 0; return FDDPD_OK;
         case FDDPD_OPT_ROW_CTAS: *value = p->g.row_ctas; return FDDPD_OK;
         case FDDPD_OPT_CONTRACTION_CTAS: *value = p->g.bin_ctas == 1 ? 1 : 2; return FDDPD_OK;
+        case FDDPD_OPT_CONTRACTION_ITEM: *value = p->g.bin_half; return FDDPD_OK;
         default: return FDDPD_ERR_ARG;
     }
 }
@@ -1156,7 +1161,7 @@ struct TuneKey {
 };
 struct TuneChoice {
     bool tc;
-    int row_ctas, bin_ctas;
+    int row_ctas, bin_ctas, bin_half;
     float ms[2];
 };
 static std::mutex g_tune_mu;
@@ -1177,6 +1182,7 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
             p->tc_bin = it->second.tc;
             p->g.row_ctas = it->second.row_ctas;
             p->g.bin_ctas = it->second.bin_ctas;
+            p->g.bin_half = it->second.bin_half;
             if (ms) {
                 ms[0] = it->second.ms[0];
                 ms[1] = it->second.ms[1];
@@ -1185,11 +1191,12 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
         }
     }
     // candidates: the contraction implementations the shape admits (tcgen05 in 16-bit plans
-    // with M <= 256, K <= 32, at two or one CTAs per SM; CUDA cores) x the row kernels'
-    // CTAs per SM (as many as fit; one)
-    float t[2][2][2] = {{{-1.0f, -1.0f}, {-1.0f, -1.0f}}, {{-1.0f, -1.0f}, {-1.0f, -1.0f}}};
+    // with M <= 256, K <= 32, at two or one CTAs per SM, with whole or half items; CUDA
+    // cores) x the row kernels' CTAs per SM (as many as fit; one)
+    float t[2][2][2][2];
+    for (int a = 0; a < 16; ++a) (&t[0][0][0][0])[a] = -1.0f;
     const bool was_tc = p->tc_bin;
-    const int was_rc = p->g.row_ctas, was_bc = p->g.bin_ctas;
+    const int was_rc = p->g.row_ctas, was_bc = p->g.bin_ctas, was_bh = p->g.bin_half;
     const bool tc_ok = p->p16 && fdk::tc_bin_supported(p->g);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     FD_CK(p, cudaEventCreate(&e0));
@@ -1200,12 +1207,13 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
     int rc = FDDPD_OK;
     for (int v = 0; v < 2 && rc == FDDPD_OK; ++v) {
         if (v == 0 && !tc_ok) continue;
-        for (int c = 0; c < 4 && rc == FDDPD_OK; ++c) {
-            const int rcta = c & 1, bcta = c >> 1;
-            if (v == 1 && bcta) continue;   // the CUDA-core contractions have one grid
+        for (int c = 0; c < 8 && rc == FDDPD_OK; ++c) {
+            const int rcta = c & 1, bcta = (c >> 1) & 1, bhalf = c >> 2;
+            if (v == 1 && (bcta || bhalf)) continue;   // the CUDA-core contractions have one form
             p->tc_bin = v == 0;
             p->g.row_ctas = rcta;
             p->g.bin_ctas = bcta;
+            p->g.bin_half = bhalf;
             rc = fddpd_distort(p, S, s, H, W, alpha, pa_coef, theta, nullptr, nullptr);   // warm-up (and re-pack)
             if (rc) break;
             if (cudaEventRecord(e0, p->stream) != cudaSuccess) { rc = set_err(p, FDDPD_ERR_CUDA, "event record"); break; }
@@ -1218,7 +1226,7 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
                 rc = set_err(p, FDDPD_ERR_CUDA, "event timing");
                 break;
             }
-            t[v][rcta][bcta] = el / reps;
+            t[v][rcta][bcta][bhalf] = el / reps;
         }
     }
     cudaEventDestroy(e0);
@@ -1227,21 +1235,27 @@ extern "C" int fddpd_autotune(fddpd_plan *p, int S, const fddpd_c32 *s, const fd
         p->tc_bin = was_tc;
         p->g.row_ctas = was_rc;
         p->g.bin_ctas = was_bc;
+        p->g.bin_half = was_bh;
         return rc;
     }
-    int bv = -1, br = 0, bb = 0;
+    int bv = -1, br = 0, bb = 0, bh = 0;
     for (int v = 0; v < 2; ++v)
         for (int r = 0; r < 2; ++r)
             for (int b = 0; b < 2; ++b)
-                if (t[v][r][b] >= 0 && (bv < 0 || t[v][r][b] < t[bv][br][bb])) { bv = v; br = r; bb = b; }
+                for (int h = 0; h < 2; ++h)
+                    if (t[v][r][b][h] >= 0 && (bv < 0 || t[v][r][b][h] < t[bv][br][bb][bh])) {
+                        bv = v; br = r; bb = b; bh = h;
+                    }
     p->tc_bin = bv == 0;
     p->g.row_ctas = br;
     p->g.bin_ctas = bb;
-    TuneChoice ch{p->tc_bin, p->g.row_ctas, p->g.bin_ctas, {-1.0f, -1.0f}};
+    p->g.bin_half = bh;
+    TuneChoice ch{p->tc_bin, p->g.row_ctas, p->g.bin_ctas, p->g.bin_half, {-1.0f, -1.0f}};
     for (int v = 0; v < 2; ++v)
         for (int r = 0; r < 2; ++r)
             for (int b = 0; b < 2; ++b)
-                if (t[v][r][b] >= 0 && (ch.ms[v] < 0 || t[v][r][b] < ch.ms[v])) ch.ms[v] = t[v][r][b];
+                for (int h = 0; h < 2; ++h)
+                    if (t[v][r][b][h] >= 0 && (ch.ms[v] < 0 || t[v][r][b][h] < ch.ms[v])) ch.ms[v] = t[v][r][b][h];
     if (ms) {
         ms[0] = ch.ms[0];
         ms[1] = ch.ms[1];

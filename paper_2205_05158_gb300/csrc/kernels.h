@@ -18,6 +18,7 @@ struct Geo {
     int in_all;              // the forward row kernel reads x_hat rows of all N bins (FD-NN chain)
     int row_ctas;            // CTAs per SM of the row kernels' persistent grids (0: as many as fit)
     int bin_ctas;            // CTAs per SM of the tensor-core contractions' grids (0: two, the most that fit)
+    int bin_half;            // the generic tensor-core contractions take items of half the subcarriers
     int G, Go, L_U, Cin, K_C, K_S, pad, N_conv, F, residual;
     int n_convw;             // N_conv * Cin * K_C * K_C
     long off_cb, off_fw, off_fb, theta_len;

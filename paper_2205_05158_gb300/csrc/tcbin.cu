@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int M = g.M, K = g.K, Nd = g.N_d;
     const int spt = K > 16 ? 1 : 2;        // subcarriers per tile (per 128-byte row)
-    const int exb = 4 * spt;               // subcarriers per item
+    const int exb = (4 * spt) >> (g.bin_half ? 1 : 0);   // subcarriers per item (half items: the
+                                                         // rest of the tiles stay zero)
     const int MH = (M + 127) >> 7;         // 128-antenna parts, one item each
     const int ngroups = (Nd + exb - 1) / exb;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
@@ -378,7 +379,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int MH = FULL ? 1 : (M + 127) >> 7;   // 128-antenna parts
     const int UH = FULL ? 1 : (K + 15) >> 4;    // 16-user halves
     const bool one_b = MH == 1 && UH == 1;      // B loaded once per item
-    const int ngroups = (Nd + RDB - 1) / RDB;
+    const int rdb = g.bin_half ? RDB / 2 : RDB;   // subcarriers per item (half items: 2 of the 4 blocks)
+    const int ngroups = (Nd + rdb - 1) / rdb;
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
     const long nitems = (long)R * ngroups;
     const uint32_t tcols = UH > 1 ? 128 : 64;
@@ -390,11 +392,11 @@ __global__ void __launch_bounds__(THREADS, 2)
     float err_acc = 0.f, sig_acc = 0.f;
 
     for (long item = blockIdx.x; item < nitems && alive; item += gridDim.x) {
-        const int r = (int)(item / ngroups), i0 = (int)(item % ngroups) * RDB;
+        const int r = (int)(item / ngroups), i0 = (int)(item % ngroups) * rdb;
         const long t0 = (long)r * g.S_per_real;
         const int nsym = (int)min((long)g.S_per_real, (long)S - t0);
         const long bin0 = (long)r * Nd + i0;
-        const int nb = min(RDB, Nd - i0);
+        const int nb = min(rdb, Nd - i0);
         // scale of the subcarrier whose TMEM lanes this warp reads, loaded early
         float sc = 0.f;
         if (warp < nb) {
@@ -511,10 +513,12 @@ __global__ void __launch_bounds__(THREADS, 2)
                     for (int h = 0; h < PER; ++h) {
                         const int e = tid + h * THREADS, m = e % MP, t = e / MP;
                         const bool ok = e < TS * MP && t < ns && m < Mp;
-                        // the blocked plane: the item's 4 subcarriers at (slot, antenna) are 16 bytes
+                        // the blocked plane: the 4 subcarriers of group i0 / 4 at (slot, antenna) are 16
+                        // bytes; a half item starts at subcarrier i0 % 4 of them
                         const uint32_t *src = reinterpret_cast<const uint32_t *>(
-                            X + BlkPlane(g).item(r, i0 / RDB) + ((long)(s0 + (ok ? t : 0)) * M + ma + (ok ? m : 0)) * RDB);
-                        if (ok && vec_ok) {
+                            X + BlkPlane(g).item(r, i0 / RDB) + ((long)(s0 + (ok ? t : 0)) * M + ma + (ok ? m : 0)) * RDB) +
+                            (i0 & (RDB - 1));
+                        if (ok && vec_ok && !(i0 & (RDB - 1))) {
                             const uint4 q4 = *reinterpret_cast<const uint4 *>(src);
                             w[h][0] = q4.x;
                             w[h][1] = b1 ? q4.y : 0u;
@@ -983,7 +987,7 @@ template <typename T16, typename TO>
 static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const float *alpha, const c32 *B, TO *out,
                             float b_scale, int *err, cudaStream_t st) {
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
-    const int exb = g.K > 16 ? EXB / 2 : EXB;
+    const int exb = (g.K > 16 ? EXB / 2 : EXB) >> (g.bin_half ? 1 : 0);
     const long items = (long)R * ((g.N_d + exb - 1) / exb) * ((g.M + 127) / 128);
     if (items == 0) return cudaSuccess;
     // one 32-byte sector = 4 FP32 or 8 BF16 subcarriers
@@ -992,7 +996,7 @@ static cudaError_t expand_t(const Geo &g, int mode, int S, const void *A, const 
     unsigned blocks = 0;
     cudaError_t e;
     if constexpr (std::is_same<T16, cbf16>::value) {
-        if (g.M == 128 && g.K == 16 && g.S_per_real <= TS && b_scale == 1.0f) {
+        if (g.M == 128 && g.K == 16 && g.S_per_real <= TS && b_scale == 1.0f && !g.bin_half) {
             if (mode == PRECODE || mode == ADJ_COMBINE_F) {
                 auto k = expand_pipe_kernel<false, false, TO>;
                 if ((e = grid_for(g, k, EX_SMEM, items, blocks)) != cudaSuccess) return e;
@@ -1022,7 +1026,8 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
                             const c32 *s_ref, c32 *gy, double *metrics, double inv_count, float b_scale, int *err,
                             cudaStream_t st) {
     const int R = (S + g.S_per_real - 1) / g.S_per_real;
-    const long items = (long)R * ((g.N_d + RDB - 1) / RDB);
+    const int rdb = g.bin_half ? RDB / 2 : RDB;
+    const long items = (long)R * ((g.N_d + rdb - 1) / rdb);
     if (items == 0) return cudaSuccess;
     // 4 subcarriers: two 16-byte FP32 loads from rows, or one of BF16 from the blocked plane
     const int vec_ok = (std::is_same<TX, c32>::value ? !(g.N_d & 1) : 1) && aligned16(B);
@@ -1031,7 +1036,7 @@ static cudaError_t reduce_t(const Geo &g, int mode, int S, const void *A, const 
     cudaError_t e;
     const bool full = g.M == 128 && g.K == 16;
     if constexpr (std::is_same<TX, cbf16>::value && std::is_same<T16, cbf16>::value) {
-        if (full && g.S_per_real <= TS && b_scale == 1.0f) {
+        if (full && g.S_per_real <= TS && b_scale == 1.0f && !g.bin_half) {
             if (mode == COMBINE) {
                 auto k = reduce_pipe_kernel<false, false, true>;
                 if ((e = grid_for(g, k, RD_SMEM, items, blocks)) != cudaSuccess) return e;

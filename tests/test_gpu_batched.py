@@ -172,14 +172,18 @@ def test_autotune_choice_stored_per_shape_and_row_ctas_exact():
     ta = a.plan.autotune(a.s, a.H, None, a.alpha, a.pa, a.theta, reps=1)
     tb = b.plan.autotune(b.s, b.H, None, b.alpha, b.pa, b.theta, reps=1)
     assert ta == tb                                   # the stored choice, not a new timing
-    for o in (fd.FDDPD_OPT_TENSOR_CONTRACTIONS, fd.FDDPD_OPT_ROW_CTAS, fd.FDDPD_OPT_CONTRACTION_CTAS):
+    for o in (fd.FDDPD_OPT_TENSOR_CONTRACTIONS, fd.FDDPD_OPT_ROW_CTAS, fd.FDDPD_OPT_CONTRACTION_CTAS,
+              fd.FDDPD_OPT_CONTRACTION_ITEM):
         assert a.plan.get_option(o) == b.plan.get_option(o)
     a.plan.set_option(fd.FDDPD_OPT_TENSOR_CONTRACTIONS, 1)
     outs = []
-    for rc, bc in ((0, 0), (1, 0), (2, 0), (0, 1), (1, 1)):   # the grid shapes change no arithmetic
+    # the grid shapes and the contraction items' size change no arithmetic
+    for rc, bc, hi in ((0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 1, 1)):
         a.plan.set_option(fd.FDDPD_OPT_ROW_CTAS, rc)
         a.plan.set_option(fd.FDDPD_OPT_CONTRACTION_CTAS, bc)
+        a.plan.set_option(fd.FDDPD_OPT_CONTRACTION_ITEM, hi)
         assert a.plan.get_option(fd.FDDPD_OPT_CONTRACTION_CTAS) == (1 if bc == 1 else 2)
+        assert a.plan.get_option(fd.FDDPD_OPT_CONTRACTION_ITEM) == hi
         y = T.empty_like(a.s)
         a.plan.distort(a.s, a.H, None, a.alpha, a.pa, a.theta, y)
         outs.append(y)
@@ -189,3 +193,5 @@ def test_autotune_choice_stored_per_shape_and_row_ctas_exact():
         a.plan.set_option(fd.FDDPD_OPT_ROW_CTAS, 9)
     with pytest.raises(fd.FddpdError):
         a.plan.set_option(fd.FDDPD_OPT_CONTRACTION_CTAS, 3)
+    with pytest.raises(fd.FddpdError):
+        a.plan.set_option(fd.FDDPD_OPT_CONTRACTION_ITEM, 2)

@@ -73,6 +73,38 @@ def test_tc_backward(name, cfg, prec):
     assert rel_l2(g_tc, g_cc) <= 2e-2, rel_l2(g_tc, g_cc)
 
 
+HALF_CFGS = [CFGS[0], CFGS[2], ("m128_k16_n2048_28", synth.CONFIGS["m128_k16_n2048"].with_(S=28)), WIDE[0], WIDE[2]]
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg", HALF_CFGS, ids=[n for n, _ in HALF_CFGS])
+def test_tc_half_items(name, cfg, prec):
+    """Contraction items of half the subcarriers (FDDPD_OPT_CONTRACTION_ITEM = 1; for the
+    128 x 16 BF16 shape the generic kernels replace the pipelined ones): forward and
+    gradient against the oracle, and against whole items.  In the generic kernels every
+    subcarrier's MMAs are the same either way, so their results are identical; the
+    pipelined kernels of the 128 x 16 BF16 shape may round differently."""
+    import paper_2205_05158_gb300 as fd
+    c = Case(cfg, S=cfg.S, fc_scale=0.3, precision=prec)
+    c.use_oracle_zf_on_gpu()
+    _opt(c, True)
+    y1, met1 = c.gpu_distort()
+    g1, _ = c.gpu_backward()
+    c.plan.set_option(fd.FDDPD_OPT_CONTRACTION_ITEM, 1)
+    yh, meth = c.gpu_distort()
+    gh, _ = c.gpu_backward()
+    Wo, alo = c.oracle_zf()
+    yo, meto = oracle.distort(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    go, _ = oracle.backward(c.d, c.w.s, c.w.H, Wo, alo, c.w.pa, c.w.theta)
+    assert nmse(yh, yo) <= 1e-4 and rel_l2(gh, go) <= 2e-2
+    assert abs(oracle.evm_db(meth) - oracle.evm_db(meto)) <= 0.1
+    pipelined = cfg.M == 128 and cfg.K == 16 and prec == 1 and cfg.S_per_real <= 16
+    if pipelined:
+        assert nmse(yh, y1) <= 1e-6 and rel_l2(gh, g1) <= 1e-3
+    else:
+        assert np.array_equal(yh, y1) and np.array_equal(gh, g1)
+
+
 def test_option_ignored_by_fp32_plans():
     c = Case(small_cfg(), fc_scale=0.3, precision=0)
     c.use_oracle_zf_on_gpu()
